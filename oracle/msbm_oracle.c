@@ -1,0 +1,322 @@
+/*
+ * msbm_oracle.c -- plain, slow FP64 CPU oracle for multi-scale hierarchical ZNCC block
+ * matching (Kaushik & Lall, "Fast Hierarchical depth map computation from stereo").
+ *
+ * TEST INFRASTRUCTURE.  Only the test suite, the smoke check and the CPU-baseline leg of
+ * the benchmark call this code.  It shares nothing with the CUDA library: no header, no
+ * helper, no table.  Every function follows the paper's steps in its own order and
+ * notation, with no blocking, fusion or reordering, so it can be read against the paper.
+ *
+ * Conventions (readings of the paper; each is listed with its reason in the design notes):
+ *   - images are row-major, (y, x) = (row, column), the LEFT image is the reference and
+ *     candidate disparity z pairs left column x with right column x - z (Eq. 1);
+ *   - window half-width n, side w = 2n+1, N = w*w window pixels; pixels outside the image
+ *     are read clamp-to-edge;
+ *   - D candidates 0..D-1 at level 0, D_k = ceil(D / 2^k) at level k (Sec. III);
+ *   - a candidate is admissible only if z <= x (its right centre lies in the image).
+ *
+ * Parity status: pyramid, ZNCC, WTA, the hierarchical driver and the soft-argmax level are
+ * pinned by the tests in tests/test_oracle_*.py (brute force, invariants, planted scenes,
+ * finite differences).  Nothing here is "parity unpinned".
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+int oracle_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void oracle_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+/* ------------------------------------------------------------------------------------
+ * Gaussian pyramid (Sec. III, Fig. 1).  The paper names a Gaussian pyramid without the
+ * kernel.  Reading: the 5-tap binomial 1,4,6,4,1 on each axis (weights /16 each, /256 in
+ * 2-D), clamp-to-edge, output ceil(W/2) x ceil(H/2), integer result rounded to nearest
+ * ((sum + 128) >> 8).  Written as the direct 2-D weighted sum.
+ * ---------------------------------------------------------------------------------- */
+void oracle_reduce(const uint8_t *src, int W, int H, uint8_t *dst) {
+    static const int c[5] = {1, 4, 6, 4, 1};
+    int W2 = (W + 1) / 2, H2 = (H + 1) / 2;
+    for (int y = 0; y < H2; ++y)
+        for (int x = 0; x < W2; ++x) {
+            long s = 0;
+            for (int a = -2; a <= 2; ++a)
+                for (int b = -2; b <= 2; ++b) {
+                    int yy = clampi(2 * y + a, 0, H - 1);
+                    int xx = clampi(2 * x + b, 0, W - 1);
+                    s += (long)c[a + 2] * c[b + 2] * src[(long)yy * W + xx];
+                }
+            dst[(long)y * W2 + x] = (uint8_t)((s + 128) >> 8);
+        }
+}
+
+/* Level sizes: level 0 is W x H, level k is ceil(W_{k-1}/2) x ceil(H_{k-1}/2). */
+void oracle_level_size(int W, int H, int k, int *Wk, int *Hk) {
+    for (int i = 0; i < k; ++i) { W = (W + 1) / 2; H = (H + 1) / 2; }
+    *Wk = W; *Hk = H;
+}
+
+/* Candidate count at level k: D_k = ceil(D / 2^k) (Sec. III, d^k_max = D_max / 2^k). */
+int oracle_level_disp(int D, int k) { return (int)((D + (1L << k) - 1) >> k); }
+
+/* All K levels of one image, concatenated level 0 first. */
+void oracle_pyramid(const uint8_t *img, int W, int H, int K, uint8_t *out) {
+    memcpy(out, img, (size_t)W * H);
+    const uint8_t *prev = out;
+    int w = W, h = H;
+    uint8_t *cur = out + (size_t)W * H;
+    for (int k = 1; k < K; ++k) {
+        oracle_reduce(prev, w, h, cur);
+        prev = cur;
+        cur += (size_t)((w + 1) / 2) * ((h + 1) / 2);
+        w = (w + 1) / 2; h = (h + 1) / 2;
+    }
+}
+
+/* ------------------------------------------------------------------------------------
+ * ZNCC matching cost (Eq. 2) between the left window centred at (y, x) and the right
+ * window centred at (y, x - z) (Eq. 1).  The paper's printed normalisation is garbled;
+ * read as the standard zero-mean normalised cross-correlation in [-1, 1]:
+ *     rho = sum (a - mean a)(b - mean b) / sqrt(sum (a - mean a)^2 * sum (b - mean b)^2)
+ * evaluated from exact integer sums as
+ *     c = N*Sab - Sa*Sb,  Va = N*Saa - Sa^2,  Vb = N*Sbb - Sb^2,  rho = c / sqrt(Va*Vb)
+ * (the N factors cancel).  A flat window (Va == 0 or Vb == 0) has rho = 0; the result is
+ * clamped to [-1, 1] against rounding.
+ * ---------------------------------------------------------------------------------- */
+double oracle_zncc(const uint8_t *A, const uint8_t *B, int W, int H, int n, int y, int x, int z) {
+    long long Sa = 0, Sb = 0, Saa = 0, Sbb = 0, Sab = 0;
+    long long N = (long long)(2 * n + 1) * (2 * n + 1);
+    for (int i = -n; i <= n; ++i) {
+        int yy = clampi(y + i, 0, H - 1);
+        for (int j = -n; j <= n; ++j) {
+            long long a = A[(long)yy * W + clampi(x + j, 0, W - 1)];
+            long long b = B[(long)yy * W + clampi(x - z + j, 0, W - 1)];
+            Sa += a; Sb += b; Saa += a * a; Sbb += b * b; Sab += a * b;
+        }
+    }
+    long long Va = N * Saa - Sa * Sa;
+    long long Vb = N * Sbb - Sb * Sb;
+    if (Va == 0 || Vb == 0) return 0.0;
+    double c = (double)(N * Sab - Sa * Sb);
+    double rho = c / sqrt((double)Va * (double)Vb);
+    if (rho > 1.0) rho = 1.0;
+    if (rho < -1.0) rho = -1.0;
+    return rho;
+}
+
+/* ------------------------------------------------------------------------------------
+ * One level of winner-take-all matching.
+ *   prior == NULL: the coarsest-level search of Sec. III-A (Eq. 3-4) over every
+ *                  admissible candidate 0 <= z <= min(D_k - 1, x).
+ *   prior != NULL: the refinement branch of Sec. III-C (Eq. 8-9, first case) at a finer
+ *                  level.  The prior is the coarser level's disparity map (Wp x Hp); its
+ *                  nearest-neighbour upsample scaled to this level's units is
+ *                  dhat = 2 * prior(y/2, x/2)  (the paper writes NN(d^{k+1}) and omits the
+ *                  factor 2 that the doubled resolution implies).  The candidates are the
+ *                  closed span dhat - r .. dhat + r (the paper's open interval around dhat
+ *                  with r = 1 gives its "3 comparisons") clipped to the admissible range.
+ *                  dhat is first clamped to 0 .. min(D_k - 1, x); for any prior produced by
+ *                  the coarser level this clamp changes nothing.
+ * Outputs: d (argmax; ties to the smallest z), C (max, Eq. 4/9), C2 (second-best value,
+ * -INFINITY when only one candidate exists).  Returns the number of (pixel, z) ZNCC
+ * evaluations.
+ * ---------------------------------------------------------------------------------- */
+long long oracle_match_level(const uint8_t *A, const uint8_t *B, int W, int H, int n, int Dk,
+                             int r, const int16_t *prior, int Wp, int Hp, int16_t *d,
+                             double *C, double *C2) {
+    long long evals = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : evals)
+    for (int y = 0; y < H; ++y) {
+        for (int x = 0; x < W; ++x) {
+            int zmax = Dk - 1 < x ? Dk - 1 : x;
+            int lo = 0, hi = zmax;
+            if (prior) {
+                int py = clampi(y / 2, 0, Hp - 1), px = clampi(x / 2, 0, Wp - 1);
+                int dh = clampi(2 * (int)prior[(long)py * Wp + px], 0, zmax);
+                lo = dh - r < 0 ? 0 : dh - r;
+                hi = dh + r > zmax ? zmax : dh + r;
+            }
+            double best = -INFINITY, second = -INFINITY;
+            int bz = lo;
+            for (int z = lo; z <= hi; ++z) {
+                double rho = oracle_zncc(A, B, W, H, n, y, x, z);
+                if (rho > best) { second = best; best = rho; bz = z; }
+                else if (rho > second) second = rho;
+            }
+            evals += hi - lo + 1;
+            d[(long)y * W + x] = (int16_t)bz;
+            C[(long)y * W + x] = best;
+            C2[(long)y * W + x] = second;
+        }
+    }
+    return evals;
+}
+
+/* ------------------------------------------------------------------------------------
+ * The whole hierarchical pass (Sec. III, Fig. 1) in its plain form: pyramid of both
+ * images, full search at the coarsest level K-1, then for k = K-2 .. 0 the restricted
+ * search around the upsampled coarser disparity.  (The alpha refinement of Sec. III-B, the
+ * beta fallback of Eq. 8-9 and the selective median of Sec. III-D are separate functions
+ * below.)  K = 1 is flat block matching.
+ * Outputs are all levels concatenated, level 0 first: d_all, C_all, C2_all sized
+ * sum_k W_k*H_k.  Returns the total evaluation count, or -1 on bad arguments.
+ * ---------------------------------------------------------------------------------- */
+long long oracle_disparity(const uint8_t *L, const uint8_t *R, int W, int H, int D, int K,
+                           int w, int r, int16_t *d_all, double *C_all, double *C2_all) {
+    if (W < 1 || H < 1 || D < 1 || K < 1 || w < 1 || (w & 1) == 0 || r < 0) return -1;
+    int n = w / 2;
+    size_t total = 0;
+    for (int k = 0; k < K; ++k) { int a, b; oracle_level_size(W, H, k, &a, &b); total += (size_t)a * b; }
+    uint8_t *pl = (uint8_t *)malloc(total), *pr = (uint8_t *)malloc(total);
+    size_t *off = (size_t *)malloc(sizeof(size_t) * K);
+    if (!pl || !pr || !off) { free(pl); free(pr); free(off); return -1; }
+    oracle_pyramid(L, W, H, K, pl);
+    oracle_pyramid(R, W, H, K, pr);
+    size_t o = 0;
+    for (int k = 0; k < K; ++k) { int a, b; oracle_level_size(W, H, k, &a, &b); off[k] = o; o += (size_t)a * b; }
+    long long evals = 0;
+    for (int k = K - 1; k >= 0; --k) {
+        int Wk, Hk, Wp = 0, Hp = 0;
+        oracle_level_size(W, H, k, &Wk, &Hk);
+        const int16_t *prior = NULL;
+        if (k < K - 1) { oracle_level_size(W, H, k + 1, &Wp, &Hp); prior = d_all + off[k + 1]; }
+        evals += oracle_match_level(pl + off[k], pr + off[k], Wk, Hk, n, oracle_level_disp(D, k),
+                                    r, prior, Wp, Hp, d_all + off[k], C_all + off[k],
+                                    C2_all + off[k]);
+    }
+    free(pl); free(pr); free(off);
+    return evals;
+}
+
+/* ------------------------------------------------------------------------------------
+ * Differentiable level (float images).  ZNCC with two-pass window means and an
+ * epsilon-regularised denominator,
+ *     rho_eps = sum ac*bc / sqrt((sum ac^2 + eps) (sum bc^2 + eps)),  ac = a - mean a,
+ * over candidates 0 <= z <= min(ndisp - 1, x); p = softmax(rho / T) over the admissible
+ * candidates; d_soft = sum z p_z.  Images are B x H x W, row-major per image.
+ * rho_out (optional, may be NULL) receives rho for every (b, y, x, z), -INFINITY where z
+ * is not admissible.
+ * ---------------------------------------------------------------------------------- */
+static double zncc_eps_window(const double *A, const double *Bm, int W, int H, int n, int y,
+                              int x, int z, double eps, double *ac, double *bc, double *Saa_o,
+                              double *Sbb_o) {
+    int w = 2 * n + 1, N = w * w, t = 0;
+    double ma = 0.0, mb = 0.0;
+    for (int i = -n; i <= n; ++i)
+        for (int j = -n; j <= n; ++j, ++t) {
+            int yy = clampi(y + i, 0, H - 1);
+            ac[t] = A[(long)yy * W + clampi(x + j, 0, W - 1)];
+            bc[t] = Bm[(long)yy * W + clampi(x - z + j, 0, W - 1)];
+            ma += ac[t]; mb += bc[t];
+        }
+    ma /= N; mb /= N;
+    double Saa = 0.0, Sbb = 0.0, Sab = 0.0;
+    for (t = 0; t < N; ++t) {
+        ac[t] -= ma; bc[t] -= mb;
+        Saa += ac[t] * ac[t]; Sbb += bc[t] * bc[t]; Sab += ac[t] * bc[t];
+    }
+    *Saa_o = Saa; *Sbb_o = Sbb;
+    return Sab / sqrt((Saa + eps) * (Sbb + eps));
+}
+
+void oracle_softargmax_fwd(const double *L, const double *R, int Bn, int H, int W, int n,
+                           int ndisp, double T, double eps, double *dsoft, double *rho_out) {
+    int N = (2 * n + 1) * (2 * n + 1);
+#pragma omp parallel
+    {
+        double *ac = (double *)malloc(sizeof(double) * N), *bc = (double *)malloc(sizeof(double) * N);
+        double *rho = (double *)malloc(sizeof(double) * (ndisp > 0 ? ndisp : 1));
+#pragma omp for schedule(dynamic, 1) collapse(2)
+        for (int b = 0; b < Bn; ++b)
+            for (int y = 0; y < H; ++y) {
+                const double *A = L + (long)b * H * W, *Bm = R + (long)b * H * W;
+                for (int x = 0; x < W; ++x) {
+                    int zmax = ndisp - 1 < x ? ndisp - 1 : x;
+                    double Saa, Sbb, m = -INFINITY;
+                    for (int z = 0; z <= zmax; ++z) {
+                        rho[z] = zncc_eps_window(A, Bm, W, H, n, y, x, z, eps, ac, bc, &Saa, &Sbb);
+                        if (rho[z] / T > m) m = rho[z] / T;
+                    }
+                    double s = 0.0, sz = 0.0;
+                    for (int z = 0; z <= zmax; ++z) {
+                        double e = exp(rho[z] / T - m);
+                        s += e; sz += z * e;
+                    }
+                    long pix = ((long)b * H + y) * W + x;
+                    dsoft[pix] = sz / s;
+                    if (rho_out)
+                        for (int z = 0; z < ndisp; ++z) rho_out[pix * ndisp + z] = z <= zmax ? rho[z] : -INFINITY;
+                }
+            }
+        free(ac); free(bc); free(rho);
+    }
+}
+
+/* Backward of the soft-argmax readout with respect to both images.  With
+ * p_z = softmax(rho_z / T) and d = sum z p_z:  dd/drho_z = p_z (z - d) / T.  For the
+ * centred window entries,  drho/dac_i = bc_i / s - rho * ac_i / (Saa + eps)  and
+ * drho/dbc_i = ac_i / s - rho * bc_i / (Sbb + eps)  with s = sqrt((Saa+eps)(Sbb+eps)); the
+ * derivative through the mean vanishes because the centred entries sum to zero.  Each
+ * window entry's gradient goes to the image pixel it was read from (clamped positions
+ * accumulate at the edge pixel).  g_d is dLoss/dd_soft; gL, gR are overwritten. */
+void oracle_softargmax_bwd(const double *L, const double *R, int Bn, int H, int W, int n,
+                           int ndisp, double T, double eps, const double *g_d, double *gL,
+                           double *gR) {
+    int w = 2 * n + 1, N = w * w;
+    memset(gL, 0, sizeof(double) * Bn * H * W);
+    memset(gR, 0, sizeof(double) * Bn * H * W);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int b = 0; b < Bn; ++b) {
+        double *ac = (double *)malloc(sizeof(double) * N), *bc = (double *)malloc(sizeof(double) * N);
+        double *rho = (double *)malloc(sizeof(double) * (ndisp > 0 ? ndisp : 1));
+        const double *A = L + (long)b * H * W, *Bm = R + (long)b * H * W;
+        double *gA = gL + (long)b * H * W, *gB = gR + (long)b * H * W;
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                int zmax = ndisp - 1 < x ? ndisp - 1 : x;
+                double Saa, Sbb, m = -INFINITY;
+                for (int z = 0; z <= zmax; ++z) {
+                    rho[z] = zncc_eps_window(A, Bm, W, H, n, y, x, z, eps, ac, bc, &Saa, &Sbb);
+                    if (rho[z] / T > m) m = rho[z] / T;
+                }
+                double s = 0.0, sz = 0.0;
+                for (int z = 0; z <= zmax; ++z) { double e = exp(rho[z] / T - m); s += e; sz += z * e; }
+                double dsoft = sz / s;
+                double g = g_d[((long)b * H + y) * W + x];
+                if (g == 0.0) continue;
+                for (int z = 0; z <= zmax; ++z) {
+                    double p = exp(rho[z] / T - m) / s;
+                    double grho = g * p * (z - dsoft) / T;
+                    double r_ = zncc_eps_window(A, Bm, W, H, n, y, x, z, eps, ac, bc, &Saa, &Sbb);
+                    double sq = sqrt((Saa + eps) * (Sbb + eps));
+                    int t = 0;
+                    for (int i = -n; i <= n; ++i)
+                        for (int j = -n; j <= n; ++j, ++t) {
+                            int yy = clampi(y + i, 0, H - 1);
+                            double da = bc[t] / sq - r_ * ac[t] / (Saa + eps);
+                            double db = ac[t] / sq - r_ * bc[t] / (Sbb + eps);
+                            gA[(long)yy * W + clampi(x + j, 0, W - 1)] += grho * da;
+                            gB[(long)yy * W + clampi(x - z + j, 0, W - 1)] += grho * db;
+                        }
+                }
+            }
+        free(ac); free(bc); free(rho);
+    }
+}
