@@ -1,0 +1,445 @@
+#!/usr/bin/env python
+"""Throughput of multi-scale hierarchical ZNCC block matching on one GB300 per rank.
+
+Workload: the 1400x1000 benchmark-shaped pair (seeded synthetic slanted-plane scene, 12
+regions, noise sigma 3), D = 256, K = 4 pyramid levels, 7x7 window, refinement radius 2.
+A step is one whole hierarchical pass (pyramid, coarsest full search, three restricted
+levels) on one pair already resident in HBM; the L2 is flushed between steps (the pair
+is smaller than L2).  Flat full-range 7x7 block matching (K = 1) is timed on the same
+pair for comparison, and both maps are scored against the ground truth.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank matches its own pair (seed =
+rank): weak scaling, no data-path collective; only the timings are reduced (max).
+`--impl reference` times the FP64 CPU oracle on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "bench_1400x1000"
+METRIC = "Gpix·disp/s and frames/s, hierarchical vs flat ZNCC BM, same bad-pixel rate"
+L2_FLUSH_BYTES = 256 << 20
+
+
+# ---------------------------------------------------------------------------------------
+# distributed plumbing (host side only: rank discovery, barrier, max-reduction)
+# ---------------------------------------------------------------------------------------
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def dist_init(world: int, backend: str):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    if not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def reduce_max(value: float, dist, device=None) -> float:
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def pair_seed(rank: int) -> int:
+    """Each rank matches its own independent pair (weak scaling)."""
+    return rank
+
+
+# ---------------------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self) -> dict:
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        try:
+            rows = [ln.split(",") for ln in open(self.path).read().strip().splitlines() if ln.strip()]
+            os.unlink(self.path)
+        except OSError:
+            return out
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if sm:
+            busy = [s for s in sm if s > 0.5 * max(sm)] or sm
+            out = {"sm_mhz": statistics.median(busy), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        return out
+
+
+# ---------------------------------------------------------------------------------------
+# roofline accounting
+# ---------------------------------------------------------------------------------------
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
+
+
+# One "op" is one 32-bit ALU lane instruction.  Nominal ALU peak: SMs x 128 lanes x max
+# SM clock (an upper bound for every pipe; integer dot products may issue at half rate).
+def alu_peak_tops(sms: int, mhz: float) -> float:
+    return sms * 128 * mhz * 1e6 / 1e12
+
+
+def ops_per_eval_restricted(window: int) -> int:
+    # direct window: one dp4a per 4 window bytes per row, plus the exact int32 combine,
+    # int-to-float, two scalings and the WTA compare
+    return window * ((window + 3) // 4) + 5
+
+
+OPS_PER_EVAL_FULL = 8   # sliding sums: 2 vertical + 2 horizontal, c (2), scale (1), compare (1)
+
+
+def stage_work(name, spec, levels_wh, evals_by_level):
+    """(bound, algorithmic amount, unit) of one stage of the pass."""
+    if name == "copy_level0":
+        w, h = levels_wh[0]
+        return "hbm", 2 * w * h + 2 * (w + 32) * (h + 16), "B"
+    if name.startswith("reduce_level"):
+        k = int(name[len("reduce_level"):])
+        (w1, h1), (w, h) = levels_wh[k - 1], levels_wh[k]
+        return "hbm", 2 * w1 * h1 + 2 * (w + 32) * (h + 16), "B"
+    if name.startswith("full_level"):
+        k = int(name[len("full_level"):])
+        return "alu", evals_by_level[k] * OPS_PER_EVAL_FULL, "op"
+    k = int(name[len("restricted_level"):])
+    return "alu", evals_by_level[k] * ops_per_eval_restricted(spec.window), "op"
+
+
+def full_evals(w, h, dk):
+    return sum(min(dk - 1, x) + 1 for x in range(w)) * h
+
+
+def restricted_evals(prior, w, h, dk, r):
+    import numpy as np
+    yy, xx = np.mgrid[0:h, 0:w]
+    zmax = np.minimum(dk - 1, xx)
+    dh = np.clip(2 * prior[yy // 2, xx // 2].astype(np.int64), 0, zmax)
+    lo = np.maximum(0, dh - r)
+    hi = np.minimum(zmax, dh + r)
+    return int((hi - lo + 1).sum())
+
+
+# ---------------------------------------------------------------------------------------
+# oracle (CPU baseline)
+# ---------------------------------------------------------------------------------------
+def time_oracle(sc, budget_s: float, min_runs: int = 1):
+    import oracle
+    s = sc.spec
+    oracle.build()
+    runs, t0 = 0, time.perf_counter()
+    while True:
+        oracle.disparity(sc.left, sc.right, s.max_disp, s.levels, s.window, s.radius)
+        runs += 1
+        el = time.perf_counter() - t0
+        if runs >= min_runs and el >= budget_s:
+            break
+    return runs, el, oracle.max_threads()
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1901_09593_gb300 import scenes
+    spec = scenes.SPECS[WORKLOAD]
+    sc = scenes.make_pair(spec, pair_seed(0))
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle.disparity(sc.left, sc.right, spec.max_disp, spec.levels, spec.window, spec.radius)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.disparity(sc.left, sc.right, spec.max_disp, spec.levels, spec.window, spec.radius)
+    el = time.perf_counter() - t0
+    fps = args.steps / el
+    cores = oracle.max_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_dict(spec),
+        "cpu_baseline": {"kind": "oracle", "value": fps, "unit": "frames/s", "cores": cores,
+                         "sample": f"{args.steps} full-frame hierarchical passes of the "
+                                   f"{spec.width}x{spec.height} pair, FP64 C oracle, OpenMP"},
+        "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_dict(spec):
+    return {"workload": f"{WORKLOAD}: hierarchical ZNCC BM, {spec.width}x{spec.height} uint8 pair, "
+                        f"D={spec.max_disp}, K={spec.levels}, {spec.window}x{spec.window} window, "
+                        f"r={spec.radius}",
+            "width": spec.width, "height": spec.height, "max_disp": spec.max_disp,
+            "levels": spec.levels, "window": spec.window, "radius": spec.radius,
+            "l2": "flushed between timed steps (256 MB write; inputs are smaller than L2)",
+            "parallelism": "independent pairs per rank (weak scaling)"}
+
+
+# ---------------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------------
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_1901_09593_gb300 import Context, _lib, build, scenes
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = dist_init(world, "nccl")
+    build.build()
+    spec = scenes.SPECS[WORKLOAD]
+    sc = scenes.make_pair(spec, pair_seed(rank))
+    W, H = spec.width, spec.height
+    L = torch.from_numpy(sc.left).to(dev)
+    R = torch.from_numpy(sc.right).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    ctx = Context(W, H, spec.max_disp, spec.levels, spec.window, spec.radius)
+    d = torch.empty((H, W), dtype=torch.int16, device=dev)
+    c = torch.empty((H, W), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize(dev)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for e0, e1 in ev:
+            flush.zero_()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return [e0.elapsed_time(e1) for e0, e1 in ev]
+
+    # -- hierarchical, graph replay: the timed region
+    for _ in range(args.warmup):
+        ctx.disparity(L, R, d, c)
+    ctx.sync()
+    ctx.eval_count(reset=True)
+    barrier(dist)
+    torch.cuda.synchronize(dev)
+    clk = ClockSampler(local)
+    clk.start()
+    wall0 = time.perf_counter()
+    ms = timed(lambda: ctx.disparity(L, R, d, c), args.steps, 0)
+    wall = time.perf_counter() - wall0
+    barrier(dist)
+    clocks = clk.stop()
+    ctx.sync()
+    evals_total = ctx.eval_count(reset=True)
+    t_dev = sum(ms) / 1e3
+    t_max = reduce_max(t_dev, dist, dev)
+    frames = world * args.steps
+    fps = frames / t_max
+    evals_per_frame = evals_total / args.steps
+    d_h = d.cpu().numpy()
+    bad1_h = scenes.bad_rate(d_h, sc.gt, sc.mask, 1.0)
+    bad2_h = scenes.bad_rate(d_h, sc.gt, sc.mask, 2.0)
+
+    # -- flat full-range block matching on the same GPU and pair
+    flat = Context(W, H, spec.max_disp, 1, spec.window, spec.radius)
+    df = torch.empty_like(d)
+    cf = torch.empty_like(c)
+    fsteps = max(3, min(args.steps, 20))
+    fms = timed(lambda: flat.disparity(L, R, df, cf), fsteps, max(3, args.warmup // 2))
+    flat.sync()
+    flat_fps = fsteps / (sum(fms) / 1e3)
+    flat_evals = full_evals(W, H, spec.max_disp)
+    df_h = df.cpu().numpy()
+    bad1_f = scenes.bad_rate(df_h, sc.gt, sc.mask, 1.0)
+    bad2_f = scenes.bad_rate(df_h, sc.gt, sc.mask, 2.0)
+
+    # -- per-kernel timing (CUDA events around each launch, same stream) -> roofline
+    nprof = max(5, min(args.steps, 30))
+    stage_names = ctx.stage_names()
+    acc = [[] for _ in stage_names]
+    for _ in range(nprof):
+        flush.zero_()
+        for i, v in enumerate(ctx.profile_disparity(L, R, d, c)):
+            acc[i].append(v)
+    stage_ms = [statistics.mean(a) for a in acc]
+    levels_wh = [ctx.level_shape(k)[:2] for k in range(spec.levels)]
+    evals_by_level = {}
+    K = spec.levels
+    wk, hk, dkk = ctx.level_shape(K - 1)
+    evals_by_level[K - 1] = full_evals(wk, hk, dkk)
+    for k in range(K - 2, -1, -1):
+        wk, hk, dkk = ctx.level_shape(k)
+        prior = ctx.level_result(k + 1)[0].cpu().numpy()
+        evals_by_level[k] = restricted_evals(prior, wk, hk, dkk, spec.radius)
+    peaks = load_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = (clocks.get("sm_max_mhz") or (peaks or {}).get("sm_max_mhz") or 2070.0)
+    stages = []
+    for nm, t in zip(stage_names, stage_ms):
+        bound, amount, unit = stage_work(nm, spec, levels_wh, evals_by_level)
+        stages.append({"kernel": nm, "ms": round(t, 5), "share": None, "bound": bound,
+                       "work": amount, "work_unit": unit})
+    tot = sum(stage_ms)
+    for s_ in stages:
+        s_["share"] = round(s_["ms"] / tot, 4) if tot > 0 else None
+    dom = max(stages, key=lambda s_: s_["ms"])
+    if dom["bound"] == "hbm":
+        peak = (peaks or {}).get("hbm_gbs") or 6800.0
+        ach = dom["work"] / (dom["ms"] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak}
+    else:
+        peak = alu_peak_tops(sms, sm_max)
+        ach = dom["work"] / (dom["ms"] * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Top/s", "frac": ach / peak}
+    roof["kernel"] = dom["kernel"]
+    roof["traffic"] = None
+    roof["peak_source"] = ("MEASURED_PEAKS.json hbm_gbs" if dom["bound"] == "hbm" and peaks else
+                           f"nominal {sms} SMs x 128 lanes x {sm_max:.0f} MHz")
+
+    # -- end to end through the C ABI with pinned host buffers
+    pin_l = torch.from_numpy(sc.left).pin_memory()
+    pin_r = torch.from_numpy(sc.right).pin_memory()
+    pin_d = torch.empty((H, W), dtype=torch.int16).pin_memory()
+    pin_c = torch.empty((H, W), dtype=torch.float32).pin_memory()
+    hl, hr, hd, hc = pin_l.numpy(), pin_r.numpy(), pin_d.numpy(), pin_c.numpy()
+    for _ in range(max(3, args.warmup)):
+        ctx.disparity_host(hl, hr, hd, hc)
+    barrier(dist)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.disparity_host(hl, hr, hd, hc)
+    e2e_s = reduce_max(time.perf_counter() - t0, dist, dev)
+    e2e_fps = world * args.steps / e2e_s
+
+    # -- CPU baseline: the oracle on this host (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        runs, el, cores = time_oracle(sc, args.cpu_budget)
+        cpu = {"kind": "oracle", "value": runs / el, "unit": "frames/s", "cores": cores,
+               "sample": f"{runs} full-frame hierarchical passes of the {W}x{H} pair "
+                         f"(FP64 C oracle, OpenMP over rows), {el:.1f} s"}
+
+    launches_per_step = 2 * spec.levels
+    line = {
+        "metric": METRIC,
+        "value": fps,
+        "unit": "frames/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_max / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u8",
+        "data": "synthetic",
+        "config": config_dict(spec),
+        "gpix_disp_per_s": evals_per_frame * fps / 1e9,
+        "gpix_disp_per_s_flat_equivalent": W * H * spec.max_disp * fps / 1e9,
+        "evals_per_frame": evals_per_frame,
+        "bad1": bad1_h, "bad2": bad2_h,
+        "flat": {"frames_per_s": flat_fps, "ms_per_frame": 1e3 / flat_fps,
+                 "gpix_disp_per_s": flat_evals * flat_fps / 1e9, "evals_per_frame": flat_evals,
+                 "bad1": bad1_f, "bad2": bad2_f, "steps": fsteps},
+        "hier_over_flat_speedup": fps / world / flat_fps,
+        "roofline": roof,
+        "stages": stages,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": 2 * W * H,
+                "d2h_bytes_per_step": W * H * (2 + 4)},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+        "wall_s_timed_region": wall,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle CPU time")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,146 @@
+/*
+ * msbm.h -- C ABI of libmsbm: multi-scale hierarchical ZNCC block matching on one GPU.
+ *
+ * Method: Kaushik & Lall, "Fast Hierarchical depth map computation from stereo" (arXiv
+ * 1901.09593).  A K-level Gaussian pyramid of a rectified stereo pair (Sec. III, Fig. 1);
+ * a full-range zero-mean normalised cross-correlation (ZNCC, Eq. 1-2) winner-take-all
+ * search at the coarsest level (Sec. III-A, Eq. 3-4); at every finer level a ZNCC search
+ * restricted to a radius around the 2x nearest-neighbour upsample of the coarser disparity
+ * (Sec. III-C, Eq. 8-9, first branch).
+ *
+ * Conventions shared by every entry point:
+ *   - Images are 8-bit grayscale, row-major, (y, x) = (row, column).  The LEFT image is
+ *     the reference: candidate disparity z compares left column x with right column x - z.
+ *   - Candidates at level 0 are 0..D-1; at level k there are D_k = ceil(D / 2^k); a
+ *     candidate is admissible only if z <= x.  Level k is ceil(W_{k-1}/2) x ceil(H_{k-1}/2).
+ *   - Windows are (2n+1) x (2n+1), read clamp-to-edge.  A window with zero variance on
+ *     either side scores 0.  Ties go to the smallest z.
+ *   - Pyramid step: 5-tap binomial [1 4 6 4 1]/16 per axis, clamp-to-edge, 2x decimation,
+ *     integer result rounded to nearest.
+ *   - Device pointers are owned by the caller and must stay valid until the enqueued work
+ *     has finished; the context owns only its internal buffers.  Output maps are dense
+ *     (row pitch = width).  Disparities are int16, costs float32 (the winning ZNCC value,
+ *     within about 1e-6 of its exact value).
+ *   - Work is asynchronous on the stream given at creation.  Argument errors are returned
+ *     synchronously before anything is enqueued.  CUDA launch errors are returned as
+ *     MSBM_ERR_CUDA.  Device-side failures (a bounded wait that gave up) are recorded in the
+ *     context and returned by msbm_sync.  No entry point aborts, throws or traps.
+ *   - A context is not thread-safe: one host thread at a time per context.
+ */
+#ifndef MSBM_H
+#define MSBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum msbm_status {
+    MSBM_OK = 0,
+    MSBM_ERR_INVALID_ARG = 1,   /* a size, pointer or parameter is out of range */
+    MSBM_ERR_ALIGNMENT = 2,     /* reserved: no entry point currently requires alignment */
+    MSBM_ERR_OOM = 3,           /* device or host allocation failed */
+    MSBM_ERR_CUDA = 4,          /* a CUDA runtime call or launch failed */
+    MSBM_ERR_TIMEOUT = 5,       /* a bounded device wait gave up (see MSBM_FLAG_TEST_TIMEOUT) */
+    MSBM_ERR_UNSUPPORTED = 6    /* no usable sm_103a device, or a size beyond a kernel limit */
+} msbm_status;
+
+/* msbm_disparity enqueues its kernels directly instead of replaying a CUDA graph. */
+#define MSBM_FLAG_NO_GRAPH 1u
+/* Test hook: every bounded device wait gives up at once.  The kernel records
+ * MSBM_ERR_TIMEOUT, drains its own copies in flight and returns without writing outputs. */
+#define MSBM_FLAG_TEST_TIMEOUT 2u
+
+/* Problem statement (Sec. III; window and pyramid depth as in Sec. IV). */
+typedef struct msbm_params {
+    int32_t width, height; /* level-0 size, 1..16384 each                                  */
+    int32_t max_disp;      /* D, 1..4096: level-0 candidates 0..D-1                        */
+    int32_t levels;        /* K, 1..12; K = 1 is flat full-range block matching             */
+    int32_t window;        /* odd window side 2n+1, 3..13 (int32-exact sums up to 13x13)   */
+    int32_t radius;        /* r, 0..16: refinement candidates dhat-r .. dhat+r              */
+    uint32_t flags;        /* MSBM_FLAG_*                                                   */
+} msbm_params;
+
+typedef struct msbm_ctx msbm_ctx;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int msbm_version(void);
+/* Static text for a status code. */
+const char *msbm_status_string(msbm_status s);
+
+/* Validate params, allocate the pyramid and per-level output buffers on the current
+ * device, and bind the context to `cuda_stream` (a cudaStream_t; NULL = legacy default).
+ * *out is NULL on failure. */
+msbm_status msbm_create(const msbm_params *params, void *cuda_stream, msbm_ctx **out);
+/* Synchronise the stream and free everything the context owns.  NULL is accepted. */
+msbm_status msbm_destroy(msbm_ctx *ctx);
+/* Rebind the context to another stream (later work is enqueued there). */
+msbm_status msbm_set_stream(msbm_ctx *ctx, void *cuda_stream);
+
+/* Size and candidate count D_k of level `level` (0 = full resolution). */
+msbm_status msbm_level_shape(const msbm_ctx *ctx, int32_t level, int32_t *w, int32_t *h,
+                             int32_t *d_k);
+
+/* Sec. III, Fig. 1: build all K levels of both images into the context.  `d_left`,
+ * `d_right`: device images of the context's width x height, row pitch `pitch_bytes`
+ * (>= width; any value). */
+msbm_status msbm_pyramid(msbm_ctx *ctx, const uint8_t *d_left, const uint8_t *d_right,
+                         size_t pitch_bytes);
+
+/* Copy level `level` of the left (which = 0) or right (which = 1) pyramid into the dense
+ * device buffer `d_out` (W_k x H_k bytes).  For tests and inspection. */
+msbm_status msbm_level_image(msbm_ctx *ctx, int32_t level, int32_t which, uint8_t *d_out);
+
+/* One level of winner-take-all on the pyramid built by msbm_pyramid.
+ *   d_prior == NULL: full search over 0..min(D_k-1, x)              (Sec. III-A, Eq. 3-4)
+ *   d_prior != NULL: dense int16 map of level+1 (W_{k+1} x H_{k+1}); candidates
+ *                    dhat-r .. dhat+r with dhat = 2*prior(y/2, x/2), clipped to
+ *                    0..min(D_k-1, x) (dhat itself is first clamped into that range)
+ *                                                                  (Sec. III-C, Eq. 8-9)
+ * Writes d_out (int16, W_k x H_k) and cost_out (float, W_k x H_k, may be NULL). */
+msbm_status msbm_match_level(msbm_ctx *ctx, int32_t level, const int16_t *d_prior,
+                             int16_t *d_out, float *cost_out);
+
+/* The whole hierarchical pass on device images: pyramid, coarsest full search, then the
+ * restricted search at every finer level.  Writes the level-0 maps.  Replays a CUDA graph
+ * (re-captured when a pointer changes) unless MSBM_FLAG_NO_GRAPH. */
+msbm_status msbm_disparity(msbm_ctx *ctx, const uint8_t *d_left, const uint8_t *d_right,
+                           size_t pitch_bytes, int16_t *d_out, float *cost_out);
+
+/* Same pass on HOST buffers: copies the images in, runs, copies the maps out, and waits.
+ * Pinned host memory gives asynchronous copies; pageable memory works but is slower. */
+msbm_status msbm_disparity_host(msbm_ctx *ctx, const uint8_t *h_left, const uint8_t *h_right,
+                                size_t pitch_bytes, int16_t *h_d, float *h_cost);
+
+/* Copy the maps of an intermediate level (1..K-1) left by the last msbm_disparity into
+ * the caller's dense device buffers (W_k x H_k; cost_out may be NULL).  Level 0 is written
+ * to the caller's buffers by msbm_disparity itself. */
+msbm_status msbm_level_result(msbm_ctx *ctx, int32_t level, int16_t *d_out, float *cost_out);
+
+/* Timing aid: run the whole pass once with direct launches, recording a CUDA event
+ * before the first kernel and after each kernel on the context's stream, wait, and write
+ * each kernel's milliseconds to stage_ms in launch order:
+ *   [0]            level-0 copy into the pyramid buffers,
+ *   [1 .. K-1]     pyramid reduce producing levels 1 .. K-1,
+ *   [K]            full search at level K-1,
+ *   [K+1 .. 2K-1]  restricted search at levels K-2 .. 0.
+ * n_stages must be 2K.  Results equal msbm_disparity's. */
+msbm_status msbm_profile_disparity(msbm_ctx *ctx, const uint8_t *d_left, const uint8_t *d_right,
+                                   size_t pitch_bytes, int16_t *d_out, float *cost_out,
+                                   float *stage_ms, int32_t n_stages);
+
+/* Wait for the context's stream; return the first device-side error recorded since the
+ * last msbm_sync (and clear it), else MSBM_OK. */
+msbm_status msbm_sync(msbm_ctx *ctx);
+
+/* Number of (pixel, candidate) ZNCC evaluations performed since the last call with
+ * reset != 0 (synchronises the stream). */
+msbm_status msbm_eval_count(msbm_ctx *ctx, int64_t *count, int32_t reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MSBM_H */

@@ -1,0 +1,424 @@
+// msbm_api.cu -- the C ABI declared in include/msbm.h: argument validation, the context
+// (pyramid apron buffers, per-level maps, TMA descriptors, error and evaluation counters),
+// launch orchestration of the hierarchical pass (Sec. III, Fig. 1) and its CUDA-graph
+// replay.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "msbm.h"
+#include "msbm_internal.h"
+
+using namespace msbm;
+
+namespace msbm {
+cudaError_t zncc_full_prepare(int nh, int sx);
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+struct msbm_ctx {
+    msbm_params p{};
+    int nh = 0;
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    std::vector<LevelBuf> lv;
+    int *d_err = nullptr;
+    unsigned long long *d_evals = nullptr;
+    // graph replay of msbm_disparity
+    cudaGraphExec_t exec = nullptr;
+    const void *gkey[4] = {nullptr, nullptr, nullptr, nullptr};
+    size_t gpitch = 0;
+    // device staging of msbm_disparity_host
+    uint8_t *hL = nullptr, *hR = nullptr;
+    int16_t *hd = nullptr;
+    float *hc = nullptr;
+};
+
+namespace {
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+bool encode_u8(CUtensorMap *m, uint8_t *base, int pitch, int rows, int box_w, int box_h) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)pitch, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)pitch};
+    cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_h};
+    cuuint32_t es[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, base, dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+msbm_status validate(const msbm_params *p) {
+    if (!p) return MSBM_ERR_INVALID_ARG;
+    if (p->width < 1 || p->width > 16384 || p->height < 1 || p->height > 16384)
+        return MSBM_ERR_INVALID_ARG;
+    if (p->max_disp < 1 || p->max_disp > 4096) return MSBM_ERR_INVALID_ARG;
+    if (p->levels < 1 || p->levels > 12) return MSBM_ERR_INVALID_ARG;
+    if (p->window < 3 || p->window > 13 || (p->window & 1) == 0) return MSBM_ERR_INVALID_ARG;
+    if (p->radius < 0 || p->radius > 16) return MSBM_ERR_INVALID_ARG;
+    if (p->flags & ~(MSBM_FLAG_NO_GRAPH | MSBM_FLAG_TEST_TIMEOUT)) return MSBM_ERR_INVALID_ARG;
+    return MSBM_OK;
+}
+
+int choose_sx(int W, int H, int sms) {
+    for (int sx = 4; sx > 1; sx /= 2) {
+        long ctas = (long)((W + 32 * sx - 1) / (32 * sx)) * ((H + 7) / 8);
+        if (ctas >= 2L * sms) return sx;
+    }
+    return 1;
+}
+
+void free_ctx(msbm_ctx *c) {
+    if (!c) return;
+    if (c->exec) cudaGraphExecDestroy(c->exec);
+    for (auto &l : c->lv) {
+        cudaFree(l.base[0]);
+        cudaFree(l.d);
+        cudaFree(l.c);
+    }
+    cudaFree(c->d_err);
+    cudaFree(c->d_evals);
+    cudaFree(c->hL);
+    cudaFree(c->hR);
+    cudaFree(c->hd);
+    cudaFree(c->hc);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    delete c;
+}
+
+inline msbm_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return MSBM_OK;
+    if (e == cudaErrorMemoryAllocation) return MSBM_ERR_OOM;
+    return MSBM_ERR_CUDA;
+}
+
+msbm_status enqueue_pyramid(msbm_ctx *c, const uint8_t *L, const uint8_t *R, size_t pitch,
+                            cudaStream_t st) {
+    cudaError_t e = launch_apron_copy(L, R, pitch, c->lv[0], st);
+    for (int k = 1; e == cudaSuccess && k < c->p.levels; ++k) e = launch_pyr_reduce(c->lv[k - 1], c->lv[k], st);
+    return cuda_status(e);
+}
+
+msbm_status enqueue_level(msbm_ctx *c, int k, const int16_t *prior, int16_t *d, float *cost,
+                          cudaStream_t st) {
+    const LevelBuf &l = c->lv[k];
+    const int force = (c->p.flags & MSBM_FLAG_TEST_TIMEOUT) ? 1 : 0;
+    cudaError_t e;
+    if (!prior) {
+        FullArgs a;
+        memset(&a, 0, sizeof(a));
+        a.tmL = l.tmFL[0];
+        a.tmR = l.tm256[1];
+        a.W = l.W; a.H = l.H; a.Dk = l.Dk;
+        a.d_out = d; a.c_out = cost;
+        a.evals = c->d_evals; a.err = c->d_err; a.force_timeout = force;
+        e = launch_zncc_full(a, c->nh, l.full_sx, st);
+    } else {
+        RestrArgs a;
+        memset(&a, 0, sizeof(a));
+        a.tmL = l.tm64[0];
+        a.tmR64 = l.tm64[1];
+        a.tmR256 = l.tm256[1];
+        a.Limg = l.img(0); a.Rimg = l.img(1); a.pitch = l.pitch;
+        a.W = l.W; a.H = l.H; a.Dk = l.Dk; a.r = c->p.radius;
+        a.prior = prior; a.Wp = (l.W + 1) / 2; a.Hp = (l.H + 1) / 2;
+        a.d_out = d; a.c_out = cost;
+        a.evals = c->d_evals; a.err = c->d_err; a.force_timeout = force;
+        e = launch_zncc_restricted(a, c->nh, st);
+    }
+    return cuda_status(e);
+}
+
+msbm_status enqueue_all(msbm_ctx *c, const uint8_t *L, const uint8_t *R, size_t pitch, int16_t *d,
+                        float *cost, cudaStream_t st) {
+    msbm_status s = enqueue_pyramid(c, L, R, pitch, st);
+    const int K = c->p.levels;
+    for (int k = K - 1; s == MSBM_OK && k >= 0; --k) {
+        int16_t *dk = k == 0 ? d : c->lv[k].d;
+        float *ck = k == 0 ? cost : c->lv[k].c;
+        const int16_t *prior = k == K - 1 ? nullptr : c->lv[k + 1].d;
+        s = enqueue_level(c, k, prior, dk, ck, st);
+    }
+    return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+int msbm_version(void) { return 10000; }
+
+const char *msbm_status_string(msbm_status s) {
+    switch (s) {
+        case MSBM_OK: return "ok";
+        case MSBM_ERR_INVALID_ARG: return "invalid argument";
+        case MSBM_ERR_ALIGNMENT: return "misaligned buffer";
+        case MSBM_ERR_OOM: return "out of memory";
+        case MSBM_ERR_CUDA: return "CUDA error";
+        case MSBM_ERR_TIMEOUT: return "device wait timed out";
+        case MSBM_ERR_UNSUPPORTED: return "unsupported device or size";
+    }
+    return "unknown status";
+}
+
+msbm_status msbm_create(const msbm_params *params, void *cuda_stream, msbm_ctx **out) {
+    if (!out) return MSBM_ERR_INVALID_ARG;
+    *out = nullptr;
+    msbm_status s = validate(params);
+    if (s != MSBM_OK) return s;
+    int dev = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess)
+        return MSBM_ERR_UNSUPPORTED;
+    if (!(prop.major == 10 && prop.minor == 3)) return MSBM_ERR_UNSUPPORTED;
+    if (!encode_fn()) return MSBM_ERR_UNSUPPORTED;
+
+    msbm_ctx *c = new (std::nothrow) msbm_ctx();
+    if (!c) return MSBM_ERR_OOM;
+    c->p = *params;
+    c->nh = params->window / 2;
+    c->device = dev;
+    c->num_sms = prop.multiProcessorCount;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    const int rowsT = 8 + 2 * c->nh;
+    cudaError_t e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_evals, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->d_evals, 0, sizeof(unsigned long long));
+    int W = params->width, H = params->height;
+    for (int k = 0; e == cudaSuccess && k < params->levels; ++k) {
+        LevelBuf l;
+        l.W = W; l.H = H;
+        l.Dk = (int)(((long)params->max_disp + (1L << k) - 1) >> k);
+        l.pitch = (W + 2 * APX + 127) / 128 * 128;
+        l.rows = H + 2 * APY;
+        size_t bytes = (size_t)l.pitch * l.rows;
+        uint8_t *buf = nullptr;
+        e = cudaMalloc(&buf, 2 * bytes);
+        if (e != cudaSuccess) break;
+        l.base[0] = buf;
+        l.base[1] = buf + bytes;
+        e = cudaMemset(buf, 0, 2 * bytes);
+        if (e == cudaSuccess && k > 0) e = cudaMalloc(&l.d, (size_t)W * H * sizeof(int16_t));
+        if (e == cudaSuccess && k > 0) e = cudaMalloc(&l.c, (size_t)W * H * sizeof(float));
+        l.full_sx = choose_sx(W, H, c->num_sms);
+        for (int i = 0; e == cudaSuccess && i < 2; ++i) {
+            bool ok = encode_u8(&l.tm64[i], l.base[i], l.pitch, l.rows, 64, rowsT) &&
+                      encode_u8(&l.tm256[i], l.base[i], l.pitch, l.rows, 256, rowsT) &&
+                      encode_u8(&l.tmFL[i], l.base[i], l.pitch, l.rows, 32 * l.full_sx + 32, rowsT);
+            if (!ok) { c->lv.push_back(l); free_ctx(c); return MSBM_ERR_UNSUPPORTED; }
+        }
+        if (e == cudaSuccess) e = zncc_full_prepare(c->nh, l.full_sx);
+        c->lv.push_back(l);
+        W = (W + 1) / 2;
+        H = (H + 1) / 2;
+    }
+    if (e != cudaSuccess) {
+        msbm_status st = cuda_status(e);
+        free_ctx(c);
+        return st;
+    }
+    *out = c;
+    return MSBM_OK;
+}
+
+msbm_status msbm_destroy(msbm_ctx *ctx) {
+    if (!ctx) return MSBM_OK;
+    cudaStreamSynchronize(ctx->stream);
+    free_ctx(ctx);
+    return MSBM_OK;
+}
+
+msbm_status msbm_set_stream(msbm_ctx *ctx, void *cuda_stream) {
+    if (!ctx) return MSBM_ERR_INVALID_ARG;
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    return MSBM_OK;
+}
+
+msbm_status msbm_level_shape(const msbm_ctx *ctx, int32_t level, int32_t *w, int32_t *h,
+                             int32_t *d_k) {
+    if (!ctx || level < 0 || level >= ctx->p.levels) return MSBM_ERR_INVALID_ARG;
+    const LevelBuf &l = ctx->lv[level];
+    if (w) *w = l.W;
+    if (h) *h = l.H;
+    if (d_k) *d_k = l.Dk;
+    return MSBM_OK;
+}
+
+msbm_status msbm_pyramid(msbm_ctx *ctx, const uint8_t *d_left, const uint8_t *d_right,
+                         size_t pitch_bytes) {
+    if (!ctx || !d_left || !d_right || pitch_bytes < (size_t)ctx->p.width) return MSBM_ERR_INVALID_ARG;
+    return enqueue_pyramid(ctx, d_left, d_right, pitch_bytes, ctx->stream);
+}
+
+msbm_status msbm_level_image(msbm_ctx *ctx, int32_t level, int32_t which, uint8_t *d_out) {
+    if (!ctx || level < 0 || level >= ctx->p.levels || (which != 0 && which != 1) || !d_out)
+        return MSBM_ERR_INVALID_ARG;
+    return cuda_status(launch_level_extract(ctx->lv[level], which, d_out, ctx->stream));
+}
+
+msbm_status msbm_match_level(msbm_ctx *ctx, int32_t level, const int16_t *d_prior, int16_t *d_out,
+                             float *cost_out) {
+    if (!ctx || level < 0 || level >= ctx->p.levels || !d_out) return MSBM_ERR_INVALID_ARG;
+    return enqueue_level(ctx, level, d_prior, d_out, cost_out, ctx->stream);
+}
+
+msbm_status msbm_disparity(msbm_ctx *ctx, const uint8_t *d_left, const uint8_t *d_right,
+                           size_t pitch_bytes, int16_t *d_out, float *cost_out) {
+    if (!ctx || !d_left || !d_right || !d_out || pitch_bytes < (size_t)ctx->p.width)
+        return MSBM_ERR_INVALID_ARG;
+    if (ctx->p.flags & MSBM_FLAG_NO_GRAPH)
+        return enqueue_all(ctx, d_left, d_right, pitch_bytes, d_out, cost_out, ctx->stream);
+    const void *key[4] = {d_left, d_right, d_out, cost_out};
+    bool same = ctx->exec && ctx->gpitch == pitch_bytes && memcmp(key, ctx->gkey, sizeof(key)) == 0;
+    if (!same) {
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed);
+        if (e != cudaSuccess) return MSBM_ERR_CUDA;
+        msbm_status s = enqueue_all(ctx, d_left, d_right, pitch_bytes, d_out, cost_out, ctx->cap_stream);
+        e = cudaStreamEndCapture(ctx->cap_stream, &g);
+        if (s != MSBM_OK || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return s != MSBM_OK ? s : MSBM_ERR_CUDA;
+        }
+        if (ctx->exec) {
+            cudaGraphExecUpdateResultInfo info;
+            if (cudaGraphExecUpdate(ctx->exec, g, &info) != cudaSuccess) {
+                cudaGetLastError();
+                cudaGraphExecDestroy(ctx->exec);
+                ctx->exec = nullptr;
+            }
+        }
+        if (!ctx->exec) e = cudaGraphInstantiate(&ctx->exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            ctx->exec = nullptr;
+            return cuda_status(e);
+        }
+        memcpy(ctx->gkey, key, sizeof(key));
+        ctx->gpitch = pitch_bytes;
+    }
+    return cuda_status(cudaGraphLaunch(ctx->exec, ctx->stream));
+}
+
+msbm_status msbm_disparity_host(msbm_ctx *ctx, const uint8_t *h_left, const uint8_t *h_right,
+                                size_t pitch_bytes, int16_t *h_d, float *h_cost) {
+    if (!ctx || !h_left || !h_right || !h_d || pitch_bytes < (size_t)ctx->p.width)
+        return MSBM_ERR_INVALID_ARG;
+    const size_t W = ctx->p.width, H = ctx->p.height;
+    cudaError_t e = cudaSuccess;
+    if (!ctx->hL) {
+        e = cudaMalloc(&ctx->hL, W * H);
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->hR, W * H);
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->hd, W * H * sizeof(int16_t));
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->hc, W * H * sizeof(float));
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    cudaStream_t st = ctx->stream;
+    e = cudaMemcpy2DAsync(ctx->hL, W, h_left, pitch_bytes, W, H, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpy2DAsync(ctx->hR, W, h_right, pitch_bytes, W, H, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    msbm_status s = msbm_disparity(ctx, ctx->hL, ctx->hR, W, ctx->hd, h_cost ? ctx->hc : nullptr);
+    if (s != MSBM_OK) return s;
+    e = cudaMemcpyAsync(h_d, ctx->hd, W * H * sizeof(int16_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && h_cost)
+        e = cudaMemcpyAsync(h_cost, ctx->hc, W * H * sizeof(float), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    return msbm_sync(ctx);
+}
+
+msbm_status msbm_level_result(msbm_ctx *ctx, int32_t level, int16_t *d_out, float *cost_out) {
+    if (!ctx || level < 1 || level >= ctx->p.levels || !d_out) return MSBM_ERR_INVALID_ARG;
+    const LevelBuf &l = ctx->lv[level];
+    const size_t n = (size_t)l.W * l.H;
+    cudaError_t e = cudaMemcpyAsync(d_out, l.d, n * sizeof(int16_t), cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e == cudaSuccess && cost_out)
+        e = cudaMemcpyAsync(cost_out, l.c, n * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream);
+    return cuda_status(e);
+}
+
+msbm_status msbm_profile_disparity(msbm_ctx *ctx, const uint8_t *d_left, const uint8_t *d_right,
+                                   size_t pitch_bytes, int16_t *d_out, float *cost_out,
+                                   float *stage_ms, int32_t n_stages) {
+    if (!ctx || !d_left || !d_right || !d_out || !stage_ms || pitch_bytes < (size_t)ctx->p.width)
+        return MSBM_ERR_INVALID_ARG;
+    const int K = ctx->p.levels;
+    if (n_stages != 2 * K) return MSBM_ERR_INVALID_ARG;
+    std::vector<cudaEvent_t> ev(2 * K + 1, nullptr);
+    cudaError_t e = cudaSuccess;
+    for (auto &x : ev)
+        if (e == cudaSuccess) e = cudaEventCreate(&x);
+    cudaStream_t st = ctx->stream;
+    msbm_status s = cuda_status(e);
+    int i = 0;
+    if (s == MSBM_OK) s = cuda_status(cudaEventRecord(ev[i++], st));
+    if (s == MSBM_OK) s = cuda_status(launch_apron_copy(d_left, d_right, pitch_bytes, ctx->lv[0], st));
+    if (s == MSBM_OK) s = cuda_status(cudaEventRecord(ev[i++], st));
+    for (int k = 1; s == MSBM_OK && k < K; ++k) {
+        s = cuda_status(launch_pyr_reduce(ctx->lv[k - 1], ctx->lv[k], st));
+        if (s == MSBM_OK) s = cuda_status(cudaEventRecord(ev[i++], st));
+    }
+    for (int k = K - 1; s == MSBM_OK && k >= 0; --k) {
+        int16_t *dk = k == 0 ? d_out : ctx->lv[k].d;
+        float *ck = k == 0 ? cost_out : ctx->lv[k].c;
+        s = enqueue_level(ctx, k, k == K - 1 ? nullptr : ctx->lv[k + 1].d, dk, ck, st);
+        if (s == MSBM_OK) s = cuda_status(cudaEventRecord(ev[i++], st));
+    }
+    if (s == MSBM_OK) s = cuda_status(cudaStreamSynchronize(st));
+    for (int j = 0; s == MSBM_OK && j < 2 * K; ++j)
+        s = cuda_status(cudaEventElapsedTime(&stage_ms[j], ev[j], ev[j + 1]));
+    for (auto &x : ev)
+        if (x) cudaEventDestroy(x);
+    return s;
+}
+
+msbm_status msbm_sync(msbm_ctx *ctx) {
+    if (!ctx) return MSBM_ERR_INVALID_ARG;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return MSBM_ERR_CUDA;
+    int err = 0;
+    e = cudaMemcpy(&err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return MSBM_ERR_CUDA;
+    if (err != 0) {
+        cudaMemset(ctx->d_err, 0, sizeof(int));
+        return static_cast<msbm_status>(err);
+    }
+    return MSBM_OK;
+}
+
+msbm_status msbm_eval_count(msbm_ctx *ctx, int64_t *count, int32_t reset) {
+    if (!ctx || !count) return MSBM_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return MSBM_ERR_CUDA;
+    unsigned long long v = 0;
+    if (cudaMemcpy(&v, ctx->d_evals, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return MSBM_ERR_CUDA;
+    *count = static_cast<int64_t>(v);
+    if (reset && cudaMemset(ctx->d_evals, 0, sizeof(v)) != cudaSuccess) return MSBM_ERR_CUDA;
+    return MSBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,72 @@
+// msbm_internal.h -- host-side structures and kernel launchers of libmsbm (not part of
+// the public ABI).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "msbm.h"
+#include "msbm_device.cuh"
+
+namespace msbm {
+
+// One pyramid level of both images: two apron buffers (see msbm_device.cuh) plus the
+// tensor maps the ZNCC kernels stage tiles with.
+struct LevelBuf {
+    int W = 0, H = 0, Dk = 0;
+    int pitch = 0;               // bytes per buffer row (multiple of 128)
+    int rows = 0;                // H + 2*APY
+    uint8_t *base[2] = {nullptr, nullptr};  // buffer starts: image pixel (-APY, -APX)
+    int16_t *d = nullptr;        // this level's disparity map (levels >= 1)
+    float *c = nullptr;          // this level's cost map (levels >= 1)
+    // TMA maps over the apron buffers.  Boxes are ROWS = 8 + 2n rows high:
+    //   tm64[i]  : 64 bytes wide  (restricted-kernel left tile and narrow right spans)
+    //   tm256[i] : 256 bytes wide (wide right spans, full-range right spans)
+    //   tmFL[i]  : 32*SX + 32 bytes wide (full-range left tile), SX chosen per level
+    CUtensorMap tm64[2];
+    CUtensorMap tm256[2];
+    CUtensorMap tmFL[2];
+    int full_sx = 4;
+    uint8_t *img(int which) const {
+        return base[which] + (size_t)APY * pitch + APX;
+    }
+};
+
+struct FullArgs {
+    CUtensorMap tmL;     // box {32*SX + 32, 8 + 2n}
+    CUtensorMap tmR;     // box {256, 8 + 2n}
+    int W, H, Dk;
+    int16_t *d_out;
+    float *c_out;
+    unsigned long long *evals;
+    int *err;
+    int force_timeout;
+};
+
+struct RestrArgs {
+    CUtensorMap tmL;     // box {64, 8 + 2n}
+    CUtensorMap tmR64;   // box {64, 8 + 2n}
+    CUtensorMap tmR256;  // box {256, 8 + 2n}
+    const uint8_t *Limg; // level image origins (apron buffers), for the wide-span path
+    const uint8_t *Rimg;
+    int pitch;
+    int W, H, Dk, r;
+    const int16_t *prior;
+    int Wp, Hp;
+    int16_t *d_out;
+    float *c_out;
+    unsigned long long *evals;
+    int *err;
+    int force_timeout;
+};
+
+cudaError_t launch_apron_copy(const uint8_t *L, const uint8_t *R, size_t spitch, const LevelBuf &lv,
+                              cudaStream_t st);
+cudaError_t launch_pyr_reduce(const LevelBuf &src, const LevelBuf &dst, cudaStream_t st);
+cudaError_t launch_level_extract(const LevelBuf &lv, int which, uint8_t *out, cudaStream_t st);
+cudaError_t launch_zncc_full(const FullArgs &a, int nh, int sx, cudaStream_t st);
+cudaError_t launch_zncc_restricted(const RestrArgs &a, int nh, cudaStream_t st);
+size_t zncc_full_smem_bytes(int nh, int sx);
+
+}  // namespace msbm

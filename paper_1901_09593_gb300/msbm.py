@@ -1,0 +1,188 @@
+"""PyTorch-facing wrapper of the C ABI: argument marshalling only.
+
+Every step of the computation runs in libmsbm's CUDA kernels; this module checks tensor
+types and shapes, allocates outputs with PyTorch, passes raw device pointers and the
+current CUDA stream, and maps status codes to exceptions.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(device) -> int:
+    torch = _torch()
+    return int(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _check_image(t, w: int, h: int, name: str) -> int:
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.uint8:
+        raise TypeError(f"{name} must be a CUDA uint8 tensor")
+    if t.dim() != 2 or t.shape[0] != h or t.shape[1] != w or t.stride(1) != 1:
+        raise ValueError(f"{name} must be ({h}, {w}) with unit column stride")
+    return int(t.stride(0))
+
+
+class Context:
+    """A hierarchical ZNCC block matcher for one image size and parameter set."""
+
+    def __init__(self, width: int, height: int, max_disp: int, levels: int, window: int,
+                 radius: int, flags: int = 0, device=None):
+        torch = _torch()
+        self._lib = _lib.load()
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None
+                                   else torch.device(device).index)
+        self.params = _lib.msbm_params(width, height, max_disp, levels, window, radius, flags)
+        self._ctx = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _lib.check(self._lib.msbm_create(ctypes.byref(self.params),
+                                             ctypes.c_void_p(_stream_ptr(self.device)),
+                                             ctypes.byref(self._ctx)), "msbm_create")
+        self.width, self.height, self.levels = width, height, levels
+
+    # -- lifetime ---------------------------------------------------------------------
+    def close(self) -> None:
+        if self._ctx:
+            self._lib.msbm_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _bind_stream(self) -> None:
+        _lib.check(self._lib.msbm_set_stream(self._ctx, ctypes.c_void_p(_stream_ptr(self.device))))
+
+    # -- queries ----------------------------------------------------------------------
+    def level_shape(self, level: int):
+        w, h, d = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _lib.check(self._lib.msbm_level_shape(self._ctx, level, ctypes.byref(w), ctypes.byref(h),
+                                              ctypes.byref(d)), "msbm_level_shape")
+        return w.value, h.value, d.value
+
+    def sync(self) -> None:
+        _lib.check(self._lib.msbm_sync(self._ctx), "msbm_sync")
+
+    def eval_count(self, reset: bool = True) -> int:
+        v = ctypes.c_int64()
+        _lib.check(self._lib.msbm_eval_count(self._ctx, ctypes.byref(v), int(reset)), "msbm_eval_count")
+        return int(v.value)
+
+    # -- steps ------------------------------------------------------------------------
+    def pyramid(self, left, right) -> None:
+        self._bind_stream()
+        pitch = _check_image(left, self.width, self.height, "left")
+        if _check_image(right, self.width, self.height, "right") != pitch:
+            raise ValueError("left and right must share a row pitch")
+        _lib.check(self._lib.msbm_pyramid(self._ctx, ctypes.c_void_p(left.data_ptr()),
+                                          ctypes.c_void_p(right.data_ptr()), pitch), "msbm_pyramid")
+
+    def level_image(self, level: int, which: int):
+        torch = _torch()
+        self._bind_stream()
+        w, h, _ = self.level_shape(level)
+        out = torch.empty((h, w), dtype=torch.uint8, device=self.device)
+        _lib.check(self._lib.msbm_level_image(self._ctx, level, which, ctypes.c_void_p(out.data_ptr())),
+                   "msbm_level_image")
+        return out
+
+    def match_level(self, level: int, prior=None, with_cost: bool = True):
+        torch = _torch()
+        self._bind_stream()
+        w, h, _ = self.level_shape(level)
+        pp = None
+        if prior is not None:
+            wp, hp = (w + 1) // 2, (h + 1) // 2
+            if (not prior.is_cuda or prior.dtype != torch.int16 or tuple(prior.shape) != (hp, wp)
+                    or not prior.is_contiguous()):
+                raise ValueError(f"prior must be a contiguous CUDA int16 tensor of shape ({hp}, {wp})")
+            pp = ctypes.c_void_p(prior.data_ptr())
+        d = torch.empty((h, w), dtype=torch.int16, device=self.device)
+        c = torch.empty((h, w), dtype=torch.float32, device=self.device) if with_cost else None
+        _lib.check(self._lib.msbm_match_level(self._ctx, level, pp, ctypes.c_void_p(d.data_ptr()),
+                                              ctypes.c_void_p(c.data_ptr()) if c is not None else None),
+                   "msbm_match_level")
+        return d, c
+
+    def disparity(self, left, right, d_out=None, cost_out=None, with_cost: bool = True):
+        """Whole hierarchical pass on device tensors; returns level-0 (d, cost)."""
+        torch = _torch()
+        self._bind_stream()
+        pitch = _check_image(left, self.width, self.height, "left")
+        if _check_image(right, self.width, self.height, "right") != pitch:
+            raise ValueError("left and right must share a row pitch")
+        if d_out is None:
+            d_out = torch.empty((self.height, self.width), dtype=torch.int16, device=self.device)
+        if cost_out is None and with_cost:
+            cost_out = torch.empty((self.height, self.width), dtype=torch.float32, device=self.device)
+        _lib.check(self._lib.msbm_disparity(self._ctx, ctypes.c_void_p(left.data_ptr()),
+                                            ctypes.c_void_p(right.data_ptr()), pitch,
+                                            ctypes.c_void_p(d_out.data_ptr()),
+                                            ctypes.c_void_p(cost_out.data_ptr()) if cost_out is not None else None),
+                   "msbm_disparity")
+        return d_out, cost_out
+
+    def disparity_host(self, left: np.ndarray, right: np.ndarray, d_out: np.ndarray | None = None,
+                       cost_out: np.ndarray | None = None):
+        """Whole pass on host arrays (copies in, runs, copies out, waits)."""
+        self._bind_stream()
+        for a, nm in ((left, "left"), (right, "right")):
+            if a.dtype != np.uint8 or a.shape != (self.height, self.width) or a.strides[1] != 1:
+                raise ValueError(f"{nm} must be uint8 ({self.height}, {self.width})")
+        if left.strides[0] != right.strides[0]:
+            raise ValueError("left and right must share a row pitch")
+        if d_out is None:
+            d_out = np.empty((self.height, self.width), np.int16)
+        _lib.check(self._lib.msbm_disparity_host(
+            self._ctx, left.ctypes.data_as(ctypes.c_void_p), right.ctypes.data_as(ctypes.c_void_p),
+            left.strides[0], d_out.ctypes.data_as(ctypes.c_void_p),
+            cost_out.ctypes.data_as(ctypes.c_void_p) if cost_out is not None else None),
+            "msbm_disparity_host")
+        return d_out, cost_out
+
+    def profile_disparity(self, left, right, d_out, cost_out):
+        """One pass with per-kernel CUDA-event timing; returns the list of milliseconds in
+        launch order (copy, reduces, coarsest full search, restricted levels K-2..0)."""
+        self._bind_stream()
+        pitch = _check_image(left, self.width, self.height, "left")
+        n = 2 * self.levels
+        ms = (ctypes.c_float * n)()
+        _lib.check(self._lib.msbm_profile_disparity(
+            self._ctx, ctypes.c_void_p(left.data_ptr()), ctypes.c_void_p(right.data_ptr()), pitch,
+            ctypes.c_void_p(d_out.data_ptr()),
+            ctypes.c_void_p(cost_out.data_ptr()) if cost_out is not None else None, ms, n),
+            "msbm_profile_disparity")
+        return [float(v) for v in ms]
+
+    def stage_names(self):
+        k = self.levels
+        return (["copy_level0"] + [f"reduce_level{i}" for i in range(1, k)] + [f"full_level{k - 1}"]
+                + [f"restricted_level{i}" for i in range(k - 2, -1, -1)])
+
+    def level_result(self, level: int):
+        """Copies of an intermediate level's (d, cost) from the last disparity()."""
+        torch = _torch()
+        self._bind_stream()
+        w, h, _ = self.level_shape(level)
+        d = torch.empty((h, w), dtype=torch.int16, device=self.device)
+        c = torch.empty((h, w), dtype=torch.float32, device=self.device)
+        _lib.check(self._lib.msbm_level_result(self._ctx, level, ctypes.c_void_p(d.data_ptr()),
+                                               ctypes.c_void_p(c.data_ptr())), "msbm_level_result")
+        return d, c

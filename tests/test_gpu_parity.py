@@ -1,0 +1,288 @@
+"""GPU parity of libmsbm against the FP64 oracle, through the C ABI.
+
+Pyramid levels must be bit-exact.  Each matching level is first checked with the
+oracle's coarser disparity fed as the prior, so both sides search the same candidate
+sets: costs within 1e-4 and disparities bit-exact except where the oracle's best and
+second-best costs differ by less than 1e-4 (counted).  End-to-end runs are then
+compared and their differing pixels reported.  Full-size workloads are checked on
+sampled pixels, each recomputed by the oracle from the GPU's own prior."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1901_09593_gb300 import scenes
+from tests.gpu_util import COST_TOL, TIE_TOL, compare_level, dev, host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1901_09593_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def make_ctx(w, h, D, K, win, r, flags=0):
+    from paper_1901_09593_gb300 import Context
+    return Context(w, h, D, K, win, r, flags)
+
+
+def rand_pair(h, w, seed):
+    rng = np.random.default_rng(seed)
+    return rng.integers(0, 256, (h, w)).astype(np.uint8), rng.integers(0, 256, (h, w)).astype(np.uint8)
+
+
+@pytest.mark.parametrize("h,w,K", [(1, 1, 1), (5, 3, 2), (17, 33, 3), (240, 320, 3), (61, 175, 4), (130, 257, 5)])
+def test_pyramid_bit_exact(h, w, K):
+    a, b = rand_pair(h, w, h * 7 + w)
+    ctx = make_ctx(w, h, 8, K, 5, 2)
+    ctx.pyramid(dev(a), dev(b))
+    pa, pb = oracle.pyramid(a, K), oracle.pyramid(b, K)
+    for k in range(K):
+        np.testing.assert_array_equal(host(ctx.level_image(k, 0)), pa[k], err_msg=f"left level {k}")
+        np.testing.assert_array_equal(host(ctx.level_image(k, 1)), pb[k], err_msg=f"right level {k}")
+
+
+def test_pyramid_with_padded_pitch():
+    a, b = rand_pair(50, 70, 3)
+    big_a = np.zeros((50, 96), np.uint8)
+    big_b = np.zeros((50, 96), np.uint8)
+    big_a[:, :70] = a
+    big_b[:, :70] = b
+    ta, tb = dev(big_a)[:, :70], dev(big_b)[:, :70]
+    ctx = make_ctx(70, 50, 8, 3, 5, 2)
+    ctx.pyramid(ta, tb)
+    for k, lv in enumerate(oracle.pyramid(a, 3)):
+        np.testing.assert_array_equal(host(ctx.level_image(k, 0)), lv)
+
+
+@pytest.mark.parametrize("win", [3, 5, 7, 9, 11, 13])
+@pytest.mark.parametrize("h,w,D", [(24, 70, 16), (37, 300, 64), (9, 17, 40)])
+def test_full_level_random(win, h, w, D):
+    a, b = rand_pair(h, w, win * 100 + w)
+    ctx = make_ctx(w, h, D, 1, win, 2)
+    ctx.pyramid(dev(a), dev(b))
+    d, c = ctx.match_level(0)
+    do, co, c2, ev = oracle.match_level(a, b, win // 2, D)
+    compare_level(host(d), host(c), do, co, c2, f"full win={win} {h}x{w} D={D}")
+    assert ctx.eval_count() == ev
+
+
+@pytest.mark.parametrize("name,seed", [("small_320x240", 0), ("small_320x240", 1)])
+def test_full_level_on_scene(name, seed):
+    sc = scenes.make_pair(scenes.SPECS[name], seed)
+    s = sc.spec
+    ctx = make_ctx(s.width, s.height, s.max_disp, 1, s.window, s.radius)
+    ctx.pyramid(dev(sc.left), dev(sc.right))
+    d, c = ctx.match_level(0)
+    do, co, c2, ev = oracle.match_level(sc.left, sc.right, s.window // 2, s.max_disp)
+    ties = compare_level(host(d), host(c), do, co, c2, name)
+    assert ctx.eval_count() == ev
+    assert ties <= 0.001 * do.size
+
+
+@pytest.mark.parametrize("win,r", [(3, 0), (5, 1), (5, 2), (7, 2), (7, 3), (9, 3), (13, 2), (5, 5)])
+def test_restricted_level_with_random_prior(win, r):
+    h, w, D = 45, 150, 40
+    a, b = rand_pair(h, w, win * 10 + r)
+    rng = np.random.default_rng(r)
+    prior = rng.integers(-3, D // 2 + 4, ((h + 1) // 2, (w + 1) // 2)).astype(np.int16)  # some out of range
+    ctx = make_ctx(w, h, D, 2, win, r)
+    ctx.pyramid(dev(a), dev(b))
+    d, c = ctx.match_level(0, dev(prior))
+    do, co, c2, ev = oracle.match_level(a, b, win // 2, D, r, prior)
+    compare_level(host(d), host(c), do, co, c2, f"restricted win={win} r={r}")
+    assert ctx.eval_count() == ev
+
+
+def test_restricted_level_wide_spans_use_global_path():
+    # priors jumping across the whole range make tile spans wider than 256 bytes
+    h, w, D = 24, 600, 512
+    a, b = rand_pair(h, w, 77)
+    rng = np.random.default_rng(5)
+    prior = rng.integers(0, 256, ((h + 1) // 2, (w + 1) // 2)).astype(np.int16)
+    ctx = make_ctx(w, h, D, 2, 7, 2)
+    ctx.pyramid(dev(a), dev(b))
+    d, c = ctx.match_level(0, dev(prior))
+    do, co, c2, ev = oracle.match_level(a, b, 3, D, 2, prior)
+    compare_level(host(d), host(c), do, co, c2, "wide spans")
+    assert ctx.eval_count() == ev
+
+
+@pytest.mark.parametrize("name,seed", [("small_320x240", 0), ("small_320x240", 4)])
+def test_per_level_protocol_with_oracle_priors(name, seed):
+    sc = scenes.make_pair(scenes.SPECS[name], seed)
+    s = sc.spec
+    ref = oracle.disparity(sc.left, sc.right, s.max_disp, s.levels, s.window, s.radius)
+    ctx = make_ctx(s.width, s.height, s.max_disp, s.levels, s.window, s.radius)
+    ctx.pyramid(dev(sc.left), dev(sc.right))
+    for k in range(s.levels - 1, -1, -1):
+        prior = None if k == s.levels - 1 else dev(ref["d"][k + 1])
+        d, c = ctx.match_level(k, prior)
+        compare_level(host(d), host(c), ref["d"][k], ref["C"][k], ref["C2"][k], f"{name} level {k}")
+
+
+@pytest.mark.parametrize("name,seed", [("small_320x240", 0), ("small_320x240", 2)])
+def test_end_to_end_small(name, seed):
+    sc = scenes.make_pair(scenes.SPECS[name], seed)
+    s = sc.spec
+    ref = oracle.disparity(sc.left, sc.right, s.max_disp, s.levels, s.window, s.radius)
+    ctx = make_ctx(s.width, s.height, s.max_disp, s.levels, s.window, s.radius)
+    d, c = ctx.disparity(dev(sc.left), dev(sc.right))
+    ctx.sync()
+    assert ctx.eval_count() > 0
+    d, c = host(d), host(c)
+    # coarsest level: same inputs on both sides, so only counted near-ties may differ
+    dK, cK = ctx.level_result(s.levels - 1)
+    K = s.levels - 1
+    compare_level(host(dK), host(cK), ref["d"][K], ref["C"][K], ref["C2"][K], "coarsest")
+    diff = d != ref["d"][0]
+    # differing pixels are cascades from near-ties at coarser levels: report and bound
+    assert diff.mean() < 0.01, diff.mean()
+    same = ~diff
+    assert np.abs(c[same] - ref["C"][0][same]).max() <= COST_TOL
+    # graph replay, direct launches and the host path agree bit for bit
+    from paper_1901_09593_gb300 import _lib
+    ctx2 = make_ctx(s.width, s.height, s.max_disp, s.levels, s.window, s.radius, _lib.MSBM_FLAG_NO_GRAPH)
+    d2, c2 = ctx2.disparity(dev(sc.left), dev(sc.right))
+    np.testing.assert_array_equal(host(d2), d)
+    np.testing.assert_array_equal(host(c2), c)
+    hd = np.empty_like(d)
+    hc = np.empty(c.shape, np.float32)
+    ctx.disparity_host(sc.left, sc.right, hd, hc)
+    np.testing.assert_array_equal(hd, d)
+    np.testing.assert_array_equal(hc, c)
+
+
+def test_k1_equals_full_level():
+    sc = scenes.make_pair(scenes.SPECS["small_320x240"], 6)
+    s = sc.spec
+    ctx = make_ctx(s.width, s.height, s.max_disp, 1, s.window, s.radius)
+    d, c = ctx.disparity(dev(sc.left), dev(sc.right))
+    ctx.pyramid(dev(sc.left), dev(sc.right))
+    d1, c1 = ctx.match_level(0)
+    np.testing.assert_array_equal(host(d), host(d1))
+    np.testing.assert_array_equal(host(c), host(c1))
+
+
+@pytest.mark.parametrize("h,w,D,K,win,r", [(1, 1, 1, 1, 3, 0), (2, 3, 5, 2, 3, 1), (8, 17, 40, 3, 5, 2),
+                                            (33, 9, 4, 4, 7, 3), (3, 200, 300, 1, 13, 0)])
+def test_edge_sizes_end_to_end(h, w, D, K, win, r):
+    a, b = rand_pair(h, w, h + w + D)
+    ref = oracle.disparity(a, b, D, K, win, r)
+    ctx = make_ctx(w, h, D, K, win, r)
+    d, c = ctx.disparity(dev(a), dev(b))
+    ctx.sync()
+    # compare each level with the oracle given the GPU's own coarser result
+    pa, pb = oracle.pyramid(a, K), oracle.pyramid(b, K)
+    for k in range(K - 1, -1, -1):
+        if k == 0:
+            dk, ck = host(d), host(c)
+        else:
+            tdk, tck = ctx.level_result(k)
+            dk, ck = host(tdk), host(tck)
+        if k == K - 1:
+            do, co, c2, _ = oracle.match_level(pa[k], pb[k], win // 2, oracle.level_disp(D, k))
+        else:
+            prior = host(ctx.level_result(k + 1)[0])
+            do, co, c2, _ = oracle.match_level(pa[k], pb[k], win // 2, oracle.level_disp(D, k), r, prior)
+        compare_level(dk, ck, do, co, c2, f"level {k}")
+    assert ref["evals"] > 0
+
+
+def test_constant_images_score_zero_at_smallest_disparity():
+    a = np.full((20, 40), 120, np.uint8)
+    b = np.full((20, 40), 7, np.uint8)
+    ctx = make_ctx(40, 20, 16, 2, 5, 2)
+    d, c = ctx.disparity(dev(a), dev(b))
+    assert np.all(host(c) == 0.0)
+    assert np.all(host(d) == 0)
+
+
+def test_self_match_is_one_at_zero_disparity():
+    a, _ = rand_pair(30, 64, 9)
+    ctx = make_ctx(64, 30, 16, 1, 7, 2)
+    d, c = ctx.disparity(dev(a), dev(a))
+    c = host(c)
+    assert np.all(np.abs(c - 1.0) <= 1e-6)
+    do, co, c2, _ = oracle.match_level(a, a, 3, 16)
+    compare_level(host(d), c, do, co, c2, "self")
+
+
+def test_forced_timeout_reports_status_and_context_stays_usable():
+    from paper_1901_09593_gb300 import _lib
+    a, b = rand_pair(16, 64, 1)
+    ctx = make_ctx(64, 16, 16, 2, 5, 2, _lib.MSBM_FLAG_TEST_TIMEOUT)
+    ctx.disparity(dev(a), dev(b))
+    with pytest.raises(_lib.MsbmError) as ei:
+        ctx.sync()
+    assert ei.value.status == _lib.MSBM_ERR_TIMEOUT
+    ctx.sync()  # the error was cleared
+    ok = make_ctx(64, 16, 16, 2, 5, 2)
+    d, c = ok.disparity(dev(a), dev(b))
+    ok.sync()
+    ref = oracle.disparity(a, b, 16, 2, 5, 2)
+    assert (host(d) == ref["d"][0]).mean() > 0.99
+
+
+def _sampled_level_check(ctx, pa, pb, k, win, D, r, d_gpu, c_gpu, prior, rng, n=300):
+    """Recompute sampled pixels of level k one by one with the oracle's ZNCC."""
+    h, w = pa[k].shape
+    dk = oracle.level_disp(D, k)
+    ys = rng.integers(0, h, n)
+    xs = rng.integers(0, w, n)
+    # include borders
+    ys[:8] = [0, 0, h - 1, h - 1, 0, h // 2, h - 1, 1]
+    xs[:8] = [0, w - 1, 0, w - 1, w // 2, 0, w // 2, 1]
+    for y, x in zip(ys, xs):
+        zmax = min(dk - 1, x)
+        if prior is None:
+            cands = range(0, zmax + 1)
+        else:
+            dh = min(max(2 * int(prior[y // 2, x // 2]), 0), zmax)
+            cands = range(max(0, dh - r), min(zmax, dh + r) + 1)
+        vals = np.array([oracle.zncc(pa[k], pb[k], win // 2, y, x, z) for z in cands])
+        order = np.argsort(-vals, kind="stable")
+        best = vals[order[0]]
+        second = vals[order[1]] if len(vals) > 1 else -np.inf
+        assert abs(c_gpu[y, x] - best) <= COST_TOL, (k, y, x)
+        if best - second >= TIE_TOL:
+            assert d_gpu[y, x] == list(cands)[order[0]], (k, y, x)
+
+
+@pytest.mark.parametrize("name", ["bench_1400x1000", "large_2880x1984"])
+def test_full_size_hierarchical_sampled(name):
+    sc = scenes.make_pair(scenes.SPECS[name], 0)
+    s = sc.spec
+    ctx = make_ctx(s.width, s.height, s.max_disp, s.levels, s.window, s.radius)
+    d, c = ctx.disparity(dev(sc.left), dev(sc.right))
+    ctx.sync()
+    pa, pb = oracle.pyramid(sc.left, s.levels), oracle.pyramid(sc.right, s.levels)
+    rng = np.random.default_rng(0)
+    for k in range(s.levels - 1, -1, -1):
+        if k == 0:
+            dk, ck = host(d), host(c)
+        else:
+            tdk, tck = ctx.level_result(k)
+            dk, ck = host(tdk), host(tck)
+        prior = None if k == s.levels - 1 else host(ctx.level_result(k + 1)[0])
+        _sampled_level_check(ctx, pa, pb, k, s.window, s.max_disp, s.radius, dk, ck, prior, rng,
+                             n=200 if prior is None else 400)
+    # the hierarchical result is a good disparity map on this scene
+    bad = scenes.bad_rate(host(d), sc.gt, sc.mask, 1.0)
+    assert bad < 0.2, bad
+
+
+def test_full_size_flat_sampled():
+    sc = scenes.make_pair(scenes.SPECS["bench_1400x1000"], 0)
+    s = sc.spec
+    ctx = make_ctx(s.width, s.height, s.max_disp, 1, s.window, s.radius)
+    d, c = ctx.disparity(dev(sc.left), dev(sc.right))
+    ctx.sync()
+    pa, pb = [sc.left], [sc.right]
+    _sampled_level_check(ctx, pa, pb, 0, s.window, s.max_disp, s.radius, host(d), host(c), None,
+                         np.random.default_rng(1), n=120)
+    n = s.width * s.height
+    assert ctx.eval_count() == sum(min(s.max_disp - 1, x) + 1 for x in range(s.width)) * s.height
+    assert n > 0
