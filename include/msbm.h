@@ -139,6 +139,41 @@ msbm_status msbm_sync(msbm_ctx *ctx);
  * reset != 0 (synchronises the stream). */
 msbm_status msbm_eval_count(msbm_ctx *ctx, int64_t *count, int32_t reset);
 
+/* ---------------------------------------------------------------------------------------
+ * Allocation-free flat matching.  The paper has no counterpart: this is a deployment aid.
+ *
+ * Some callers cannot call cudaMalloc: cudaMalloc and cudaFree may synchronise the whole
+ * device, which a real-time loop sharing the GPU with other streams cannot afford while a
+ * frame is in flight, and some host frameworks own all device memory through their own
+ * pool and forbid allocations made outside it.  For them this entry point runs flat
+ * full-range block matching (the K = 1 case of msbm_disparity: every admissible candidate
+ * 0 <= z <= min(max_disp - 1, x), winner-take-all, ties to the smallest z) without
+ * allocating: it calls no cudaMalloc, cudaFree or other allocating routine.  Its scratch
+ * (two replicated-apron image buffers and a status word) is a fixed device array of
+ * MSBM_NOALLOC_SCRATCH_BYTES compiled into the library; every GPU that loads this part of
+ * the library keeps that array until the process exits.
+ *   d_left, d_right : device images, width x height, row pitch pitch_bytes (>= width).
+ *   d_out           : device int16 map, width x height, dense.          (written)
+ *   cost_out        : device float map, width x height, dense, or NULL. (written)
+ *   d_status        : device int32, or NULL.  Set to 0 on the stream before the kernels
+ *                     run; a device wait that gave up leaves MSBM_ERR_TIMEOUT there.
+ *   cuda_stream     : cudaStream_t the work is enqueued on (asynchronous).
+ * Sizes: width, height 1..16384, max_disp 1..4096, window odd 3..13.  A size whose two
+ * apron buffers, (round_up(width + 32, 128) * (height + 16) bytes each, rounded up to 256)
+ * plus 256 bytes, exceed MSBM_NOALLOC_SCRATCH_BYTES returns MSBM_ERR_UNSUPPORTED before
+ * any work is enqueued (2880 x 1984 fits; 4096 x 2160 does not).
+ * The first call on each device resolves the array's device address with
+ * cudaGetSymbolAddress (with that device current) and sets kernel attributes; make that
+ * first call outside any stream capture.  All calls share the one array and it keeps the
+ * last call's contents: calls whose work overlaps on the GPU (on different streams, or
+ * from different host threads without ordering) race on it and must be serialised by the
+ * caller. */
+#define MSBM_NOALLOC_SCRATCH_BYTES (16 << 20)
+msbm_status msbm_flat_disparity_noalloc(const uint8_t *d_left, const uint8_t *d_right,
+                                        size_t pitch_bytes, int32_t width, int32_t height,
+                                        int32_t max_disp, int32_t window, int16_t *d_out,
+                                        float *cost_out, int32_t *d_status, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif
