@@ -140,6 +140,40 @@ msbm_status msbm_sync(msbm_ctx *ctx);
 msbm_status msbm_eval_count(msbm_ctx *ctx, int64_t *count, int32_t reset);
 
 /* ---------------------------------------------------------------------------------------
+ * Differentiable level: soft-argmax readout of a ZNCC cost volume (Eq. 2 on float images).
+ * For each pixel of each image of a batch (B x H x W, float32, dense, row-major):
+ *   rho_z = sum ac*bc / sqrt((sum ac^2 + eps)(sum bc^2 + eps)) over the (2n+1)^2 window
+ *           (ac, bc centred on their window means, clamp-to-edge reads), for the admissible
+ *           candidates 0 <= z <= min(ndisp - 1, x);
+ *   p_z    = softmax_z(rho_z / temperature);   d_soft = sum_z z p_z.
+ * The cost volume is never stored.  window: odd 3..9; ndisp 1..256 with batch * ndisp
+ * <= 65535; temperature > 0;
+ * eps >= 0 (1e-6 * window^2 is the default used by the Python binding).
+ * Forward writes d_soft, and the softmax statistics m_out (max of rho_z * log2(e) / T) and
+ * l_out (sum of 2^(rho_z log2(e)/T - m)) that the backward reuses. */
+msbm_status msbm_zncc_softargmax_fwd(const float *d_left, const float *d_right, int32_t batch,
+                                     int32_t height, int32_t width, int32_t window, int32_t ndisp,
+                                     float temperature, float eps, float *d_soft, float *m_out,
+                                     float *l_out, void *cuda_stream);
+
+/* Bytes of device workspace msbm_zncc_softargmax_bwd needs (0 for invalid sizes): the
+ * per-(pixel, z) coefficient volume, its box-filtered copy and six per-pixel arrays. */
+size_t msbm_zncc_softargmax_workspace_bytes(int32_t batch, int32_t height, int32_t width,
+                                            int32_t window, int32_t ndisp);
+
+/* Backward of msbm_zncc_softargmax_fwd: given g_d = dLoss/dd_soft, writes g_left and
+ * g_right (dLoss/dLeft, dLoss/dRight, same layout as the images; overwritten).  The window
+ * statistics and rho are recomputed, not read from the forward.  workspace: caller-owned
+ * device memory of at least msbm_zncc_softargmax_workspace_bytes, 256-byte aligned
+ * (MSBM_ERR_ALIGNMENT otherwise).  Asynchronous on cuda_stream. */
+msbm_status msbm_zncc_softargmax_bwd(const float *d_left, const float *d_right, int32_t batch,
+                                     int32_t height, int32_t width, int32_t window, int32_t ndisp,
+                                     float temperature, float eps, const float *d_soft,
+                                     const float *m_in, const float *l_in, const float *g_d,
+                                     float *g_left, float *g_right, void *workspace,
+                                     size_t workspace_bytes, void *cuda_stream);
+
+/* ---------------------------------------------------------------------------------------
  * Allocation-free flat matching.  The paper has no counterpart: this is a deployment aid.
  *
  * Some callers cannot call cudaMalloc: cudaMalloc and cudaFree may synchronise the whole

@@ -50,6 +50,13 @@ SIGNATURES = {
                                 P(ctypes.c_float), c_int32], ctypes.c_int),
     "msbm_sync": ([c_void_p], ctypes.c_int),
     "msbm_eval_count": ([c_void_p, P(ctypes.c_int64), c_int32], ctypes.c_int),
+    "msbm_zncc_softargmax_fwd": ([c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_int32,
+                                  ctypes.c_float, ctypes.c_float, c_void_p, c_void_p, c_void_p, c_void_p],
+                                 ctypes.c_int),
+    "msbm_zncc_softargmax_workspace_bytes": ([c_int32, c_int32, c_int32, c_int32, c_int32], c_size_t),
+    "msbm_zncc_softargmax_bwd": ([c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_int32,
+                                  ctypes.c_float, ctypes.c_float, c_void_p, c_void_p, c_void_p, c_void_p,
+                                  c_void_p, c_void_p, c_void_p, c_size_t, c_void_p], ctypes.c_int),
     "msbm_flat_disparity_noalloc": ([c_void_p, c_void_p, c_size_t, c_int32, c_int32, c_int32, c_int32,
                                      c_void_p, c_void_p, c_void_p, c_void_p], ctypes.c_int),
 }

@@ -1,0 +1,468 @@
+// softargmax.cu -- differentiable ZNCC level: soft-argmax disparity readout over a level's
+// cost volume and its backward with respect to both images.  The paper's ZNCC (Eq. 2) on
+// float images, with an epsilon-regularised denominator,
+//     rho(p, z) = sum ac*bc / sqrt((sum ac^2 + eps)(sum bc^2 + eps)),   ac = a - mean(a)
+// over candidates 0 <= z <= min(ndisp - 1, x); p_z = softmax_z(rho / T);
+// d_soft = sum_z z p_z.  This stands beside the hard winner-take-all of the method
+// (Sec. III-A, Eq. 3) as a differentiable readout; the cost volume is never stored.
+//
+// Forward (one thread per pixel, 32 x 8 pixels per CTA): both images' tiles are staged in
+// shared memory (clamp-to-edge); right-window means and rsqrt(sum bc^2 + eps) are computed
+// per CTA two-pass; the left window is centred in registers (two-pass); per candidate the
+// right window slides one column (a (2n+1) x (2n+1) register window used cyclically, so one
+// new column is loaded per candidate); the softmax is accumulated online in base 2.  Saved:
+// d_soft and the softmax max m and sum l per pixel.
+//
+// Backward.  With g = dLoss/dd_soft, g_rho = g p_z (z - d_soft) / T and s = the denominator,
+// the derivative of rho through the centred windows (the mean terms cancel because centred
+// entries sum to zero) gives, for every image position q of the clamp-extended images,
+//   gL(q)  = sum_z R(q - z) A_z(q) - box(zeta)(q) - L(q) box(beta)(q) + box(beta*ma)(q)
+//   gR(q') = sum_z L(q' + z) A_z(q' + z) - box(er)(q') - R(q') box(delta)(q') + box(delta*mb)(q')
+// where A_z = box filter over the window of alpha(p, z) = g_rho / s, and per pixel / right
+// centre r:  beta(p) = sum_z g_rho rho / (Saa + eps),  zeta(p) = sum_z alpha mb(p - z),
+// delta(r) = sum_z g_rho rho / (Sbb + eps) and er(r) = sum_z alpha ma at p = r + z.
+// Positions outside the image are folded into the clamped edge pixel.  Four kernels:
+// coefficients (recomputes rho and the window statistics), the box filter of the alpha
+// volume, and the two gathers.  Everything is FP32.
+#include <math.h>
+
+#include "msbm.h"
+#include "msbm_device.cuh"
+#include "msbm_internal.h"
+
+namespace msbm {
+
+namespace {
+
+constexpr int SA_TX = 32, SA_TY = 8;
+constexpr float LOG2E = 1.4426950408889634f;
+
+struct SaArgs {
+    const float *L, *R;
+    int B, H, W, ndisp;
+    float invT2;    // log2(e) / T
+    float invT;     // 1 / T
+    float eps;
+    // forward outputs / backward inputs
+    float *dsoft, *m2, *l;
+    // backward
+    const float *g;
+    float *alpha;   // [B][Z][H][W]
+    float *zeta, *beta, *ma, *mb, *delta, *er;   // [B][H][W]
+};
+
+template <int NH>
+struct SaCfg {
+    static constexpr int WIN = 2 * NH + 1;
+    static constexpr int N = WIN * WIN;
+    static constexpr int ROWS = SA_TY + 2 * NH;
+    static constexpr int LTP = SA_TX + 2 * NH;
+};
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// Stage the left tile, the right span and the right-window statistics of one CTA.
+// Layout: Lt[ROWS][LTP], Rt[ROWS][RTP], st[TY][RSW] (float2 {mean, rsqrt(Sbb + eps)}).
+template <int NH>
+__device__ void sa_stage(const SaArgs &a, const float *L, const float *R, int x0, int y0, float *Lt, float *Rt,
+                         float2 *st, int RTP, int RSW) {
+    using C = SaCfg<NH>;
+    const int tid = threadIdx.y * SA_TX + threadIdx.x, nthr = SA_TX * SA_TY;
+    const int W = a.W, H = a.H;
+    for (int i = tid; i < C::ROWS * C::LTP; i += nthr) {
+        int t = i / C::LTP, u = i - t * C::LTP;
+        int yy = clampi(y0 - NH + t, 0, H - 1), xx = clampi(x0 - NH + u, 0, W - 1);
+        Lt[i] = L[(size_t)yy * W + xx];
+    }
+    const int rx0 = x0 - (a.ndisp - 1) - NH;   // image column of Rt column 0
+    for (int i = tid; i < C::ROWS * RTP; i += nthr) {
+        int t = i / RTP, u = i - t * RTP;
+        int yy = clampi(y0 - NH + t, 0, H - 1), xx = clampi(rx0 + u, 0, W - 1);
+        Rt[i] = R[(size_t)yy * W + xx];
+    }
+    __syncthreads();
+    // right centre v <-> image column x0 - (ndisp-1) + v; its window is Rt cols v .. v+2n
+    for (int i = tid; i < SA_TY * RSW; i += nthr) {
+        int ry = i / RSW, v = i - ry * RSW;
+        float s = 0.f;
+#pragma unroll
+        for (int t = 0; t < C::WIN; ++t)
+#pragma unroll
+            for (int j = 0; j < C::WIN; ++j) s += Rt[(ry + t) * RTP + v + j];
+        const float mean = s * (1.0f / C::N);
+        float q = 0.f;
+#pragma unroll
+        for (int t = 0; t < C::WIN; ++t)
+#pragma unroll
+            for (int j = 0; j < C::WIN; ++j) {
+                float d = Rt[(ry + t) * RTP + v + j] - mean;
+                q = fmaf(d, d, q);
+            }
+        st[i] = make_float2(mean, rsqrtf(q + a.eps));
+    }
+    __syncthreads();
+}
+
+// Per-pixel ZNCC over all admissible candidates, calling visit(z, rho, v2, mb, rsb) for each.
+template <int NH, typename F>
+__device__ __forceinline__ void sa_scan(const SaArgs &a, const float *Lt, const float *Rt, const float2 *st,
+                                        int RTP, int RSW, int tx, int ty, int x, float &ma_out, float &rsa_out,
+                                        F &&visit) {
+    using C = SaCfg<NH>;
+    constexpr int WIN = C::WIN;
+    float ac[WIN][WIN];
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < WIN; ++i)
+#pragma unroll
+        for (int j = 0; j < WIN; ++j) {
+            ac[i][j] = Lt[(ty + i) * C::LTP + tx + j];
+            s += ac[i][j];
+        }
+    const float ma = s * (1.0f / C::N);
+    float saa = 0.f, sac = 0.f;
+#pragma unroll
+    for (int i = 0; i < WIN; ++i)
+#pragma unroll
+        for (int j = 0; j < WIN; ++j) {
+            ac[i][j] -= ma;
+            saa = fmaf(ac[i][j], ac[i][j], saa);
+            sac += ac[i][j];
+        }
+    const float rsa = rsqrtf(saa + a.eps);
+    ma_out = ma;
+    rsa_out = rsa;
+    const int zmax = min(a.ndisp - 1, x);
+    // Rt column of image column (x - n - z) is tx + ndisp - 1 - z
+    const int cb = tx + a.ndisp - 1;
+    float rw[WIN][WIN];
+#pragma unroll
+    for (int i = 0; i < WIN; ++i)
+#pragma unroll
+        for (int j = 0; j < WIN; ++j) rw[i][j] = Rt[(ty + i) * RTP + cb + j];
+    for (int z0 = 0; z0 <= zmax; z0 += WIN) {
+#pragma unroll
+        for (int zz = 0; zz < WIN; ++zz) {
+            const int z = z0 + zz;
+            if (z > zmax) break;
+            if (z > 0) {
+                // new logical column 0 (image column x - z - n) goes into the slot of the
+                // column that just left the window; logical column j lives in slot
+                // (j - zz) mod WIN, so the indices below are compile-time constants
+#pragma unroll
+                for (int i = 0; i < WIN; ++i) rw[i][(WIN - zz) % WIN] = Rt[(ty + i) * RTP + cb - z];
+            }
+            float sab = 0.f;
+#pragma unroll
+            for (int i = 0; i < WIN; ++i)
+#pragma unroll
+                for (int j = 0; j < WIN; ++j) sab = fmaf(ac[i][j], rw[i][(j - zz + WIN) % WIN], sab);
+            const float2 q = st[ty * RSW + cb - z];   // statistics of the right centre x - z
+            // sum ac*(b - mb) = sum ac*b - mb * sum ac (sum ac is the centring residual)
+            const float rho = (sab - q.x * sac) * rsa * q.y;
+            visit(z, rho, rho * a.invT2, q.x, q.y);
+        }
+    }
+}
+
+template <int NH>
+__global__ void __launch_bounds__(256) sa_fwd_kernel(const SaArgs a) {
+    using C = SaCfg<NH>;
+    extern __shared__ float sm[];
+    const int RTP = SA_TX + a.ndisp - 1 + 2 * NH, RSW = SA_TX + a.ndisp - 1;
+    float *Lt = sm;
+    float *Rt = Lt + C::ROWS * C::LTP;
+    float2 *st = reinterpret_cast<float2 *>(Rt + ((C::ROWS * RTP + 1) & ~1));
+    const int b = blockIdx.z, x0 = blockIdx.x * SA_TX, y0 = blockIdx.y * SA_TY;
+    const size_t plane = (size_t)a.H * a.W;
+    sa_stage<NH>(a, a.L + b * plane, a.R + b * plane, x0, y0, Lt, Rt, st, RTP, RSW);
+    const int tx = threadIdx.x, ty = threadIdx.y, x = x0 + tx, y = y0 + ty;
+    if (x >= a.W || y >= a.H) return;
+    float m2 = -INFINITY, l = 0.f, s = 0.f, ma, rsa;
+    sa_scan<NH>(a, Lt, Rt, st, RTP, RSW, tx, ty, x, ma, rsa, [&](int z, float, float v2, float, float) {
+        if (v2 > m2) {
+            const float sc = exp2f(m2 - v2);
+            l = fmaf(l, sc, 1.f);
+            s = fmaf(s, sc, static_cast<float>(z));
+            m2 = v2;
+        } else {
+            const float e = exp2f(v2 - m2);
+            l += e;
+            s = fmaf(static_cast<float>(z), e, s);
+        }
+    });
+    const size_t p = b * plane + (size_t)y * a.W + x;
+    a.dsoft[p] = s / l;
+    a.m2[p] = m2;
+    a.l[p] = l;
+}
+
+template <int NH>
+__global__ void __launch_bounds__(256) sa_bwd_coef_kernel(const SaArgs a) {
+    using C = SaCfg<NH>;
+    extern __shared__ float sm[];
+    const int RTP = SA_TX + a.ndisp - 1 + 2 * NH, RSW = SA_TX + a.ndisp - 1;
+    float *Lt = sm;
+    float *Rt = Lt + C::ROWS * C::LTP;
+    float2 *st = reinterpret_cast<float2 *>(Rt + ((C::ROWS * RTP + 1) & ~1));
+    float *accD = reinterpret_cast<float *>(st + SA_TY * RSW);
+    float *accE = accD + SA_TY * RSW;
+    const int b = blockIdx.z, x0 = blockIdx.x * SA_TX, y0 = blockIdx.y * SA_TY;
+    const size_t plane = (size_t)a.H * a.W;
+    const int tid = threadIdx.y * SA_TX + threadIdx.x;
+    for (int i = tid; i < 2 * SA_TY * RSW; i += SA_TX * SA_TY) accD[i] = 0.f;
+    sa_stage<NH>(a, a.L + b * plane, a.R + b * plane, x0, y0, Lt, Rt, st, RTP, RSW);
+    const int tx = threadIdx.x, ty = threadIdx.y, x = x0 + tx, y = y0 + ty;
+    if (x < a.W && y < a.H) {
+        const size_t p = b * plane + (size_t)y * a.W + x;
+        const float g = a.g[p], d = a.dsoft[p], m2 = a.m2[p], invl = 1.f / a.l[p];
+        float beta = 0.f, zeta = 0.f, ma = 0.f, rsa = 0.f;
+        float *alpha = a.alpha + (size_t)b * a.ndisp * plane + (size_t)y * a.W + x;
+        float *accDrow = accD + ty * RSW + tx + a.ndisp - 1;   // right centre x - z at [-z]
+        float *accErow = accE + ty * RSW + tx + a.ndisp - 1;
+        int zmax = -1;   // ma and rsa are set by sa_scan before its first callback
+        sa_scan<NH>(a, Lt, Rt, st, RTP, RSW, tx, ty, x, ma, rsa, [&](int z, float rho, float v2, float mb, float rsb) {
+            const float pz = exp2f(v2 - m2) * invl;
+            const float grho = g * pz * (static_cast<float>(z) - d) * a.invT;
+            const float al = grho * rsa * rsb;
+            beta = fmaf(grho * rho, rsa * rsa, beta);
+            zeta = fmaf(al, mb, zeta);
+            atomicAdd(accDrow - z, grho * rho * rsb * rsb);
+            atomicAdd(accErow - z, al * ma);
+            alpha[(size_t)z * plane] = al;
+            zmax = z;
+        });
+        for (int z = zmax + 1; z < a.ndisp; ++z) alpha[(size_t)z * plane] = 0.f;
+        a.beta[p] = beta;
+        a.zeta[p] = zeta;
+        a.ma[p] = ma;
+        a.mb[p] = st[ty * RSW + tx + a.ndisp - 1].x;   // right centre x (z = 0)
+    }
+    __syncthreads();
+    // flush the right-centre accumulators: centre v <-> image column x0 - (ndisp-1) + v
+    float *delta = a.delta + b * plane, *er = a.er + b * plane;
+    for (int i = tid; i < SA_TY * RSW; i += SA_TX * SA_TY) {
+        int ry = i / RSW, v = i - ry * RSW;
+        int yy = y0 + ry, xx = x0 - (a.ndisp - 1) + v;
+        if (yy >= a.H || xx < 0 || xx >= a.W) continue;
+        if (accD[i] != 0.f) atomicAdd(delta + (size_t)yy * a.W + xx, accD[i]);
+        if (accE[i] != 0.f) atomicAdd(er + (size_t)yy * a.W + xx, accE[i]);
+    }
+}
+
+// A_z over the clamp-extended domain: A[b][z][Y][X], Y in [0, H+2n), X in [0, W+2n), the
+// sum of alpha(b, z) over the (2n+1)^2 image pixels around (Y-n, X-n) (zero outside).
+template <int NH>
+__global__ void __launch_bounds__(256) sa_box_kernel(const SaArgs a, float *A) {
+    constexpr int WIN = 2 * NH + 1;
+    __shared__ float tile[SA_TY + 2 * NH][SA_TX + 2 * NH];
+    __shared__ float hs[SA_TY + 2 * NH][SA_TX];
+    const int bz = blockIdx.z;                       // b * ndisp + z
+    const int Wp = a.W + 2 * NH, Hp = a.H + 2 * NH;
+    const int X0 = blockIdx.x * SA_TX, Y0 = blockIdx.y * SA_TY;
+    const float *al = a.alpha + (size_t)bz * a.H * a.W;
+    const int tid = threadIdx.y * SA_TX + threadIdx.x;
+    for (int i = tid; i < (SA_TY + 2 * NH) * (SA_TX + 2 * NH); i += SA_TX * SA_TY) {
+        int t = i / (SA_TX + 2 * NH), u = i - t * (SA_TX + 2 * NH);
+        // tile (t, u) <-> image (Y0 - 2n + t, X0 - 2n + u)
+        int yy = Y0 - 2 * NH + t, xx = X0 - 2 * NH + u;
+        tile[t][u] = (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W) ? al[(size_t)yy * a.W + xx] : 0.f;
+    }
+    __syncthreads();
+    for (int i = tid; i < (SA_TY + 2 * NH) * SA_TX; i += SA_TX * SA_TY) {
+        int t = i / SA_TX, u = i - t * SA_TX;
+        float s = 0.f;
+#pragma unroll
+        for (int j = 0; j < WIN; ++j) s += tile[t][u + j];
+        hs[t][u] = s;
+    }
+    __syncthreads();
+    const int X = X0 + threadIdx.x, Y = Y0 + threadIdx.y;
+    if (X >= Wp || Y >= Hp) return;
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < WIN; ++i) s += hs[threadIdx.y + i][threadIdx.x];
+    A[(size_t)bz * Hp * Wp + (size_t)Y * Wp + X] = s;
+}
+
+// Gathers over the clamp-extended domain, folded into the edge pixel by atomicAdd.
+template <int NH, bool LEFT>
+__global__ void __launch_bounds__(256) sa_grad_kernel(const SaArgs a, const float *A, float *gout) {
+    constexpr int WIN = 2 * NH + 1;
+    const int b = blockIdx.z;
+    const int Wp = a.W + 2 * NH, Hp = a.H + 2 * NH;
+    const int X = blockIdx.x * SA_TX + threadIdx.x, Y = blockIdx.y * SA_TY + threadIdx.y;
+    if (X >= Wp || Y >= Hp) return;
+    const int qy = Y - NH, qx = X - NH;                  // image coordinates (may lie outside)
+    const size_t plane = (size_t)a.H * a.W;
+    const int cy = clampi(qy, 0, a.H - 1);
+    const float *Lb = a.L + b * plane, *Rb = a.R + b * plane;
+    const float *Ab = A + (size_t)b * a.ndisp * Hp * Wp + (size_t)Y * Wp;
+    float val = 0.f;
+    if (LEFT) {
+        const int zm = min(a.ndisp - 1, qx + NH);
+        for (int z = 0; z <= zm; ++z)
+            val = fmaf(Rb[(size_t)cy * a.W + clampi(qx - z, 0, a.W - 1)], Ab[(size_t)z * Hp * Wp + X], val);
+    } else {
+        for (int z = 0; z < a.ndisp; ++z) {
+            const int xx = X + z;                       // extended column of q' + z
+            if (xx >= Wp) break;
+            val = fmaf(Lb[(size_t)cy * a.W + clampi(qx + z, 0, a.W - 1)], Ab[(size_t)z * Hp * Wp + xx], val);
+        }
+    }
+    // box sums over the image pixels whose window covers q
+    const float *s1 = (LEFT ? a.zeta : a.er) + b * plane;
+    const float *s2 = (LEFT ? a.beta : a.delta) + b * plane;
+    const float *mm = (LEFT ? a.ma : a.mb) + b * plane;
+    float b1 = 0.f, b2 = 0.f, b3 = 0.f;
+    for (int i = -NH; i <= NH; ++i) {
+        const int yy = qy + i;
+        if (yy < 0 || yy >= a.H) continue;
+        for (int j = -NH; j <= NH; ++j) {
+            const int xx = qx + j;
+            if (xx < 0 || xx >= a.W) continue;
+            const size_t o = (size_t)yy * a.W + xx;
+            b1 += s1[o];
+            b2 += s2[o];
+            b3 = fmaf(s2[o], mm[o], b3);
+        }
+    }
+    const float own = (LEFT ? Lb : Rb)[(size_t)cy * a.W + clampi(qx, 0, a.W - 1)];
+    val += b3 - b1 - own * b2;
+    atomicAdd(gout + b * plane + (size_t)cy * a.W + clampi(qx, 0, a.W - 1), val);
+}
+
+size_t sa_fwd_smem(int nh, int ndisp, bool bwd) {
+    const int rows = SA_TY + 2 * nh, ltp = SA_TX + 2 * nh;
+    const int rtp = SA_TX + ndisp - 1 + 2 * nh, rsw = SA_TX + ndisp - 1;
+    size_t f = (size_t)rows * ltp + (((size_t)rows * rtp + 1) & ~(size_t)1) + 2 * (size_t)SA_TY * rsw;
+    if (bwd) f += 2 * (size_t)SA_TY * rsw;
+    return f * sizeof(float);
+}
+
+template <int NH>
+cudaError_t sa_run(const SaArgs &a, bool bwd, float *A, float *gL, float *gR, cudaStream_t st) {
+    dim3 blk(SA_TX, SA_TY);
+    dim3 grd((a.W + SA_TX - 1) / SA_TX, (a.H + SA_TY - 1) / SA_TY, a.B);
+    size_t smem = sa_fwd_smem(NH, a.ndisp, bwd);
+    cudaError_t e;
+    if (!bwd) {
+        e = cudaFuncSetAttribute(sa_fwd_kernel<NH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        sa_fwd_kernel<NH><<<grd, blk, smem, st>>>(a);
+        return cudaGetLastError();
+    }
+    e = cudaFuncSetAttribute(sa_bwd_coef_kernel<NH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    sa_bwd_coef_kernel<NH><<<grd, blk, smem, st>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int Wp = a.W + 2 * NH, Hp = a.H + 2 * NH;
+    dim3 gbox((Wp + SA_TX - 1) / SA_TX, (Hp + SA_TY - 1) / SA_TY, a.B * a.ndisp);
+    sa_box_kernel<NH><<<gbox, blk, 0, st>>>(a, A);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    dim3 gext((Wp + SA_TX - 1) / SA_TX, (Hp + SA_TY - 1) / SA_TY, a.B);
+    sa_grad_kernel<NH, true><<<gext, blk, 0, st>>>(a, A, gL);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    sa_grad_kernel<NH, false><<<gext, blk, 0, st>>>(a, A, gR);
+    return cudaGetLastError();
+}
+
+cudaError_t sa_dispatch(int nh, const SaArgs &a, bool bwd, float *A, float *gL, float *gR, cudaStream_t st) {
+    switch (nh) {
+        case 1: return sa_run<1>(a, bwd, A, gL, gR, st);
+        case 2: return sa_run<2>(a, bwd, A, gL, gR, st);
+        case 3: return sa_run<3>(a, bwd, A, gL, gR, st);
+        case 4: return sa_run<4>(a, bwd, A, gL, gR, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+msbm_status sa_validate(const float *L, const float *R, int B, int H, int W, int window, int ndisp, float T,
+                        float eps) {
+    if (!L || !R) return MSBM_ERR_INVALID_ARG;
+    if (B < 1 || B > 65535 || H < 1 || H > 16384 || W < 1 || W > 16384) return MSBM_ERR_INVALID_ARG;
+    if (window < 3 || window > 9 || (window & 1) == 0) return MSBM_ERR_INVALID_ARG;
+    if (ndisp < 1 || ndisp > 256) return MSBM_ERR_INVALID_ARG;
+    if ((long)B * ndisp > 65535) return MSBM_ERR_INVALID_ARG;   // box-filter grid z extent
+    if (!(T > 0.f) || !(eps >= 0.f) || !isfinite(T) || !isfinite(eps)) return MSBM_ERR_INVALID_ARG;
+    return MSBM_OK;
+}
+
+struct SaWorkspace {
+    size_t alpha, A, arrays, total;
+};
+
+SaWorkspace sa_workspace(int B, int H, int W, int window, int ndisp) {
+    const int nh = window / 2;
+    SaWorkspace w;
+    auto al = [](size_t v) { return (v + 255) / 256 * 256; };
+    w.alpha = al((size_t)B * ndisp * H * W * sizeof(float));
+    w.A = al((size_t)B * ndisp * (H + 2 * nh) * (W + 2 * nh) * sizeof(float));
+    w.arrays = al((size_t)B * H * W * sizeof(float));
+    w.total = w.alpha + w.A + 6 * w.arrays;
+    return w;
+}
+
+}  // namespace
+
+}  // namespace msbm
+
+using namespace msbm;
+
+extern "C" {
+
+msbm_status msbm_zncc_softargmax_fwd(const float *d_left, const float *d_right, int32_t batch, int32_t height,
+                                     int32_t width, int32_t window, int32_t ndisp, float temperature, float eps,
+                                     float *d_soft, float *m_out, float *l_out, void *cuda_stream) {
+    msbm_status s = sa_validate(d_left, d_right, batch, height, width, window, ndisp, temperature, eps);
+    if (s != MSBM_OK) return s;
+    if (!d_soft || !m_out || !l_out) return MSBM_ERR_INVALID_ARG;
+    SaArgs a = {};
+    a.L = d_left; a.R = d_right;
+    a.B = batch; a.H = height; a.W = width; a.ndisp = ndisp;
+    a.invT2 = LOG2E / temperature; a.invT = 1.f / temperature; a.eps = eps;
+    a.dsoft = d_soft; a.m2 = m_out; a.l = l_out;
+    cudaError_t e = sa_dispatch(window / 2, a, false, nullptr, nullptr, nullptr, static_cast<cudaStream_t>(cuda_stream));
+    return e == cudaSuccess ? MSBM_OK : MSBM_ERR_CUDA;
+}
+
+size_t msbm_zncc_softargmax_workspace_bytes(int32_t batch, int32_t height, int32_t width, int32_t window,
+                                            int32_t ndisp) {
+    if (batch < 1 || height < 1 || width < 1 || window < 3 || ndisp < 1) return 0;
+    return sa_workspace(batch, height, width, window, ndisp).total;
+}
+
+msbm_status msbm_zncc_softargmax_bwd(const float *d_left, const float *d_right, int32_t batch, int32_t height,
+                                     int32_t width, int32_t window, int32_t ndisp, float temperature, float eps,
+                                     const float *d_soft, const float *m_in, const float *l_in, const float *g_d,
+                                     float *g_left, float *g_right, void *workspace, size_t workspace_bytes,
+                                     void *cuda_stream) {
+    msbm_status s = sa_validate(d_left, d_right, batch, height, width, window, ndisp, temperature, eps);
+    if (s != MSBM_OK) return s;
+    if (!d_soft || !m_in || !l_in || !g_d || !g_left || !g_right || !workspace) return MSBM_ERR_INVALID_ARG;
+    SaWorkspace w = sa_workspace(batch, height, width, window, ndisp);
+    if (workspace_bytes < w.total) return MSBM_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return MSBM_ERR_ALIGNMENT;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    uint8_t *ws = static_cast<uint8_t *>(workspace);
+    SaArgs a = {};
+    a.L = d_left; a.R = d_right;
+    a.B = batch; a.H = height; a.W = width; a.ndisp = ndisp;
+    a.invT2 = LOG2E / temperature; a.invT = 1.f / temperature; a.eps = eps;
+    a.dsoft = const_cast<float *>(d_soft); a.m2 = const_cast<float *>(m_in); a.l = const_cast<float *>(l_in);
+    a.g = g_d;
+    a.alpha = reinterpret_cast<float *>(ws);
+    float *A = reinterpret_cast<float *>(ws + w.alpha);
+    float *arr = reinterpret_cast<float *>(ws + w.alpha + w.A);
+    const size_t na = w.arrays / sizeof(float);
+    a.zeta = arr; a.beta = arr + na; a.ma = arr + 2 * na; a.mb = arr + 3 * na; a.delta = arr + 4 * na;
+    a.er = arr + 5 * na;
+    const size_t plane_bytes = (size_t)batch * height * width * sizeof(float);
+    cudaError_t e = cudaMemsetAsync(a.delta, 0, 2 * w.arrays, st);   // delta and er accumulate
+    if (e == cudaSuccess) e = cudaMemsetAsync(g_left, 0, plane_bytes, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g_right, 0, plane_bytes, st);
+    if (e == cudaSuccess) e = sa_dispatch(window / 2, a, true, A, g_left, g_right, st);
+    return e == cudaSuccess ? MSBM_OK : MSBM_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,132 @@
+"""Differentiable ZNCC level: soft-argmax disparity with a hand-written backward.
+
+``ZnccSoftArgmax.apply(left, right, window, ndisp, temperature, eps)`` maps float32 image
+batches (B, H, W) on the GPU to d_soft (B, H, W).  Forward and backward run in libmsbm's
+kernels (msbm_zncc_softargmax_fwd / _bwd); the backward recomputes the window statistics
+and the costs instead of storing the cost volume.
+"""
+from __future__ import annotations
+
+import ctypes
+
+from . import _lib
+
+
+def _p(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def default_eps(window: int) -> float:
+    return 1e-6 * window * window
+
+
+def _check(t, name):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32:
+        raise TypeError(f"{name} must be a CUDA float32 tensor")
+    if t.dim() != 3 or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous (B, H, W) tensor")
+
+
+def forward_raw(left, right, window: int, ndisp: int, temperature: float, eps: float):
+    """Returns (d_soft, m, l)."""
+    torch = _torch()
+    _check(left, "left")
+    _check(right, "right")
+    if left.shape != right.shape:
+        raise ValueError("left and right must have the same shape")
+    lib = _lib.load()
+    b, h, w = left.shape
+    d = torch.empty_like(left)
+    m = torch.empty_like(left)
+    l = torch.empty_like(left)
+    st = torch.cuda.current_stream(left.device).cuda_stream
+    _lib.check(lib.msbm_zncc_softargmax_fwd(_p(left), _p(right), b, h, w, window, ndisp,
+                                            float(temperature), float(eps), _p(d), _p(m), _p(l),
+                                            ctypes.c_void_p(st)), "msbm_zncc_softargmax_fwd")
+    return d, m, l
+
+
+def backward_raw(left, right, window, ndisp, temperature, eps, d, m, l, g):
+    torch = _torch()
+    lib = _lib.load()
+    b, h, w = left.shape
+    nbytes = lib.msbm_zncc_softargmax_workspace_bytes(b, h, w, window, ndisp)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=left.device)
+    gl = torch.empty_like(left)
+    gr = torch.empty_like(left)
+    g = g.contiguous()
+    st = torch.cuda.current_stream(left.device).cuda_stream
+    _lib.check(lib.msbm_zncc_softargmax_bwd(_p(left), _p(right), b, h, w, window, ndisp,
+                                            float(temperature), float(eps), _p(d), _p(m), _p(l), _p(g),
+                                            _p(gl), _p(gr), _p(ws), nbytes, ctypes.c_void_p(st)),
+               "msbm_zncc_softargmax_bwd")
+    return gl, gr
+
+
+def _make_function():
+    torch = _torch()
+
+    class ZnccSoftArgmax(torch.autograd.Function):
+        """d_soft = sum_z z softmax_z(ZNCC_eps(left, right, z) / T) over 0 <= z <= min(ndisp-1, x)."""
+
+        @staticmethod
+        def forward(ctx, left, right, window=7, ndisp=64, temperature=0.05, eps=None):
+            eps = default_eps(window) if eps is None else eps
+            left = left.contiguous()
+            right = right.contiguous()
+            d, m, l = forward_raw(left, right, window, ndisp, temperature, eps)
+            ctx.save_for_backward(left, right, d, m, l)
+            ctx.cfg = (window, ndisp, temperature, eps)
+            return d
+
+        @staticmethod
+        def backward(ctx, g):
+            left, right, d, m, l = ctx.saved_tensors
+            window, ndisp, temperature, eps = ctx.cfg
+            gl, gr = backward_raw(left, right, window, ndisp, temperature, eps, d, m, l, g)
+            return gl, gr, None, None, None, None
+
+    return ZnccSoftArgmax
+
+
+_FN = None
+
+
+def __getattr__(name):
+    global _FN
+    if name == "ZnccSoftArgmax":
+        if _FN is None:
+            _FN = _make_function()
+        return _FN
+    raise AttributeError(name)
+
+
+def smoke_check() -> None:
+    """Tiny forward + backward on cuda:0 against the FP64 oracle (used by smoke())."""
+    import numpy as np
+    import oracle
+    torch = _torch()
+    rng = np.random.default_rng(0)
+    L = rng.random((1, 12, 40))
+    R = rng.random((1, 12, 40))
+    win, nd, T = 5, 8, 0.05
+    eps = default_eps(win)
+    lt = torch.tensor(L, dtype=torch.float32, device="cuda", requires_grad=True)
+    rt = torch.tensor(R, dtype=torch.float32, device="cuda", requires_grad=True)
+    fn = __getattr__("ZnccSoftArgmax")
+    d = fn.apply(lt, rt, win, nd, T, eps)
+    g = rng.standard_normal(L.shape)
+    d.backward(torch.tensor(g, dtype=torch.float32, device="cuda"))
+    ref = oracle.softargmax_fwd(L.astype(np.float32).astype(np.float64), R.astype(np.float32).astype(np.float64),
+                                win // 2, nd, T, eps)
+    gl, gr = oracle.softargmax_bwd(L.astype(np.float32).astype(np.float64),
+                                   R.astype(np.float32).astype(np.float64), win // 2, nd, T, eps, g)
+    assert np.abs(d.detach().cpu().numpy() - ref).max() < 1e-3
+    rel = np.abs(lt.grad.cpu().numpy() - gl).max() / max(np.abs(gl).max(), 1e-12)
+    assert rel < 1e-2, rel

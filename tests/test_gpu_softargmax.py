@@ -1,0 +1,127 @@
+"""GPU parity of the differentiable level (soft-argmax ZNCC forward and hand-written
+backward) against the FP64 oracle, through the C ABI via the autograd.Function.
+
+The oracle's gradient is itself pinned to FP64 central differences (tests/
+test_oracle_softargmax.py); here the GPU gradient is compared with it element-wise (max
+error relative to the largest gradient magnitude <= 1e-3), and directly with FP64 central
+differences of the oracle's loss along random directions on a 64x48 crop."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1901_09593_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+T = 0.05
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1901_09593_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def run_gpu(L, R, win, nd, T_, eps, g):
+    import torch
+    from paper_1901_09593_gb300.softargmax import ZnccSoftArgmax
+    lt = torch.tensor(L, dtype=torch.float32, device="cuda", requires_grad=True)
+    rt = torch.tensor(R, dtype=torch.float32, device="cuda", requires_grad=True)
+    d = ZnccSoftArgmax.apply(lt, rt, win, nd, T_, eps)
+    d.backward(torch.tensor(g, dtype=torch.float32, device="cuda"))
+    torch.cuda.synchronize()
+    return d.detach().cpu().numpy(), lt.grad.cpu().numpy(), rt.grad.cpu().numpy()
+
+
+def f32(a):
+    return np.asarray(a, np.float32).astype(np.float64)
+
+
+def rel_err(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-30)
+
+
+@pytest.mark.parametrize("win,nd,h,w", [(3, 4, 5, 9), (5, 8, 12, 40), (7, 16, 20, 64), (9, 12, 16, 37),
+                                        (7, 64, 24, 100), (5, 1, 6, 10), (7, 20, 9, 11)])
+def test_forward_and_backward_match_oracle_random(win, nd, h, w):
+    rng = np.random.default_rng(win * 100 + nd)
+    L = rng.random((2, h, w))
+    R = rng.random((2, h, w))
+    g = rng.standard_normal((2, h, w))
+    eps = 1e-6 * win * win
+    d, gl, gr = run_gpu(L, R, win, nd, T, eps, g)
+    Lf, Rf = f32(L), f32(R)
+    dref = oracle.softargmax_fwd(Lf, Rf, win // 2, nd, T, eps)
+    glr, grr = oracle.softargmax_bwd(Lf, Rf, win // 2, nd, T, eps, g)
+    assert np.abs(d - dref).max() <= 2e-3 + 1e-4 * nd
+    if nd == 1:
+        assert np.all(d == 0) and np.all(gl == 0) and np.all(gr == 0)
+        return
+    assert rel_err(gl, glr) <= 1e-3, rel_err(gl, glr)
+    assert rel_err(gr, grr) <= 1e-3, rel_err(gr, grr)
+
+
+def test_scene_crop_64x48_against_central_differences():
+    sc = scenes.make_float_pair(scenes.SPECS["diff_640x480"], 3)
+    L = sc.left[200:248, 300:364][None].copy()
+    R = sc.right[200:248, 300:364][None].copy()
+    win, nd = 7, 64
+    eps = 1e-6 * 49
+    rng = np.random.default_rng(7)
+    wts = rng.standard_normal(L.shape)
+    d, gl, gr = run_gpu(L, R, win, nd, T, eps, wts)
+    Lf, Rf = f32(L), f32(R)
+    glr, grr = oracle.softargmax_bwd(Lf, Rf, 3, nd, T, eps, wts)
+    assert rel_err(gl, glr) <= 1e-3 and rel_err(gr, grr) <= 1e-3
+
+    def loss(a, b):
+        return float((oracle.softargmax_fwd(a, b, 3, nd, T, eps) * wts).sum())
+
+    h = 1e-6
+    for _ in range(3):
+        vL = rng.standard_normal(L.shape)
+        vR = rng.standard_normal(R.shape)
+        fd = (loss(Lf + h * vL, Rf + h * vR) - loss(Lf - h * vL, Rf - h * vR)) / (2 * h)
+        an = float((gl * vL).sum() + (gr * vR).sum())
+        assert abs(an - fd) <= 1e-3 * abs(fd), (an, fd)
+
+
+def test_full_size_batch_forward_and_one_image_backward():
+    import torch
+    from paper_1901_09593_gb300.softargmax import ZnccSoftArgmax
+    spec = scenes.SPECS["diff_640x480"]
+    pairs = [scenes.make_float_pair(spec, s) for s in range(8)]
+    L = np.stack([p.left for p in pairs])
+    R = np.stack([p.right for p in pairs])
+    win, nd, eps = 7, 64, 1e-6 * 49
+    lt = torch.tensor(L, dtype=torch.float32, device="cuda", requires_grad=True)
+    rt = torch.tensor(R, dtype=torch.float32, device="cuda", requires_grad=True)
+    d = ZnccSoftArgmax.apply(lt, rt, win, nd, T, eps)
+    g = np.random.default_rng(1).standard_normal(L.shape)
+    d.backward(torch.tensor(g, dtype=torch.float32, device="cuda"))
+    torch.cuda.synchronize()
+    d = d.detach().cpu().numpy()
+    Lf, Rf = f32(L[:1]), f32(R[:1])
+    dref = oracle.softargmax_fwd(Lf, Rf, 3, nd, T, eps)
+    assert np.abs(d[:1] - dref).max() <= 1e-2
+    assert np.mean(np.abs(d[:1] - dref) <= 2e-3) > 0.999
+    glr, grr = oracle.softargmax_bwd(Lf, Rf, 3, nd, T, eps, g[:1])
+    assert rel_err(lt.grad[:1].cpu().numpy(), glr) <= 1e-3
+    assert rel_err(rt.grad[:1].cpu().numpy(), grr) <= 1e-3
+    # soft disparities track the scene where the match is clear
+    assert np.all(np.isfinite(d))
+
+
+def test_bad_arguments_are_rejected():
+    import ctypes
+    from paper_1901_09593_gb300 import _lib
+    lib = _lib.load()
+    p = ctypes.c_void_p(256)
+    assert lib.msbm_zncc_softargmax_fwd(p, p, 1, 8, 8, 4, 8, 0.05, 1e-5, p, p, p, None) == _lib.MSBM_ERR_INVALID_ARG
+    assert lib.msbm_zncc_softargmax_fwd(p, p, 1, 8, 8, 11, 8, 0.05, 1e-5, p, p, p, None) == _lib.MSBM_ERR_INVALID_ARG
+    assert lib.msbm_zncc_softargmax_fwd(p, p, 1, 8, 8, 7, 300, 0.05, 1e-5, p, p, p, None) == _lib.MSBM_ERR_INVALID_ARG
+    assert lib.msbm_zncc_softargmax_fwd(p, p, 1, 8, 8, 7, 8, 0.0, 1e-5, p, p, p, None) == _lib.MSBM_ERR_INVALID_ARG
+    assert lib.msbm_zncc_softargmax_bwd(p, p, 1, 8, 8, 7, 8, 0.05, 1e-5, p, p, p, p, p, p, p, 16, None) \
+        == _lib.MSBM_ERR_INVALID_ARG
+    assert lib.msbm_zncc_softargmax_workspace_bytes(1, 8, 8, 7, 8) > 0
