@@ -233,6 +233,109 @@ def run_reference(args):
     return 0
 
 
+def bench_batch(args, dev, flush, stream):
+    """48 seeded pairs of mixed sizes through one persistent launch (graph replay)."""
+    import numpy as np
+    import torch
+
+    from paper_1901_09593_gb300 import Batch, autotune, scenes
+    specs_s = scenes.make_batch_specs(48, 0)
+    specs = [(s.width, s.height, s.max_disp, s.levels, s.window, s.radius) for s in specs_s]
+    # one seeded scene per size class (content reused across pairs of that size)
+    by_size = {}
+    for s in specs_s:
+        key = (s.width, s.height)
+        if key not in by_size:
+            by_size[key] = scenes.make_pair(s, 100 + len(by_size))
+    Ls = [torch.from_numpy(by_size[(s.width, s.height)].left).to(dev) for s in specs_s]
+    Rs = [torch.from_numpy(by_size[(s.width, s.height)].right).to(dev) for s in specs_s]
+    sx, zb = autotune.tune_batch(specs)
+    b = Batch(specs, sx, zb)
+    d, c = b.alloc_outputs()
+    for _ in range(max(3, args.warmup)):
+        b.run(Ls, Rs, d, c)
+    b.sync()
+    b.eval_count(reset=True)
+    steps = max(3, min(args.steps, 50))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for e0, e1 in ev:
+        flush.zero_()
+        e0.record(stream)
+        b.run(Ls, Rs, d, c)
+        e1.record(stream)
+    b.sync()
+    ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    evals = b.eval_count(reset=True) / steps
+    t = sum(ms) / 1e3 / steps
+    # the same pairs one by one through per-pair contexts (graph replay each)
+    from paper_1901_09593_gb300 import Context
+    ctxs = [Context(*sp) for sp in specs]
+    for _ in range(3):
+        for i, cx in enumerate(ctxs):
+            cx.disparity(Ls[i], Rs[i], d[i], c[i])
+    torch.cuda.synchronize(dev)
+    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for e0, e1 in ev2:
+        flush.zero_()
+        e0.record(stream)
+        for i, cx in enumerate(ctxs):
+            cx.disparity(Ls[i], Rs[i], d[i], c[i])
+        e1.record(stream)
+    torch.cuda.synchronize(dev)
+    t_seq = sum(e0.elapsed_time(e1) for e0, e1 in ev2) / 1e3 / steps
+    info = b.info()
+    return {"workload": "48 seeded mixed-size pairs (320x240 .. 1920x1080, D = W/5, K to width >= 160, "
+                        "window 5/7, r = 2), one persistent launch per pass",
+            "pairs_per_s": 48 / t, "ms_per_batch": 1e3 * t, "gpix_disp_per_s": evals / t / 1e9,
+            "evals_per_batch": evals, "sequential_contexts_ms": 1e3 * t_seq,
+            "speedup_vs_sequential": t_seq / t, "queue_items": info["items"], "grid_ctas": info["grid"],
+            "steps": steps, "gpu_launches_per_batch": 1}
+
+
+def bench_diff(args, dev, flush, stream):
+    """Soft-argmax ZNCC level forward + backward, 8 x 640 x 480, 64 candidates, 7x7, T=0.05."""
+    import numpy as np
+    import torch
+
+    from paper_1901_09593_gb300 import scenes
+    from paper_1901_09593_gb300.softargmax import ZnccSoftArgmax, default_eps
+    spec = scenes.SPECS["diff_640x480"]
+    pairs = [scenes.make_float_pair(spec, s) for s in range(8)]
+    L = torch.tensor(np.stack([p.left for p in pairs]), dtype=torch.float32, device=dev)
+    R = torch.tensor(np.stack([p.right for p in pairs]), dtype=torch.float32, device=dev)
+    g = torch.ones_like(L)
+
+    def step():
+        lt = L.detach().requires_grad_(True)
+        rt = R.detach().requires_grad_(True)
+        out = ZnccSoftArgmax.apply(lt, rt, 7, 64, 0.05, default_eps(7))
+        out.backward(g)
+        return out
+
+    def fwd():
+        with torch.no_grad():
+            return ZnccSoftArgmax.apply(L, R, 7, 64, 0.05, default_eps(7))
+
+    res = {}
+    for name, fn in (("forward", fwd), ("forward_backward", step)):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize(dev)
+        steps = max(3, min(args.steps, 10))
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for e0, e1 in ev:
+            flush.zero_()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+        torch.cuda.synchronize(dev)
+        res[name + "_ms"] = statistics.median(e0.elapsed_time(e1) for e0, e1 in ev)
+    evals = 8 * 480 * sum(min(63, x) + 1 for x in range(640))
+    res.update({"workload": "8 x 640 x 480 float32 pairs, 7x7 ZNCC over 64 candidates, soft-argmax T=0.05",
+                "evals": evals, "forward_gpix_disp_per_s": evals / (res["forward_ms"] * 1e-3) / 1e9})
+    return res
+
+
 def config_dict(spec):
     return {"workload": f"{WORKLOAD}: hierarchical ZNCC BM, {spec.width}x{spec.height} uint8 pair, "
                         f"D={spec.max_disp}, K={spec.levels}, {spec.window}x{spec.window} window, "
@@ -386,6 +489,11 @@ def run_gpu(args):
                "sample": f"{runs} full-frame hierarchical passes of the {W}x{H} pair "
                          f"(FP64 C oracle, OpenMP over rows), {el:.1f} s"}
 
+    additions = {}
+    if rank == 0 and not args.no_additions:
+        additions["batching"] = bench_batch(args, dev, flush, stream)
+        additions["differentiable"] = bench_diff(args, dev, flush, stream)
+
     launches_per_step = 2 * spec.levels
     line = {
         "metric": METRIC,
@@ -417,6 +525,7 @@ def run_gpu(args):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
         "wall_s_timed_region": wall,
+        "additions": additions,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -433,6 +542,7 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle CPU time")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-additions", action="store_true", help="skip the batching and differentiable lines")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

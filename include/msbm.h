@@ -139,6 +139,42 @@ msbm_status msbm_sync(msbm_ctx *ctx);
  * reset != 0 (synchronises the stream). */
 msbm_status msbm_eval_count(msbm_ctx *ctx, int64_t *count, int32_t reset);
 
+/* Tuning of the full-range search at `level` (used at the coarsest level and by K = 1):
+ * tiles of 32*sx columns x 8 rows (sx in {1, 2, 4}) and z-blocks of `zblock` candidates
+ * staged per pass (a multiple of 32; 0 = the largest the tile allows).  Results do not
+ * depend on it.  The next msbm_disparity re-captures its graph. */
+msbm_status msbm_set_level_tuning(msbm_ctx *ctx, int32_t level, int32_t sx, int32_t zblock);
+
+/* ---------------------------------------------------------------------------------------
+ * Batching: many pairs of different sizes, disparity ranges, depths, windows and radii
+ * through the whole hierarchical pass (pyramid, coarsest full search, restricted levels)
+ * in ONE persistent kernel launch over a (pair, stage, tile) work queue, replayed from a
+ * CUDA graph.  The paper processes one pair at a time; this is a throughput addition with
+ * the same per-pair results as msbm_disparity.
+ *   pairs[i]         : per-pair parameters as for msbm_create (window 3..9 here; the flag
+ *                      MSBM_FLAG_TEST_TIMEOUT on pairs[0] makes the queue withhold its first
+ *                      stage so that every dependent wait gives up after ~1 ms: test hook).
+ *   full_sx[i]       : NULL or the coarsest-level tile width 32*sx, sx in {1, 2}.
+ *   full_zblock[i]   : NULL or the coarsest-level z-block (multiple of 32, 0 = maximum).
+ * The batch owns each pair's pyramid and intermediate maps. */
+typedef struct msbm_batch msbm_batch;
+msbm_status msbm_batch_create(const msbm_params *pairs, int32_t n_pairs, const int32_t *full_sx,
+                              const int32_t *full_zblock, void *cuda_stream, msbm_batch **out);
+/* Enqueue one pass over all pairs.  Arrays of n_pairs device pointers (images width x
+ * height at pitches[i]; level-0 maps dense; cost_outs may be NULL or hold NULLs).  When a
+ * pointer differs from the previous call, the device pointer table is re-uploaded (this
+ * waits for the stream).  Asynchronous otherwise. */
+msbm_status msbm_batch_run(msbm_batch *b, const uint8_t *const *d_lefts,
+                           const uint8_t *const *d_rights, const size_t *pitches,
+                           int16_t *const *d_outs, float *const *cost_outs);
+/* Wait for the stream; return (and clear) a recorded device error (MSBM_ERR_TIMEOUT). */
+msbm_status msbm_batch_sync(msbm_batch *b);
+msbm_status msbm_batch_eval_count(msbm_batch *b, int64_t *count, int32_t reset);
+/* Queue length, persistent grid size (CTAs) and number of (pair, stage) segments. */
+msbm_status msbm_batch_info(const msbm_batch *b, int64_t *n_items, int32_t *grid,
+                            int32_t *n_segments);
+msbm_status msbm_batch_destroy(msbm_batch *b);
+
 /* ---------------------------------------------------------------------------------------
  * Differentiable level: soft-argmax readout of a ZNCC cost volume (Eq. 2 on float images).
  * For each pixel of each image of a batch (B x H x W, float32, dense, row-major):

@@ -6,9 +6,10 @@ on first use and raises if it has not been built.
 """
 import importlib
 
-__all__ = ["Context", "build", "scenes"]
+__all__ = ["Context", "Batch", "ZnccSoftArgmax", "build", "scenes", "autotune"]
 
-_LAZY = {"Context": (".msbm", "Context")}
+_LAZY = {"Context": (".msbm", "Context"), "Batch": (".batch", "Batch"),
+         "ZnccSoftArgmax": (".softargmax", "ZnccSoftArgmax")}
 
 
 def __getattr__(name):

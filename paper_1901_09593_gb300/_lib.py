@@ -50,6 +50,13 @@ SIGNATURES = {
                                 P(ctypes.c_float), c_int32], ctypes.c_int),
     "msbm_sync": ([c_void_p], ctypes.c_int),
     "msbm_eval_count": ([c_void_p, P(ctypes.c_int64), c_int32], ctypes.c_int),
+    "msbm_set_level_tuning": ([c_void_p, c_int32, c_int32, c_int32], ctypes.c_int),
+    "msbm_batch_create": ([P(msbm_params), c_int32, c_void_p, c_void_p, c_void_p, P(c_void_p)], ctypes.c_int),
+    "msbm_batch_run": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], ctypes.c_int),
+    "msbm_batch_sync": ([c_void_p], ctypes.c_int),
+    "msbm_batch_eval_count": ([c_void_p, P(ctypes.c_int64), c_int32], ctypes.c_int),
+    "msbm_batch_info": ([c_void_p, P(ctypes.c_int64), P(c_int32), P(c_int32)], ctypes.c_int),
+    "msbm_batch_destroy": ([c_void_p], ctypes.c_int),
     "msbm_zncc_softargmax_fwd": ([c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_int32,
                                   ctypes.c_float, ctypes.c_float, c_void_p, c_void_p, c_void_p, c_void_p],
                                  ctypes.c_int),

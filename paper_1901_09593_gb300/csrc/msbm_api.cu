@@ -16,10 +16,6 @@
 
 using namespace msbm;
 
-namespace msbm {
-cudaError_t zncc_full_prepare(int nh, int sx);
-}
-
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -133,9 +129,9 @@ msbm_status enqueue_level(msbm_ctx *c, int k, const int16_t *prior, int16_t *d, 
         memset(&a, 0, sizeof(a));
         a.tmL = l.tmFL[0];
         a.tmR = l.tm256[1];
-        a.W = l.W; a.H = l.H; a.Dk = l.Dk;
-        a.d_out = d; a.c_out = cost;
-        a.evals = c->d_evals; a.err = c->d_err; a.force_timeout = force;
+        a.t.W = l.W; a.t.H = l.H; a.t.Dk = l.Dk; a.t.zblock = l.full_zblock;
+        a.t.d_out = d; a.t.c_out = cost;
+        a.t.evals = c->d_evals; a.t.err = c->d_err; a.t.force_timeout = force;
         e = launch_zncc_full(a, c->nh, l.full_sx, st);
     } else {
         RestrArgs a;
@@ -143,11 +139,11 @@ msbm_status enqueue_level(msbm_ctx *c, int k, const int16_t *prior, int16_t *d, 
         a.tmL = l.tm64[0];
         a.tmR64 = l.tm64[1];
         a.tmR256 = l.tm256[1];
-        a.Limg = l.img(0); a.Rimg = l.img(1); a.pitch = l.pitch;
-        a.W = l.W; a.H = l.H; a.Dk = l.Dk; a.r = c->p.radius;
-        a.prior = prior; a.Wp = (l.W + 1) / 2; a.Hp = (l.H + 1) / 2;
-        a.d_out = d; a.c_out = cost;
-        a.evals = c->d_evals; a.err = c->d_err; a.force_timeout = force;
+        a.t.Limg = l.img(0); a.t.Rimg = l.img(1); a.t.pitch = l.pitch;
+        a.t.W = l.W; a.t.H = l.H; a.t.Dk = l.Dk; a.t.r = c->p.radius;
+        a.t.prior = prior; a.t.Wp = (l.W + 1) / 2; a.t.Hp = (l.H + 1) / 2;
+        a.t.d_out = d; a.t.c_out = cost;
+        a.t.evals = c->d_evals; a.t.err = c->d_err; a.t.force_timeout = force;
         e = launch_zncc_restricted(a, c->nh, st);
     }
     return cuda_status(e);
@@ -267,6 +263,24 @@ msbm_status msbm_level_shape(const msbm_ctx *ctx, int32_t level, int32_t *w, int
     if (w) *w = l.W;
     if (h) *h = l.H;
     if (d_k) *d_k = l.Dk;
+    return MSBM_OK;
+}
+
+msbm_status msbm_set_level_tuning(msbm_ctx *ctx, int32_t level, int32_t sx, int32_t zblock) {
+    if (!ctx || level < 0 || level >= ctx->p.levels) return MSBM_ERR_INVALID_ARG;
+    if ((sx != 1 && sx != 2 && sx != 4) || zblock < 0 || zblock % 32 != 0) return MSBM_ERR_INVALID_ARG;
+    LevelBuf &l = ctx->lv[level];
+    const int rowsT = 8 + 2 * ctx->nh;
+    for (int i = 0; i < 2; ++i)
+        if (!encode_u8(&l.tmFL[i], l.base[i], l.pitch, l.rows, 32 * sx + 32, rowsT)) return MSBM_ERR_UNSUPPORTED;
+    cudaError_t e = zncc_full_prepare(ctx->nh, sx);
+    if (e != cudaSuccess) return cuda_status(e);
+    l.full_sx = sx;
+    l.full_zblock = zblock;
+    if (ctx->exec) {   // the captured graph holds the old launch configuration
+        cudaGraphExecDestroy(ctx->exec);
+        ctx->exec = nullptr;
+    }
     return MSBM_OK;
 }
 

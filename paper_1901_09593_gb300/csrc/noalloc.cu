@@ -24,10 +24,6 @@
 
 using namespace msbm;
 
-namespace msbm {
-cudaError_t zncc_full_prepare(int nh, int sx);
-}
-
 namespace {
 
 // Scratch: [0, 256) status word, then the left and right apron buffers.
@@ -134,16 +130,17 @@ extern "C" msbm_status msbm_flat_disparity_noalloc(const uint8_t *d_left, const 
     if (!encode_map(&a.tmL, lv.base[0], pitch, rows, 32 * sx + 32, rowsT) ||
         !encode_map(&a.tmR, lv.base[1], pitch, rows, 256, rowsT))
         return MSBM_ERR_UNSUPPORTED;
-    a.W = width;
-    a.H = height;
-    a.Dk = max_disp;
-    a.d_out = d_out;
-    a.c_out = cost_out;
-    a.evals = nullptr;
+    a.t.W = width;
+    a.t.H = height;
+    a.t.Dk = max_disp;
+    a.t.zblock = 0;
+    a.t.d_out = d_out;
+    a.t.c_out = cost_out;
+    a.t.evals = nullptr;
     // the failure word starts at zero on every call
-    a.err = d_status ? d_status : reinterpret_cast<int *>(scratch);
-    a.force_timeout = 0;
-    cudaError_t e = cudaMemsetAsync(a.err, 0, sizeof(int32_t), st);
+    a.t.err = d_status ? d_status : reinterpret_cast<int *>(scratch);
+    a.t.force_timeout = 0;
+    cudaError_t e = cudaMemsetAsync(a.t.err, 0, sizeof(int32_t), st);
     if (e == cudaSuccess) e = launch_apron_copy(d_left, d_right, pitch_bytes, lv, st);
     if (e == cudaSuccess) e = launch_zncc_full(a, nh, sx, st);
     return e == cudaSuccess ? MSBM_OK : MSBM_ERR_CUDA;

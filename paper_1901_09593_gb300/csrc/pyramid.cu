@@ -12,6 +12,7 @@
 // levels of a frame are small enough to stay resident in L2.
 #include "msbm_device.cuh"
 #include "msbm_internal.h"
+#include "pyramid_ops.cuh"
 
 namespace msbm {
 
@@ -25,16 +26,7 @@ __global__ void apron_copy_kernel(const uint8_t *__restrict__ srcL, const uint8_
     int X0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4 - APX;
     int Y = blockIdx.y * blockDim.y + threadIdx.y - APY;
     if (Y >= H + APY || X0 >= W + APX) return;
-    int y = min(max(Y, 0), H - 1);
-    const uint8_t *row = src + (size_t)y * spitch;
-    uint32_t v = 0;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        int x = min(max(X0 + i, 0), W - 1);
-        v |= static_cast<uint32_t>(__ldg(row + x)) << (8 * i);
-    }
-    // X0 + APX is a multiple of 4 and the buffer row start is 128-byte aligned.
-    *reinterpret_cast<uint32_t *>(dst + (ptrdiff_t)Y * dpitch + X0) = v;
+    copy_quad(src, spitch, W, H, dst, dpitch, X0, Y);
 }
 
 // Level k from level k-1.  One thread per 4 consecutive output bytes.
@@ -46,24 +38,7 @@ __global__ void pyr_reduce_kernel(const uint8_t *__restrict__ srcL, const uint8_
     int X0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4 - APX;
     int Y = blockIdx.y * blockDim.y + threadIdx.y - APY;
     if (Y >= Hd + APY || X0 >= Wd + APX) return;
-    int y = min(max(Y, 0), Hd - 1);
-    uint32_t v = 0;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        int x = min(max(X0 + i, 0), Wd - 1);
-        // vertical taps first (exact ints), then horizontal
-        int acc = 0;
-        const uint8_t *base = src + (ptrdiff_t)(2 * y - 2) * spitch + (2 * x - 2);
-#pragma unroll
-        for (int b = 0; b < 5; ++b) {
-            const int cb = (b == 0 || b == 4) ? 1 : (b == 2 ? 6 : 4);
-            int col = __ldg(base + b) + 4 * __ldg(base + spitch + b) + 6 * __ldg(base + 2 * spitch + b) +
-                      4 * __ldg(base + 3 * spitch + b) + __ldg(base + 4 * spitch + b);
-            acc += cb * col;
-        }
-        v |= static_cast<uint32_t>((acc + 128) >> 8) << (8 * i);
-    }
-    *reinterpret_cast<uint32_t *>(dst + (ptrdiff_t)Y * dpitch + X0) = v;
+    reduce_quad(src, spitch, dst, dpitch, Wd, Hd, X0, Y);
 }
 
 static dim3 apron_grid(int W, int H, dim3 blk) {

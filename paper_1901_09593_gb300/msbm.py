@@ -77,6 +77,10 @@ class Context:
                                               ctypes.byref(d)), "msbm_level_shape")
         return w.value, h.value, d.value
 
+    def set_level_tuning(self, level: int, sx: int, zblock: int = 0) -> None:
+        """Full-range tile width 32*sx and z-block at `level` (speed only)."""
+        _lib.check(self._lib.msbm_set_level_tuning(self._ctx, level, sx, zblock), "msbm_set_level_tuning")
+
     def sync(self) -> None:
         _lib.check(self._lib.msbm_sync(self._ctx), "msbm_sync")
 
