@@ -51,6 +51,15 @@ def _load():
             lib.oracle_disparity.restype = ll
             lib.oracle_softargmax_fwd.argtypes = [P, P, i, i, i, i, i, d, d, P, P]
             lib.oracle_softargmax_bwd.argtypes = [P, P, i, i, i, i, i, d, d, P, P, P]
+            lib.oracle_bicubic_at.argtypes = [P, i, i, d, d]
+            lib.oracle_bicubic_at.restype = d
+            lib.oracle_upsample_cost.argtypes = [P, i, i, i, i, P]
+            lib.oracle_match_level_beta.argtypes = [P, P, i, i, i, i, i, P, P, i, i, d, P, P, P, P, P]
+            lib.oracle_match_level_beta.restype = ll
+            lib.oracle_alpha_refine.argtypes = [P, P, i, i, i, i, d, P, P, P, P]
+            lib.oracle_selective_median.argtypes = [P, P, i, i, d, P]
+            lib.oracle_disparity_full.argtypes = [P, P, i, i, i, i, i, i, d, d, i, P, P, P]
+            lib.oracle_disparity_full.restype = ll
             lib.oracle_max_threads.restype = i
             lib.oracle_set_threads.argtypes = [i]
             _lib = lib
@@ -185,3 +194,88 @@ def softargmax_bwd(left, right, n: int, ndisp: int, T: float, eps: float, g_d):
     _load().oracle_softargmax_bwd(_ptr(left), _ptr(right), b, h, w, n, ndisp, T, eps,
                                   _ptr(g_d), _ptr(gl), _ptr(gr))
     return gl, gr
+
+
+# --- gated steps of the full method (alpha refinement, beta fallback, selective median) ---
+ALPHA_REFINE, BETA_FALLBACK, SELECTIVE_MEDIAN = 1, 2, 4
+FULL_METHOD = ALPHA_REFINE | BETA_FALLBACK | SELECTIVE_MEDIAN
+
+
+def bicubic_at(cost, cy: float, cx: float) -> float:
+    cost = np.ascontiguousarray(cost, dtype=np.float64)
+    h, w = cost.shape
+    return float(_load().oracle_bicubic_at(_ptr(cost), w, h, cy, cx))
+
+
+def upsample_cost(cost, width: int, height: int) -> np.ndarray:
+    """Bicubic cost prior of Sec. III-C at the finer level's size."""
+    cost = np.ascontiguousarray(cost, dtype=np.float64)
+    h, w = cost.shape
+    out = np.empty((height, width), np.float64)
+    _load().oracle_upsample_cost(_ptr(cost), w, h, width, height, _ptr(out))
+    return out
+
+
+def match_level_beta(a_img, b_img, n: int, dk: int, r: int, prior, cprior, beta: float):
+    """Eq. 8-9 (both branches).  Returns (d, C, C2, evals, fallback mask, C_hat)."""
+    a_img, b_img = _u8(a_img), _u8(b_img)
+    h, w = a_img.shape
+    prior = np.ascontiguousarray(prior, dtype=np.int16)
+    cprior = np.ascontiguousarray(cprior, dtype=np.float64)
+    hp, wp = prior.shape
+    d = np.empty((h, w), np.int16)
+    c = np.empty((h, w), np.float64)
+    c2 = np.empty((h, w), np.float64)
+    fb = np.empty((h, w), np.uint8)
+    ch = np.empty((h, w), np.float64)
+    ev = _load().oracle_match_level_beta(_ptr(a_img), _ptr(b_img), w, h, n, dk, r, _ptr(prior),
+                                         _ptr(cprior), wp, hp, beta, _ptr(d), _ptr(c), _ptr(c2),
+                                         _ptr(fb), _ptr(ch))
+    return d, c, c2, int(ev), fb.astype(bool), ch
+
+
+def alpha_refine(a_img, b_img, n: int, dk: int, alpha: float, d, cost, cost2=None):
+    """Eq. 5-7 on a coarsest-level result.  Returns (d, C, C2, refined mask) (new arrays)."""
+    a_img, b_img = _u8(a_img), _u8(b_img)
+    h, w = a_img.shape
+    d = np.array(d, dtype=np.int16, copy=True, order="C")
+    c = np.array(cost, dtype=np.float64, copy=True, order="C")
+    c2 = np.full((h, w), -np.inf) if cost2 is None else np.array(cost2, dtype=np.float64, copy=True, order="C")
+    ref = np.empty((h, w), np.uint8)
+    _load().oracle_alpha_refine(_ptr(a_img), _ptr(b_img), w, h, n, dk, alpha, _ptr(d), _ptr(c), _ptr(c2),
+                                _ptr(ref))
+    return d, c, c2, ref.astype(bool)
+
+
+def selective_median(d, cost, alpha: float) -> np.ndarray:
+    """Eq. 10."""
+    d = np.ascontiguousarray(d, dtype=np.int16)
+    cost = np.ascontiguousarray(cost, dtype=np.float64)
+    h, w = d.shape
+    out = np.empty_like(d)
+    _load().oracle_selective_median(_ptr(d), _ptr(cost), w, h, alpha, _ptr(out))
+    return out
+
+
+def disparity_full(left, right, max_disp: int, levels: int, window: int, radius: int,
+                   alpha: float = 0.9, beta: float = 0.9, flags: int = FULL_METHOD):
+    """The full method (plain method plus the gated steps selected by ``flags``)."""
+    left, right = _u8(left), _u8(right)
+    h, w = left.shape
+    sizes = [level_size(w, h, k) for k in range(levels)]
+    tot = sum(a * b for a, b in sizes)
+    d = np.empty(tot, np.int16)
+    c = np.empty(tot, np.float64)
+    c2 = np.empty(tot, np.float64)
+    ev = _load().oracle_disparity_full(_ptr(left), _ptr(right), w, h, max_disp, levels, window, radius,
+                                       alpha, beta, flags, _ptr(d), _ptr(c), _ptr(c2))
+    if ev < 0:
+        raise ValueError("invalid arguments")
+    out = {"d": [], "C": [], "C2": [], "evals": int(ev)}
+    o = 0
+    for a, b in sizes:
+        out["d"].append(d[o:o + a * b].reshape(b, a))
+        out["C"].append(c[o:o + a * b].reshape(b, a))
+        out["C2"].append(c2[o:o + a * b].reshape(b, a))
+        o += a * b
+    return out

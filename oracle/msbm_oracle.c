@@ -320,3 +320,208 @@ void oracle_softargmax_bwd(const double *L, const double *R, int Bn, int H, int 
         free(ac); free(bc); free(rho);
     }
 }
+
+/* ====================================================================================
+ * The gated steps of the full method (Sec. III-B, III-C second branch, III-D).
+ * ==================================================================================== */
+
+/* Keys cubic convolution kernel with a = -1/2 (Catmull-Rom). */
+static double cubic_w(double t) {
+    t = fabs(t);
+    if (t < 1.0) return (1.5 * t - 2.5) * t * t + 1.0;
+    if (t < 2.0) return ((-0.5 * t + 2.5) * t - 4.0) * t + 2.0;
+    return 0.0;
+}
+
+/* Sec. III-C: the cost prior C_hat^k = BI(C^{k+1}), bicubic upsampling.  Reading: the fine
+ * pixel (y, x) sits at coarse coordinates (y/2, x/2) (coarse pixel i is the reduce of fine
+ * pixel 2i), samples outside the coarse map are clamped to its edge.  Written as the plain
+ * 4 x 4 weighted sum. */
+double oracle_bicubic_at(const double *Cc, int Wc, int Hc, double cy, double cx) {
+    int iy = (int)floor(cy), ix = (int)floor(cx);
+    double fy = cy - iy, fx = cx - ix, s = 0.0;
+    for (int a = -1; a <= 2; ++a) {
+        double wy = cubic_w(a - fy);
+        int yy = clampi(iy + a, 0, Hc - 1);
+        for (int b = -1; b <= 2; ++b) {
+            double wx = cubic_w(b - fx);
+            int xx = clampi(ix + b, 0, Wc - 1);
+            s += wy * wx * Cc[(long)yy * Wc + xx];
+        }
+    }
+    return s;
+}
+
+void oracle_upsample_cost(const double *Cc, int Wc, int Hc, int W, int H, double *out) {
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) out[(long)y * W + x] = oracle_bicubic_at(Cc, Wc, Hc, 0.5 * y, 0.5 * x);
+}
+
+/* Eq. 8-9, both branches: where the upsampled cost C_hat exceeds beta the restricted
+ * search around dhat (first branch, as oracle_match_level), otherwise the full search over
+ * 0 .. min(D_k - 1, x) (second branch).  Cprior is the coarser level's cost map (Wp x Hp).
+ * fallback (optional) receives 1 where the second branch was taken; chat (optional)
+ * receives C_hat.  Returns the evaluation count. */
+long long oracle_match_level_beta(const uint8_t *A, const uint8_t *B, int W, int H, int n, int Dk,
+                                  int r, const int16_t *prior, const double *Cprior, int Wp, int Hp,
+                                  double beta, int16_t *d, double *C, double *C2, uint8_t *fallback,
+                                  double *chat) {
+    long long evals = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : evals)
+    for (int y = 0; y < H; ++y) {
+        for (int x = 0; x < W; ++x) {
+            int zmax = Dk - 1 < x ? Dk - 1 : x;
+            double ch = oracle_bicubic_at(Cprior, Wp, Hp, 0.5 * y, 0.5 * x);
+            int full = !(ch > beta);
+            int lo = 0, hi = zmax;
+            if (!full) {
+                int py = clampi(y / 2, 0, Hp - 1), px = clampi(x / 2, 0, Wp - 1);
+                int dh = clampi(2 * (int)prior[(long)py * Wp + px], 0, zmax);
+                lo = dh - r < 0 ? 0 : dh - r;
+                hi = dh + r > zmax ? zmax : dh + r;
+            }
+            double best = -INFINITY, second = -INFINITY;
+            int bz = lo;
+            for (int z = lo; z <= hi; ++z) {
+                double rho = oracle_zncc(A, B, W, H, n, y, x, z);
+                if (rho > best) { second = best; best = rho; bz = z; }
+                else if (rho > second) second = rho;
+            }
+            evals += hi - lo + 1;
+            long o = (long)y * W + x;
+            d[o] = (int16_t)bz; C[o] = best; C2[o] = second;
+            if (fallback) fallback[o] = (uint8_t)full;
+            if (chat) chat[o] = ch;
+        }
+    }
+    return evals;
+}
+
+/* Sec. III-B, Eq. 5-7: for every pixel whose matched cost C' is not above alpha, average
+ * the DSI over its 3 x 3 neighbourhood N(i, j) (neighbours inside the image; the paper
+ * leaves the size unstated and writes a sum, which has the same argmax; the average keeps
+ * C on the ZNCC scale) and take the argmax over the pixel's own admissible candidates
+ * 0 .. min(D_k - 1, x).  Each neighbour's E(z) is the ZNCC of its window at disparity z
+ * (clamp-to-edge windows).  d, C are updated in place from copies of the inputs; C2
+ * receives the second-best averaged value for refined pixels (untouched otherwise);
+ * refined (optional) marks the refined pixels. */
+void oracle_alpha_refine(const uint8_t *A, const uint8_t *B, int W, int H, int n, int Dk,
+                         double alpha, int16_t *d, double *C, double *C2, uint8_t *refined) {
+    double *Cin = (double *)malloc(sizeof(double) * (size_t)W * H);
+    memcpy(Cin, C, sizeof(double) * (size_t)W * H);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int y = 0; y < H; ++y) {
+        for (int x = 0; x < W; ++x) {
+            long o = (long)y * W + x;
+            if (refined) refined[o] = 0;
+            if (Cin[o] > alpha) continue;
+            int zmax = Dk - 1 < x ? Dk - 1 : x;
+            double best = -INFINITY, second = -INFINITY;
+            int bz = 0;
+            for (int z = 0; z <= zmax; ++z) {
+                double s = 0.0;
+                int cnt = 0;
+                for (int m = y - 1; m <= y + 1; ++m)
+                    for (int q = x - 1; q <= x + 1; ++q) {
+                        if (m < 0 || m >= H || q < 0 || q >= W) continue;
+                        s += oracle_zncc(A, B, W, H, n, m, q, z);
+                        ++cnt;
+                    }
+                double e = s / cnt;
+                if (e > best) { second = best; best = e; bz = z; }
+                else if (e > second) second = e;
+            }
+            d[o] = (int16_t)bz;
+            C[o] = best;
+            C2[o] = second;
+            if (refined) refined[o] = 1;
+        }
+    }
+    free(Cin);
+}
+
+/* Sec. III-D, Eq. 10: for every pixel whose cost is not above alpha, the median of the
+ * disparities of the 5 x 5 neighbours (inside the image) whose cost is above alpha; the
+ * lower median for an even count; unchanged when no neighbour qualifies.  Reads d_in, C;
+ * writes d_out (may not alias d_in). */
+void oracle_selective_median(const int16_t *d_in, const double *C, int W, int H, double alpha,
+                             int16_t *d_out) {
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            long o = (long)y * W + x;
+            d_out[o] = d_in[o];
+            if (C[o] > alpha) continue;
+            int v[25], cnt = 0;
+            for (int m = y - 2; m <= y + 2; ++m)
+                for (int q = x - 2; q <= x + 2; ++q) {
+                    if (m < 0 || m >= H || q < 0 || q >= W) continue;
+                    long p = (long)m * W + q;
+                    if (C[p] > alpha) v[cnt++] = d_in[p];
+                }
+            if (cnt == 0) continue;
+            for (int i = 1; i < cnt; ++i) {            /* insertion sort */
+                int t = v[i], j = i - 1;
+                while (j >= 0 && v[j] > t) { v[j + 1] = v[j]; --j; }
+                v[j + 1] = t;
+            }
+            d_out[o] = (int16_t)v[(cnt - 1) / 2];
+        }
+}
+
+/* The full method of Sec. III (Fig. 1): coarsest WTA, then (flags & 1) alpha refinement;
+ * at each finer level the beta-gated search (flags & 2; else the restricted branch only),
+ * then (flags & 4) the selective median.  Outputs as oracle_disparity: all levels, level 0
+ * first; d_all holds each level's final (post-median) map, C_all its cost (the median
+ * changes d only), C2_all the second-best cost.  Returns the evaluation count (alpha
+ * refinement counts its 3x3 x candidates evaluations), or -1 on bad arguments. */
+long long oracle_disparity_full(const uint8_t *L, const uint8_t *R, int W, int H, int D, int K,
+                                int w, int r, double alpha, double beta, int flags, int16_t *d_all,
+                                double *C_all, double *C2_all) {
+    if (W < 1 || H < 1 || D < 1 || K < 1 || w < 1 || (w & 1) == 0 || r < 0) return -1;
+    int n = w / 2;
+    size_t total = 0;
+    for (int k = 0; k < K; ++k) { int a, b; oracle_level_size(W, H, k, &a, &b); total += (size_t)a * b; }
+    uint8_t *pl = (uint8_t *)malloc(total), *pr = (uint8_t *)malloc(total);
+    size_t *off = (size_t *)malloc(sizeof(size_t) * K);
+    int16_t *tmp = (int16_t *)malloc(sizeof(int16_t) * (size_t)W * H);
+    if (!pl || !pr || !off || !tmp) { free(pl); free(pr); free(off); free(tmp); return -1; }
+    oracle_pyramid(L, W, H, K, pl);
+    oracle_pyramid(R, W, H, K, pr);
+    size_t o = 0;
+    for (int k = 0; k < K; ++k) { int a, b; oracle_level_size(W, H, k, &a, &b); off[k] = o; o += (size_t)a * b; }
+    long long evals = 0;
+    for (int k = K - 1; k >= 0; --k) {
+        int Wk, Hk, Wp = 0, Hp = 0;
+        oracle_level_size(W, H, k, &Wk, &Hk);
+        int Dk = oracle_level_disp(D, k);
+        int16_t *dk = d_all + off[k];
+        double *ck = C_all + off[k], *c2k = C2_all + off[k];
+        if (k == K - 1) {
+            evals += oracle_match_level(pl + off[k], pr + off[k], Wk, Hk, n, Dk, 0, NULL, 0, 0, dk, ck, c2k);
+            if (flags & 1) {
+                for (long i = 0; i < (long)Wk * Hk; ++i)
+                    if (ck[i] <= alpha) {
+                        int x = (int)(i % Wk), y = (int)(i / Wk);
+                        int cnt = (y > 0) + 1 + (y < Hk - 1);
+                        cnt *= (x > 0) + 1 + (x < Wk - 1);
+                        evals += (long long)cnt * ((Dk - 1 < x ? Dk - 1 : x) + 1);
+                    }
+                oracle_alpha_refine(pl + off[k], pr + off[k], Wk, Hk, n, Dk, alpha, dk, ck, c2k, NULL);
+            }
+            continue;
+        }
+        oracle_level_size(W, H, k + 1, &Wp, &Hp);
+        const int16_t *prior = d_all + off[k + 1];
+        if (flags & 2)
+            evals += oracle_match_level_beta(pl + off[k], pr + off[k], Wk, Hk, n, Dk, r, prior,
+                                             C_all + off[k + 1], Wp, Hp, beta, dk, ck, c2k, NULL, NULL);
+        else
+            evals += oracle_match_level(pl + off[k], pr + off[k], Wk, Hk, n, Dk, r, prior, Wp, Hp, dk, ck, c2k);
+        if (flags & 4) {
+            oracle_selective_median(dk, ck, Wk, Hk, alpha, tmp);
+            memcpy(dk, tmp, sizeof(int16_t) * (size_t)Wk * Hk);
+        }
+    }
+    free(pl); free(pr); free(off); free(tmp);
+    return evals;
+}
