@@ -284,7 +284,28 @@ def bench_batch(args, dev, flush, stream):
     torch.cuda.synchronize(dev)
     t_seq = sum(e0.elapsed_time(e1) for e0, e1 in ev2) / 1e3 / steps
     info = b.info()
-    return {"workload": "48 seeded mixed-size pairs (320x240 .. 1920x1080, D = W/5, K to width >= 160, "
+    # the benchmark pair alone through the persistent kernel (one launch per frame)
+    spec1 = scenes.SPECS[WORKLOAD]
+    sc1 = scenes.make_pair(spec1, 0)
+    L1 = torch.from_numpy(sc1.left).to(dev)
+    R1 = torch.from_numpy(sc1.right).to(dev)
+    one_spec = [(spec1.width, spec1.height, spec1.max_disp, spec1.levels, spec1.window, spec1.radius)]
+    sx1, zb1 = autotune.tune_batch(one_spec)
+    b1 = Batch(one_spec, sx1, zb1)
+    d1, c1 = b1.alloc_outputs()
+    for _ in range(5):
+        b1.run([L1], [R1], d1, c1)
+    b1.sync()
+    ev3 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for e0, e1 in ev3:
+        flush.zero_()
+        e0.record(stream)
+        b1.run([L1], [R1], d1, c1)
+        e1.record(stream)
+    b1.sync()
+    t_one = sum(e0.elapsed_time(e1) for e0, e1 in ev3) / 1e3 / steps
+    return {"single_pair_persistent_ms": 1e3 * t_one,
+            "workload": "48 seeded mixed-size pairs (320x240 .. 1920x1080, D = W/5, K to width >= 160, "
                         "window 5/7, r = 2), one persistent launch per pass",
             "pairs_per_s": 48 / t, "ms_per_batch": 1e3 * t, "gpix_disp_per_s": evals / t / 1e9,
             "evals_per_batch": evals, "sequential_contexts_ms": 1e3 * t_seq,
@@ -423,6 +444,27 @@ def run_gpu(args):
     bad1_f = scenes.bad_rate(df_h, sc.gt, sc.mask, 1.0)
     bad2_f = scenes.bad_rate(df_h, sc.gt, sc.mask, 2.0)
 
+    # -- the gated steps of the full method on the same pair (Sec. III-B/C/D)
+    methods = {}
+    for name, fl in (("selective_median", _lib.MSBM_FLAG_SELECTIVE_MEDIAN),
+                     ("full_method", _lib.MSBM_FLAGS_FULL_METHOD)):
+        cx = Context(W, H, spec.max_disp, spec.levels, spec.window, spec.radius, fl, alpha=0.9, beta=0.9)
+        dm = torch.empty_like(d)
+        cm = torch.empty_like(c)
+        msteps = max(3, min(args.steps, 50))
+        mms = timed(lambda: cx.disparity(L, R, dm, cm), msteps, max(3, args.warmup // 2))
+        cx.sync()
+        cx.eval_count(reset=True)
+        cx.disparity(L, R, dm, cm)
+        ev_m = cx.eval_count(reset=True)
+        dmh = dm.cpu().numpy()
+        methods[name] = {"frames_per_s": msteps / (sum(mms) / 1e3), "ms_per_frame": sum(mms) / msteps,
+                         "evals_per_frame": ev_m, "bad1": scenes.bad_rate(dmh, sc.gt, sc.mask, 1.0),
+                         "bad2": scenes.bad_rate(dmh, sc.gt, sc.mask, 2.0), "alpha": 0.9, "beta": 0.9}
+        cx.close()
+    methods["plain"] = {"frames_per_s": fps / world, "ms_per_frame": 1e3 * t_max / args.steps,
+                        "evals_per_frame": evals_per_frame, "bad1": bad1_h, "bad2": bad2_h}
+
     # -- per-kernel timing (CUDA events around each launch, same stream) -> roofline
     nprof = max(5, min(args.steps, 30))
     stage_names = ctx.stage_names()
@@ -517,6 +559,7 @@ def run_gpu(args):
                  "gpix_disp_per_s": flat_evals * flat_fps / 1e9, "evals_per_frame": flat_evals,
                  "bad1": bad1_f, "bad2": bad2_f, "steps": fsteps},
         "hier_over_flat_speedup": fps / world / flat_fps,
+        "methods": methods,
         "roofline": roof,
         "stages": stages,
         "cpu_baseline": cpu,

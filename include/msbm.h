@@ -52,6 +52,19 @@ typedef enum msbm_status {
 /* Test hook: every bounded device wait gives up at once.  The kernel records
  * MSBM_ERR_TIMEOUT, drains its own copies in flight and returns without writing outputs. */
 #define MSBM_FLAG_TEST_TIMEOUT 2u
+/* The gated steps of the full method (Sec. III), each optional; none of them is the plain
+ * method's hot path:
+ *   ALPHA_REFINE     Eq. 5-7: at the coarsest level, pixels whose cost is not above alpha
+ *                    take the argmax of the ZNCC averaged over their 3 x 3 neighbourhood;
+ *   BETA_FALLBACK    Eq. 8-9, second branch: at finer levels, pixels whose bicubic cost
+ *                    prior BI(C^{k+1}) (fine pixel (y, x) at coarse (y/2, x/2)) is not above
+ *                    beta take the full search instead of the restricted one;
+ *   SELECTIVE_MEDIAN Eq. 10: after each finer level, pixels whose cost is not above alpha
+ *                    take the lower median of the 5 x 5 neighbours whose cost is above it. */
+#define MSBM_FLAG_ALPHA_REFINE 4u
+#define MSBM_FLAG_BETA_FALLBACK 8u
+#define MSBM_FLAG_SELECTIVE_MEDIAN 16u
+#define MSBM_FLAGS_FULL_METHOD (MSBM_FLAG_ALPHA_REFINE | MSBM_FLAG_BETA_FALLBACK | MSBM_FLAG_SELECTIVE_MEDIAN)
 
 /* Problem statement (Sec. III; window and pyramid depth as in Sec. IV). */
 typedef struct msbm_params {
@@ -61,6 +74,8 @@ typedef struct msbm_params {
     int32_t window;        /* odd window side 2n+1, 3..13 (int32-exact sums up to 13x13)   */
     int32_t radius;        /* r, 0..16: refinement candidates dhat-r .. dhat+r              */
     uint32_t flags;        /* MSBM_FLAG_*                                                   */
+    float alpha;           /* threshold of ALPHA_REFINE and SELECTIVE_MEDIAN (paper: 0.9)  */
+    float beta;            /* threshold of BETA_FALLBACK (paper: 0.9)                      */
 } msbm_params;
 
 typedef struct msbm_ctx msbm_ctx;
@@ -103,8 +118,25 @@ msbm_status msbm_level_image(msbm_ctx *ctx, int32_t level, int32_t which, uint8_
 msbm_status msbm_match_level(msbm_ctx *ctx, int32_t level, const int16_t *d_prior,
                              int16_t *d_out, float *cost_out);
 
+/* Gated steps on caller buffers of level `level` (dense W_k x H_k), for step-by-step use and
+ * tests; msbm_disparity chains them itself when the flags ask for them.
+ *   msbm_alpha_refine      : Eq. 5-7 in place on (d, cost), using the pyramid built by
+ *                            msbm_pyramid; pixels with cost > alpha are untouched.
+ *   msbm_selective_median  : Eq. 10, d_out from (d_in, cost); d_out must not alias d_in.
+ *   msbm_match_level_beta  : Eq. 8-9 with both branches: prior and cost_prior are the
+ *                            coarser level's maps (W_{k+1} x H_{k+1}); fallback_out (may
+ *                            be NULL) receives 1 where the full search was taken. */
+msbm_status msbm_alpha_refine(msbm_ctx *ctx, int32_t level, int16_t *d, float *cost);
+msbm_status msbm_selective_median(msbm_ctx *ctx, int32_t level, const int16_t *d_in,
+                                  const float *cost, int16_t *d_out);
+msbm_status msbm_match_level_beta(msbm_ctx *ctx, int32_t level, const int16_t *d_prior,
+                                  const float *cost_prior, int16_t *d_out, float *cost_out,
+                                  uint8_t *fallback_out);
+
 /* The whole hierarchical pass on device images: pyramid, coarsest full search, then the
- * restricted search at every finer level.  Writes the level-0 maps.  Replays a CUDA graph
+ * restricted search at every finer level, with the gated steps the context's flags select.
+ * Writes the level-0 maps (with SELECTIVE_MEDIAN, d_out holds the filtered map and cost_out
+ * the matching cost it was filtered with).  Replays a CUDA graph
  * (re-captured when a pointer changes) unless MSBM_FLAG_NO_GRAPH. */
 msbm_status msbm_disparity(msbm_ctx *ctx, const uint8_t *d_left, const uint8_t *d_right,
                            size_t pitch_bytes, int16_t *d_out, float *cost_out);

@@ -21,6 +21,10 @@ MSBM_ERR_UNSUPPORTED = 6
 
 MSBM_FLAG_NO_GRAPH = 1
 MSBM_FLAG_TEST_TIMEOUT = 2
+MSBM_FLAG_ALPHA_REFINE = 4
+MSBM_FLAG_BETA_FALLBACK = 8
+MSBM_FLAG_SELECTIVE_MEDIAN = 16
+MSBM_FLAGS_FULL_METHOD = 28
 
 # Every function the header declares, with its ctypes signature.
 c_void_p, c_int32, c_uint32, c_size_t = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_size_t
@@ -30,7 +34,7 @@ P = ctypes.POINTER
 class msbm_params(ctypes.Structure):
     _fields_ = [("width", c_int32), ("height", c_int32), ("max_disp", c_int32),
                 ("levels", c_int32), ("window", c_int32), ("radius", c_int32),
-                ("flags", c_uint32)]
+                ("flags", c_uint32), ("alpha", ctypes.c_float), ("beta", ctypes.c_float)]
 
 
 SIGNATURES = {
@@ -49,6 +53,9 @@ SIGNATURES = {
     "msbm_profile_disparity": ([c_void_p, c_void_p, c_void_p, c_size_t, c_void_p, c_void_p,
                                 P(ctypes.c_float), c_int32], ctypes.c_int),
     "msbm_sync": ([c_void_p], ctypes.c_int),
+    "msbm_alpha_refine": ([c_void_p, c_int32, c_void_p, c_void_p], ctypes.c_int),
+    "msbm_selective_median": ([c_void_p, c_int32, c_void_p, c_void_p, c_void_p], ctypes.c_int),
+    "msbm_match_level_beta": ([c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], ctypes.c_int),
     "msbm_eval_count": ([c_void_p, P(ctypes.c_int64), c_int32], ctypes.c_int),
     "msbm_set_level_tuning": ([c_void_p, c_int32, c_int32, c_int32], ctypes.c_int),
     "msbm_batch_create": ([P(msbm_params), c_int32, c_void_p, c_void_p, c_void_p, P(c_void_p)], ctypes.c_int),

@@ -26,7 +26,7 @@ class Batch:
         n = len(self.specs)
         arr = (_lib.msbm_params * n)()
         for i, (w, h, d, k, win, r) in enumerate(self.specs):
-            arr[i] = _lib.msbm_params(w, h, d, k, win, r, flags)
+            arr[i] = _lib.msbm_params(w, h, d, k, win, r, flags, 0.9, 0.9)
         sx = (ctypes.c_int32 * n)(*full_sx) if full_sx is not None else None
         zb = (ctypes.c_int32 * n)(*full_zblock) if full_zblock is not None else None
         self.device = torch.device("cuda", torch.cuda.current_device())

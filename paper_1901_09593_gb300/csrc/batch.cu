@@ -5,7 +5,7 @@
 //   stage 0          level-0 copy into the pair's apron buffers      (row bands)
 //   stage 1 .. K-1   pyramid reduce producing level k                 (row bands)
 //   stage K          full-range search at level K-1 (Eq. 3-4)         (TX x 8 tiles)
-//   stage K+1+j      restricted search at level K-2-j (Eq. 8-9)       (32 x 8 tiles)
+//   stage K+1+j      restricted search at level K-2-j (Eq. 8-9)       (64 x 16 tiles)
 // Stage s of a pair needs every tile of stage s-1 of the same pair.  The host lays the
 // (pair, stage) segments out stage-major (stage 0 of every pair, then stage 1, ...), which is
 // a topological order, and the CTAs of one persistent grid take items from the flattened
@@ -47,6 +47,7 @@ constexpr int BT_THREADS = 256;
 constexpr int BT_BAND = 16;          // apron rows per copy/reduce item
 constexpr int BT_MAX_NH = 4;         // windows up to 9 x 9
 constexpr int BT_ZC = 4;             // candidates per lane chunk in batched full-range tiles
+constexpr int BT_RTX = RCfg<1, 32>::TX;   // restricted tile width (64 pixels, 256 threads)
 constexpr long long BT_WAIT_LIMIT = 4000000000LL;   // ~2 s at 2 GHz
 constexpr long long BT_TEST_WAIT_LIMIT = 2000000LL; // ~1 ms (MSBM_FLAG_TEST_TIMEOUT)
 
@@ -65,7 +66,7 @@ struct BPair {
 };
 
 struct BMaps {               // TMA descriptors of one (pair, level), 64-byte aligned
-    CUtensorMap m64L, m64R, m256R, mFL;
+    CUtensorMap mRL, mR128, mR256, mF256, mFL;
 };
 
 struct BIO {                 // per-run caller pointers of one pair
@@ -112,18 +113,18 @@ __device__ bool run_match(const BatchArgs &a, const BPair &P, const BMaps *mp, c
     if (stage == K) {                                    // coarsest full search
         const int k = K - 1;
         const BLevel &l = P.lv[k];
-        FullTileArgs t;
+        FullTileArgs t = {};   // no gating in the batch: mask / tile flags stay NULL
         t.W = l.W; t.H = l.H; t.Dk = l.Dk; t.zblock = l.zblock;
         t.d_out = k == 0 ? io.d : l.d;
         t.c_out = k == 0 ? io.c : l.c;
         t.evals = a.evals; t.err = a.err; t.force_timeout = 0;
         const int bx = tile % l.tiles_x, by = tile / l.tiles_x;
-        if (l.sx == 1) return full_tile<NH, 1, BT_ZC>(t, &mp[k].mFL, &mp[k].m256R, bx, by, smem, parity);
-        return full_tile<NH, 2, BT_ZC>(t, &mp[k].mFL, &mp[k].m256R, bx, by, smem, parity);
+        if (l.sx == 1) return full_tile<NH, 1, BT_ZC>(t, &mp[k].mFL, &mp[k].mF256, bx, by, smem, parity);
+        return full_tile<NH, 2, BT_ZC>(t, &mp[k].mFL, &mp[k].mF256, bx, by, smem, parity);
     }
     const int k = K - 2 - (stage - K - 1);              // restricted level
     const BLevel &l = P.lv[k];
-    RestrTileArgs t;
+    RestrTileArgs t = {};
     t.Limg = l.L; t.Rimg = l.R; t.pitch = l.pitch;
     t.W = l.W; t.H = l.H; t.Dk = l.Dk; t.r = P.r;
     t.prior = P.lv[k + 1].d; t.Wp = P.lv[k + 1].W; t.Hp = P.lv[k + 1].H;
@@ -132,10 +133,10 @@ __device__ bool run_match(const BatchArgs &a, const BPair &P, const BMaps *mp, c
     t.evals = a.evals; t.err = a.err; t.force_timeout = 0;
     const int bx = tile % l.tiles_x, by = tile / l.tiles_x;
     switch (P.r) {
-        case 0: return restr_tile<NH, 1>(t, &mp[k].m64L, &mp[k].m64R, &mp[k].m256R, bx, by, smem, parity);
-        case 1: return restr_tile<NH, 3>(t, &mp[k].m64L, &mp[k].m64R, &mp[k].m256R, bx, by, smem, parity);
-        case 2: return restr_tile<NH, 5>(t, &mp[k].m64L, &mp[k].m64R, &mp[k].m256R, bx, by, smem, parity);
-        default: return restr_tile<NH, 7>(t, &mp[k].m64L, &mp[k].m64R, &mp[k].m256R, bx, by, smem, parity);
+        case 0: return restr_tile<NH, 1>(t, &mp[k].mRL, &mp[k].mR128, &mp[k].mR256, bx, by, smem, parity);
+        case 1: return restr_tile<NH, 3>(t, &mp[k].mRL, &mp[k].mR128, &mp[k].mR256, bx, by, smem, parity);
+        case 2: return restr_tile<NH, 5>(t, &mp[k].mRL, &mp[k].mR128, &mp[k].mR256, bx, by, smem, parity);
+        default: return restr_tile<NH, 7>(t, &mp[k].mRL, &mp[k].mR128, &mp[k].mR256, bx, by, smem, parity);
     }
 }
 
@@ -346,7 +347,7 @@ msbm_status msbm_batch_create(const msbm_params *pairs, int32_t n_pairs, const i
         memset(&P, 0, sizeof(P));
         P.W = p.width; P.H = p.height; P.D = p.max_disp; P.K = p.levels; P.nh = p.window / 2; P.r = p.radius;
         int W = p.width, H = p.height;
-        const int rowsT = 8 + 2 * P.nh;
+        const int rowsF = 8 + 2 * P.nh, rowsR = RT_TY + 2 * P.nh;
         for (int k = 0; k < P.K && e == cudaSuccess; ++k) {
             BLevel &l = P.lv[k];
             l.W = W; l.H = H;
@@ -366,12 +367,13 @@ msbm_status msbm_batch_create(const msbm_params *pairs, int32_t n_pairs, const i
             }
             l.sx = full_sx ? full_sx[i] : (W >= 512 ? 2 : 1);
             l.zblock = full_zblock ? full_zblock[i] : 0;
-            l.tiles_x = (k == P.K - 1) ? (W + 32 * l.sx - 1) / (32 * l.sx) : (W + 31) / 32;
+            l.tiles_x = (k == P.K - 1) ? (W + 32 * l.sx - 1) / (32 * l.sx) : (W + BT_RTX - 1) / BT_RTX;
             BMaps &m = maps[(size_t)i * BT_MAXK + k];
-            enc_ok = enc_ok && encode_b(&m.m64L, buf, l.pitch, rows, 64, rowsT) &&
-                     encode_b(&m.m64R, buf + bytes, l.pitch, rows, 64, rowsT) &&
-                     encode_b(&m.m256R, buf + bytes, l.pitch, rows, 256, rowsT) &&
-                     encode_b(&m.mFL, buf, l.pitch, rows, 32 * l.sx + 32, rowsT);
+            enc_ok = enc_ok && encode_b(&m.mRL, buf, l.pitch, rows, BT_RTX + 32, rowsR) &&
+                     encode_b(&m.mR128, buf + bytes, l.pitch, rows, 128, rowsR) &&
+                     encode_b(&m.mR256, buf + bytes, l.pitch, rows, 256, rowsR) &&
+                     encode_b(&m.mF256, buf + bytes, l.pitch, rows, 256, rowsF) &&
+                     encode_b(&m.mFL, buf, l.pitch, rows, 32 * l.sx + 32, rowsF);
             W = (W + 1) / 2;
             H = (H + 1) / 2;
         }
@@ -388,7 +390,8 @@ msbm_status msbm_batch_create(const msbm_params *pairs, int32_t n_pairs, const i
     auto ntiles = [](const BPair &P, int s) {
         if (s < P.K) return (P.lv[s].H + 2 * APY + BT_BAND - 1) / BT_BAND;
         const int k = s == P.K ? P.K - 1 : P.K - 2 - (s - P.K - 1);
-        return P.lv[k].tiles_x * ((P.lv[k].H + 7) / 8);
+        const int th = s == P.K ? 8 : RT_TY;   // full-range tiles are 8 rows, restricted 16
+        return P.lv[k].tiles_x * ((P.lv[k].H + th - 1) / th);
     };
     long long pos = 0;
     for (int s = 0; s < max_stages; ++s) {

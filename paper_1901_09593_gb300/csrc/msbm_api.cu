@@ -35,6 +35,8 @@ struct msbm_ctx {
     cudaGraphExec_t exec = nullptr;
     const void *gkey[4] = {nullptr, nullptr, nullptr, nullptr};
     size_t gpitch = 0;
+    // level-0 cost when the caller passes none but a gated step needs one
+    float *c0 = nullptr;
     // device staging of msbm_disparity_host
     uint8_t *hL = nullptr, *hR = nullptr;
     int16_t *hd = nullptr;
@@ -76,7 +78,10 @@ msbm_status validate(const msbm_params *p) {
     if (p->levels < 1 || p->levels > 12) return MSBM_ERR_INVALID_ARG;
     if (p->window < 3 || p->window > 13 || (p->window & 1) == 0) return MSBM_ERR_INVALID_ARG;
     if (p->radius < 0 || p->radius > 16) return MSBM_ERR_INVALID_ARG;
-    if (p->flags & ~(MSBM_FLAG_NO_GRAPH | MSBM_FLAG_TEST_TIMEOUT)) return MSBM_ERR_INVALID_ARG;
+    if (p->flags & ~(MSBM_FLAG_NO_GRAPH | MSBM_FLAG_TEST_TIMEOUT | MSBM_FLAGS_FULL_METHOD)) return MSBM_ERR_INVALID_ARG;
+    if ((p->flags & (MSBM_FLAG_ALPHA_REFINE | MSBM_FLAG_SELECTIVE_MEDIAN)) && !(p->alpha > -2.f && p->alpha < 2.f))
+        return MSBM_ERR_INVALID_ARG;
+    if ((p->flags & MSBM_FLAG_BETA_FALLBACK) && !(p->beta > -2.f && p->beta < 2.f)) return MSBM_ERR_INVALID_ARG;
     return MSBM_OK;
 }
 
@@ -95,7 +100,11 @@ void free_ctx(msbm_ctx *c) {
         cudaFree(l.base[0]);
         cudaFree(l.d);
         cudaFree(l.c);
+        cudaFree(l.dtmp);
+        cudaFree(l.mask);
+        cudaFree(l.tile_flags);
     }
+    cudaFree(c->c0);
     cudaFree(c->d_err);
     cudaFree(c->d_evals);
     cudaFree(c->hL);
@@ -120,25 +129,29 @@ msbm_status enqueue_pyramid(msbm_ctx *c, const uint8_t *L, const uint8_t *R, siz
 }
 
 msbm_status enqueue_level(msbm_ctx *c, int k, const int16_t *prior, int16_t *d, float *cost,
-                          cudaStream_t st) {
+                          cudaStream_t st, const uint8_t *mask = nullptr, const int *tile_flags = nullptr,
+                          const uint8_t *skip = nullptr) {
     const LevelBuf &l = c->lv[k];
     const int force = (c->p.flags & MSBM_FLAG_TEST_TIMEOUT) ? 1 : 0;
     cudaError_t e;
     if (!prior) {
         FullArgs a;
         memset(&a, 0, sizeof(a));
-        a.tmL = l.tmFL[0];
-        a.tmR = l.tm256[1];
+        a.tmL = l.tmFL;
+        a.tmR = l.tmR256;
         a.t.W = l.W; a.t.H = l.H; a.t.Dk = l.Dk; a.t.zblock = l.full_zblock;
+        a.t.mask = mask; a.t.tile_flags = tile_flags;
+        a.t.tiles_x = (l.W + 32 * l.full_sx - 1) / (32 * l.full_sx);
         a.t.d_out = d; a.t.c_out = cost;
         a.t.evals = c->d_evals; a.t.err = c->d_err; a.t.force_timeout = force;
         e = launch_zncc_full(a, c->nh, l.full_sx, st);
     } else {
         RestrArgs a;
         memset(&a, 0, sizeof(a));
-        a.tmL = l.tm64[0];
-        a.tmR64 = l.tm64[1];
-        a.tmR256 = l.tm256[1];
+        a.tmL = l.tmL64;
+        a.tmR64 = l.tmR64;
+        a.tmR256 = l.tmR256;
+        a.t.skip = skip;
         a.t.Limg = l.img(0); a.t.Rimg = l.img(1); a.t.pitch = l.pitch;
         a.t.W = l.W; a.t.H = l.H; a.t.Dk = l.Dk; a.t.r = c->p.radius;
         a.t.prior = prior; a.t.Wp = (l.W + 1) / 2; a.t.Hp = (l.H + 1) / 2;
@@ -149,15 +162,44 @@ msbm_status enqueue_level(msbm_ctx *c, int k, const int16_t *prior, int16_t *d, 
     return cuda_status(e);
 }
 
+// Eq. 8-9 with both branches at level k: gate from the coarser cost, restricted search for
+// every pixel (fallback pixels are not counted), then the full search over the flagged
+// tiles writing the fallback pixels.
+msbm_status enqueue_level_beta(msbm_ctx *c, int k, const int16_t *prior, const float *cprior, int16_t *d,
+                               float *cost, cudaStream_t st) {
+    LevelBuf &l = c->lv[k];
+    const LevelBuf &lp = c->lv[k + 1];
+    cudaError_t e = launch_beta_gate(cprior, lp.W, lp.H, l.W, l.H, c->p.beta, l.mask, l.tile_flags,
+                                     32 * l.full_sx, 8, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    msbm_status s = enqueue_level(c, k, prior, d, cost, st, nullptr, nullptr, l.mask);
+    if (s != MSBM_OK) return s;
+    return enqueue_level(c, k, nullptr, d, cost, st, l.mask, l.tile_flags);
+}
+
 msbm_status enqueue_all(msbm_ctx *c, const uint8_t *L, const uint8_t *R, size_t pitch, int16_t *d,
                         float *cost, cudaStream_t st) {
     msbm_status s = enqueue_pyramid(c, L, R, pitch, st);
     const int K = c->p.levels;
+    const uint32_t f = c->p.flags;
     for (int k = K - 1; s == MSBM_OK && k >= 0; --k) {
-        int16_t *dk = k == 0 ? d : c->lv[k].d;
-        float *ck = k == 0 ? cost : c->lv[k].c;
-        const int16_t *prior = k == K - 1 ? nullptr : c->lv[k + 1].d;
-        s = enqueue_level(c, k, prior, dk, ck, st);
+        LevelBuf &l = c->lv[k];
+        int16_t *dk = k == 0 ? d : l.d;                        // final map of this level
+        float *ck = k == 0 ? (cost ? cost : c->c0) : l.c;      // its cost
+        if (k == K - 1) {
+            s = enqueue_level(c, k, nullptr, dk, ck, st);
+            if (s == MSBM_OK && (f & MSBM_FLAG_ALPHA_REFINE))
+                s = cuda_status(launch_alpha_refine(l, c->nh, c->p.alpha, dk, ck, c->d_evals, st));
+            continue;
+        }
+        const int16_t *prior = c->lv[k + 1].d;
+        const bool med = (f & MSBM_FLAG_SELECTIVE_MEDIAN) != 0;
+        int16_t *dm = med ? l.dtmp : dk;                      // matching output
+        if (f & MSBM_FLAG_BETA_FALLBACK)
+            s = enqueue_level_beta(c, k, prior, c->lv[k + 1].c, dm, ck, st);
+        else
+            s = enqueue_level(c, k, prior, dm, ck, st);
+        if (s == MSBM_OK && med) s = cuda_status(launch_selective_median(dm, ck, l.W, l.H, c->p.alpha, dk, st));
     }
     return s;
 }
@@ -200,7 +242,7 @@ msbm_status msbm_create(const msbm_params *params, void *cuda_stream, msbm_ctx *
     c->device = dev;
     c->num_sms = prop.multiProcessorCount;
     c->stream = static_cast<cudaStream_t>(cuda_stream);
-    const int rowsT = 8 + 2 * c->nh;
+    const int rowsT = 8 + 2 * c->nh;   // staged rows of the full-range and restricted tiles
     cudaError_t e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_evals, sizeof(unsigned long long));
@@ -222,11 +264,21 @@ msbm_status msbm_create(const msbm_params *params, void *cuda_stream, msbm_ctx *
         e = cudaMemset(buf, 0, 2 * bytes);
         if (e == cudaSuccess && k > 0) e = cudaMalloc(&l.d, (size_t)W * H * sizeof(int16_t));
         if (e == cudaSuccess && k > 0) e = cudaMalloc(&l.c, (size_t)W * H * sizeof(float));
+        const bool finer = k < params->levels - 1;
+        if (e == cudaSuccess && finer && (params->flags & MSBM_FLAG_SELECTIVE_MEDIAN))
+            e = cudaMalloc(&l.dtmp, (size_t)W * H * sizeof(int16_t));
+        if (e == cudaSuccess && finer && (params->flags & MSBM_FLAG_BETA_FALLBACK)) {
+            const int sx = choose_sx(W, H, c->num_sms);
+            const long tiles = (long)((W + 32 * sx - 1) / (32 * sx)) * ((H + 7) / 8);
+            e = cudaMalloc(&l.mask, (size_t)W * H);
+            if (e == cudaSuccess) e = cudaMalloc(&l.tile_flags, sizeof(int) * tiles);
+        }
         l.full_sx = choose_sx(W, H, c->num_sms);
-        for (int i = 0; e == cudaSuccess && i < 2; ++i) {
-            bool ok = encode_u8(&l.tm64[i], l.base[i], l.pitch, l.rows, 64, rowsT) &&
-                      encode_u8(&l.tm256[i], l.base[i], l.pitch, l.rows, 256, rowsT) &&
-                      encode_u8(&l.tmFL[i], l.base[i], l.pitch, l.rows, 32 * l.full_sx + 32, rowsT);
+        if (e == cudaSuccess) {
+            bool ok = encode_u8(&l.tmL64, l.base[0], l.pitch, l.rows, 64, rowsT) &&
+                      encode_u8(&l.tmR64, l.base[1], l.pitch, l.rows, 64, rowsT) &&
+                      encode_u8(&l.tmR256, l.base[1], l.pitch, l.rows, 256, rowsT) &&
+                      encode_u8(&l.tmFL, l.base[0], l.pitch, l.rows, 32 * l.full_sx + 32, rowsT);
             if (!ok) { c->lv.push_back(l); free_ctx(c); return MSBM_ERR_UNSUPPORTED; }
         }
         if (e == cudaSuccess) e = zncc_full_prepare(c->nh, l.full_sx);
@@ -234,6 +286,8 @@ msbm_status msbm_create(const msbm_params *params, void *cuda_stream, msbm_ctx *
         W = (W + 1) / 2;
         H = (H + 1) / 2;
     }
+    if (e == cudaSuccess && (params->flags & MSBM_FLAGS_FULL_METHOD))
+        e = cudaMalloc(&c->c0, (size_t)params->width * params->height * sizeof(float));
     if (e != cudaSuccess) {
         msbm_status st = cuda_status(e);
         free_ctx(c);
@@ -271,8 +325,7 @@ msbm_status msbm_set_level_tuning(msbm_ctx *ctx, int32_t level, int32_t sx, int3
     if ((sx != 1 && sx != 2 && sx != 4) || zblock < 0 || zblock % 32 != 0) return MSBM_ERR_INVALID_ARG;
     LevelBuf &l = ctx->lv[level];
     const int rowsT = 8 + 2 * ctx->nh;
-    for (int i = 0; i < 2; ++i)
-        if (!encode_u8(&l.tmFL[i], l.base[i], l.pitch, l.rows, 32 * sx + 32, rowsT)) return MSBM_ERR_UNSUPPORTED;
+    if (!encode_u8(&l.tmFL, l.base[0], l.pitch, l.rows, 32 * sx + 32, rowsT)) return MSBM_ERR_UNSUPPORTED;
     cudaError_t e = zncc_full_prepare(ctx->nh, sx);
     if (e != cudaSuccess) return cuda_status(e);
     l.full_sx = sx;
@@ -300,6 +353,32 @@ msbm_status msbm_match_level(msbm_ctx *ctx, int32_t level, const int16_t *d_prio
                              float *cost_out) {
     if (!ctx || level < 0 || level >= ctx->p.levels || !d_out) return MSBM_ERR_INVALID_ARG;
     return enqueue_level(ctx, level, d_prior, d_out, cost_out, ctx->stream);
+}
+
+msbm_status msbm_alpha_refine(msbm_ctx *ctx, int32_t level, int16_t *d, float *cost) {
+    if (!ctx || level < 0 || level >= ctx->p.levels || !d || !cost) return MSBM_ERR_INVALID_ARG;
+    return cuda_status(launch_alpha_refine(ctx->lv[level], ctx->nh, ctx->p.alpha, d, cost, ctx->d_evals, ctx->stream));
+}
+
+msbm_status msbm_selective_median(msbm_ctx *ctx, int32_t level, const int16_t *d_in, const float *cost,
+                                  int16_t *d_out) {
+    if (!ctx || level < 0 || level >= ctx->p.levels || !d_in || !cost || !d_out || d_in == d_out)
+        return MSBM_ERR_INVALID_ARG;
+    const LevelBuf &l = ctx->lv[level];
+    return cuda_status(launch_selective_median(d_in, cost, l.W, l.H, ctx->p.alpha, d_out, ctx->stream));
+}
+
+msbm_status msbm_match_level_beta(msbm_ctx *ctx, int32_t level, const int16_t *d_prior, const float *cost_prior,
+                                  int16_t *d_out, float *cost_out, uint8_t *fallback_out) {
+    if (!ctx || level < 0 || level >= ctx->p.levels - 1 || !d_prior || !cost_prior || !d_out || !cost_out)
+        return MSBM_ERR_INVALID_ARG;
+    if (!(ctx->p.flags & MSBM_FLAG_BETA_FALLBACK)) return MSBM_ERR_INVALID_ARG;   // buffers not allocated
+    msbm_status s = enqueue_level_beta(ctx, level, d_prior, cost_prior, d_out, cost_out, ctx->stream);
+    if (s == MSBM_OK && fallback_out) {
+        const LevelBuf &l = ctx->lv[level];
+        s = cuda_status(cudaMemcpyAsync(fallback_out, l.mask, (size_t)l.W * l.H, cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    return s;
 }
 
 msbm_status msbm_disparity(msbm_ctx *ctx, const uint8_t *d_left, const uint8_t *d_right,

@@ -20,13 +20,15 @@ struct LevelBuf {
     uint8_t *base[2] = {nullptr, nullptr};  // buffer starts: image pixel (-APY, -APX)
     int16_t *d = nullptr;        // this level's disparity map (levels >= 1)
     float *c = nullptr;          // this level's cost map (levels >= 1)
-    // TMA maps over the apron buffers.  Boxes are ROWS = 8 + 2n rows high:
-    //   tm64[i]  : 64 bytes wide  (restricted-kernel left tile and narrow right spans)
-    //   tm256[i] : 256 bytes wide (wide right spans, full-range right spans)
-    //   tmFL[i]  : 32*SX + 32 bytes wide (full-range left tile), SX chosen per level
-    CUtensorMap tm64[2];
-    CUtensorMap tm256[2];
-    CUtensorMap tmFL[2];
+    int16_t *dtmp = nullptr;     // pre-median disparity map (SELECTIVE_MEDIAN)
+    uint8_t *mask = nullptr;     // fallback mask (BETA_FALLBACK)
+    int *tile_flags = nullptr;   // full-range tiles holding a fallback pixel (BETA_FALLBACK)
+    // TMA maps over the apron buffers, all 8 + 2n rows high:
+    //   tmL64  : left,  64 bytes wide  (restricted tile's left tile)
+    //   tmR64  : right, 64 bytes wide  (restricted tile's narrow right spans)
+    //   tmR256 : right, 256 bytes wide (restricted wide spans, full-range right spans)
+    //   tmFL   : left,  32*SX + 32 bytes wide (full-range left tile), SX per level
+    CUtensorMap tmL64, tmR64, tmR256, tmFL;
     int full_sx = 4;             // full-range tile width 32*full_sx at this level
     int full_zblock = 0;         // full-range z-block (0 = the tile's maximum)
     uint8_t *img(int which) const {
@@ -38,6 +40,11 @@ struct LevelBuf {
 struct FullTileArgs {
     int W, H, Dk;
     int zblock;          // candidates staged per pass (multiple of 32; 0 = the tile's maximum)
+    // gated pass (beta fallback): only tiles whose flag is set run, only masked pixels are
+    // written and counted; both NULL for the ordinary full-range search
+    const uint8_t *mask;
+    const int *tile_flags;
+    int tiles_x;
     int16_t *d_out;
     float *c_out;
     unsigned long long *evals;
@@ -53,6 +60,7 @@ struct FullArgs {
 
 // Per-tile arguments of the restricted ZNCC tile (zncc_restricted_tile.cuh).
 struct RestrTileArgs {
+    const uint8_t *skip; // NULL, or pixels a later gated pass overwrites (not counted here)
     const uint8_t *Limg; // level image origins (apron buffers), for the wide-span path
     const uint8_t *Rimg;
     int pitch;
@@ -67,9 +75,9 @@ struct RestrTileArgs {
 };
 
 struct RestrArgs {
-    CUtensorMap tmL;     // box {64, 8 + 2n}
-    CUtensorMap tmR64;   // box {64, 8 + 2n}
-    CUtensorMap tmR256;  // box {256, 8 + 2n}
+    CUtensorMap tmL;     // box {64, 8 + 2n} over the left apron buffer
+    CUtensorMap tmR64;   // box {64, 8 + 2n} over the right apron buffer
+    CUtensorMap tmR256;  // box {256, 8 + 2n} over the right apron buffer
     RestrTileArgs t;
 };
 
@@ -78,6 +86,12 @@ cudaError_t launch_apron_copy(const uint8_t *L, const uint8_t *R, size_t spitch,
 cudaError_t launch_pyr_reduce(const LevelBuf &src, const LevelBuf &dst, cudaStream_t st);
 cudaError_t launch_level_extract(const LevelBuf &lv, int which, uint8_t *out, cudaStream_t st);
 cudaError_t launch_zncc_full(const FullArgs &a, int nh, int sx, cudaStream_t st);
+cudaError_t launch_beta_gate(const float *Cc, int Wc, int Hc, int W, int H, float beta, uint8_t *mask,
+                             int *tile_flags, int tile_w, int tile_h, cudaStream_t st);
+cudaError_t launch_alpha_refine(const LevelBuf &l, int nh, float alpha, int16_t *d, float *C,
+                                unsigned long long *evals, cudaStream_t st);
+cudaError_t launch_selective_median(const int16_t *d_in, const float *C, int W, int H, float alpha, int16_t *d_out,
+                                    cudaStream_t st);
 cudaError_t zncc_full_prepare(int nh, int sx);
 cudaError_t launch_zncc_restricted(const RestrArgs &a, int nh, cudaStream_t st);
 size_t zncc_full_smem_bytes(int nh, int sx);

@@ -123,12 +123,12 @@ extern "C" msbm_status msbm_flat_disparity_noalloc(const uint8_t *d_left, const 
     lv.rows = rows;
     lv.base[0] = scratch + 256;
     lv.base[1] = scratch + 256 + img_bytes;
-    const int nh = window / 2, rowsT = 8 + 2 * nh;
+    const int nh = window / 2, rowsF = 8 + 2 * nh;
     const int sx = pick_sx(width, height, g_num_sms[dev]);
     FullArgs a;
     memset(&a, 0, sizeof(a));
-    if (!encode_map(&a.tmL, lv.base[0], pitch, rows, 32 * sx + 32, rowsT) ||
-        !encode_map(&a.tmR, lv.base[1], pitch, rows, 256, rowsT))
+    if (!encode_map(&a.tmL, lv.base[0], pitch, rows, 32 * sx + 32, rowsF) ||
+        !encode_map(&a.tmR, lv.base[1], pitch, rows, 256, rowsF))
         return MSBM_ERR_UNSUPPORTED;
     a.t.W = width;
     a.t.H = height;

@@ -17,19 +17,45 @@
 namespace msbm {
 
 // Level 0: copy the caller's image (any pitch) into the apron buffer with replication.
-// One thread per 4 consecutive output bytes; blockIdx.z selects left (0) / right (1).
+// One thread per 16 consecutive output bytes of one apron row; blockIdx.z selects left (0)
+// / right (1).  Interior runs whose source is 8-byte aligned are moved with two 8-byte
+// loads and one 16-byte store; runs touching the apron or misaligned fall back to bytes.
 __global__ void apron_copy_kernel(const uint8_t *__restrict__ srcL, const uint8_t *__restrict__ srcR,
                                   size_t spitch, int W, int H, uint8_t *dstL, uint8_t *dstR,
                                   int dpitch) {
     const uint8_t *src = blockIdx.z ? srcR : srcL;
     uint8_t *dst = blockIdx.z ? dstR : dstL;   // points at image (0, 0)
-    int X0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4 - APX;
-    int Y = blockIdx.y * blockDim.y + threadIdx.y - APY;
+    const int X0 = (blockIdx.x * blockDim.x + threadIdx.x) * 16 - APX;
+    const int Y = blockIdx.y * blockDim.y + threadIdx.y - APY;
     if (Y >= H + APY || X0 >= W + APX) return;
-    copy_quad(src, spitch, W, H, dst, dpitch, X0, Y);
+    const int y = min(max(Y, 0), H - 1);
+    const uint8_t *row = src + (size_t)y * spitch;
+    uint4 out;
+    if (X0 >= 0 && X0 + 16 <= W && ((reinterpret_cast<uintptr_t>(row + X0) & 7) == 0)) {
+        const uint2 a = __ldg(reinterpret_cast<const uint2 *>(row + X0));
+        const uint2 b = __ldg(reinterpret_cast<const uint2 *>(row + X0 + 8));
+        out = make_uint4(a.x, a.y, b.x, b.y);
+    } else {
+        uint32_t w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint32_t v = 0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int x = min(max(X0 + 4 * q + i, 0), W - 1);
+                v |= static_cast<uint32_t>(__ldg(row + x)) << (8 * i);
+            }
+            w[q] = v;
+        }
+        out = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    // X0 + APX is a multiple of 16 and rows are 128-byte aligned; the 16 bytes may run past
+    // W + APX into the row's padding (the pitch is a multiple of 128 >= W + 2*APX).
+    *reinterpret_cast<uint4 *>(dst + (ptrdiff_t)Y * dpitch + X0) = out;
 }
 
-// Level k from level k-1.  One thread per 4 consecutive output bytes.
+// Level k from level k-1.  One thread per 4 consecutive output bytes (the 5x5 support is
+// read through the L1 cache; at these level sizes this beats a shared-memory staging pass).
 __global__ void pyr_reduce_kernel(const uint8_t *__restrict__ srcL, const uint8_t *__restrict__ srcR,
                                   int spitch, uint8_t *dstL, uint8_t *dstR, int dpitch, int Wd,
                                   int Hd) {
@@ -41,24 +67,21 @@ __global__ void pyr_reduce_kernel(const uint8_t *__restrict__ srcL, const uint8_
     reduce_quad(src, spitch, dst, dpitch, Wd, Hd, X0, Y);
 }
 
-static dim3 apron_grid(int W, int H, dim3 blk) {
-    int cols4 = (W + 2 * APX + 3) / 4;
-    return dim3((cols4 + blk.x - 1) / blk.x, (H + 2 * APY + blk.y - 1) / blk.y, 2);
-}
-
 cudaError_t launch_apron_copy(const uint8_t *L, const uint8_t *R, size_t spitch, const LevelBuf &lv,
                               cudaStream_t st) {
     dim3 blk(32, 8);
-    apron_copy_kernel<<<apron_grid(lv.W, lv.H, blk), blk, 0, st>>>(L, R, spitch, lv.W, lv.H, lv.img(0),
-                                                                 lv.img(1), lv.pitch);
+    const int cols16 = (lv.W + 2 * APX + 15) / 16;
+    dim3 grd((cols16 + blk.x - 1) / blk.x, (lv.H + 2 * APY + blk.y - 1) / blk.y, 2);
+    apron_copy_kernel<<<grd, blk, 0, st>>>(L, R, spitch, lv.W, lv.H, lv.img(0), lv.img(1), lv.pitch);
     return cudaGetLastError();
 }
 
 cudaError_t launch_pyr_reduce(const LevelBuf &src, const LevelBuf &dst, cudaStream_t st) {
     dim3 blk(32, 8);
-    pyr_reduce_kernel<<<apron_grid(dst.W, dst.H, blk), blk, 0, st>>>(src.img(0), src.img(1), src.pitch,
-                                                                    dst.img(0), dst.img(1), dst.pitch,
-                                                                    dst.W, dst.H);
+    const int cols4 = (dst.W + 2 * APX + 3) / 4;
+    dim3 grd((cols4 + blk.x - 1) / blk.x, (dst.H + 2 * APY + blk.y - 1) / blk.y, 2);
+    pyr_reduce_kernel<<<grd, blk, 0, st>>>(src.img(0), src.img(1), src.pitch, dst.img(0), dst.img(1), dst.pitch,
+                                           dst.W, dst.H);
     return cudaGetLastError();
 }
 

@@ -29,7 +29,7 @@ cudaError_t launch_full_t(const FullArgs *a, cudaStream_t st) {
         return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     static_cast<int>(C::BYTES));
     dim3 grd((a->t.W + C::TX - 1) / C::TX, (a->t.H + C::TY - 1) / C::TY);
-    kern<<<grd, 128, C::BYTES, st>>>(*a);
+    kern<<<grd, dim3(128), C::BYTES, st>>>(*a);
     return cudaGetLastError();
 }
 

@@ -263,6 +263,7 @@ __device__ bool full_tile(const FullTileArgs &a, const CUtensorMap *tmL, const C
     const int Dk = a.Dk;
     const int ZBmax = (a.zblock > 0 && a.zblock <= C::ZB) ? (a.zblock & ~31) : C::ZB;
     const bool force_to = a.force_timeout != 0;
+    if (a.tile_flags && a.tile_flags[by * a.tiles_x + bx] == 0) return true;   // no fallback pixel here
 
     // ---- left tile: image columns [x0 - 16, x0 + TX + 16), rows [y0 - n, y0 + TY + n)
     if (tid == 0) {
@@ -319,10 +320,12 @@ __device__ bool full_tile(const FullTileArgs &a, const CUtensorMap *tmL, const C
     }
 
     // ---- finalize: rho = score * rsqrt(Va), clamp, write
+    unsigned long long cnt = 0;
     for (int i = tid; i < TY * TX; i += blockDim.x) {
         int ry = i / TX, px = i - ry * TX;
         int x = x0 + px, y = y0 + ry;
         if (x >= a.W || y >= a.H) continue;
+        if (a.mask && !a.mask[(size_t)y * a.W + x]) continue;
         unsigned long long k = best[i];
         int z = static_cast<int>(0xFFFFFFFFu - static_cast<uint32_t>(k & 0xFFFFFFFFull));
         float sc = float_from_order_key(static_cast<uint32_t>(k >> 32));
@@ -330,13 +333,9 @@ __device__ bool full_tile(const FullTileArgs &a, const CUtensorMap *tmL, const C
         rho = fminf(1.f, fmaxf(-1.f, rho));
         a.d_out[(size_t)y * a.W + x] = static_cast<int16_t>(z);
         if (a.c_out) a.c_out[(size_t)y * a.W + x] = rho;
+        cnt += min(Dk - 1, x) + 1;
     }
-    if (tid == 0 && a.evals) {
-        unsigned long long n = 0;
-        for (int px = 0; px < TX && x0 + px < a.W; ++px) n += min(Dk - 1, x0 + px) + 1;
-        n *= static_cast<unsigned long long>(min(TY, a.H - y0));
-        atomicAdd(a.evals, n);
-    }
+    if (a.evals && cnt) atomicAdd(a.evals, cnt);
     return true;
 }
 

@@ -1,7 +1,7 @@
 // zncc_restricted.cu -- standalone launch of the restricted ZNCC winner-take-all tile
-// (Sec. III-C, Eq. 8-9, first branch; design in zncc_restricted_tile.cuh): one CTA of
-// 256 threads per 32 x 8 tile.
-#include "zncc_restricted_tile.cuh"
+// (Sec. III-C, Eq. 8-9, first branch; design in zncc_restricted_px_tile.cuh): one CTA of
+// 256 threads, one per pixel, per 32 x 8 tile.
+#include "zncc_restricted_px_tile.cuh"
 
 namespace msbm {
 
@@ -18,15 +18,15 @@ __global__ void __launch_bounds__(256) zncc_restricted_kernel(const __grid_const
     }
     __syncthreads();
     uint32_t parity = 0;
-    restr_tile<NH, G>(a.t, &a.tmL, &a.tmR64, &a.tmR256, blockIdx.x, blockIdx.y, smem, parity);
+    restr_tile_px<NH, G>(a.t, &a.tmL, &a.tmR64, &a.tmR256, blockIdx.x, blockIdx.y, smem, parity);
 }
 
 template <int NH, int G>
 cudaError_t launch_restr_t(const RestrArgs &a, cudaStream_t st) {
-    using C = RCfg<NH>;
+    using C = RCfgPx<NH>;
     static_assert(C::BYTES <= 48 * 1024, "restricted tile fits the default shared memory");
-    dim3 grd((a.t.W + RT_TX - 1) / RT_TX, (a.t.H + RT_TY - 1) / RT_TY);
-    zncc_restricted_kernel<NH, G><<<grd, RT_TX * RT_TY, C::BYTES, st>>>(a);
+    dim3 grd((a.t.W + PX_TX - 1) / PX_TX, (a.t.H + PX_TY - 1) / PX_TY);
+    zncc_restricted_kernel<NH, G><<<grd, PX_TX * PX_TY, C::BYTES, st>>>(a);
     return cudaGetLastError();
 }
 

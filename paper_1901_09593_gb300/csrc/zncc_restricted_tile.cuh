@@ -1,27 +1,29 @@
-// zncc_restricted_tile.cuh -- the restricted ZNCC winner-take-all tile, shared by the
-// standalone kernel (zncc_restricted.cu) and the batched persistent kernel (batch.cu).
-// Refinement search at a finer pyramid level (Sec. III-C, Eq. 8-9,
-// first branch): each pixel evaluates only dhat - r .. dhat + r around the nearest-
-// neighbour upsample dhat = 2 * d^{k+1}(y/2, x/2) of the coarser disparity (the paper's
-// "3 comparisons per pixel" is r = 1), clipped to 0 .. min(D_k - 1, x).
+// zncc_restricted_tile.cuh -- the restricted ZNCC winner-take-all tile (Sec. III-C,
+// Eq. 8-9, first branch), shared by the standalone kernel (zncc_restricted.cu) and the
+// batched persistent kernel (batch.cu).  Each pixel evaluates dhat - r .. dhat + r around
+// the nearest-neighbour upsample dhat = 2 * d^{k+1}(y/2, x/2) of the coarser disparity (the
+// paper's "3 comparisons per pixel" is r = 1), clipped to 0 .. min(D_k - 1, x); dhat is
+// first clamped into that range (a no-op for priors produced by the coarser level).
 //
-// Design (per CTA: 32 x 8 pixels, one thread per pixel):
-//  * Each thread reads its prior; the CTA reduces the union [zlo, zhi] of its pixels'
-//    candidate spans.  The left tile and the right span [x0 - zhi - n, x1 - zlo + n] are
-//    staged into shared memory by TMA (one 64-byte box for the left tile, one 64- or
-//    256-byte box for the right span, one mbarrier, bounded wait).  A span wider than
-//    256 bytes (a tile straddling a large disparity jump) reads the right image straight
-//    from global memory instead.
-//  * Right-window statistics for the span are built once per CTA with separable sums.
-//  * Each thread packs its left window (2n+1 rows of ceil((2n+1)/4) words, zero-padded)
-//    into registers and gets Sa, Saa with dp4a.  For each window row it loads the right
-//    bytes covering a group of G consecutive candidates once, aligns them with funnel
-//    shifts, and accumulates sum a*b for every candidate of the group with dp4a.  All sums
-//    are exact int32 (windows up to 13 x 13); c = N*Sab - Sa*Sb is exact; the only
-//    rounding is rho = float(c) * rsqrt(Va) * rsqrt(Vb).
-//  * WTA on a 64-bit (ordered rho, ~z) key, so exact ties keep the smallest z.
-// Bound: the integer dot-product pipe (about 2*ceil((2n+1)/4)*(2n+1) dp4a + shifts per
-// evaluation); HBM traffic is a few bytes per pixel.
+// Design (per CTA: a (2*QX) x 16 pixel tile of QX x 8 threads, QX = 32 or 16; each thread
+// owns one 2 x 2 block):
+//  * The four pixels of a 2 x 2 block aligned to even coordinates share one prior cell,
+//    hence one candidate span (up to the per-pixel clip at x, handled by masking).
+//  * The CTA reduces the union [zlo, zhi] of its spans; the left tile (a (2*QX+32)-byte box) and the
+//    right span [x0 - zhi - n, x1 - zlo + n] (128- or 256-byte box) are staged into shared
+//    memory by TMA with one mbarrier and a bounded wait.  A span wider than 256 bytes (a
+//    tile straddling a large disparity jump) reads the right image from global memory.
+//  * Right-window statistics of the span are built once per CTA by all threads (vertical
+//    sums, then horizontal sums; exact integers).
+//  * Each thread packs the 2n+2 left rows of its two columns as dp4a words.  For each
+//    staged right row and each group of G consecutive candidates it loads the right bytes
+//    once, aligns them with funnel shifts, extracts the G+1 distinct window offsets its two
+//    columns need, and accumulates sum a*b with dp4a.  The two pixels of a column share
+//    the products of their 2n common rows.  All sums are exact int32 (windows up to
+//    13 x 13); c = N*Sab - Sa*Sb is exact; the only rounding is
+//    rho = float(c) * rsqrt(Vb) * rsqrt(Va).
+//  * WTA in ascending z with a strict compare, so exact ties keep the smallest z.
+// Bound: the integer dot-product pipe; HBM traffic is a few bytes per pixel.
 #pragma once
 
 #include <limits.h>
@@ -33,24 +35,26 @@
 namespace msbm {
 namespace tiles {
 
+constexpr int RT_TY = 16;      // tile height (pixels)
 
-constexpr int RT_TX = 32;
-constexpr int RT_TY = 8;
-
-template <int NH>
+template <int NH, int QX = 32>
 struct RCfg {
+    static constexpr int TX = 2 * QX;            // tile width (pixels)
+    static constexpr int THREADS = QX * 8;
     static constexpr int WIN = 2 * NH + 1;
     static constexpr int N = WIN * WIN;
     static constexpr int NW = (WIN + 3) / 4;     // words per packed window row
-    static constexpr int ROWS = RT_TY + 2 * NH;
+    static constexpr int ROWS = RT_TY + 2 * NH;  // staged rows
+    static constexpr int LBOX = TX + 32;         // left box: image columns x0-16 .. x0+TX+16
     static constexpr uint32_t LASTMASK =
         (WIN % 4 == 0) ? 0xFFFFFFFFu : ((1u << (8 * (WIN % 4))) - 1u);
     // shared memory carve (bytes): [0,128) barrier, flag, span scalars, evaluation sum
     static constexpr size_t al(size_t v) { return (v + 127) / 128 * 128; }
     static constexpr size_t OFF_SL = 128;
-    static constexpr size_t OFF_SR = OFF_SL + al((size_t)ROWS * 64);
+    static constexpr size_t PAD_R = 128;         // readable slack before the right span
+    static constexpr size_t OFF_SR = OFF_SL + al((size_t)ROWS * LBOX) + PAD_R;
     static constexpr size_t OFF_TMP = OFF_SR + al((size_t)(ROWS + 1) * 256);
-    static constexpr size_t OFF_STR = OFF_TMP + (size_t)RT_TY * 256 * 8;
+    static constexpr size_t OFF_STR = OFF_TMP + (size_t)RT_TY * 256 * 4;
     static constexpr size_t BYTES = OFF_STR + (size_t)RT_TY * 256 * 8;
 };
 
@@ -58,19 +62,21 @@ __device__ __forceinline__ uint32_t fsr(uint32_t lo, uint32_t hi, int bytes) {
     return __funnelshift_r(lo, hi, 8 * bytes);
 }
 
-// Restricted WTA of one 32 x 8 tile (bx, by) by the calling CTA (blockDim.x = 256, one
-// thread per pixel).  `smem` holds RCfg::BYTES bytes, 128-aligned; its first 8 bytes are an
-// mbarrier the caller has initialised (count 1) and `parity` is its next phase parity,
-// advanced here.  Returns false if a bounded wait gave up (the error word is then set).
-template <int NH, int G>
-__device__ bool restr_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const CUtensorMap *tmR64,
+// Restricted WTA of one (2*QX) x 16 tile (bx, by) by the calling CTA (blockDim.x = QX*8).
+// `smem` holds RCfg::BYTES bytes, 128-aligned; its first 8 bytes are an mbarrier the caller
+// has initialised (count 1) and `parity` is its next phase parity, advanced here.  tmL is a
+// (2*QX + 32)-byte-wide box over the left apron buffer, tmR128/tmR256 128/256-byte boxes
+// over the right one.  Returns false if a bounded wait gave up (the error word is then set).
+template <int NH, int G, int QX = 32>
+__device__ bool restr_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const CUtensorMap *tmR128,
                            const CUtensorMap *tmR256, int bx, int by, uint8_t *smem, uint32_t &parity) {
-    using C = RCfg<NH>;
+    using C = RCfg<NH, QX>;
+    constexpr int RT_TX = C::TX, RT_THREADS = C::THREADS;
     constexpr int ROWS = C::ROWS, WIN = C::WIN, NW = C::NW;
-    // right bytes per row for one candidate group (after alignment) and words to load
-    constexpr int GB = G - 1 + WIN;
-    constexpr int NWA = (GB + 3) / 4 + 1;     // aligned words after the shift
-    constexpr int NWL = NWA + 1;              // raw words loaded
+    // right bytes one row of a candidate group needs for both columns: G + WIN, plus up to
+    // 3 of misalignment; NWA aligned words hold them with one word to spare for extraction
+    constexpr int NWA = (G + WIN + 3) / 4 + 1;
+    constexpr int NWL = NWA + 1;              // raw words loaded per row
     uint64_t &bar = *reinterpret_cast<uint64_t *>(smem);
     int &flag = *reinterpret_cast<int *>(smem + 8);
     int &zlo_s = *reinterpret_cast<int *>(smem + 12);
@@ -78,38 +84,51 @@ __device__ bool restr_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const
     int &mode_s = *reinterpret_cast<int *>(smem + 20);
     int &xs_s = *reinterpret_cast<int *>(smem + 24);
     unsigned long long &evsum = *reinterpret_cast<unsigned long long *>(smem + 32);
-    uint8_t (*sL)[64] = reinterpret_cast<uint8_t (*)[64]>(smem + C::OFF_SL);
-    // right span: ROWS rows of 64 (narrow box) or 256 (wide box) bytes, plus one spare
-    // row so that a candidate group's over-read past the last row stays in the array
-    uint8_t *sR = smem + C::OFF_SR;
-    int2 (*tmpV)[256] = reinterpret_cast<int2 (*)[256]>(smem + C::OFF_TMP);
-    int2 (*stR)[256] = reinterpret_cast<int2 (*)[256]>(smem + C::OFF_STR);   // {Sb, bits(rsqrt(Vb))}
+    uint8_t *sL = smem + C::OFF_SL;                       // [ROWS][LBOX]
+    uint8_t *sR = smem + C::OFF_SR;                       // [ROWS + 1][64|128|256] + slack before
+    uint32_t *tmpV = reinterpret_cast<uint32_t *>(smem + C::OFF_TMP);   // [RT_TY][256] packed (Q | S << 20)
+    int2 *stR = reinterpret_cast<int2 *>(smem + C::OFF_STR);           // [RT_TY][256] {Sb, bits(rsqrt(Vb))}
 
-    const int tid = threadIdx.x, tx = tid & (RT_TX - 1), ty = tid / RT_TX;
+    const int tid = threadIdx.x, qx = tid % QX, qy = tid / QX;
     const int x0 = bx * RT_TX, y0 = by * RT_TY;
-    const int x = x0 + tx, y = y0 + ty;
-    const bool active = x < a.W && y < a.H;
+    const int xa = x0 + 2 * qx, ya = y0 + 2 * qy;       // top-left pixel of this thread's block
     const int Dk = a.Dk;
+    const bool colv[2] = {xa < a.W, xa + 1 < a.W};
+    const bool rowv[2] = {ya < a.H, ya + 1 < a.H};
+    const bool any = colv[0] && rowv[0];
 
-    int lo = INT_MAX, hi = -1;
-    if (active) {
-        int zmx = min(Dk - 1, x);
-        int py = min(y >> 1, a.Hp - 1), px = min(x >> 1, a.Wp - 1);
-        int dh = 2 * static_cast<int>(a.prior[(size_t)py * a.Wp + px]);
-        dh = min(max(dh, 0), zmx);
-        lo = max(0, dh - a.r);
-        hi = min(zmx, dh + a.r);
+    // candidate spans of the two columns (rows share them)
+    int lo_c[2] = {INT_MAX, INT_MAX}, hi_c[2] = {-1, -1};
+    if (any) {
+        const int py = min(ya >> 1, a.Hp - 1), px = min(xa >> 1, a.Wp - 1);
+        const int p2 = 2 * static_cast<int>(a.prior[(size_t)py * a.Wp + px]);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            if (!colv[c]) continue;
+            const int zmx = min(Dk - 1, xa + c);
+            const int dh = min(max(p2, 0), zmx);
+            lo_c[c] = max(0, dh - a.r);
+            hi_c[c] = min(zmx, dh + a.r);
+        }
     }
+    const int lo_u = min(lo_c[0], lo_c[1]);
+    const int hi_u = max(hi_c[0], hi_c[1]);
     if (tid == 0) {
         zlo_s = INT_MAX; zhi_s = -1; evsum = 0ull;
     }
     __syncthreads();
     {
-        int wlo = __reduce_min_sync(0xFFFFFFFFu, lo);
-        int whi = __reduce_max_sync(0xFFFFFFFFu, hi);
-        unsigned cnt = active ? static_cast<unsigned>(hi - lo + 1) : 0u;
-        unsigned wcnt = __reduce_add_sync(0xFFFFFFFFu, cnt);
-        if (tx == 0) {
+        const int wlo = __reduce_min_sync(0xFFFFFFFFu, lo_u);
+        const int whi = __reduce_max_sync(0xFFFFFFFFu, hi_u);
+        unsigned cnt = 0;
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int r2 = 0; r2 < 2; ++r2)
+                if (colv[c] && rowv[r2] && !(a.skip && a.skip[(size_t)(ya + r2) * a.W + xa + c]))
+                    cnt += static_cast<unsigned>(hi_c[c] - lo_c[c] + 1);
+        const unsigned wcnt = __reduce_add_sync(0xFFFFFFFFu, cnt);
+        if ((tid & 31) == 0) {
             atomicMin(&zlo_s, wlo);
             atomicMax(&zhi_s, whi);
             atomicAdd(&evsum, static_cast<unsigned long long>(wcnt));
@@ -121,155 +140,239 @@ __device__ bool restr_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const
     const int rs = x0 - zhi - NH;              // first right column any window reads
     const int re = xlast - zlo + NH;           // last
     if (tid == 0) {
-        int xs = (rs + APX) & ~15;
-        int width = re + APX + 1 - xs;
-        int mode = width <= 64 ? 1 : (width <= 256 ? 2 : 0);
+        const int xs = (rs + APX) & ~15;
+        const int width = re + APX + 1 - xs;
+        const int mode = width <= 128 ? 1 : (width <= 256 ? 2 : 0);
         mode_s = mode;
         xs_s = xs;
-        uint32_t bytes = ROWS * 64 + (mode == 1 ? ROWS * 64 : (mode == 2 ? ROWS * 256 : 0));
+        const uint32_t bytes = ROWS * C::LBOX + (mode == 1 ? ROWS * 128 : (mode == 2 ? ROWS * 256 : 0));
         fence_proxy_async_smem();
         mbar_arrive_expect_tx(&bar, bytes);
-        tma_load_2d(&sL[0][0], tmL, &bar, x0 - 16 + APX, y0 - NH + APY);
-        if (mode == 1) tma_load_2d(sR, tmR64, &bar, xs, y0 - NH + APY);
+        tma_load_2d(sL, tmL, &bar, x0 - 16 + APX, y0 - NH + APY);
+        if (mode == 1) tma_load_2d(sR, tmR128, &bar, xs, y0 - NH + APY);
         if (mode == 2) tma_load_2d(sR, tmR256, &bar, xs, y0 - NH + APY);
     }
     if (!tma_batch_wait(&bar, parity, &flag, a.force_timeout != 0, a.err)) return false;
     parity ^= 1;
     const int mode = mode_s, xs = xs_s;
     const int soff = APX - xs;                 // staging column of image column X: X + soff
-    const int rst = mode == 1 ? 64 : 256;      // staging row stride
+    const int rst = mode == 1 ? 128 : 256;     // staging row stride
 
-    // ---- right statistics over the span (staged modes)
+    // ---- right statistics over the span (staged modes), all threads
     const int SW = re - rs + 1 - 2 * NH;       // statistics columns: image rs + n + v
     if (mode != 0) {
-        for (int c = tid; c < SW + 2 * NH; c += RT_TX * RT_TY) {
-            const int col = rs + c + soff;
-            int s = 0, q = 0;
-#pragma unroll
-            for (int t = 0; t < WIN; ++t) { int v = sR[t * rst + col]; s += v; q += v * v; }
-            tmpV[0][c] = make_int2(s, q);
-#pragma unroll 1
-            for (int ry = 1; ry < RT_TY; ++ry) {
-                int vn = sR[(ry + 2 * NH) * rst + col], vo = sR[(ry - 1) * rst + col];
-                s += vn - vo;
-                q += vn * vn - vo * vo;
-                tmpV[ry][c] = make_int2(s, q);
-            }
-        }
-        __syncthreads();
-        for (int i = tid; i < RT_TY * SW; i += RT_TX * RT_TY) {
-            int ry = i / SW, v = i - ry * SW;
-            int s = 0, q = 0;
-#pragma unroll
-            for (int j = 0; j < WIN; ++j) { int2 t = tmpV[ry][v + j]; s += t.x; q += t.y; }
-            int V = C::N * q - s * s;
-            float r = V > 0 ? rsqrtf(static_cast<float>(V)) : 0.f;
-            stR[ry][v] = make_int2(s, __float_as_int(r));
-        }
-        __syncthreads();
-    }
-    if (!active) return true;
-
-    // ---- left window, packed: row t holds columns x-n .. x+n in NW words
-    uint32_t Lw[WIN][NW];
-    uint32_t Sa = 0, Saa = 0;
-    {
-        const int sc = tx + 16 - NH;           // staging column of x - n
-        const int w0 = sc >> 2, sh = sc & 3;
-#pragma unroll
-        for (int t = 0; t < WIN; ++t) {
-            const uint32_t *row = reinterpret_cast<const uint32_t *>(&sL[ty + t][0]);
-            uint32_t raw[NW + 1];
-#pragma unroll
-            for (int k = 0; k <= NW; ++k) raw[k] = row[w0 + k];
-#pragma unroll
-            for (int k = 0; k < NW; ++k) Lw[t][k] = fsr(raw[k], raw[k + 1], sh);
-            Lw[t][NW - 1] &= C::LASTMASK;
-#pragma unroll
-            for (int k = 0; k < NW; ++k) {
-                Sa = dp4a_u8(Lw[t][k], 0x01010101u, Sa);
-                Saa = dp4a_u8(Lw[t][k], Lw[t][k], Saa);
-            }
-        }
-    }
-    const int Va = C::N * static_cast<int>(Saa) - static_cast<int>(Sa) * static_cast<int>(Sa);
-    const float rA = Va > 0 ? rsqrtf(static_cast<float>(Va)) : 0.f;
-
-    unsigned long long bestk = 0ull;
-    if (mode != 0) {
-        // groups of G candidates, walking down from hi: group covers z = zg - j, j < G
-        for (int zg = hi; zg >= lo; zg -= G) {
-            uint32_t acc[G];
-#pragma unroll
-            for (int j = 0; j < G; ++j) acc[j] = 0;
-            // staging column of the first byte of candidate j's window: sc0 + j
-            const int sc0 = x - zg - NH + soff;
-            const int w0 = sc0 >> 2, sh = sc0 & 3;
+        // vertical window sums of every (output row, span column), spread over all threads
+        const int cols = SW + 2 * NH;
+        for (int i = tid; i < RT_TY * cols; i += RT_THREADS) {
+            const int ry = i / cols, c = i - ry * cols;
+            const uint8_t *p = sR + ry * rst + rs + c + soff;
+            uint32_t s = 0, q = 0;
 #pragma unroll
             for (int t = 0; t < WIN; ++t) {
-                const uint32_t *row = reinterpret_cast<const uint32_t *>(sR + (ty + t) * rst);
-                uint32_t raw[NWL], al[NWA];
+                const uint32_t v = p[t * rst];
+                s += v;
+                q += v * v;
+            }
+            tmpV[ry * 256 + c] = q | (s << 20);    // s < 4096, q < 2^20 for windows <= 13
+        }
+        __syncthreads();
+        // horizontal sums, then rsqrt of the window variance
+        for (int i = tid; i < RT_TY * SW; i += RT_THREADS) {
+            const int ry = i / SW, v = i - ry * SW;
+            int s = 0, q = 0;
+#pragma unroll
+            for (int j = 0; j < WIN; ++j) {
+                const uint32_t t = tmpV[ry * 256 + v + j];
+                s += static_cast<int>(t >> 20);
+                q += static_cast<int>(t & 0xFFFFFu);
+            }
+            const int V = C::N * q - s * s;
+            const float r = V > 0 ? rsqrtf(static_cast<float>(V)) : 0.f;
+            stR[ry * 256 + v] = make_int2(s, __float_as_int(r));
+        }
+        __syncthreads();
+    }
+    if (!any) return true;
+
+    // ---- left windows: rows ya-n .. ya+1+n (2n+2) of columns xa and xa+1, packed
+    uint32_t Lw[2][WIN + 1][NW];
+    int Sa[2][2], rAi[2][2];
+    float rA[2][2];
+    {
+        const int sc = 2 * qx + 16 - NH;       // staging column of xa - n
+        const int w0 = sc >> 2, sh = sc & 3;
+#pragma unroll
+        for (int t = 0; t <= WIN; ++t) {
+            const uint32_t *row = reinterpret_cast<const uint32_t *>(sL + (2 * qy + t) * C::LBOX);
+            uint32_t raw[NW + 2];
+#pragma unroll
+            for (int k = 0; k < NW + 2; ++k) raw[k] = row[w0 + k];
+            uint32_t alw[NW + 1];
+#pragma unroll
+            for (int k = 0; k <= NW; ++k) alw[k] = fsr(raw[k], raw[k + 1], sh);
+#pragma unroll
+            for (int k = 0; k < NW; ++k) {
+                Lw[0][t][k] = alw[k];
+                Lw[1][t][k] = fsr(alw[k], alw[k + 1], 1);
+            }
+            Lw[0][t][NW - 1] &= C::LASTMASK;
+            Lw[1][t][NW - 1] &= C::LASTMASK;
+        }
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            uint32_t s_mid = 0, q_mid = 0, s0 = 0, q0 = 0, s1 = 0, q1 = 0;
+#pragma unroll
+            for (int t = 1; t < WIN; ++t)
+#pragma unroll
+                for (int k = 0; k < NW; ++k) {
+                    s_mid = dp4a_u8(Lw[c][t][k], 0x01010101u, s_mid);
+                    q_mid = dp4a_u8(Lw[c][t][k], Lw[c][t][k], q_mid);
+                }
+#pragma unroll
+            for (int k = 0; k < NW; ++k) {
+                s0 = dp4a_u8(Lw[c][0][k], 0x01010101u, s0);
+                q0 = dp4a_u8(Lw[c][0][k], Lw[c][0][k], q0);
+                s1 = dp4a_u8(Lw[c][WIN][k], 0x01010101u, s1);
+                q1 = dp4a_u8(Lw[c][WIN][k], Lw[c][WIN][k], q1);
+            }
+            const int sa0 = static_cast<int>(s_mid + s0), sa1 = static_cast<int>(s_mid + s1);
+            const int va0 = C::N * static_cast<int>(q_mid + q0) - sa0 * sa0;
+            const int va1 = C::N * static_cast<int>(q_mid + q1) - sa1 * sa1;
+            Sa[c][0] = sa0;
+            Sa[c][1] = sa1;
+            rA[c][0] = va0 > 0 ? rsqrtf(static_cast<float>(va0)) : 0.f;
+            rA[c][1] = va1 > 0 ? rsqrtf(static_cast<float>(va1)) : 0.f;
+            rAi[c][0] = va0 > 0;
+            rAi[c][1] = va1 > 0;
+        }
+    }
+
+    float best[2][2];
+    int bz[2][2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int r2 = 0; r2 < 2; ++r2) {
+            best[c][r2] = -INFINITY;
+            bz[c][r2] = lo_c[c];
+        }
+
+    if (mode != 0) {
+        for (int zg = lo_u; zg <= hi_u; zg += G) {
+            // accumulators: rows 1..2n shared by both pixel rows, row 0 and row 2n+1 apart
+            uint32_t mid[2][G], top[2][G], bot[2][G];
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+#pragma unroll
+                for (int j = 0; j < G; ++j) mid[c][j] = top[c][j] = bot[c][j] = 0;
+            // window of column c, candidate zg + j starts at staging column b0 + (G-1-j) + c
+            const int b0 = xa - (zg + G - 1) - NH + soff;      // >= -(G-1): inside the slack
+            const int w0 = b0 >> 2, sh = b0 & 3;                // arithmetic shift: floor
+#pragma unroll
+            for (int t = 0; t <= WIN; ++t) {
+                const uint32_t *row = reinterpret_cast<const uint32_t *>(sR + (2 * qy + t) * rst);
+                uint32_t raw[NWL], alw[NWA];
 #pragma unroll
                 for (int k = 0; k < NWL; ++k) raw[k] = row[w0 + k];
 #pragma unroll
-                for (int k = 0; k < NWA; ++k) al[k] = fsr(raw[k], raw[k + 1], sh);
+                for (int k = 0; k < NWA; ++k) alw[k] = fsr(raw[k], raw[k + 1], sh);
+                // the G + 1 distinct window offsets o = 0 .. G
+                uint32_t Wo[G + 1][NW];
 #pragma unroll
-                for (int j = 0; j < G; ++j) {
+                for (int o = 0; o <= G; ++o)
 #pragma unroll
-                    for (int k = 0; k < NW; ++k) {
-                        uint32_t b = (j & 3) ? fsr(al[(j >> 2) + k], al[(j >> 2) + k + 1], j & 3)
-                                             : al[(j >> 2) + k];
-                        acc[j] = dp4a_u8(Lw[t][k], b, acc[j]);
+                    for (int k = 0; k < NW; ++k)
+                        Wo[o][k] = (o & 3) ? fsr(alw[(o >> 2) + k], alw[(o >> 2) + k + 1], o & 3)
+                                           : alw[(o >> 2) + k];
+#pragma unroll
+                for (int c = 0; c < 2; ++c)
+#pragma unroll
+                    for (int j = 0; j < G; ++j) {
+                        const int o = G - 1 - j + c;
+#pragma unroll
+                        for (int k = 0; k < NW; ++k) {
+                            if (t == 0)
+                                top[c][j] = dp4a_u8(Lw[c][t][k], Wo[o][k], top[c][j]);
+                            else if (t == WIN)
+                                bot[c][j] = dp4a_u8(Lw[c][t][k], Wo[o][k], bot[c][j]);
+                            else
+                                mid[c][j] = dp4a_u8(Lw[c][t][k], Wo[o][k], mid[c][j]);
+                        }
                     }
-                }
             }
 #pragma unroll
             for (int j = 0; j < G; ++j) {
-                const int z = zg - j;
-                if (z < lo) break;
-                const int2 st = stR[ty][x - z - (rs + NH)];
-                const int c = C::N * static_cast<int>(acc[j]) - static_cast<int>(Sa) * st.x;
-                const float rho = static_cast<float>(c) * rA * __int_as_float(st.y);
-                unsigned long long k = wta_key(rho, z);
-                bestk = k > bestk ? k : bestk;
+                const int z = zg + j;
+                if (z > hi_u) break;
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    if (!colv[c] || z < lo_c[c] || z > hi_c[c]) continue;
+                    const int col = xa + c - z - (rs + NH);   // statistics column of x - z
+#pragma unroll
+                    for (int r2 = 0; r2 < 2; ++r2) {
+                        if (!rowv[r2]) continue;
+                        const int2 st = stR[(2 * qy + r2) * 256 + col];
+                        const int sab = static_cast<int>(mid[c][j] + (r2 ? bot[c][j] : top[c][j]));
+                        const int cc = C::N * sab - Sa[c][r2] * st.x;
+                        const float rho = static_cast<float>(cc) * __int_as_float(st.y);
+                        if (rho > best[c][r2]) {
+                            best[c][r2] = rho;
+                            bz[c][r2] = z;
+                        }
+                    }
+                }
             }
         }
     } else {
         // wide span: read the right image from global memory (apron buffer, no clamping)
-        for (int z = lo; z <= hi; ++z) {
-            uint32_t Sab = 0, Sb = 0, Sbb = 0;
 #pragma unroll
-            for (int t = 0; t < WIN; ++t) {
-                const uint8_t *rrow = a.Rimg + (ptrdiff_t)(y - NH + t) * a.pitch + (x - z - NH);
-                uint32_t raw[NW];
+        for (int c = 0; c < 2; ++c) {
+            if (!colv[c]) continue;
 #pragma unroll
-                for (int k = 0; k < NW; ++k) {
-                    uint32_t w = 0;
+            for (int r2 = 0; r2 < 2; ++r2) {
+                if (!rowv[r2]) continue;
+                const int x = xa + c, y = ya + r2;
+                for (int z = lo_c[c]; z <= hi_c[c]; ++z) {
+                    uint32_t Sab = 0, Sb = 0, Sbb = 0;
 #pragma unroll
-                    for (int b = 0; b < 4; ++b)
-                        if (4 * k + b < WIN) w |= static_cast<uint32_t>(__ldg(rrow + 4 * k + b)) << (8 * b);
-                    raw[k] = w;
-                }
+                    for (int t = 0; t < WIN; ++t) {
+                        const uint8_t *rrow = a.Rimg + (ptrdiff_t)(y - NH + t) * a.pitch + (x - z - NH);
 #pragma unroll
-                for (int k = 0; k < NW; ++k) {
-                    Sab = dp4a_u8(Lw[t][k], raw[k], Sab);
-                    Sb = dp4a_u8(raw[k], 0x01010101u, Sb);
-                    Sbb = dp4a_u8(raw[k], raw[k], Sbb);
+                        for (int k = 0; k < NW; ++k) {
+                            uint32_t w = 0;
+#pragma unroll
+                            for (int b = 0; b < 4; ++b)
+                                if (4 * k + b < WIN) w |= static_cast<uint32_t>(__ldg(rrow + 4 * k + b)) << (8 * b);
+                            Sab = dp4a_u8(Lw[c][t + r2][k], w, Sab);
+                            Sb = dp4a_u8(w, 0x01010101u, Sb);
+                            Sbb = dp4a_u8(w, w, Sbb);
+                        }
+                    }
+                    const int Vb = C::N * static_cast<int>(Sbb) - static_cast<int>(Sb) * static_cast<int>(Sb);
+                    const float rB = Vb > 0 ? rsqrtf(static_cast<float>(Vb)) : 0.f;
+                    const int cc = C::N * static_cast<int>(Sab) - Sa[c][r2] * static_cast<int>(Sb);
+                    const float rho = static_cast<float>(cc) * rB;
+                    if (rho > best[c][r2]) {
+                        best[c][r2] = rho;
+                        bz[c][r2] = z;
+                    }
                 }
             }
-            const int Vb = C::N * static_cast<int>(Sbb) - static_cast<int>(Sb) * static_cast<int>(Sb);
-            const float rB = Vb > 0 ? rsqrtf(static_cast<float>(Vb)) : 0.f;
-            const int c = C::N * static_cast<int>(Sab) - static_cast<int>(Sa) * static_cast<int>(Sb);
-            const float rho = static_cast<float>(c) * rA * rB;
-            unsigned long long k = wta_key(rho, z);
-            bestk = k > bestk ? k : bestk;
         }
     }
-    const int z = static_cast<int>(0xFFFFFFFFu - static_cast<uint32_t>(bestk & 0xFFFFFFFFull));
-    float rho = float_from_order_key(static_cast<uint32_t>(bestk >> 32));
-    rho = fminf(1.f, fmaxf(-1.f, rho));
-    a.d_out[(size_t)y * a.W + x] = static_cast<int16_t>(z);
-    if (a.c_out) a.c_out[(size_t)y * a.W + x] = rho;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int r2 = 0; r2 < 2; ++r2) {
+            if (!colv[c] || !rowv[r2]) continue;
+            // rsqrt(Va) scales every candidate of the pixel alike: applied once here.  A flat
+            // left window has c = 0 for every candidate, so the smallest z wins with rho = 0.
+            float rho = rAi[c][r2] ? best[c][r2] * rA[c][r2] : 0.f;
+            rho = fminf(1.f, fmaxf(-1.f, rho));
+            const size_t o = (size_t)(ya + r2) * a.W + xa + c;
+            a.d_out[o] = static_cast<int16_t>(bz[c][r2]);
+            if (a.c_out) a.c_out[o] = rho;
+        }
     if (tid == 0 && a.evals) atomicAdd(a.evals, evsum);
     return true;
 }

@@ -36,12 +36,12 @@ class Context:
     """A hierarchical ZNCC block matcher for one image size and parameter set."""
 
     def __init__(self, width: int, height: int, max_disp: int, levels: int, window: int,
-                 radius: int, flags: int = 0, device=None):
+                 radius: int, flags: int = 0, device=None, alpha: float = 0.9, beta: float = 0.9):
         torch = _torch()
         self._lib = _lib.load()
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None
                                    else torch.device(device).index)
-        self.params = _lib.msbm_params(width, height, max_disp, levels, window, radius, flags)
+        self.params = _lib.msbm_params(width, height, max_disp, levels, window, radius, flags, alpha, beta)
         self._ctx = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             _lib.check(self._lib.msbm_create(ctypes.byref(self.params),
@@ -124,6 +124,36 @@ class Context:
                                               ctypes.c_void_p(c.data_ptr()) if c is not None else None),
                    "msbm_match_level")
         return d, c
+
+    def alpha_refine(self, level: int, d, cost) -> None:
+        """Eq. 5-7 in place on (d, cost) of `level` (pyramid from pyramid())."""
+        self._bind_stream()
+        _lib.check(self._lib.msbm_alpha_refine(self._ctx, level, ctypes.c_void_p(d.data_ptr()),
+                                               ctypes.c_void_p(cost.data_ptr())), "msbm_alpha_refine")
+
+    def selective_median(self, level: int, d, cost):
+        """Eq. 10: returns the filtered map."""
+        torch = _torch()
+        self._bind_stream()
+        out = torch.empty_like(d)
+        _lib.check(self._lib.msbm_selective_median(self._ctx, level, ctypes.c_void_p(d.data_ptr()),
+                                                   ctypes.c_void_p(cost.data_ptr()),
+                                                   ctypes.c_void_p(out.data_ptr())), "msbm_selective_median")
+        return out
+
+    def match_level_beta(self, level: int, prior, cost_prior):
+        """Eq. 8-9 (both branches): returns (d, cost, fallback mask)."""
+        torch = _torch()
+        self._bind_stream()
+        w, h, _ = self.level_shape(level)
+        d = torch.empty((h, w), dtype=torch.int16, device=self.device)
+        c = torch.empty((h, w), dtype=torch.float32, device=self.device)
+        fb = torch.empty((h, w), dtype=torch.uint8, device=self.device)
+        _lib.check(self._lib.msbm_match_level_beta(
+            self._ctx, level, ctypes.c_void_p(prior.data_ptr()), ctypes.c_void_p(cost_prior.data_ptr()),
+            ctypes.c_void_p(d.data_ptr()), ctypes.c_void_p(c.data_ptr()), ctypes.c_void_p(fb.data_ptr())),
+            "msbm_match_level_beta")
+        return d, c, fb
 
     def disparity(self, left, right, d_out=None, cost_out=None, with_cost: bool = True):
         """Whole hierarchical pass on device tensors; returns level-0 (d, cost)."""

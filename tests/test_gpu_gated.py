@@ -1,0 +1,114 @@
+"""GPU parity of the gated steps of the full method against the oracle, each fed the same
+inputs: the selective median (Eq. 10) bit for bit, alpha refinement (Eq. 5-7) and the
+beta-gated level (Eq. 8-9) within the usual tolerances (gate decisions taken within 1e-5 of
+the threshold and near-ties counted, not failed), then the whole gated pass end to end."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1901_09593_gb300 import scenes
+from tests.gpu_util import COST_TOL, TIE_TOL, compare_level, dev, host
+
+pytestmark = pytest.mark.gpu
+
+ALPHA = float(np.float32(0.9))   # the kernels compare float costs with the float threshold
+BETA = float(np.float32(0.9))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1901_09593_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def ctx_for(w, h, D, K, win, r, flags):
+    from paper_1901_09593_gb300 import Context
+    return Context(w, h, D, K, win, r, flags, alpha=ALPHA, beta=BETA)
+
+
+def test_selective_median_bit_exact():
+    from paper_1901_09593_gb300 import _lib
+    rng = np.random.default_rng(0)
+    h, w = 37, 83
+    d = rng.integers(0, 60, (h, w)).astype(np.int16)
+    c = (rng.random((h, w)) * 1.3 - 0.2).astype(np.float32)
+    ctx = ctx_for(w, h, 64, 1, 5, 2, _lib.MSBM_FLAG_SELECTIVE_MEDIAN)
+    out = host(ctx.selective_median(0, dev(d), dev(c)))
+    ref = oracle.selective_median(d, c.astype(np.float64), ALPHA)
+    np.testing.assert_array_equal(out, ref)
+
+
+def test_alpha_refinement_matches_oracle():
+    from paper_1901_09593_gb300 import _lib
+    sc = scenes.make_pair(scenes.SPECS["small_320x240"], 2)
+    a, b = sc.left[:80, :128].copy(), sc.right[:80, :128].copy()
+    ctx = ctx_for(128, 80, 24, 1, 5, 2, _lib.MSBM_FLAG_ALPHA_REFINE)
+    ctx.pyramid(dev(a), dev(b))
+    d, c = ctx.match_level(0)
+    d0, c0 = host(d).copy(), host(c).copy()
+    ctx.alpha_refine(0, d, c)
+    dg, cg = host(d), host(c)
+    do, co, c2o, ref = oracle.alpha_refine(a, b, 2, 24, ALPHA, d0, c0.astype(np.float64))
+    assert ref.any() and not ref.all()
+    np.testing.assert_array_equal(dg[~ref], d0[~ref])
+    np.testing.assert_array_equal(cg[~ref], c0[~ref])
+    assert np.abs(cg[ref] - co[ref]).max() <= COST_TOL
+    near = (co - c2o) < TIE_TOL
+    assert np.all((dg == do) | near)
+
+
+def test_beta_level_matches_oracle_with_oracle_priors():
+    from paper_1901_09593_gb300 import _lib
+    sc = scenes.make_pair(scenes.SPECS["small_320x240"], 3)
+    s = sc.spec
+    K = 3
+    ref = oracle.disparity(sc.left, sc.right, s.max_disp, K, s.window, s.radius)
+    ctx = ctx_for(s.width, s.height, s.max_disp, K, s.window, s.radius, _lib.MSBM_FLAG_BETA_FALLBACK)
+    ctx.pyramid(dev(sc.left), dev(sc.right))
+    pa, pb = oracle.pyramid(sc.left, K), oracle.pyramid(sc.right, K)
+    for k in (1, 0):
+        prior, cprior = ref["d"][k + 1], ref["C"][k + 1].astype(np.float32)
+        d, c, fb = ctx.match_level_beta(k, dev(prior), dev(cprior))
+        dk = oracle.level_disp(s.max_disp, k)
+        do, co, c2o, ev, fbo, ch = oracle.match_level_beta(pa[k], pb[k], s.window // 2, dk, s.radius, prior,
+                                                           cprior.astype(np.float64), BETA)
+        fbg = host(fb).astype(bool)
+        near_gate = np.abs(ch - BETA) < 1e-5
+        assert np.all((fbg == fbo) | near_gate)
+        same = fbg == fbo
+        assert fbo.any() and not fbo.all()
+        compare_level(host(d)[same], host(c)[same], do[same], co[same], c2o[same], f"beta level {k}")
+
+
+def test_gated_pass_end_to_end_small():
+    from paper_1901_09593_gb300 import _lib
+    sc = scenes.make_pair(scenes.SPECS["small_320x240"], 4)
+    s = sc.spec
+    ctx = ctx_for(s.width, s.height, s.max_disp, s.levels, s.window, s.radius, _lib.MSBM_FLAGS_FULL_METHOD)
+    d, c = ctx.disparity(dev(sc.left), dev(sc.right))
+    ctx.sync()
+    ref = oracle.disparity_full(sc.left, sc.right, s.max_disp, s.levels, s.window, s.radius, ALPHA, BETA,
+                                oracle.FULL_METHOD)
+    dg = host(d)
+    assert (dg == ref["d"][0]).mean() > 0.99
+    bg = scenes.bad_rate(dg, sc.gt, sc.mask)
+    bo = scenes.bad_rate(ref["d"][0], sc.gt, sc.mask)
+    assert abs(bg - bo) < 0.005
+    assert ctx.eval_count() > 0
+
+
+@pytest.mark.parametrize("flags_name", ["MSBM_FLAG_SELECTIVE_MEDIAN", "MSBM_FLAGS_FULL_METHOD"])
+def test_gated_pass_beats_flat_bad_rate_on_benchmark_pair(flags_name):
+    from paper_1901_09593_gb300 import _lib
+    sc = scenes.make_pair(scenes.SPECS["bench_1400x1000"], 0)
+    s = sc.spec
+    ctx = ctx_for(s.width, s.height, s.max_disp, s.levels, s.window, s.radius, getattr(_lib, flags_name))
+    d, c = ctx.disparity(dev(sc.left), dev(sc.right))
+    flat = ctx_for(s.width, s.height, s.max_disp, 1, s.window, s.radius, 0)
+    df, cf = flat.disparity(dev(sc.left), dev(sc.right))
+    ctx.sync()
+    flat.sync()
+    bad_h = scenes.bad_rate(host(d), sc.gt, sc.mask)
+    bad_f = scenes.bad_rate(host(df), sc.gt, sc.mask)
+    assert bad_h <= bad_f, (bad_h, bad_f)
