@@ -157,13 +157,10 @@ OPS_PER_EVAL_FULL = 8   # sliding sums: 2 vertical + 2 horizontal, c (2), scale 
 
 def stage_work(name, spec, levels_wh, evals_by_level):
     """(bound, algorithmic amount, unit) of one stage of the pass."""
-    if name == "copy_level0":
-        w, h = levels_wh[0]
-        return "hbm", 2 * w * h + 2 * (w + 32) * (h + 16), "B"
-    if name.startswith("reduce_level"):
-        k = int(name[len("reduce_level"):])
-        (w1, h1), (w, h) = levels_wh[k - 1], levels_wh[k]
-        return "hbm", 2 * w1 * h1 + 2 * (w + 32) * (h + 16), "B"
+    if name == "pyramid":
+        # read both input images once, write every level's apron buffer of both images
+        w0, h0 = levels_wh[0]
+        return "hbm", 2 * w0 * h0 + sum(2 * (w + 32) * (h + 16) for w, h in levels_wh), "B"
     if name.startswith("full_level"):
         k = int(name[len("full_level"):])
         return "alu", evals_by_level[k] * OPS_PER_EVAL_FULL, "op"
@@ -458,9 +455,12 @@ def run_gpu(args):
         cx.disparity(L, R, dm, cm)
         ev_m = cx.eval_count(reset=True)
         dmh = dm.cpu().numpy()
+        prof = [cx.profile_disparity(L, R, dm, cm) for _ in range(5)]
         methods[name] = {"frames_per_s": msteps / (sum(mms) / 1e3), "ms_per_frame": sum(mms) / msteps,
                          "evals_per_frame": ev_m, "bad1": scenes.bad_rate(dmh, sc.gt, sc.mask, 1.0),
-                         "bad2": scenes.bad_rate(dmh, sc.gt, sc.mask, 2.0), "alpha": 0.9, "beta": 0.9}
+                         "bad2": scenes.bad_rate(dmh, sc.gt, sc.mask, 2.0), "alpha": 0.9, "beta": 0.9,
+                         "stages_ms": {nm: round(statistics.mean(v), 5)
+                                       for nm, v in zip(cx.stage_names(), zip(*prof))}}
         cx.close()
     methods["plain"] = {"frames_per_s": fps / world, "ms_per_frame": 1e3 * t_max / args.steps,
                         "evals_per_frame": evals_per_frame, "bad1": bad1_h, "bad2": bad2_h}

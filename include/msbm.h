@@ -152,13 +152,13 @@ msbm_status msbm_disparity_host(msbm_ctx *ctx, const uint8_t *h_left, const uint
 msbm_status msbm_level_result(msbm_ctx *ctx, int32_t level, int16_t *d_out, float *cost_out);
 
 /* Timing aid: run the whole pass once with direct launches, recording a CUDA event
- * before the first kernel and after each kernel on the context's stream, wait, and write
- * each kernel's milliseconds to stage_ms in launch order:
- *   [0]            level-0 copy into the pyramid buffers,
- *   [1 .. K-1]     pyramid reduce producing levels 1 .. K-1,
- *   [K]            full search at level K-1,
- *   [K+1 .. 2K-1]  restricted search at levels K-2 .. 0.
- * n_stages must be 2K.  Results equal msbm_disparity's. */
+ * before the first kernel and after each stage on the context's stream, wait, and write
+ * each stage's milliseconds to stage_ms in launch order:
+ *   [0]          the pyramid: level-0 copy and reduces to levels 1 .. K-1 (fused launches),
+ *   [1]          full search at level K-1 (+ alpha refinement when enabled),
+ *   [2 .. K]     levels K-2 .. 0: restricted search (+ beta gate and gated full search,
+ *                + selective median, when enabled).
+ * n_stages must be K + 1.  Results equal msbm_disparity's. */
 msbm_status msbm_profile_disparity(msbm_ctx *ctx, const uint8_t *d_left, const uint8_t *d_right,
                                    size_t pitch_bytes, int16_t *d_out, float *cost_out,
                                    float *stage_ms, int32_t n_stages);

@@ -7,7 +7,7 @@
 //    the fallback pixels);
 //  * alpha refinement (Eq. 5-7) at the coarsest level: for a pixel with C' <= alpha, the
 //    average of the ZNCC over its 3 x 3 neighbourhood (neighbours inside the image) for
-//    every admissible candidate, and its argmax / max;
+//    every admissible candidate z <= min(D_k - 1, x), and its argmax / max;
 //  * selective median (Eq. 10): for a pixel with C <= alpha, the lower median of the 5 x 5
 //    neighbours whose cost exceeds alpha (unchanged when none does).
 #include <math.h>
@@ -54,87 +54,286 @@ __global__ void beta_gate_kernel(const float *__restrict__ Cc, int Wc, int Hc, i
     }
 }
 
-// Exact-integer ZNCC of the left window at (y, x) and the right window at (y, x - z), read
-// from apron buffers (no clamping needed); rho from c * rsqrt(Va) * rsqrt(Vb).
+// Alpha refinement on a 16 x 8 tile.  E(q, z), the ZNCC of every pixel q of the tile's
+// 18 x 10 neighbourhood region at every candidate z, is computed once per 32-candidate chunk
+// into shared memory, then each refined pixel (cost <= alpha) averages E over its in-image
+// 3 x 3 neighbours (rows, then columns) and keeps the WTA of the averages on a 64-bit
+// (ordered mean, ~z) key: ties keep the smallest z.  E uses exact integer window sums of the
+// staged image rows (clamp-to-edge): each thread packs its left window as dp4a words, and for
+// 4 consecutive candidates loads the right row words once and extracts the 4 windows with
+// funnel shifts; rho = float(N Sab - Sa Sb) * rsqrt(Va) * rsqrt(Vb), 0 for a flat window.
+constexpr int AR_TW = 16, AR_TH = 8, AR_RW = AR_TW + 2, AR_RH = AR_TH + 2, AR_ZC = 32;
+constexpr int AR_NP = AR_RW * AR_RH;     // region pixels (180)
+
 template <int NH>
-__device__ __forceinline__ float zncc_direct(const uint8_t *L, const uint8_t *R, int pitch, int y, int x, int z) {
-    constexpr int WIN = 2 * NH + 1, N = WIN * WIN;
-    int sa = 0, sb = 0, saa = 0, sbb = 0, sab = 0;
+__global__ void __launch_bounds__(256) alpha_refine_kernel(const uint8_t *L, const uint8_t *R, int pitch, int W,
+                                                           int H, int Dk, float alpha, int16_t *d, float *C,
+                                                           unsigned long long *evals) {
+    constexpr int WIN = 2 * NH + 1, N = WIN * WIN, NW = (WIN + 3) / 4;
+    constexpr int SLW = AR_RW + 2 * NH, SLH = AR_RH + 2 * NH;   // staged left region
+    constexpr int SU = AR_RW + AR_ZC - 1;                        // right window columns per chunk
+    constexpr int SRW = SU + 2 * NH;                             // staged right columns per chunk
+    constexpr int SRWW = (SRW + 3) / 4 + 2;                      // words per staged right row
+    __shared__ uint8_t sL[SLH][SLW];
+    __shared__ uint32_t sR[SLH][SRWW];
+    __shared__ int2 stR[AR_RH][SU];              // {Sb, bits(rsqrt(Vb)) or 0}
+    __shared__ int vs[AR_RH][SRW], vq[AR_RH][SRW];
+    __shared__ float E[AR_NP][AR_ZC + 1];
+    __shared__ unsigned long long best[AR_TW * AR_TH];
+    __shared__ int qual[AR_TW * AR_TH];
+    __shared__ int any;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int x0 = blockIdx.x * AR_TW, y0 = blockIdx.y * AR_TH;
+    const int rx0 = x0 - 1, ry0 = y0 - 1;        // region origin (may lie outside the image)
+    if (tid == 0) any = 0;
+    __syncthreads();
+    if (tid < AR_TW * AR_TH) {
+        const int x = x0 + tid % AR_TW, y = y0 + tid / AR_TW;
+        const int q = x < W && y < H && !(C[(size_t)y * W + x] > alpha);
+        qual[tid] = q;
+        best[tid] = 0ull;
+        if (q) any = 1;
+    }
+    {
+        constexpr int T = (SLH * SLW + 255) / 256;
+        uint8_t v[T];
 #pragma unroll
-    for (int i = -NH; i <= NH; ++i) {
-        const uint8_t *lr = L + (ptrdiff_t)(y + i) * pitch + x;
-        const uint8_t *rr = R + (ptrdiff_t)(y + i) * pitch + x - z;
+        for (int t = 0; t < T; ++t) {
+            const int i = tid + 256 * t, r = i / SLW, c = i - r * SLW;
+            const int yy = min(max(ry0 - NH + r, 0), H - 1), xx = min(max(rx0 - NH + c, 0), W - 1);
+            v[t] = i < SLH * SLW ? L[(ptrdiff_t)yy * pitch + xx] : 0;
+        }
 #pragma unroll
-        for (int j = -NH; j <= NH; ++j) {
-            const int a = __ldg(lr + j), b = __ldg(rr + j);
-            sa += a; sb += b; saa += a * a; sbb += b * b; sab += a * b;
+        for (int t = 0; t < T; ++t) {
+            const int i = tid + 256 * t;
+            if (i < SLH * SLW) sL[i / SLW][i % SLW] = v[t];
         }
     }
-    const int va = N * saa - sa * sa, vb = N * sbb - sb * sb;
-    if (va <= 0 || vb <= 0) return 0.f;
-    return static_cast<float>(N * sab - sa * sb) * rsqrtf(static_cast<float>(va)) * rsqrtf(static_cast<float>(vb));
-}
-
-// One warp per pixel; the warp skips pixels whose cost exceeds alpha.
-template <int NH>
-__global__ void alpha_refine_kernel(const uint8_t *L, const uint8_t *R, int pitch, int W, int H, int Dk,
-                                    float alpha, int16_t *d, float *C, unsigned long long *evals) {
-    const int lane = threadIdx.x & 31;
-    const int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (p >= W * H) return;
-    const int y = p / W, x = p - y * W;
-    if (C[p] > alpha) return;
-    const int zmax = min(Dk - 1, x);
-    const int y0 = max(y - 1, 0), y1 = min(y + 1, H - 1), x0 = max(x - 1, 0), x1 = min(x + 1, W - 1);
-    const float inv = 1.f / static_cast<float>((y1 - y0 + 1) * (x1 - x0 + 1));
-    unsigned long long best = 0ull;
-    for (int z = lane; z <= zmax; z += 32) {
-        float s = 0.f;
-        for (int m = y0; m <= y1; ++m)
-            for (int q = x0; q <= x1; ++q) s += zncc_direct<NH>(L, R, pitch, m, q, z);
-        const unsigned long long k = wta_key(s * inv, z);
-        best = k > best ? k : best;
-    }
+    __syncthreads();
+    if (!any) return;
+    // this thread's region pixel: packed left window and its statistics
+    const int pr = tid / AR_RW, pc = tid - pr * AR_RW;
+    uint32_t Lw[WIN][NW];
+    int2 la = make_int2(0, 0);
+    if (tid < AR_NP) {
+        uint32_t s = 0, q = 0;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long k = __shfl_xor_sync(0xFFFFFFFFu, best, o);
-        best = k > best ? k : best;
+        for (int i = 0; i < WIN; ++i)
+#pragma unroll
+            for (int k = 0; k < NW; ++k) {
+                uint32_t w = 0;
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+                    if (4 * k + b < WIN) w |= static_cast<uint32_t>(sL[pr + i][pc + 4 * k + b]) << (8 * b);
+                Lw[i][k] = w;
+                s = dp4a_u8(w, 0x01010101u, s);
+                q = dp4a_u8(w, w, q);
+            }
+        const int V = N * static_cast<int>(q) - static_cast<int>(s) * static_cast<int>(s);
+        la = make_int2(static_cast<int>(s), V > 0 ? __float_as_int(rsqrtf(static_cast<float>(V))) : 0);
     }
-    if (lane == 0) {
-        d[p] = static_cast<int16_t>(0xFFFFFFFFu - static_cast<uint32_t>(best & 0xFFFFFFFFull));
-        C[p] = float_from_order_key(static_cast<uint32_t>(best >> 32));
-        if (evals)
-            atomicAdd(evals, static_cast<unsigned long long>((y1 - y0 + 1) * (x1 - x0 + 1)) * (zmax + 1));
+    const int zmax_tile = min(Dk - 1, min(x0 + AR_TW, W) - 1);
+    for (int z0 = 0; z0 <= zmax_tile; z0 += AR_ZC) {
+        __syncthreads();      // the previous chunk's E and staging are consumed
+        // right image columns cx .. cx + SRW - 1 (clamp-to-edge), zero padding after them
+        const int cx = rx0 - (z0 + AR_ZC - 1) - NH;
+        {
+            constexpr int NB = SLH * SRWW * 4, T = (NB + 255) / 256;
+            uint8_t v[T];
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                const int i = tid + 256 * t, r = i / (SRWW * 4), c = i - r * (SRWW * 4);
+                const int yy = min(max(ry0 - NH + r, 0), H - 1), xx = min(max(cx + c, 0), W - 1);
+                v[t] = (i < NB && c < SRW) ? R[(ptrdiff_t)yy * pitch + xx] : 0;
+            }
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                const int i = tid + 256 * t;
+                if (i < NB) reinterpret_cast<uint8_t *>(&sR[0][0])[i] = v[t];
+            }
+        }
+        __syncthreads();
+        // right window statistics of the chunk: vertical, then horizontal sums
+        for (int i = tid; i < AR_RH * SRW; i += 256) {
+            const int r = i / SRW, c = i - r * SRW;
+            const uint8_t *col = reinterpret_cast<const uint8_t *>(&sR[r][0]) + c;
+            int s = 0, q = 0;
+#pragma unroll
+            for (int a = 0; a < WIN; ++a) {
+                const int v = col[a * SRWW * 4];
+                s += v;
+                q += v * v;
+            }
+            vs[r][c] = s;
+            vq[r][c] = q;
+        }
+        __syncthreads();
+        for (int i = tid; i < AR_RH * SU; i += 256) {
+            const int r = i / SU, u = i - r * SU;
+            int s = 0, q = 0;
+#pragma unroll
+            for (int b = 0; b < WIN; ++b) {
+                s += vs[r][u + b];
+                q += vq[r][u + b];
+            }
+            const int V = N * q - s * s;
+            stR[r][u] = make_int2(s, V > 0 ? __float_as_int(rsqrtf(static_cast<float>(V))) : 0);
+        }
+        __syncthreads();
+        if (tid < AR_NP) {
+#pragma unroll 1
+            for (int g = 0; g < AR_ZC / 4; ++g) {
+                const int um = pc + AR_ZC - 4 - 4 * g;       // first staged column, candidate 4g + 3
+                const int w0 = um >> 2, sh = um & 3;
+                uint32_t sab[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+                for (int i = 0; i < WIN; ++i) {
+                    const uint32_t *row = &sR[pr + i][w0];
+                    uint32_t raw[NW + 2], alw[NW + 1];
+#pragma unroll
+                    for (int k = 0; k < NW + 2; ++k) raw[k] = row[k];
+#pragma unroll
+                    for (int k = 0; k <= NW; ++k) alw[k] = __funnelshift_r(raw[k], raw[k + 1], 8 * sh);
+#pragma unroll
+                    for (int o = 0; o < 4; ++o)
+#pragma unroll
+                        for (int k = 0; k < NW; ++k) {
+                            const uint32_t w = o ? __funnelshift_r(alw[k], alw[k + 1], 8 * o) : alw[k];
+                            sab[o] = dp4a_u8(Lw[i][k], w, sab[o]);
+                        }
+                }
+#pragma unroll
+                for (int o = 0; o < 4; ++o) {
+                    const int2 rb = stR[pr][um + o];
+                    float e = 0.f;
+                    if (la.y != 0 && rb.y != 0)
+                        e = static_cast<float>(N * static_cast<int>(sab[o]) - la.x * rb.x) * __int_as_float(la.y) *
+                            __int_as_float(rb.y);
+                    E[tid][4 * g + 3 - o] = e;
+                }
+            }
+        }
+        __syncthreads();
+        for (int o = warp; o < AR_TW * AR_TH; o += 8) {
+            if (!qual[o]) continue;
+            const int x = x0 + o % AR_TW, y = y0 + o / AR_TW, z = z0 + lane;
+            unsigned long long k = 0ull;
+            if (z <= min(Dk - 1, x)) {
+                const int ya = max(y - 1, 0), yb = min(y + 1, H - 1), xa = max(x - 1, 0), xb = min(x + 1, W - 1);
+                const float inv = 1.f / static_cast<float>((yb - ya + 1) * (xb - xa + 1));
+                float s = 0.f;
+                for (int m = ya; m <= yb; ++m)
+                    for (int q = xa; q <= xb; ++q) s += E[(m - ry0) * AR_RW + (q - rx0)][lane];
+                k = wta_key(s * inv, z);
+            }
+#pragma unroll
+            for (int sh = 16; sh > 0; sh >>= 1) {
+                const unsigned long long t = __shfl_xor_sync(0xFFFFFFFFu, k, sh);
+                k = t > k ? t : k;
+            }
+            if (lane == 0 && k > best[o]) best[o] = k;
+        }
+    }
+    __syncthreads();
+    if (tid < AR_TW * AR_TH && qual[tid]) {
+        const int x = x0 + tid % AR_TW, y = y0 + tid / AR_TW;
+        const size_t p = (size_t)y * W + x;
+        const unsigned long long k = best[tid];
+        d[p] = static_cast<int16_t>(0xFFFFFFFFu - static_cast<uint32_t>(k & 0xFFFFFFFFull));
+        C[p] = float_from_order_key(static_cast<uint32_t>(k >> 32));
+        if (evals) {
+            const int ya = max(y - 1, 0), yb = min(y + 1, H - 1), xa = max(x - 1, 0), xb = min(x + 1, W - 1);
+            atomicAdd(evals, static_cast<unsigned long long>((yb - ya + 1) * (xb - xa + 1)) * (min(Dk - 1, x) + 1));
+        }
     }
 }
 
-__global__ void selective_median_kernel(const int16_t *__restrict__ d_in, const float *__restrict__ C, int W,
-                                        int H, float alpha, int16_t *d_out) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+// Comparator list of Batcher's merge-exchange sort (Knuth, TAOCP vol. 3, Sec. 5.2.2,
+// Algorithm M) for n inputs, built at compile time.
+template <int n>
+struct MergeExchange {
+    static constexpr int count() {
+        int t = 0;
+        while ((1 << t) < n) ++t;
+        int m = 0;
+        for (int p = 1 << (t - 1); p > 0; p >>= 1)
+            for (int q = 1 << (t - 1), r = 0, d = p; d > 0; d = q - p, q >>= 1, r = p)
+                for (int i = 0; i + d < n; ++i)
+                    if ((i & p) == r) ++m;
+        return m;
+    }
+    static constexpr int M = count();
+    int a[M], b[M];
+    constexpr MergeExchange() : a(), b() {
+        int t = 0;
+        while ((1 << t) < n) ++t;
+        int m = 0;
+        for (int p = 1 << (t - 1); p > 0; p >>= 1)
+            for (int q = 1 << (t - 1), r = 0, d = p; d > 0; d = q - p, q >>= 1, r = p)
+                for (int i = 0; i + d < n; ++i)
+                    if ((i & p) == r) {
+                        a[m] = i;
+                        b[m] = i + d;
+                        ++m;
+                    }
+    }
+};
+
+constexpr int MED_TX = 32, MED_TY = 8, MED_R = 2;
+constexpr int MED_SW = MED_TX + 2 * MED_R, MED_SH = MED_TY + 2 * MED_R;
+constexpr int MED_NONE = 0x7FFF;     // a neighbour that does not vote (outside, or cost <= alpha)
+
+// Eq. 10 on a 32 x 8 tile: the 5 x 5 neighbourhood (inside the image) is staged in shared
+// memory as voting disparities (cost > alpha) or MED_NONE; a pixel with cost <= alpha sorts
+// its 24 neighbours (it does not vote itself) with a merge-exchange network, so the voters
+// come first in ascending order, and takes the lower median of the voters.
+__global__ void __launch_bounds__(MED_TX * MED_TY)
+selective_median_kernel(const int16_t *__restrict__ d_in, const float *__restrict__ C, int W, int H, float alpha,
+                        int16_t *d_out) {
+    __shared__ int16_t sv[MED_SH][MED_SW];
+    const int x0 = blockIdx.x * MED_TX, y0 = blockIdx.y * MED_TY;
+    const int tid = threadIdx.y * MED_TX + threadIdx.x;
+    for (int i = tid; i < MED_SH * MED_SW; i += MED_TX * MED_TY) {
+        const int yy = y0 - MED_R + i / MED_SW, xx = x0 - MED_R + i % MED_SW;
+        int v = MED_NONE;
+        if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
+            const size_t p = (size_t)yy * W + xx;
+            if (__ldg(C + p) > alpha) v = __ldg(d_in + p);
+        }
+        sv[i / MED_SW][i % MED_SW] = static_cast<int16_t>(v);
+    }
+    __syncthreads();
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
     if (x >= W || y >= H) return;
     const size_t o = (size_t)y * W + x;
-    int16_t out = d_in[o];
+    int out = d_in[o];
     if (!(C[o] > alpha)) {
-        int v[25], cnt = 0;
-        for (int m = max(y - 2, 0); m <= min(y + 2, H - 1); ++m)
-            for (int q = max(x - 2, 0); q <= min(x + 2, W - 1); ++q) {
-                const size_t p = (size_t)m * W + q;
-                if (__ldg(C + p) > alpha) v[cnt++] = __ldg(d_in + p);
+        constexpr int NB = (2 * MED_R + 1) * (2 * MED_R + 1) - 1;
+        int v[NB], cnt = 0;
+#pragma unroll
+        for (int m = 0, k = 0; m <= 2 * MED_R; ++m)
+#pragma unroll
+            for (int q = 0; q <= 2 * MED_R; ++q) {
+                if (m == MED_R && q == MED_R) continue;
+                v[k] = sv[threadIdx.y + m][threadIdx.x + q];
+                cnt += v[k] != MED_NONE;
+                ++k;
             }
         if (cnt > 0) {
-            for (int i = 1; i < cnt; ++i) {           // insertion sort of at most 24 values
-                const int t = v[i];
-                int j = i - 1;
-                while (j >= 0 && v[j] > t) {
-                    v[j + 1] = v[j];
-                    --j;
-                }
-                v[j + 1] = t;
+            constexpr MergeExchange<NB> net;
+#pragma unroll
+            for (int c = 0; c < net.M; ++c) {
+                const int lo = min(v[net.a[c]], v[net.b[c]]), hi = max(v[net.a[c]], v[net.b[c]]);
+                v[net.a[c]] = lo;
+                v[net.b[c]] = hi;
             }
-            out = static_cast<int16_t>(v[(cnt - 1) / 2]);
+            const int want = (cnt - 1) / 2;       // at most NB / 2 - 1
+#pragma unroll
+            for (int i = 0; i < NB / 2; ++i)
+                if (i == want) out = v[i];
         }
     }
-    d_out[o] = out;
+    d_out[o] = static_cast<int16_t>(out);
 }
 
 }  // namespace
@@ -152,9 +351,8 @@ cudaError_t launch_beta_gate(const float *Cc, int Wc, int Hc, int W, int H, floa
 template <int NH>
 static cudaError_t alpha_launch(const LevelBuf &l, float alpha, int16_t *d, float *C, unsigned long long *evals,
                                 cudaStream_t st) {
-    const int warps = 8;
-    dim3 blk(32 * warps), grd((l.W * l.H + warps - 1) / warps);
-    alpha_refine_kernel<NH><<<grd, blk, 0, st>>>(l.img(0), l.img(1), l.pitch, l.W, l.H, l.Dk, alpha, d, C, evals);
+    dim3 grd((l.W + AR_TW - 1) / AR_TW, (l.H + AR_TH - 1) / AR_TH);
+    alpha_refine_kernel<NH><<<grd, 256, 0, st>>>(l.img(0), l.img(1), l.pitch, l.W, l.H, l.Dk, alpha, d, C, evals);
     return cudaGetLastError();
 }
 
@@ -173,7 +371,7 @@ cudaError_t launch_alpha_refine(const LevelBuf &l, int nh, float alpha, int16_t 
 
 cudaError_t launch_selective_median(const int16_t *d_in, const float *C, int W, int H, float alpha, int16_t *d_out,
                                     cudaStream_t st) {
-    dim3 blk(32, 8), grd((W + 31) / 32, (H + 7) / 8);
+    dim3 blk(MED_TX, MED_TY), grd((W + MED_TX - 1) / MED_TX, (H + MED_TY - 1) / MED_TY);
     selective_median_kernel<<<grd, blk, 0, st>>>(d_in, C, W, H, alpha, d_out);
     return cudaGetLastError();
 }

@@ -8,6 +8,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -121,10 +122,31 @@ inline msbm_status cuda_status(cudaError_t e) {
     return MSBM_ERR_CUDA;
 }
 
+// The pyramid: a plain copy for one level, else fused launches of up to PF_MAXF reductions
+// each (the first also writing level 0).
 msbm_status enqueue_pyramid(msbm_ctx *c, const uint8_t *L, const uint8_t *R, size_t pitch,
                             cudaStream_t st) {
-    cudaError_t e = launch_apron_copy(L, R, pitch, c->lv[0], st);
-    for (int k = 1; e == cudaSuccess && k < c->p.levels; ++k) e = launch_pyr_reduce(c->lv[k - 1], c->lv[k], st);
+    const int K = c->p.levels;
+    if (K == 1) return cuda_status(launch_apron_copy(L, R, pitch, c->lv[0], st));
+    cudaError_t e = cudaSuccess;
+    for (int s = 0; e == cudaSuccess && s < K - 1; s += PF_MAXF) {
+        PyrFuseArgs a;
+        memset(&a, 0, sizeof(a));
+        a.F = std::min(PF_MAXF, K - 1 - s);
+        a.write_src = s == 0;
+        a.src[0] = s == 0 ? L : c->lv[s].img(0);
+        a.src[1] = s == 0 ? R : c->lv[s].img(1);
+        a.spitch = s == 0 ? pitch : (size_t)c->lv[s].pitch;
+        for (int j = 0; j <= a.F; ++j) {
+            const LevelBuf &l = c->lv[s + j];
+            a.W[j] = l.W;
+            a.H[j] = l.H;
+            a.dst[j][0] = l.img(0);
+            a.dst[j][1] = l.img(1);
+            a.dpitch[j] = l.pitch;
+        }
+        e = launch_pyr_fused(a, st);
+    }
     return cuda_status(e);
 }
 
@@ -148,9 +170,9 @@ msbm_status enqueue_level(msbm_ctx *c, int k, const int16_t *prior, int16_t *d, 
     } else {
         RestrArgs a;
         memset(&a, 0, sizeof(a));
-        a.tmL = l.tmL64;
-        a.tmR64 = l.tmR64;
-        a.tmR256 = l.tmR256;
+        a.tmL = l.tmRL;
+        a.tmR128 = l.tmRR128;
+        a.tmR256 = l.tmRR256;
         a.t.skip = skip;
         a.t.Limg = l.img(0); a.t.Rimg = l.img(1); a.t.pitch = l.pitch;
         a.t.W = l.W; a.t.H = l.H; a.t.Dk = l.Dk; a.t.r = c->p.radius;
@@ -177,30 +199,37 @@ msbm_status enqueue_level_beta(msbm_ctx *c, int k, const int16_t *prior, const f
     return enqueue_level(c, k, nullptr, d, cost, st, l.mask, l.tile_flags);
 }
 
+// Level k of the pass with the gated steps the context's flags select: the full-range
+// search (+ alpha refinement) at the coarsest level, the restricted search (+ beta fallback,
+// + selective median) below it.  Writes the level's final map to d / cost at level 0.
+msbm_status enqueue_match(msbm_ctx *c, int k, int16_t *d, float *cost, cudaStream_t st) {
+    const int K = c->p.levels;
+    const uint32_t f = c->p.flags;
+    LevelBuf &l = c->lv[k];
+    int16_t *dk = k == 0 ? d : l.d;                        // final map of this level
+    float *ck = k == 0 ? (cost ? cost : c->c0) : l.c;      // its cost
+    msbm_status s;
+    if (k == K - 1) {
+        s = enqueue_level(c, k, nullptr, dk, ck, st);
+        if (s == MSBM_OK && (f & MSBM_FLAG_ALPHA_REFINE))
+            s = cuda_status(launch_alpha_refine(l, c->nh, c->p.alpha, dk, ck, c->d_evals, st));
+        return s;
+    }
+    const int16_t *prior = c->lv[k + 1].d;
+    const bool med = (f & MSBM_FLAG_SELECTIVE_MEDIAN) != 0;
+    int16_t *dm = med ? l.dtmp : dk;                      // matching output
+    if (f & MSBM_FLAG_BETA_FALLBACK)
+        s = enqueue_level_beta(c, k, prior, c->lv[k + 1].c, dm, ck, st);
+    else
+        s = enqueue_level(c, k, prior, dm, ck, st);
+    if (s == MSBM_OK && med) s = cuda_status(launch_selective_median(dm, ck, l.W, l.H, c->p.alpha, dk, st));
+    return s;
+}
+
 msbm_status enqueue_all(msbm_ctx *c, const uint8_t *L, const uint8_t *R, size_t pitch, int16_t *d,
                         float *cost, cudaStream_t st) {
     msbm_status s = enqueue_pyramid(c, L, R, pitch, st);
-    const int K = c->p.levels;
-    const uint32_t f = c->p.flags;
-    for (int k = K - 1; s == MSBM_OK && k >= 0; --k) {
-        LevelBuf &l = c->lv[k];
-        int16_t *dk = k == 0 ? d : l.d;                        // final map of this level
-        float *ck = k == 0 ? (cost ? cost : c->c0) : l.c;      // its cost
-        if (k == K - 1) {
-            s = enqueue_level(c, k, nullptr, dk, ck, st);
-            if (s == MSBM_OK && (f & MSBM_FLAG_ALPHA_REFINE))
-                s = cuda_status(launch_alpha_refine(l, c->nh, c->p.alpha, dk, ck, c->d_evals, st));
-            continue;
-        }
-        const int16_t *prior = c->lv[k + 1].d;
-        const bool med = (f & MSBM_FLAG_SELECTIVE_MEDIAN) != 0;
-        int16_t *dm = med ? l.dtmp : dk;                      // matching output
-        if (f & MSBM_FLAG_BETA_FALLBACK)
-            s = enqueue_level_beta(c, k, prior, c->lv[k + 1].c, dm, ck, st);
-        else
-            s = enqueue_level(c, k, prior, dm, ck, st);
-        if (s == MSBM_OK && med) s = cuda_status(launch_selective_median(dm, ck, l.W, l.H, c->p.alpha, dk, st));
-    }
+    for (int k = c->p.levels - 1; s == MSBM_OK && k >= 0; --k) s = enqueue_match(c, k, d, cost, st);
     return s;
 }
 
@@ -242,7 +271,7 @@ msbm_status msbm_create(const msbm_params *params, void *cuda_stream, msbm_ctx *
     c->device = dev;
     c->num_sms = prop.multiProcessorCount;
     c->stream = static_cast<cudaStream_t>(cuda_stream);
-    const int rowsT = 8 + 2 * c->nh;   // staged rows of the full-range and restricted tiles
+    const int rowsT = 8 + 2 * c->nh;   // staged rows of the full-range tile
     cudaError_t e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_evals, sizeof(unsigned long long));
@@ -275,13 +304,16 @@ msbm_status msbm_create(const msbm_params *params, void *cuda_stream, msbm_ctx *
         }
         l.full_sx = choose_sx(W, H, c->num_sms);
         if (e == cudaSuccess) {
-            bool ok = encode_u8(&l.tmL64, l.base[0], l.pitch, l.rows, 64, rowsT) &&
-                      encode_u8(&l.tmR64, l.base[1], l.pitch, l.rows, 64, rowsT) &&
+            const int rowsR = 16 + 2 * c->nh;
+            bool ok = encode_u8(&l.tmFL, l.base[0], l.pitch, l.rows, 32 * l.full_sx + 32, rowsT) &&
                       encode_u8(&l.tmR256, l.base[1], l.pitch, l.rows, 256, rowsT) &&
-                      encode_u8(&l.tmFL, l.base[0], l.pitch, l.rows, 32 * l.full_sx + 32, rowsT);
+                      encode_u8(&l.tmRL, l.base[0], l.pitch, l.rows, 64, rowsR) &&
+                      encode_u8(&l.tmRR128, l.base[1], l.pitch, l.rows, 128, rowsR) &&
+                      encode_u8(&l.tmRR256, l.base[1], l.pitch, l.rows, 256, rowsR);
             if (!ok) { c->lv.push_back(l); free_ctx(c); return MSBM_ERR_UNSUPPORTED; }
         }
         if (e == cudaSuccess) e = zncc_full_prepare(c->nh, l.full_sx);
+        if (e == cudaSuccess) e = zncc_restricted_prepare(c->nh);
         c->lv.push_back(l);
         W = (W + 1) / 2;
         H = (H + 1) / 2;
@@ -461,8 +493,8 @@ msbm_status msbm_profile_disparity(msbm_ctx *ctx, const uint8_t *d_left, const u
     if (!ctx || !d_left || !d_right || !d_out || !stage_ms || pitch_bytes < (size_t)ctx->p.width)
         return MSBM_ERR_INVALID_ARG;
     const int K = ctx->p.levels;
-    if (n_stages != 2 * K) return MSBM_ERR_INVALID_ARG;
-    std::vector<cudaEvent_t> ev(2 * K + 1, nullptr);
+    if (n_stages != K + 1) return MSBM_ERR_INVALID_ARG;
+    std::vector<cudaEvent_t> ev(K + 2, nullptr);
     cudaError_t e = cudaSuccess;
     for (auto &x : ev)
         if (e == cudaSuccess) e = cudaEventCreate(&x);
@@ -470,20 +502,14 @@ msbm_status msbm_profile_disparity(msbm_ctx *ctx, const uint8_t *d_left, const u
     msbm_status s = cuda_status(e);
     int i = 0;
     if (s == MSBM_OK) s = cuda_status(cudaEventRecord(ev[i++], st));
-    if (s == MSBM_OK) s = cuda_status(launch_apron_copy(d_left, d_right, pitch_bytes, ctx->lv[0], st));
+    if (s == MSBM_OK) s = enqueue_pyramid(ctx, d_left, d_right, pitch_bytes, st);
     if (s == MSBM_OK) s = cuda_status(cudaEventRecord(ev[i++], st));
-    for (int k = 1; s == MSBM_OK && k < K; ++k) {
-        s = cuda_status(launch_pyr_reduce(ctx->lv[k - 1], ctx->lv[k], st));
-        if (s == MSBM_OK) s = cuda_status(cudaEventRecord(ev[i++], st));
-    }
     for (int k = K - 1; s == MSBM_OK && k >= 0; --k) {
-        int16_t *dk = k == 0 ? d_out : ctx->lv[k].d;
-        float *ck = k == 0 ? cost_out : ctx->lv[k].c;
-        s = enqueue_level(ctx, k, k == K - 1 ? nullptr : ctx->lv[k + 1].d, dk, ck, st);
+        s = enqueue_match(ctx, k, d_out, cost_out, st);
         if (s == MSBM_OK) s = cuda_status(cudaEventRecord(ev[i++], st));
     }
     if (s == MSBM_OK) s = cuda_status(cudaStreamSynchronize(st));
-    for (int j = 0; s == MSBM_OK && j < 2 * K; ++j)
+    for (int j = 0; s == MSBM_OK && j < K + 1; ++j)
         s = cuda_status(cudaEventElapsedTime(&stage_ms[j], ev[j], ev[j + 1]));
     for (auto &x : ev)
         if (x) cudaEventDestroy(x);

@@ -23,12 +23,13 @@ struct LevelBuf {
     int16_t *dtmp = nullptr;     // pre-median disparity map (SELECTIVE_MEDIAN)
     uint8_t *mask = nullptr;     // fallback mask (BETA_FALLBACK)
     int *tile_flags = nullptr;   // full-range tiles holding a fallback pixel (BETA_FALLBACK)
-    // TMA maps over the apron buffers, all 8 + 2n rows high:
-    //   tmL64  : left,  64 bytes wide  (restricted tile's left tile)
-    //   tmR64  : right, 64 bytes wide  (restricted tile's narrow right spans)
-    //   tmR256 : right, 256 bytes wide (restricted wide spans, full-range right spans)
-    //   tmFL   : left,  32*SX + 32 bytes wide (full-range left tile), SX per level
-    CUtensorMap tmL64, tmR64, tmR256, tmFL;
+    // TMA maps over the apron buffers.  Full-range tile (8 + 2n rows high):
+    //   tmFL   : left,  32*SX + 32 bytes wide, SX per level
+    //   tmR256 : right, 256 bytes wide
+    // Restricted tile (16 + 2n rows high):
+    //   tmRL   : left,  64 bytes wide
+    //   tmRR128, tmRR256 : right, 128 / 256 bytes wide (narrow / wide candidate spans)
+    CUtensorMap tmFL, tmR256, tmRL, tmRR128, tmRR256;
     int full_sx = 4;             // full-range tile width 32*full_sx at this level
     int full_zblock = 0;         // full-range z-block (0 = the tile's maximum)
     uint8_t *img(int which) const {
@@ -75,15 +76,28 @@ struct RestrTileArgs {
 };
 
 struct RestrArgs {
-    CUtensorMap tmL;     // box {64, 8 + 2n} over the left apron buffer
-    CUtensorMap tmR64;   // box {64, 8 + 2n} over the right apron buffer
-    CUtensorMap tmR256;  // box {256, 8 + 2n} over the right apron buffer
+    CUtensorMap tmL;     // box {64, 16 + 2n} over the left apron buffer
+    CUtensorMap tmR128;  // box {128, 16 + 2n} over the right apron buffer
+    CUtensorMap tmR256;  // box {256, 16 + 2n} over the right apron buffer
     RestrTileArgs t;
 };
 
 cudaError_t launch_apron_copy(const uint8_t *L, const uint8_t *R, size_t spitch, const LevelBuf &lv,
                               cudaStream_t st);
 cudaError_t launch_pyr_reduce(const LevelBuf &src, const LevelBuf &dst, cudaStream_t st);
+
+// Fused pyramid launch: levels s+1 .. s+F from level s (index 0 below is level s).
+constexpr int PF_MAXF = 3;
+struct PyrFuseArgs {
+    const uint8_t *src[2];      // level s image origins: the caller's images (s = 0) or apron buffers
+    size_t spitch;
+    int F;                      // reductions fused, 1 .. PF_MAXF
+    int write_src;              // 1: also write level s's apron buffers (s = 0)
+    int W[PF_MAXF + 1], H[PF_MAXF + 1];
+    uint8_t *dst[PF_MAXF + 1][2];   // apron buffer image origins of levels s .. s+F
+    int dpitch[PF_MAXF + 1];
+};
+cudaError_t launch_pyr_fused(const PyrFuseArgs &a, cudaStream_t st);
 cudaError_t launch_level_extract(const LevelBuf &lv, int which, uint8_t *out, cudaStream_t st);
 cudaError_t launch_zncc_full(const FullArgs &a, int nh, int sx, cudaStream_t st);
 cudaError_t launch_beta_gate(const float *Cc, int Wc, int Hc, int W, int H, float beta, uint8_t *mask,
@@ -93,6 +107,7 @@ cudaError_t launch_alpha_refine(const LevelBuf &l, int nh, float alpha, int16_t 
 cudaError_t launch_selective_median(const int16_t *d_in, const float *C, int W, int H, float alpha, int16_t *d_out,
                                     cudaStream_t st);
 cudaError_t zncc_full_prepare(int nh, int sx);
+cudaError_t zncc_restricted_prepare(int nh);
 cudaError_t launch_zncc_restricted(const RestrArgs &a, int nh, cudaStream_t st);
 size_t zncc_full_smem_bytes(int nh, int sx);
 

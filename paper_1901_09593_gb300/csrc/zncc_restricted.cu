@@ -1,7 +1,8 @@
 // zncc_restricted.cu -- standalone launch of the restricted ZNCC winner-take-all tile
-// (Sec. III-C, Eq. 8-9, first branch; design in zncc_restricted_px_tile.cuh): one CTA of
-// 256 threads, one per pixel, per 32 x 8 tile.
-#include "zncc_restricted_px_tile.cuh"
+// (Sec. III-C, Eq. 8-9, first branch; design in zncc_restricted_tile.cuh): one CTA of
+// 256 threads per 32 x 16 tile, each thread a vertical pair of pixels that share a prior
+// cell and the products of their 2n common window rows.
+#include "zncc_restricted_tile.cuh"
 
 namespace msbm {
 
@@ -9,8 +10,11 @@ namespace {
 
 using namespace tiles;
 
+constexpr int SA_QX = 32;    // threads per tile row; tile width SA_QX pixels
+constexpr int SA_NCOL = 1;
+
 template <int NH, int G>
-__global__ void __launch_bounds__(256) zncc_restricted_kernel(const __grid_constant__ RestrArgs a) {
+__global__ void __launch_bounds__(SA_QX * 8) zncc_restricted_kernel(const __grid_constant__ RestrArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
     if (threadIdx.x == 0) {
         mbar_init(reinterpret_cast<uint64_t *>(smem), 1);
@@ -18,16 +22,33 @@ __global__ void __launch_bounds__(256) zncc_restricted_kernel(const __grid_const
     }
     __syncthreads();
     uint32_t parity = 0;
-    restr_tile_px<NH, G>(a.t, &a.tmL, &a.tmR64, &a.tmR256, blockIdx.x, blockIdx.y, smem, parity);
+    restr_tile<NH, G, SA_QX, SA_NCOL>(a.t, &a.tmL, &a.tmR128, &a.tmR256, blockIdx.x, blockIdx.y, smem, parity);
+}
+
+template <int NH, int G>
+cudaError_t prepare_t() {
+    using C = RCfg<NH, SA_QX, SA_NCOL>;
+    return cudaFuncSetAttribute(zncc_restricted_kernel<NH, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(C::BYTES));
 }
 
 template <int NH, int G>
 cudaError_t launch_restr_t(const RestrArgs &a, cudaStream_t st) {
-    using C = RCfgPx<NH>;
-    static_assert(C::BYTES <= 48 * 1024, "restricted tile fits the default shared memory");
-    dim3 grd((a.t.W + PX_TX - 1) / PX_TX, (a.t.H + PX_TY - 1) / PX_TY);
-    zncc_restricted_kernel<NH, G><<<grd, PX_TX * PX_TY, C::BYTES, st>>>(a);
+    using C = RCfg<NH, SA_QX, SA_NCOL>;
+    static_assert(C::TX == 32 && C::BYTES <= 227 * 1024, "restricted tile shape");
+    dim3 grd((a.t.W + C::TX - 1) / C::TX, (a.t.H + RT_TY - 1) / RT_TY);
+    zncc_restricted_kernel<NH, G><<<grd, C::THREADS, C::BYTES, st>>>(a);
     return cudaGetLastError();
+}
+
+// G, the candidates a thread evaluates per staged right word group, is 2r + 1 (at most 7)
+template <int NH>
+cudaError_t prepare_nh() {
+    cudaError_t e = prepare_t<NH, 1>();
+    if (e == cudaSuccess) e = prepare_t<NH, 3>();
+    if (e == cudaSuccess) e = prepare_t<NH, 5>();
+    if (e == cudaSuccess) e = prepare_t<NH, 7>();
+    return e;
 }
 
 template <int NH>
@@ -41,6 +62,18 @@ cudaError_t launch_restr_nh(const RestrArgs &a, cudaStream_t st) {
 }
 
 }  // namespace
+
+cudaError_t zncc_restricted_prepare(int nh) {
+    switch (nh) {
+        case 1: return prepare_nh<1>();
+        case 2: return prepare_nh<2>();
+        case 3: return prepare_nh<3>();
+        case 4: return prepare_nh<4>();
+        case 5: return prepare_nh<5>();
+        case 6: return prepare_nh<6>();
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 cudaError_t launch_zncc_restricted(const RestrArgs &a, int nh, cudaStream_t st) {
     switch (nh) {

@@ -5,19 +5,19 @@
 // paper's "3 comparisons per pixel" is r = 1), clipped to 0 .. min(D_k - 1, x); dhat is
 // first clamped into that range (a no-op for priors produced by the coarser level).
 //
-// Design (per CTA: a (2*QX) x 16 pixel tile of QX x 8 threads, QX = 32 or 16; each thread
-// owns one 2 x 2 block):
-//  * The four pixels of a 2 x 2 block aligned to even coordinates share one prior cell,
-//    hence one candidate span (up to the per-pixel clip at x, handled by masking).
-//  * The CTA reduces the union [zlo, zhi] of its spans; the left tile (a (2*QX+32)-byte box) and the
+// Design (per CTA: a (NCOL*QX) x 16 pixel tile of QX x 8 threads; each thread owns an
+// NCOL x 2 block of pixels, NCOL = 2 (2 x 2 blocks) or 1 (vertical pairs)):
+//  * The pixels of a block aligned to even coordinates share one prior cell, hence one
+//    candidate span (up to the per-pixel clip at x, handled by masking).
+//  * The CTA reduces the union [zlo, zhi] of its spans; the left tile (a (TX+32)-byte box) and the
 //    right span [x0 - zhi - n, x1 - zlo + n] (128- or 256-byte box) are staged into shared
 //    memory by TMA with one mbarrier and a bounded wait.  A span wider than 256 bytes (a
 //    tile straddling a large disparity jump) reads the right image from global memory.
 //  * Right-window statistics of the span are built once per CTA by all threads (vertical
 //    sums, then horizontal sums; exact integers).
-//  * Each thread packs the 2n+2 left rows of its two columns as dp4a words.  For each
-//    staged right row and each group of G consecutive candidates it loads the right bytes
-//    once, aligns them with funnel shifts, extracts the G+1 distinct window offsets its two
+//  * Each thread packs the 2n+2 left rows of its columns as dp4a words.  For each staged
+//    right row and each group of G consecutive candidates it loads the right bytes once,
+//    aligns them with funnel shifts, extracts the G+NCOL-1 distinct window offsets its
 //    columns need, and accumulates sum a*b with dp4a.  The two pixels of a column share
 //    the products of their 2n common rows.  All sums are exact int32 (windows up to
 //    13 x 13); c = N*Sab - Sa*Sb is exact; the only rounding is
@@ -37,9 +37,9 @@ namespace tiles {
 
 constexpr int RT_TY = 16;      // tile height (pixels)
 
-template <int NH, int QX = 32>
+template <int NH, int QX = 32, int NCOL = 2>
 struct RCfg {
-    static constexpr int TX = 2 * QX;            // tile width (pixels)
+    static constexpr int TX = NCOL * QX;         // tile width (pixels)
     static constexpr int THREADS = QX * 8;
     static constexpr int WIN = 2 * NH + 1;
     static constexpr int N = WIN * WIN;
@@ -62,20 +62,21 @@ __device__ __forceinline__ uint32_t fsr(uint32_t lo, uint32_t hi, int bytes) {
     return __funnelshift_r(lo, hi, 8 * bytes);
 }
 
-// Restricted WTA of one (2*QX) x 16 tile (bx, by) by the calling CTA (blockDim.x = QX*8).
+// Restricted WTA of one (NCOL*QX) x 16 tile (bx, by) by the calling CTA (blockDim.x = QX*8).
 // `smem` holds RCfg::BYTES bytes, 128-aligned; its first 8 bytes are an mbarrier the caller
 // has initialised (count 1) and `parity` is its next phase parity, advanced here.  tmL is a
-// (2*QX + 32)-byte-wide box over the left apron buffer, tmR128/tmR256 128/256-byte boxes
+// (NCOL*QX + 32)-byte-wide box over the left apron buffer, tmR128/tmR256 128/256-byte boxes
 // over the right one.  Returns false if a bounded wait gave up (the error word is then set).
-template <int NH, int G, int QX = 32>
+template <int NH, int G, int QX = 32, int NCOL = 2>
 __device__ bool restr_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const CUtensorMap *tmR128,
                            const CUtensorMap *tmR256, int bx, int by, uint8_t *smem, uint32_t &parity) {
-    using C = RCfg<NH, QX>;
+    using C = RCfg<NH, QX, NCOL>;
     constexpr int RT_TX = C::TX, RT_THREADS = C::THREADS;
     constexpr int ROWS = C::ROWS, WIN = C::WIN, NW = C::NW;
     // right bytes one row of a candidate group needs for both columns: G + WIN, plus up to
     // 3 of misalignment; NWA aligned words hold them with one word to spare for extraction
-    constexpr int NWA = (G + WIN + 3) / 4 + 1;
+    constexpr int NO = G + NCOL - 1;          // distinct window offsets of a candidate group
+    constexpr int NWA = (NO - 1 + WIN + 3) / 4 + 1;
     constexpr int NWL = NWA + 1;              // raw words loaded per row
     uint64_t &bar = *reinterpret_cast<uint64_t *>(smem);
     int &flag = *reinterpret_cast<int *>(smem + 8);
@@ -91,19 +92,26 @@ __device__ bool restr_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const
 
     const int tid = threadIdx.x, qx = tid % QX, qy = tid / QX;
     const int x0 = bx * RT_TX, y0 = by * RT_TY;
-    const int xa = x0 + 2 * qx, ya = y0 + 2 * qy;       // top-left pixel of this thread's block
+    const int xa = x0 + NCOL * qx, ya = y0 + 2 * qy;    // top-left pixel of this thread's block
     const int Dk = a.Dk;
-    const bool colv[2] = {xa < a.W, xa + 1 < a.W};
+    bool colv[NCOL];
+#pragma unroll
+    for (int c = 0; c < NCOL; ++c) colv[c] = xa + c < a.W;
     const bool rowv[2] = {ya < a.H, ya + 1 < a.H};
     const bool any = colv[0] && rowv[0];
 
     // candidate spans of the two columns (rows share them)
-    int lo_c[2] = {INT_MAX, INT_MAX}, hi_c[2] = {-1, -1};
+    int lo_c[NCOL], hi_c[NCOL];
+#pragma unroll
+    for (int c = 0; c < NCOL; ++c) {
+        lo_c[c] = INT_MAX;
+        hi_c[c] = -1;
+    }
     if (any) {
         const int py = min(ya >> 1, a.Hp - 1), px = min(xa >> 1, a.Wp - 1);
         const int p2 = 2 * static_cast<int>(a.prior[(size_t)py * a.Wp + px]);
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
+        for (int c = 0; c < NCOL; ++c) {
             if (!colv[c]) continue;
             const int zmx = min(Dk - 1, xa + c);
             const int dh = min(max(p2, 0), zmx);
@@ -111,8 +119,12 @@ __device__ bool restr_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const
             hi_c[c] = min(zmx, dh + a.r);
         }
     }
-    const int lo_u = min(lo_c[0], lo_c[1]);
-    const int hi_u = max(hi_c[0], hi_c[1]);
+    int lo_u = lo_c[0], hi_u = hi_c[0];
+#pragma unroll
+    for (int c = 1; c < NCOL; ++c) {
+        lo_u = min(lo_u, lo_c[c]);
+        hi_u = max(hi_u, hi_c[c]);
+    }
     if (tid == 0) {
         zlo_s = INT_MAX; zhi_s = -1; evsum = 0ull;
     }
@@ -122,7 +134,7 @@ __device__ bool restr_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const
         const int whi = __reduce_max_sync(0xFFFFFFFFu, hi_u);
         unsigned cnt = 0;
 #pragma unroll
-        for (int c = 0; c < 2; ++c)
+        for (int c = 0; c < NCOL; ++c)
 #pragma unroll
             for (int r2 = 0; r2 < 2; ++r2)
                 if (colv[c] && rowv[r2] && !(a.skip && a.skip[(size_t)(ya + r2) * a.W + xa + c]))
@@ -195,11 +207,11 @@ __device__ bool restr_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const
     if (!any) return true;
 
     // ---- left windows: rows ya-n .. ya+1+n (2n+2) of columns xa and xa+1, packed
-    uint32_t Lw[2][WIN + 1][NW];
-    int Sa[2][2], rAi[2][2];
-    float rA[2][2];
+    uint32_t Lw[NCOL][WIN + 1][NW];
+    int Sa[NCOL][2], rAi[NCOL][2];
+    float rA[NCOL][2];
     {
-        const int sc = 2 * qx + 16 - NH;       // staging column of xa - n
+        const int sc = NCOL * qx + 16 - NH;    // staging column of xa - n
         const int w0 = sc >> 2, sh = sc & 3;
 #pragma unroll
         for (int t = 0; t <= WIN; ++t) {
@@ -213,13 +225,13 @@ __device__ bool restr_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const
 #pragma unroll
             for (int k = 0; k < NW; ++k) {
                 Lw[0][t][k] = alw[k];
-                Lw[1][t][k] = fsr(alw[k], alw[k + 1], 1);
+                if constexpr (NCOL == 2) Lw[NCOL - 1][t][k] = fsr(alw[k], alw[k + 1], 1);
             }
-            Lw[0][t][NW - 1] &= C::LASTMASK;
-            Lw[1][t][NW - 1] &= C::LASTMASK;
+#pragma unroll
+            for (int c = 0; c < NCOL; ++c) Lw[c][t][NW - 1] &= C::LASTMASK;
         }
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
+        for (int c = 0; c < NCOL; ++c) {
             uint32_t s_mid = 0, q_mid = 0, s0 = 0, q0 = 0, s1 = 0, q1 = 0;
 #pragma unroll
             for (int t = 1; t < WIN; ++t)
@@ -247,10 +259,10 @@ __device__ bool restr_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const
         }
     }
 
-    float best[2][2];
-    int bz[2][2];
+    float best[NCOL][2];
+    int bz[NCOL][2];
 #pragma unroll
-    for (int c = 0; c < 2; ++c)
+    for (int c = 0; c < NCOL; ++c)
 #pragma unroll
         for (int r2 = 0; r2 < 2; ++r2) {
             best[c][r2] = -INFINITY;
@@ -260,9 +272,9 @@ __device__ bool restr_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const
     if (mode != 0) {
         for (int zg = lo_u; zg <= hi_u; zg += G) {
             // accumulators: rows 1..2n shared by both pixel rows, row 0 and row 2n+1 apart
-            uint32_t mid[2][G], top[2][G], bot[2][G];
+            uint32_t mid[NCOL][G], top[NCOL][G], bot[NCOL][G];
 #pragma unroll
-            for (int c = 0; c < 2; ++c)
+            for (int c = 0; c < NCOL; ++c)
 #pragma unroll
                 for (int j = 0; j < G; ++j) mid[c][j] = top[c][j] = bot[c][j] = 0;
             // window of column c, candidate zg + j starts at staging column b0 + (G-1-j) + c
@@ -276,16 +288,16 @@ __device__ bool restr_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const
                 for (int k = 0; k < NWL; ++k) raw[k] = row[w0 + k];
 #pragma unroll
                 for (int k = 0; k < NWA; ++k) alw[k] = fsr(raw[k], raw[k + 1], sh);
-                // the G + 1 distinct window offsets o = 0 .. G
-                uint32_t Wo[G + 1][NW];
+                // the NO distinct window offsets o = 0 .. G + NCOL - 2
+                uint32_t Wo[NO][NW];
 #pragma unroll
-                for (int o = 0; o <= G; ++o)
+                for (int o = 0; o < NO; ++o)
 #pragma unroll
                     for (int k = 0; k < NW; ++k)
                         Wo[o][k] = (o & 3) ? fsr(alw[(o >> 2) + k], alw[(o >> 2) + k + 1], o & 3)
                                            : alw[(o >> 2) + k];
 #pragma unroll
-                for (int c = 0; c < 2; ++c)
+                for (int c = 0; c < NCOL; ++c)
 #pragma unroll
                     for (int j = 0; j < G; ++j) {
                         const int o = G - 1 - j + c;
@@ -305,7 +317,7 @@ __device__ bool restr_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const
                 const int z = zg + j;
                 if (z > hi_u) break;
 #pragma unroll
-                for (int c = 0; c < 2; ++c) {
+                for (int c = 0; c < NCOL; ++c) {
                     if (!colv[c] || z < lo_c[c] || z > hi_c[c]) continue;
                     const int col = xa + c - z - (rs + NH);   // statistics column of x - z
 #pragma unroll
@@ -326,7 +338,7 @@ __device__ bool restr_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const
     } else {
         // wide span: read the right image from global memory (apron buffer, no clamping)
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
+        for (int c = 0; c < NCOL; ++c) {
             if (!colv[c]) continue;
 #pragma unroll
             for (int r2 = 0; r2 < 2; ++r2) {
@@ -361,7 +373,7 @@ __device__ bool restr_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const
         }
     }
 #pragma unroll
-    for (int c = 0; c < 2; ++c)
+    for (int c = 0; c < NCOL; ++c)
 #pragma unroll
         for (int r2 = 0; r2 < 2; ++r2) {
             if (!colv[c] || !rowv[r2]) continue;

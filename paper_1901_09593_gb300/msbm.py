@@ -192,11 +192,11 @@ class Context:
         return d_out, cost_out
 
     def profile_disparity(self, left, right, d_out, cost_out):
-        """One pass with per-kernel CUDA-event timing; returns the list of milliseconds in
-        launch order (copy, reduces, coarsest full search, restricted levels K-2..0)."""
+        """One pass with per-stage CUDA-event timing; returns the list of milliseconds in
+        launch order (pyramid, coarsest full search, restricted levels K-2..0)."""
         self._bind_stream()
         pitch = _check_image(left, self.width, self.height, "left")
-        n = 2 * self.levels
+        n = self.levels + 1
         ms = (ctypes.c_float * n)()
         _lib.check(self._lib.msbm_profile_disparity(
             self._ctx, ctypes.c_void_p(left.data_ptr()), ctypes.c_void_p(right.data_ptr()), pitch,
@@ -206,9 +206,11 @@ class Context:
         return [float(v) for v in ms]
 
     def stage_names(self):
-        k = self.levels
-        return (["copy_level0"] + [f"reduce_level{i}" for i in range(1, k)] + [f"full_level{k - 1}"]
-                + [f"restricted_level{i}" for i in range(k - 2, -1, -1)])
+        k, f = self.levels, self.params.flags
+        top = f"full_level{k - 1}" + ("+alpha" if f & _lib.MSBM_FLAG_ALPHA_REFINE else "")
+        fin = (("+beta" if f & _lib.MSBM_FLAG_BETA_FALLBACK else "")
+               + ("+median" if f & _lib.MSBM_FLAG_SELECTIVE_MEDIAN else ""))
+        return (["pyramid"] + [top] + [f"restricted_level{i}{fin}" for i in range(k - 2, -1, -1)])
 
     def level_result(self, level: int):
         """Copies of an intermediate level's (d, cost) from the last disparity()."""

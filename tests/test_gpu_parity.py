@@ -33,7 +33,8 @@ def rand_pair(h, w, seed):
     return rng.integers(0, 256, (h, w)).astype(np.uint8), rng.integers(0, 256, (h, w)).astype(np.uint8)
 
 
-@pytest.mark.parametrize("h,w,K", [(1, 1, 1), (5, 3, 2), (17, 33, 3), (240, 320, 3), (61, 175, 4), (130, 257, 5)])
+@pytest.mark.parametrize("h,w,K", [(1, 1, 1), (5, 3, 2), (17, 33, 3), (240, 320, 3), (61, 175, 4), (130, 257, 5),
+                                   (37, 1000, 7), (300, 9, 6), (1000, 1400, 4)])
 def test_pyramid_bit_exact(h, w, K):
     a, b = rand_pair(h, w, h * 7 + w)
     ctx = make_ctx(w, h, 8, K, 5, 2)
