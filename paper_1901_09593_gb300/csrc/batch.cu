@@ -133,10 +133,10 @@ __device__ bool run_match(const BatchArgs &a, const BPair &P, const BMaps *mp, c
     t.evals = a.evals; t.err = a.err; t.force_timeout = 0;
     const int bx = tile % l.tiles_x, by = tile / l.tiles_x;
     switch (P.r) {
-        case 0: return restr_tile<NH, 1>(t, &mp[k].mRL, &mp[k].mR128, &mp[k].mR256, bx, by, smem, parity);
-        case 1: return restr_tile<NH, 3>(t, &mp[k].mRL, &mp[k].mR128, &mp[k].mR256, bx, by, smem, parity);
-        case 2: return restr_tile<NH, 5>(t, &mp[k].mRL, &mp[k].mR128, &mp[k].mR256, bx, by, smem, parity);
-        default: return restr_tile<NH, 7>(t, &mp[k].mRL, &mp[k].mR128, &mp[k].mR256, bx, by, smem, parity);
+        case 0: return restr_tile<NH, 1>(t, &mp[k].mRL, &mp[k].mR128, &mp[k].mR256, nullptr, nullptr, bx, by, smem, parity);
+        case 1: return restr_tile<NH, 3>(t, &mp[k].mRL, &mp[k].mR128, &mp[k].mR256, nullptr, nullptr, bx, by, smem, parity);
+        case 2: return restr_tile<NH, 5>(t, &mp[k].mRL, &mp[k].mR128, &mp[k].mR256, nullptr, nullptr, bx, by, smem, parity);
+        default: return restr_tile<NH, 7>(t, &mp[k].mRL, &mp[k].mR128, &mp[k].mR256, nullptr, nullptr, bx, by, smem, parity);
     }
 }
 

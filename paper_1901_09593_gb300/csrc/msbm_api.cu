@@ -29,6 +29,9 @@ struct msbm_ctx {
     int num_sms = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;
+    // second stream of the pass: the statistics planes, beside the coarsest level's search
+    cudaStream_t side_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::vector<LevelBuf> lv;
     int *d_err = nullptr;
     unsigned long long *d_evals = nullptr;
@@ -71,6 +74,19 @@ bool encode_u8(CUtensorMap *m, uint8_t *base, int pitch, int rows, int box_w, in
               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// 2-D map over a plane of 8-byte entries: `rows` rows of `pitch` entries.
+bool encode_u64(CUtensorMap *m, void *base, int pitch, int rows, int box_w, int box_h) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)pitch, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)pitch * 8};
+    cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_h};
+    cuuint32_t es[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, base, dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 msbm_status validate(const msbm_params *p) {
     if (!p) return MSBM_ERR_INVALID_ARG;
     if (p->width < 1 || p->width > 16384 || p->height < 1 || p->height > 16384)
@@ -104,6 +120,7 @@ void free_ctx(msbm_ctx *c) {
         cudaFree(l.dtmp);
         cudaFree(l.mask);
         cudaFree(l.tile_flags);
+        cudaFree(l.rstat);
     }
     cudaFree(c->c0);
     cudaFree(c->d_err);
@@ -113,6 +130,9 @@ void free_ctx(msbm_ctx *c) {
     cudaFree(c->hd);
     cudaFree(c->hc);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->side_stream) cudaStreamDestroy(c->side_stream);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     delete c;
 }
 
@@ -150,9 +170,10 @@ msbm_status enqueue_pyramid(msbm_ctx *c, const uint8_t *L, const uint8_t *R, siz
     return cuda_status(e);
 }
 
+// stats_ready: the level's right-window statistics plane is already computed in stream order.
 msbm_status enqueue_level(msbm_ctx *c, int k, const int16_t *prior, int16_t *d, float *cost,
                           cudaStream_t st, const uint8_t *mask = nullptr, const int *tile_flags = nullptr,
-                          const uint8_t *skip = nullptr) {
+                          const uint8_t *skip = nullptr, bool stats_ready = false) {
     const LevelBuf &l = c->lv[k];
     const int force = (c->p.flags & MSBM_FLAG_TEST_TIMEOUT) ? 1 : 0;
     cudaError_t e;
@@ -173,13 +194,16 @@ msbm_status enqueue_level(msbm_ctx *c, int k, const int16_t *prior, int16_t *d, 
         a.tmL = l.tmRL;
         a.tmR128 = l.tmRR128;
         a.tmR256 = l.tmRR256;
+        a.tmS128 = l.tmS128;
+        a.tmS256 = l.tmS256;
         a.t.skip = skip;
         a.t.Limg = l.img(0); a.t.Rimg = l.img(1); a.t.pitch = l.pitch;
         a.t.W = l.W; a.t.H = l.H; a.t.Dk = l.Dk; a.t.r = c->p.radius;
         a.t.prior = prior; a.t.Wp = (l.W + 1) / 2; a.t.Hp = (l.H + 1) / 2;
         a.t.d_out = d; a.t.c_out = cost;
         a.t.evals = c->d_evals; a.t.err = c->d_err; a.t.force_timeout = force;
-        e = launch_zncc_restricted(a, c->nh, st);
+        e = stats_ready ? cudaSuccess : launch_right_stats(&l, 1, c->nh, st);
+        if (e == cudaSuccess) e = launch_zncc_restricted(a, c->nh, st);
     }
     return cuda_status(e);
 }
@@ -188,13 +212,13 @@ msbm_status enqueue_level(msbm_ctx *c, int k, const int16_t *prior, int16_t *d, 
 // every pixel (fallback pixels are not counted), then the full search over the flagged
 // tiles writing the fallback pixels.
 msbm_status enqueue_level_beta(msbm_ctx *c, int k, const int16_t *prior, const float *cprior, int16_t *d,
-                               float *cost, cudaStream_t st) {
+                               float *cost, cudaStream_t st, bool stats_ready = false) {
     LevelBuf &l = c->lv[k];
     const LevelBuf &lp = c->lv[k + 1];
     cudaError_t e = launch_beta_gate(cprior, lp.W, lp.H, l.W, l.H, c->p.beta, l.mask, l.tile_flags,
                                      32 * l.full_sx, 8, st);
     if (e != cudaSuccess) return cuda_status(e);
-    msbm_status s = enqueue_level(c, k, prior, d, cost, st, nullptr, nullptr, l.mask);
+    msbm_status s = enqueue_level(c, k, prior, d, cost, st, nullptr, nullptr, l.mask, stats_ready);
     if (s != MSBM_OK) return s;
     return enqueue_level(c, k, nullptr, d, cost, st, l.mask, l.tile_flags);
 }
@@ -202,7 +226,9 @@ msbm_status enqueue_level_beta(msbm_ctx *c, int k, const int16_t *prior, const f
 // Level k of the pass with the gated steps the context's flags select: the full-range
 // search (+ alpha refinement) at the coarsest level, the restricted search (+ beta fallback,
 // + selective median) below it.  Writes the level's final map to d / cost at level 0.
-msbm_status enqueue_match(msbm_ctx *c, int k, int16_t *d, float *cost, cudaStream_t st) {
+// stats_ready: the restricted levels' statistics planes are already computed in stream order.
+msbm_status enqueue_match(msbm_ctx *c, int k, int16_t *d, float *cost, cudaStream_t st,
+                          bool stats_ready = false) {
     const int K = c->p.levels;
     const uint32_t f = c->p.flags;
     LevelBuf &l = c->lv[k];
@@ -219,9 +245,9 @@ msbm_status enqueue_match(msbm_ctx *c, int k, int16_t *d, float *cost, cudaStrea
     const bool med = (f & MSBM_FLAG_SELECTIVE_MEDIAN) != 0;
     int16_t *dm = med ? l.dtmp : dk;                      // matching output
     if (f & MSBM_FLAG_BETA_FALLBACK)
-        s = enqueue_level_beta(c, k, prior, c->lv[k + 1].c, dm, ck, st);
+        s = enqueue_level_beta(c, k, prior, c->lv[k + 1].c, dm, ck, st, stats_ready);
     else
-        s = enqueue_level(c, k, prior, dm, ck, st);
+        s = enqueue_level(c, k, prior, dm, ck, st, nullptr, nullptr, nullptr, stats_ready);
     if (s == MSBM_OK && med) s = cuda_status(launch_selective_median(dm, ck, l.W, l.H, c->p.alpha, dk, st));
     return s;
 }
@@ -229,7 +255,20 @@ msbm_status enqueue_match(msbm_ctx *c, int k, int16_t *d, float *cost, cudaStrea
 msbm_status enqueue_all(msbm_ctx *c, const uint8_t *L, const uint8_t *R, size_t pitch, int16_t *d,
                         float *cost, cudaStream_t st) {
     msbm_status s = enqueue_pyramid(c, L, R, pitch, st);
-    for (int k = c->p.levels - 1; s == MSBM_OK && k >= 0; --k) s = enqueue_match(c, k, d, cost, st);
+    const int K = c->p.levels;
+    // fork: the statistics planes of levels 0 .. K-2 on the side stream, beside the coarsest
+    // level's full-range search; join before the first restricted level
+    if (s == MSBM_OK && K >= 2) {
+        cudaError_t e = cudaEventRecord(c->ev_fork, st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0);
+        if (e == cudaSuccess) e = launch_right_stats(c->lv.data(), K - 1, c->nh, c->side_stream);
+        if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->side_stream);
+        s = cuda_status(e);
+    }
+    for (int k = K - 1; s == MSBM_OK && k >= 0; --k) {
+        if (k == K - 2) s = cuda_status(cudaStreamWaitEvent(st, c->ev_join, 0));
+        if (s == MSBM_OK) s = enqueue_match(c, k, d, cost, st, true);
+    }
     return s;
 }
 
@@ -273,6 +312,9 @@ msbm_status msbm_create(const msbm_params *params, void *cuda_stream, msbm_ctx *
     c->stream = static_cast<cudaStream_t>(cuda_stream);
     const int rowsT = 8 + 2 * c->nh;   // staged rows of the full-range tile
     cudaError_t e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_evals, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
@@ -293,6 +335,8 @@ msbm_status msbm_create(const msbm_params *params, void *cuda_stream, msbm_ctx *
         e = cudaMemset(buf, 0, 2 * bytes);
         if (e == cudaSuccess && k > 0) e = cudaMalloc(&l.d, (size_t)W * H * sizeof(int16_t));
         if (e == cudaSuccess && k > 0) e = cudaMalloc(&l.c, (size_t)W * H * sizeof(float));
+        l.rspitch = (W + 15) / 16 * 16;
+        if (e == cudaSuccess) e = cudaMalloc(&l.rstat, (size_t)l.rspitch * H * sizeof(int2));
         const bool finer = k < params->levels - 1;
         if (e == cudaSuccess && finer && (params->flags & MSBM_FLAG_SELECTIVE_MEDIAN))
             e = cudaMalloc(&l.dtmp, (size_t)W * H * sizeof(int16_t));
@@ -309,7 +353,9 @@ msbm_status msbm_create(const msbm_params *params, void *cuda_stream, msbm_ctx *
                       encode_u8(&l.tmR256, l.base[1], l.pitch, l.rows, 256, rowsT) &&
                       encode_u8(&l.tmRL, l.base[0], l.pitch, l.rows, 64, rowsR) &&
                       encode_u8(&l.tmRR128, l.base[1], l.pitch, l.rows, 128, rowsR) &&
-                      encode_u8(&l.tmRR256, l.base[1], l.pitch, l.rows, 256, rowsR);
+                      encode_u8(&l.tmRR256, l.base[1], l.pitch, l.rows, 256, rowsR) &&
+                      encode_u64(&l.tmS128, l.rstat, l.rspitch, H, 128, 16) &&
+                      encode_u64(&l.tmS256, l.rstat, l.rspitch, H, 256, 16);
             if (!ok) { c->lv.push_back(l); free_ctx(c); return MSBM_ERR_UNSUPPORTED; }
         }
         if (e == cudaSuccess) e = zncc_full_prepare(c->nh, l.full_sx);

@@ -23,13 +23,16 @@ struct LevelBuf {
     int16_t *dtmp = nullptr;     // pre-median disparity map (SELECTIVE_MEDIAN)
     uint8_t *mask = nullptr;     // fallback mask (BETA_FALLBACK)
     int *tile_flags = nullptr;   // full-range tiles holding a fallback pixel (BETA_FALLBACK)
+    int2 *rstat = nullptr;       // right-window statistics plane {S, bits(rsqrt(V)) or 0}: H rows
+    int rspitch = 0;             // of rspitch entries (a multiple of 16), one per pixel
     // TMA maps over the apron buffers.  Full-range tile (8 + 2n rows high):
     //   tmFL   : left,  32*SX + 32 bytes wide, SX per level
     //   tmR256 : right, 256 bytes wide
     // Restricted tile (16 + 2n rows high):
     //   tmRL   : left,  64 bytes wide
     //   tmRR128, tmRR256 : right, 128 / 256 bytes wide (narrow / wide candidate spans)
-    CUtensorMap tmFL, tmR256, tmRL, tmRR128, tmRR256;
+    //   tmS128, tmS256   : statistics plane, 128 / 256 entries wide, 16 rows
+    CUtensorMap tmFL, tmR256, tmRL, tmRR128, tmRR256, tmS128, tmS256;
     int full_sx = 4;             // full-range tile width 32*full_sx at this level
     int full_zblock = 0;         // full-range z-block (0 = the tile's maximum)
     uint8_t *img(int which) const {
@@ -79,6 +82,8 @@ struct RestrArgs {
     CUtensorMap tmL;     // box {64, 16 + 2n} over the left apron buffer
     CUtensorMap tmR128;  // box {128, 16 + 2n} over the right apron buffer
     CUtensorMap tmR256;  // box {256, 16 + 2n} over the right apron buffer
+    CUtensorMap tmS128;  // box {128, 16} over the right statistics plane
+    CUtensorMap tmS256;  // box {256, 16} over the right statistics plane
     RestrTileArgs t;
 };
 
@@ -107,6 +112,8 @@ cudaError_t launch_alpha_refine(const LevelBuf &l, int nh, float alpha, int16_t 
 cudaError_t launch_selective_median(const int16_t *d_in, const float *C, int W, int H, float alpha, int16_t *d_out,
                                     cudaStream_t st);
 cudaError_t zncc_full_prepare(int nh, int sx);
+// Right-window statistics planes of n consecutive levels (lv[0 .. n-1]) in one launch.
+cudaError_t launch_right_stats(const LevelBuf *lv, int n, int nh, cudaStream_t st);
 cudaError_t zncc_restricted_prepare(int nh);
 cudaError_t launch_zncc_restricted(const RestrArgs &a, int nh, cudaStream_t st);
 size_t zncc_full_smem_bytes(int nh, int sx);

@@ -1,7 +1,8 @@
 // zncc_restricted.cu -- standalone launch of the restricted ZNCC winner-take-all tile
 // (Sec. III-C, Eq. 8-9, first branch; design in zncc_restricted_tile.cuh): one CTA of
 // 256 threads per 32 x 16 tile, each thread a vertical pair of pixels that share a prior
-// cell and the products of their 2n common window rows.
+// cell and the products of their 2n common window rows; right-window statistics from the
+// level's plane (level_stats.cu).
 #include "zncc_restricted_tile.cuh"
 
 namespace msbm {
@@ -22,19 +23,20 @@ __global__ void __launch_bounds__(SA_QX * 8) zncc_restricted_kernel(const __grid
     }
     __syncthreads();
     uint32_t parity = 0;
-    restr_tile<NH, G, SA_QX, SA_NCOL>(a.t, &a.tmL, &a.tmR128, &a.tmR256, blockIdx.x, blockIdx.y, smem, parity);
+    restr_tile<NH, G, SA_QX, SA_NCOL, true>(a.t, &a.tmL, &a.tmR128, &a.tmR256, &a.tmS128, &a.tmS256, blockIdx.x,
+                                            blockIdx.y, smem, parity);
 }
 
 template <int NH, int G>
 cudaError_t prepare_t() {
-    using C = RCfg<NH, SA_QX, SA_NCOL>;
+    using C = RCfg<NH, SA_QX, SA_NCOL, true>;
     return cudaFuncSetAttribute(zncc_restricted_kernel<NH, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 static_cast<int>(C::BYTES));
 }
 
 template <int NH, int G>
 cudaError_t launch_restr_t(const RestrArgs &a, cudaStream_t st) {
-    using C = RCfg<NH, SA_QX, SA_NCOL>;
+    using C = RCfg<NH, SA_QX, SA_NCOL, true>;
     static_assert(C::TX == 32 && C::BYTES <= 227 * 1024, "restricted tile shape");
     dim3 grd((a.t.W + C::TX - 1) / C::TX, (a.t.H + RT_TY - 1) / RT_TY);
     zncc_restricted_kernel<NH, G><<<grd, C::THREADS, C::BYTES, st>>>(a);

@@ -14,7 +14,8 @@
 //    memory by TMA with one mbarrier and a bounded wait.  A span wider than 256 bytes (a
 //    tile straddling a large disparity jump) reads the right image from global memory.
 //  * Right-window statistics of the span are built once per CTA by all threads (vertical
-//    sums, then horizontal sums; exact integers).
+//    sums, then horizontal sums; exact integers), or, in plane mode, staged by TMA with the
+//    image rows from the level's precomputed statistics plane.
 //  * Each thread packs the 2n+2 left rows of its columns as dp4a words.  For each staged
 //    right row and each group of G consecutive candidates it loads the right bytes once,
 //    aligns them with funnel shifts, extracts the G+NCOL-1 distinct window offsets its
@@ -37,7 +38,7 @@ namespace tiles {
 
 constexpr int RT_TY = 16;      // tile height (pixels)
 
-template <int NH, int QX = 32, int NCOL = 2>
+template <int NH, int QX = 32, int NCOL = 2, bool PLANE = false>
 struct RCfg {
     static constexpr int TX = NCOL * QX;         // tile width (pixels)
     static constexpr int THREADS = QX * 8;
@@ -55,7 +56,9 @@ struct RCfg {
     static constexpr size_t OFF_SR = OFF_SL + al((size_t)ROWS * LBOX) + PAD_R;
     static constexpr size_t OFF_TMP = OFF_SR + al((size_t)(ROWS + 1) * 256);
     static constexpr size_t OFF_STR = OFF_TMP + (size_t)RT_TY * 256 * 4;
-    static constexpr size_t BYTES = OFF_STR + (size_t)RT_TY * 256 * 8;
+    // plane mode stages the span's entries of the level's statistics plane at OFF_TMP instead
+    static constexpr size_t OFF_SS = OFF_TMP;
+    static constexpr size_t BYTES = PLANE ? OFF_SS + (size_t)RT_TY * 256 * 8 : OFF_STR + (size_t)RT_TY * 256 * 8;
 };
 
 __device__ __forceinline__ uint32_t fsr(uint32_t lo, uint32_t hi, int bytes) {
@@ -66,11 +69,14 @@ __device__ __forceinline__ uint32_t fsr(uint32_t lo, uint32_t hi, int bytes) {
 // `smem` holds RCfg::BYTES bytes, 128-aligned; its first 8 bytes are an mbarrier the caller
 // has initialised (count 1) and `parity` is its next phase parity, advanced here.  tmL is a
 // (NCOL*QX + 32)-byte-wide box over the left apron buffer, tmR128/tmR256 128/256-byte boxes
-// over the right one.  Returns false if a bounded wait gave up (the error word is then set).
-template <int NH, int G, int QX = 32, int NCOL = 2>
+// over the right one.  PLANE: the right-window statistics are staged by TMA from the level's
+// statistics plane (tmS128 / tmS256: 128 / 256 x 16 boxes of 8-byte entries) instead of being
+// built in the CTA.  Returns false if a bounded wait gave up (the error word is then set).
+template <int NH, int G, int QX = 32, int NCOL = 2, bool PLANE = false>
 __device__ bool restr_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const CUtensorMap *tmR128,
-                           const CUtensorMap *tmR256, int bx, int by, uint8_t *smem, uint32_t &parity) {
-    using C = RCfg<NH, QX, NCOL>;
+                           const CUtensorMap *tmR256, const CUtensorMap *tmS128, const CUtensorMap *tmS256,
+                           int bx, int by, uint8_t *smem, uint32_t &parity) {
+    using C = RCfg<NH, QX, NCOL, PLANE>;
     constexpr int RT_TX = C::TX, RT_THREADS = C::THREADS;
     constexpr int ROWS = C::ROWS, WIN = C::WIN, NW = C::NW;
     // right bytes one row of a candidate group needs for both columns: G + WIN, plus up to
@@ -89,6 +95,7 @@ __device__ bool restr_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const
     uint8_t *sR = smem + C::OFF_SR;                       // [ROWS + 1][64|128|256] + slack before
     uint32_t *tmpV = reinterpret_cast<uint32_t *>(smem + C::OFF_TMP);   // [RT_TY][256] packed (Q | S << 20)
     int2 *stR = reinterpret_cast<int2 *>(smem + C::OFF_STR);           // [RT_TY][256] {Sb, bits(rsqrt(Vb))}
+    const int2 *stS = reinterpret_cast<const int2 *>(smem + C::OFF_SS);  // plane mode: [RT_TY][128|256]
 
     const int tid = threadIdx.x, qx = tid % QX, qy = tid / QX;
     const int x0 = bx * RT_TX, y0 = by * RT_TY;
@@ -151,28 +158,32 @@ __device__ bool restr_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const
     const int xlast = min(x0 + RT_TX, a.W) - 1;
     const int rs = x0 - zhi - NH;              // first right column any window reads
     const int re = xlast - zlo + NH;           // last
+    const int sxs = (x0 - zhi) & ~1;           // plane mode: first staged plane column (even)
     if (tid == 0) {
         const int xs = (rs + APX) & ~15;
         const int width = re + APX + 1 - xs;
         const int mode = width <= 128 ? 1 : (width <= 256 ? 2 : 0);
         mode_s = mode;
         xs_s = xs;
-        const uint32_t bytes = ROWS * C::LBOX + (mode == 1 ? ROWS * 128 : (mode == 2 ? ROWS * 256 : 0));
+        uint32_t bytes = ROWS * C::LBOX + (mode == 1 ? ROWS * 128 : (mode == 2 ? ROWS * 256 : 0));
+        if (PLANE) bytes += mode == 1 ? RT_TY * 128 * 8 : (mode == 2 ? RT_TY * 256 * 8 : 0);
         fence_proxy_async_smem();
         mbar_arrive_expect_tx(&bar, bytes);
         tma_load_2d(sL, tmL, &bar, x0 - 16 + APX, y0 - NH + APY);
         if (mode == 1) tma_load_2d(sR, tmR128, &bar, xs, y0 - NH + APY);
         if (mode == 2) tma_load_2d(sR, tmR256, &bar, xs, y0 - NH + APY);
+        if (PLANE && mode == 1) tma_load_2d(const_cast<int2 *>(stS), tmS128, &bar, sxs, y0);
+        if (PLANE && mode == 2) tma_load_2d(const_cast<int2 *>(stS), tmS256, &bar, sxs, y0);
     }
     if (!tma_batch_wait(&bar, parity, &flag, a.force_timeout != 0, a.err)) return false;
     parity ^= 1;
     const int mode = mode_s, xs = xs_s;
     const int soff = APX - xs;                 // staging column of image column X: X + soff
-    const int rst = mode == 1 ? 128 : 256;     // staging row stride
+    const int rst = mode == 1 ? 128 : 256;     // staging row stride (bytes; plane entries)
 
-    // ---- right statistics over the span (staged modes), all threads
+    // ---- right statistics over the span (staged modes, no plane), all threads
     const int SW = re - rs + 1 - 2 * NH;       // statistics columns: image rs + n + v
-    if (mode != 0) {
+    if (!PLANE && mode != 0) {
         // vertical window sums of every (output row, span column), spread over all threads
         const int cols = SW + 2 * NH;
         for (int i = tid; i < RT_TY * cols; i += RT_THREADS) {
@@ -323,7 +334,8 @@ __device__ bool restr_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const
 #pragma unroll
                     for (int r2 = 0; r2 < 2; ++r2) {
                         if (!rowv[r2]) continue;
-                        const int2 st = stR[(2 * qy + r2) * 256 + col];
+                        const int2 st = PLANE ? stS[(2 * qy + r2) * rst + (xa + c - z - sxs)]
+                                              : stR[(2 * qy + r2) * 256 + col];
                         const int sab = static_cast<int>(mid[c][j] + (r2 ? bot[c][j] : top[c][j]));
                         const int cc = C::N * sab - Sa[c][r2] * st.x;
                         const float rho = static_cast<float>(cc) * __int_as_float(st.y);
