@@ -14,6 +14,7 @@
 
 #include "msbm_device.cuh"
 #include "msbm_internal.h"
+#include "zncc_region.cuh"
 
 namespace msbm {
 
@@ -56,33 +57,33 @@ __global__ void beta_gate_kernel(const float *__restrict__ Cc, int Wc, int Hc, i
 
 // Alpha refinement on a 16 x 8 tile.  E(q, z), the ZNCC of every pixel q of the tile's
 // 18 x 10 neighbourhood region at every candidate z, is computed once per 32-candidate chunk
-// into shared memory, then each refined pixel (cost <= alpha) averages E over its in-image
-// 3 x 3 neighbours (rows, then columns) and keeps the WTA of the averages on a 64-bit
-// (ordered mean, ~z) key: ties keep the smallest z.  E uses exact integer window sums of the
-// staged image rows (clamp-to-edge): each thread packs its left window as dp4a words, and for
-// 4 consecutive candidates loads the right row words once and extracts the 4 windows with
-// funnel shifts; rho = float(N Sab - Sa Sb) * rsqrt(Va) * rsqrt(Vb), 0 for a flat window.
-constexpr int AR_TW = 16, AR_TH = 8, AR_RW = AR_TW + 2, AR_RH = AR_TH + 2, AR_ZC = 32;
+// into shared memory (zncc_region.cuh; 0 for region pixels outside the image), then two
+// threads per refined pixel (cost <= alpha) sum E over its 3 x 3 neighbours (rows, then
+// columns: the in-image neighbours, since the others add 0) for 16 candidates each, scale by
+// 1 / (in-image neighbours) and keep the WTA of the means on a 64-bit (ordered mean, ~z)
+// key: ties keep the smallest z.
+constexpr int AR_TW = 16, AR_TH = 8, AR_RW = AR_TW + 2, AR_RH = AR_TH + 2;
 constexpr int AR_NP = AR_RW * AR_RH;     // region pixels (180)
 
 template <int NH>
 __global__ void __launch_bounds__(256) alpha_refine_kernel(const uint8_t *L, const uint8_t *R, int pitch, int W,
                                                            int H, int Dk, float alpha, int16_t *d, float *C,
                                                            unsigned long long *evals) {
-    constexpr int WIN = 2 * NH + 1, N = WIN * WIN, NW = (WIN + 3) / 4;
+    using region::ZC;
+    constexpr int WIN = 2 * NH + 1, NW = (WIN + 3) / 4;
     constexpr int SLW = AR_RW + 2 * NH, SLH = AR_RH + 2 * NH;   // staged left region
-    constexpr int SU = AR_RW + AR_ZC - 1;                        // right window columns per chunk
-    constexpr int SRW = SU + 2 * NH;                             // staged right columns per chunk
-    constexpr int SRWW = (SRW + 3) / 4 + 2;                      // words per staged right row
-    __shared__ uint8_t sL[SLH][SLW];
-    __shared__ uint32_t sR[SLH][SRWW];
-    __shared__ int2 stR[AR_RH][SU];              // {Sb, bits(rsqrt(Vb)) or 0}
-    __shared__ int vs[AR_RH][SRW], vq[AR_RH][SRW];
-    __shared__ float E[AR_NP][AR_ZC + 1];
+    constexpr int SU = AR_RW + ZC - 1;                          // right window columns per chunk
+    constexpr int SRW = SU + 2 * NH;                            // staged right columns per chunk
+    constexpr int SRWW = (SRW + 3) / 4 + 2;                     // words per staged right row
+    __shared__ uint8_t sL[SLH * SLW];
+    __shared__ uint32_t sR[SLH * SRWW];
+    __shared__ int vs[AR_RH * SRW], vq[AR_RH * SRW];
+    __shared__ int2 stR[AR_RH * SU];
+    __shared__ float E[AR_NP][ZC + 1];
     __shared__ unsigned long long best[AR_TW * AR_TH];
     __shared__ int qual[AR_TW * AR_TH];
     __shared__ int any;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     const int x0 = blockIdx.x * AR_TW, y0 = blockIdx.y * AR_TH;
     const int rx0 = x0 - 1, ry0 = y0 - 1;        // region origin (may lie outside the image)
     if (tid == 0) any = 0;
@@ -94,156 +95,67 @@ __global__ void __launch_bounds__(256) alpha_refine_kernel(const uint8_t *L, con
         best[tid] = 0ull;
         if (q) any = 1;
     }
-    {
-        constexpr int T = (SLH * SLW + 255) / 256;
-        uint8_t v[T];
-#pragma unroll
-        for (int t = 0; t < T; ++t) {
-            const int i = tid + 256 * t, r = i / SLW, c = i - r * SLW;
-            const int yy = min(max(ry0 - NH + r, 0), H - 1), xx = min(max(rx0 - NH + c, 0), W - 1);
-            v[t] = i < SLH * SLW ? L[(ptrdiff_t)yy * pitch + xx] : 0;
-        }
-#pragma unroll
-        for (int t = 0; t < T; ++t) {
-            const int i = tid + 256 * t;
-            if (i < SLH * SLW) sL[i / SLW][i % SLW] = v[t];
-        }
-    }
+    region::stage_rows<SLH, SLW, SLW>(sL, L, pitch, W, H, ry0 - NH, rx0 - NH);
     __syncthreads();
     if (!any) return;
     // this thread's region pixel: packed left window and its statistics
     const int pr = tid / AR_RW, pc = tid - pr * AR_RW;
+    const bool pin = tid < AR_NP && ry0 + pr >= 0 && ry0 + pr < H && rx0 + pc >= 0 && rx0 + pc < W;
     uint32_t Lw[WIN][NW];
     int2 la = make_int2(0, 0);
-    if (tid < AR_NP) {
-        uint32_t s = 0, q = 0;
-#pragma unroll
-        for (int i = 0; i < WIN; ++i)
-#pragma unroll
-            for (int k = 0; k < NW; ++k) {
-                uint32_t w = 0;
-#pragma unroll
-                for (int b = 0; b < 4; ++b)
-                    if (4 * k + b < WIN) w |= static_cast<uint32_t>(sL[pr + i][pc + 4 * k + b]) << (8 * b);
-                Lw[i][k] = w;
-                s = dp4a_u8(w, 0x01010101u, s);
-                q = dp4a_u8(w, w, q);
-            }
-        const int V = N * static_cast<int>(q) - static_cast<int>(s) * static_cast<int>(s);
-        la = make_int2(static_cast<int>(s), V > 0 ? __float_as_int(rsqrtf(static_cast<float>(V))) : 0);
-    }
+    if (tid < AR_NP) la = region::pack_left<NH, SLW>(sL, pr, pc, Lw);
+    // the refined pixel and candidate half of this thread in the averaging step
+    const int ow = tid & (AR_TW * AR_TH - 1), oh = tid >> 7;
+    const int xw = x0 + ow % AR_TW, yw = y0 + ow / AR_TW;
+    const int e0 = (ow / AR_TW) * AR_RW + ow % AR_TW;     // region index of (yw - 1, xw - 1)
+    const int zmax_w = min(Dk - 1, xw);
+    const float inv = 1.f / static_cast<float>((min(yw + 1, H - 1) - max(yw - 1, 0) + 1) *
+                                               (min(xw + 1, W - 1) - max(xw - 1, 0) + 1));
     const int zmax_tile = min(Dk - 1, min(x0 + AR_TW, W) - 1);
-    for (int z0 = 0; z0 <= zmax_tile; z0 += AR_ZC) {
+    for (int z0 = 0; z0 <= zmax_tile; z0 += ZC) {
         __syncthreads();      // the previous chunk's E and staging are consumed
-        // right image columns cx .. cx + SRW - 1 (clamp-to-edge), zero padding after them
-        const int cx = rx0 - (z0 + AR_ZC - 1) - NH;
-        {
-            constexpr int NB = SLH * SRWW * 4, T = (NB + 255) / 256;
-            uint8_t v[T];
-#pragma unroll
-            for (int t = 0; t < T; ++t) {
-                const int i = tid + 256 * t, r = i / (SRWW * 4), c = i - r * (SRWW * 4);
-                const int yy = min(max(ry0 - NH + r, 0), H - 1), xx = min(max(cx + c, 0), W - 1);
-                v[t] = (i < NB && c < SRW) ? R[(ptrdiff_t)yy * pitch + xx] : 0;
-            }
-#pragma unroll
-            for (int t = 0; t < T; ++t) {
-                const int i = tid + 256 * t;
-                if (i < NB) reinterpret_cast<uint8_t *>(&sR[0][0])[i] = v[t];
-            }
-        }
+        region::stage_rows<SLH, SRW, SRWW * 4>(reinterpret_cast<uint8_t *>(sR), R, pitch, W, H, ry0 - NH,
+                                                rx0 - (z0 + ZC - 1) - NH);
         __syncthreads();
-        // right window statistics of the chunk: vertical, then horizontal sums
-        for (int i = tid; i < AR_RH * SRW; i += 256) {
-            const int r = i / SRW, c = i - r * SRW;
-            const uint8_t *col = reinterpret_cast<const uint8_t *>(&sR[r][0]) + c;
-            int s = 0, q = 0;
-#pragma unroll
-            for (int a = 0; a < WIN; ++a) {
-                const int v = col[a * SRWW * 4];
-                s += v;
-                q += v * v;
-            }
-            vs[r][c] = s;
-            vq[r][c] = q;
-        }
-        __syncthreads();
-        for (int i = tid; i < AR_RH * SU; i += 256) {
-            const int r = i / SU, u = i - r * SU;
-            int s = 0, q = 0;
-#pragma unroll
-            for (int b = 0; b < WIN; ++b) {
-                s += vs[r][u + b];
-                q += vq[r][u + b];
-            }
-            const int V = N * q - s * s;
-            stR[r][u] = make_int2(s, V > 0 ? __float_as_int(rsqrtf(static_cast<float>(V))) : 0);
-        }
-        __syncthreads();
+        region::window_stats<NH, AR_RH, SU, SRWW * 4>(reinterpret_cast<const uint8_t *>(sR), vs, vq, stR);
         if (tid < AR_NP) {
 #pragma unroll 1
-            for (int g = 0; g < AR_ZC / 4; ++g) {
-                const int um = pc + AR_ZC - 4 - 4 * g;       // first staged column, candidate 4g + 3
-                const int w0 = um >> 2, sh = um & 3;
-                uint32_t sab[4] = {0u, 0u, 0u, 0u};
+            for (int g = 0; g < ZC / 4; ++g) {
+                const int um = pc + ZC - 4 - 4 * g;       // staged column of candidate z0 + 4g + 3
+                uint32_t sab[4];
+                region::sab4<NH, SRWW>(sR, pr, um, Lw, sab);
 #pragma unroll
-                for (int i = 0; i < WIN; ++i) {
-                    const uint32_t *row = &sR[pr + i][w0];
-                    uint32_t raw[NW + 2], alw[NW + 1];
-#pragma unroll
-                    for (int k = 0; k < NW + 2; ++k) raw[k] = row[k];
-#pragma unroll
-                    for (int k = 0; k <= NW; ++k) alw[k] = __funnelshift_r(raw[k], raw[k + 1], 8 * sh);
-#pragma unroll
-                    for (int o = 0; o < 4; ++o)
-#pragma unroll
-                        for (int k = 0; k < NW; ++k) {
-                            const uint32_t w = o ? __funnelshift_r(alw[k], alw[k + 1], 8 * o) : alw[k];
-                            sab[o] = dp4a_u8(Lw[i][k], w, sab[o]);
-                        }
-                }
-#pragma unroll
-                for (int o = 0; o < 4; ++o) {
-                    const int2 rb = stR[pr][um + o];
-                    float e = 0.f;
-                    if (la.y != 0 && rb.y != 0)
-                        e = static_cast<float>(N * static_cast<int>(sab[o]) - la.x * rb.x) * __int_as_float(la.y) *
-                            __int_as_float(rb.y);
-                    E[tid][4 * g + 3 - o] = e;
-                }
+                for (int o = 0; o < 4; ++o)
+                    E[tid][4 * g + 3 - o] = pin ? region::rho_of<NH>(sab[o], la, stR[pr * SU + um + o]) : 0.f;
             }
         }
         __syncthreads();
-        for (int o = warp; o < AR_TW * AR_TH; o += 8) {
-            if (!qual[o]) continue;
-            const int x = x0 + o % AR_TW, y = y0 + o / AR_TW, z = z0 + lane;
+        if (qual[ow]) {
             unsigned long long k = 0ull;
-            if (z <= min(Dk - 1, x)) {
-                const int ya = max(y - 1, 0), yb = min(y + 1, H - 1), xa = max(x - 1, 0), xb = min(x + 1, W - 1);
-                const float inv = 1.f / static_cast<float>((yb - ya + 1) * (xb - xa + 1));
+#pragma unroll 4
+            for (int zz = 16 * oh; zz < 16 * oh + 16; ++zz) {
+                const int z = z0 + zz;
+                if (z > zmax_w) break;
                 float s = 0.f;
-                for (int m = ya; m <= yb; ++m)
-                    for (int q = xa; q <= xb; ++q) s += E[(m - ry0) * AR_RW + (q - rx0)][lane];
-                k = wta_key(s * inv, z);
-            }
 #pragma unroll
-            for (int sh = 16; sh > 0; sh >>= 1) {
-                const unsigned long long t = __shfl_xor_sync(0xFFFFFFFFu, k, sh);
-                k = t > k ? t : k;
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) s += E[e0 + a * AR_RW + b][zz];
+                const unsigned long long kk = wta_key(s * inv, z);
+                k = kk > k ? kk : k;
             }
-            if (lane == 0 && k > best[o]) best[o] = k;
+            if (k) atomicMax(&best[ow], k);
         }
     }
     __syncthreads();
     if (tid < AR_TW * AR_TH && qual[tid]) {
-        const int x = x0 + tid % AR_TW, y = y0 + tid / AR_TW;
-        const size_t p = (size_t)y * W + x;
+        const size_t p = (size_t)yw * W + xw;
         const unsigned long long k = best[tid];
         d[p] = static_cast<int16_t>(0xFFFFFFFFu - static_cast<uint32_t>(k & 0xFFFFFFFFull));
         C[p] = float_from_order_key(static_cast<uint32_t>(k >> 32));
         if (evals) {
-            const int ya = max(y - 1, 0), yb = min(y + 1, H - 1), xa = max(x - 1, 0), xb = min(x + 1, W - 1);
-            atomicAdd(evals, static_cast<unsigned long long>((yb - ya + 1) * (xb - xa + 1)) * (min(Dk - 1, x) + 1));
+            const int ya = max(yw - 1, 0), yb = min(yw + 1, H - 1), xa = max(xw - 1, 0), xb = min(xw + 1, W - 1);
+            atomicAdd(evals, static_cast<unsigned long long>((yb - ya + 1) * (xb - xa + 1)) * (zmax_w + 1));
         }
     }
 }

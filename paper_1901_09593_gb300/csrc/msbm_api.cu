@@ -177,7 +177,9 @@ msbm_status enqueue_level(msbm_ctx *c, int k, const int16_t *prior, int16_t *d, 
     const LevelBuf &l = c->lv[k];
     const int force = (c->p.flags & MSBM_FLAG_TEST_TIMEOUT) ? 1 : 0;
     cudaError_t e;
-    if (!prior) {
+    if (!prior && !mask && l.coarse) {
+        e = launch_zncc_coarse(l, c->nh, d, cost, c->d_evals, st);
+    } else if (!prior) {
         FullArgs a;
         memset(&a, 0, sizeof(a));
         a.tmL = l.tmFL;
@@ -347,6 +349,7 @@ msbm_status msbm_create(const msbm_params *params, void *cuda_stream, msbm_ctx *
             if (e == cudaSuccess) e = cudaMalloc(&l.tile_flags, sizeof(int) * tiles);
         }
         l.full_sx = choose_sx(W, H, c->num_sms);
+        l.coarse = zncc_coarse_fits(W, H, c->num_sms);
         if (e == cudaSuccess) {
             const int rowsR = 16 + 2 * c->nh;
             bool ok = encode_u8(&l.tmFL, l.base[0], l.pitch, l.rows, 32 * l.full_sx + 32, rowsT) &&
@@ -408,6 +411,7 @@ msbm_status msbm_set_level_tuning(msbm_ctx *ctx, int32_t level, int32_t sx, int3
     if (e != cudaSuccess) return cuda_status(e);
     l.full_sx = sx;
     l.full_zblock = zblock;
+    l.coarse = false;            // explicit tuning selects the full-range tile kernel
     if (ctx->exec) {   // the captured graph holds the old launch configuration
         cudaGraphExecDestroy(ctx->exec);
         ctx->exec = nullptr;

@@ -35,6 +35,7 @@ struct LevelBuf {
     CUtensorMap tmFL, tmR256, tmRL, tmRR128, tmRR256, tmS128, tmS256;
     int full_sx = 4;             // full-range tile width 32*full_sx at this level
     int full_zblock = 0;         // full-range z-block (0 = the tile's maximum)
+    bool coarse = false;         // plain full-range search by the small-level kernel
     uint8_t *img(int which) const {
         return base[which] + (size_t)APY * pitch + APX;
     }
@@ -105,6 +106,11 @@ struct PyrFuseArgs {
 cudaError_t launch_pyr_fused(const PyrFuseArgs &a, cudaStream_t st);
 cudaError_t launch_level_extract(const LevelBuf &lv, int which, uint8_t *out, cudaStream_t st);
 cudaError_t launch_zncc_full(const FullArgs &a, int nh, int sx, cudaStream_t st);
+// Small-level full-range search (one thread per pixel); fits: the full-range tiles of a
+// W x H level would not fill the GPU.
+bool zncc_coarse_fits(int W, int H, int sms);
+cudaError_t launch_zncc_coarse(const LevelBuf &l, int nh, int16_t *d, float *c, unsigned long long *evals,
+                               cudaStream_t st);
 cudaError_t launch_beta_gate(const float *Cc, int Wc, int Hc, int W, int H, float beta, uint8_t *mask,
                              int *tile_flags, int tile_w, int tile_h, cudaStream_t st);
 cudaError_t launch_alpha_refine(const LevelBuf &l, int nh, float alpha, int16_t *d, float *C,

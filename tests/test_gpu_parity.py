@@ -59,22 +59,30 @@ def test_pyramid_with_padded_pitch():
 
 
 @pytest.mark.parametrize("win", [3, 5, 7, 9, 11, 13])
-@pytest.mark.parametrize("h,w,D", [(24, 70, 16), (37, 300, 64), (9, 17, 40)])
-def test_full_level_random(win, h, w, D):
+@pytest.mark.parametrize("h,w,D", [(24, 70, 16), (37, 300, 64), (9, 17, 40), (20, 260, 100)])
+@pytest.mark.parametrize("kernel", ["auto", "tile"])
+def test_full_level_random(win, h, w, D, kernel):
+    # "auto": the context's choice (the small-level kernel at these sizes); "tile": explicit
+    # tuning selects the full-range tile kernel
     a, b = rand_pair(h, w, win * 100 + w)
     ctx = make_ctx(w, h, D, 1, win, 2)
+    if kernel == "tile":
+        ctx.set_level_tuning(0, 2, 0)
     ctx.pyramid(dev(a), dev(b))
     d, c = ctx.match_level(0)
     do, co, c2, ev = oracle.match_level(a, b, win // 2, D)
-    compare_level(host(d), host(c), do, co, c2, f"full win={win} {h}x{w} D={D}")
+    compare_level(host(d), host(c), do, co, c2, f"full ({kernel}) win={win} {h}x{w} D={D}")
     assert ctx.eval_count() == ev
 
 
-@pytest.mark.parametrize("name,seed", [("small_320x240", 0), ("small_320x240", 1)])
-def test_full_level_on_scene(name, seed):
+@pytest.mark.parametrize("name,seed,kernel", [("small_320x240", 0, "auto"), ("small_320x240", 1, "auto"),
+                                              ("small_320x240", 0, "tile")])
+def test_full_level_on_scene(name, seed, kernel):
     sc = scenes.make_pair(scenes.SPECS[name], seed)
     s = sc.spec
     ctx = make_ctx(s.width, s.height, s.max_disp, 1, s.window, s.radius)
+    if kernel == "tile":
+        ctx.set_level_tuning(0, 1, 32)
     ctx.pyramid(dev(sc.left), dev(sc.right))
     d, c = ctx.match_level(0)
     do, co, c2, ev = oracle.match_level(sc.left, sc.right, s.window // 2, s.max_disp)
