@@ -158,9 +158,11 @@ OPS_PER_EVAL_FULL = 8   # sliding sums: 2 vertical + 2 horizontal, c (2), scale 
 def stage_work(name, spec, levels_wh, evals_by_level):
     """(bound, algorithmic amount, unit) of one stage of the pass."""
     if name == "pyramid":
-        # read both input images once, write every level's apron buffer of both images
+        # read both input images once, write every level's apron buffer of both images; read
+        # the right image of levels 0..K-2 and write their 8-byte statistics planes
         w0, h0 = levels_wh[0]
-        return "hbm", 2 * w0 * h0 + sum(2 * (w + 32) * (h + 16) for w, h in levels_wh), "B"
+        return "hbm", (2 * w0 * h0 + sum(2 * (w + 32) * (h + 16) for w, h in levels_wh)
+                       + sum(9 * w * h for w, h in levels_wh[:-1])), "B"
     if name.startswith("full_level"):
         k = int(name[len("full_level"):])
         return "alu", evals_by_level[k] * OPS_PER_EVAL_FULL, "op"
@@ -536,7 +538,7 @@ def run_gpu(args):
         additions["batching"] = bench_batch(args, dev, flush, stream)
         additions["differentiable"] = bench_diff(args, dev, flush, stream)
 
-    launches_per_step = 2 * spec.levels
+    launches_per_step = ctx.pass_kernel_count()
     line = {
         "metric": METRIC,
         "value": fps,

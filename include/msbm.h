@@ -154,7 +154,9 @@ msbm_status msbm_level_result(msbm_ctx *ctx, int32_t level, int16_t *d_out, floa
 /* Timing aid: run the whole pass once with direct launches, recording a CUDA event
  * before the first kernel and after each stage on the context's stream, wait, and write
  * each stage's milliseconds to stage_ms in launch order:
- *   [0]          the pyramid: level-0 copy and reduces to levels 1 .. K-1 (fused launches),
+ *   [0]          the pyramid (level-0 copy and reduces to levels 1 .. K-1, fused launches)
+ *                and the right-window statistics planes of levels 0 .. K-2 (one launch; the
+ *                pass itself runs that launch beside the coarsest level's search),
  *   [1]          full search at level K-1 (+ alpha refinement when enabled),
  *   [2 .. K]     levels K-2 .. 0: restricted search (+ beta gate and gated full search,
  *                + selective median, when enabled).
@@ -170,6 +172,10 @@ msbm_status msbm_sync(msbm_ctx *ctx);
 /* Number of (pixel, candidate) ZNCC evaluations performed since the last call with
  * reset != 0 (synchronises the stream). */
 msbm_status msbm_eval_count(msbm_ctx *ctx, int64_t *count, int32_t reset);
+
+/* Kernel launches in one msbm_disparity call: the kernel nodes of the pass graph captured
+ * by the last msbm_disparity (0 before the first call or with MSBM_FLAG_NO_GRAPH). */
+msbm_status msbm_pass_kernel_count(const msbm_ctx *ctx, int32_t *count);
 
 /* Tuning of the full-range search at `level` (used at the coarsest level and by K = 1):
  * tiles of 32*sx columns x 8 rows (sx in {1, 2, 4}) and z-blocks of `zblock` candidates

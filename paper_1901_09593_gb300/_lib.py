@@ -57,6 +57,7 @@ SIGNATURES = {
     "msbm_selective_median": ([c_void_p, c_int32, c_void_p, c_void_p, c_void_p], ctypes.c_int),
     "msbm_match_level_beta": ([c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], ctypes.c_int),
     "msbm_eval_count": ([c_void_p, P(ctypes.c_int64), c_int32], ctypes.c_int),
+    "msbm_pass_kernel_count": ([c_void_p, P(c_int32)], ctypes.c_int),
     "msbm_set_level_tuning": ([c_void_p, c_int32, c_int32, c_int32], ctypes.c_int),
     "msbm_batch_create": ([P(msbm_params), c_int32, c_void_p, c_void_p, c_void_p, P(c_void_p)], ctypes.c_int),
     "msbm_batch_run": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], ctypes.c_int),

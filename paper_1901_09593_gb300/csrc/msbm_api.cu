@@ -39,6 +39,7 @@ struct msbm_ctx {
     cudaGraphExec_t exec = nullptr;
     const void *gkey[4] = {nullptr, nullptr, nullptr, nullptr};
     size_t gpitch = 0;
+    int graph_kernels = 0;       // kernel nodes of the captured pass graph
     // level-0 cost when the caller passes none but a gated step needs one
     float *c0 = nullptr;
     // device staging of msbm_disparity_host
@@ -85,6 +86,19 @@ bool encode_u64(CUtensorMap *m, void *base, int pitch, int rows, int box_w, int 
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, base, dims, strides, box, es,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int count_kernel_nodes(cudaGraph_t g) {
+    size_t n = 0;
+    if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess || n == 0) return 0;
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return 0;
+    int k = 0;
+    for (size_t i = 0; i < n; ++i) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+    }
+    return k;
 }
 
 msbm_status validate(const msbm_params *p) {
@@ -490,6 +504,7 @@ msbm_status msbm_disparity(msbm_ctx *ctx, const uint8_t *d_left, const uint8_t *
             }
         }
         if (!ctx->exec) e = cudaGraphInstantiate(&ctx->exec, g, 0);
+        ctx->graph_kernels = count_kernel_nodes(g);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) {
             ctx->exec = nullptr;
@@ -553,9 +568,10 @@ msbm_status msbm_profile_disparity(msbm_ctx *ctx, const uint8_t *d_left, const u
     int i = 0;
     if (s == MSBM_OK) s = cuda_status(cudaEventRecord(ev[i++], st));
     if (s == MSBM_OK) s = enqueue_pyramid(ctx, d_left, d_right, pitch_bytes, st);
+    if (s == MSBM_OK && K >= 2) s = cuda_status(launch_right_stats(ctx->lv.data(), K - 1, ctx->nh, st));
     if (s == MSBM_OK) s = cuda_status(cudaEventRecord(ev[i++], st));
     for (int k = K - 1; s == MSBM_OK && k >= 0; --k) {
-        s = enqueue_match(ctx, k, d_out, cost_out, st);
+        s = enqueue_match(ctx, k, d_out, cost_out, st, true);
         if (s == MSBM_OK) s = cuda_status(cudaEventRecord(ev[i++], st));
     }
     if (s == MSBM_OK) s = cuda_status(cudaStreamSynchronize(st));
@@ -564,6 +580,12 @@ msbm_status msbm_profile_disparity(msbm_ctx *ctx, const uint8_t *d_left, const u
     for (auto &x : ev)
         if (x) cudaEventDestroy(x);
     return s;
+}
+
+msbm_status msbm_pass_kernel_count(const msbm_ctx *ctx, int32_t *count) {
+    if (!ctx || !count) return MSBM_ERR_INVALID_ARG;
+    *count = ctx->exec ? ctx->graph_kernels : 0;
+    return MSBM_OK;
 }
 
 msbm_status msbm_sync(msbm_ctx *ctx) {

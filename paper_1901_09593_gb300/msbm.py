@@ -89,6 +89,12 @@ class Context:
         _lib.check(self._lib.msbm_eval_count(self._ctx, ctypes.byref(v), int(reset)), "msbm_eval_count")
         return int(v.value)
 
+    def pass_kernel_count(self) -> int:
+        """Kernel launches of one disparity() call (the captured pass graph's kernel nodes)."""
+        v = ctypes.c_int32()
+        _lib.check(self._lib.msbm_pass_kernel_count(self._ctx, ctypes.byref(v)), "msbm_pass_kernel_count")
+        return int(v.value)
+
     # -- steps ------------------------------------------------------------------------
     def pyramid(self, left, right) -> None:
         self._bind_stream()
