@@ -1,11 +1,14 @@
 // batch.cu -- many stereo pairs of uneven sizes and disparity ranges through all pyramid
 // levels in one persistent launch (the hierarchical pass of Sec. III, Fig. 1, per pair).
 //
-// Work queue.  Each pair's pass is a chain of 2K stages:
-//   stage 0          level-0 copy into the pair's apron buffers      (row bands)
-//   stage 1 .. K-1   pyramid reduce producing level k                 (row bands)
-//   stage K          full-range search at level K-1 (Eq. 3-4)         (TX x 8 tiles)
-//   stage K+1+j      restricted search at level K-2-j (Eq. 8-9)       (64 x 16 tiles)
+// Work queue.  Each pair's pass is a chain of stages (the host's per-pair stage table):
+//   pyramid          fused groups of up to 3 reduce levels (pyramid_fused.cuh), 16 x 8 tiles
+//                    of the group's coarsest level per image; a plain band copy when K = 1
+//   coarsest level   full-range search at level K-1 (Eq. 3-4): the small-level tile
+//                    (zncc_coarse_tile.cuh) for D_k <= 64, else the full-range tile
+//   statistics       right-window statistics planes of levels 0 .. K-2 (level_stats_tile.cuh)
+//   restricted       level K-2 .. 0 (Eq. 8-9), 32 x 16 tiles of vertical pixel pairs reading
+//                    the level's statistics plane (zncc_restricted_tile.cuh, plane mode)
 // Stage s of a pair needs every tile of stage s-1 of the same pair.  The host lays the
 // (pair, stage) segments out stage-major (stage 0 of every pair, then stage 1, ...), which is
 // a topological order, and the CTAs of one persistent grid take items from the flattened
@@ -15,11 +18,11 @@
 // cannot deadlock whatever the grid size.  On a timeout the kernel records MSBM_ERR_TIMEOUT
 // and all CTAs stop taking work.
 //
-// Tiles are the same device functions as the standalone kernels (zncc_full_tile.cuh,
-// zncc_restricted_tile.cuh, pyramid_ops.cuh); the full-range tile width (sx) and z-block per
-// pair come from the caller (the autotuner).  The grid is sized from the occupancy of the
-// kernel (co-resident CTAs).  The launch (counter resets + kernel) is captured in a CUDA
-// graph; per-run caller pointers live in a small device table copied before each replay.
+// Tiles are the same device functions as the standalone kernels; the full-range tile width
+// (sx) and z-block per pair come from the caller (the autotuner).  The grid is sized from the
+// occupancy of the kernel (co-resident CTAs).  The launch (counter resets + kernel) is
+// captured in a CUDA graph; per-run caller pointers live in a small device table copied
+// before each replay.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -32,7 +35,10 @@
 #include "msbm.h"
 #include "msbm_device.cuh"
 #include "msbm_internal.h"
+#include "level_stats_tile.cuh"
+#include "pyramid_fused.cuh"
 #include "pyramid_ops.cuh"
+#include "zncc_coarse_tile.cuh"
 #include "zncc_full_tile.cuh"
 #include "zncc_restricted_tile.cuh"
 
@@ -43,30 +49,52 @@ namespace {
 using namespace tiles;
 
 constexpr int BT_MAXK = 12;
+constexpr int BT_MAXG = (BT_MAXK + PF_MAXF - 2) / PF_MAXF;   // fused pyramid groups
+constexpr int BT_MAXS = BT_MAXG + 2 + BT_MAXK;              // stages per pair
 constexpr int BT_THREADS = 256;
-constexpr int BT_BAND = 16;          // apron rows per copy/reduce item
+// Two builds of the kernel: with the full-range tile (its 128-register, ~57 KB footprint
+// allows 2 CTAs per SM) for batches whose coarsest levels exceed BT_COARSE_DK candidates, and
+// without it (64 registers: 4 CTAs per SM) otherwise.
+constexpr int BT_CTAS_FULL = 2, BT_CTAS_LEAN = 4;
+constexpr int BT_BAND = 16;          // apron rows per copy item (K = 1)
 constexpr int BT_MAX_NH = 4;         // windows up to 9 x 9
 constexpr int BT_ZC = 4;             // candidates per lane chunk in batched full-range tiles
-constexpr int BT_RTX = RCfg<1, 32>::TX;   // restricted tile width (64 pixels, 256 threads)
+constexpr int BT_COARSE_DK = 64;     // coarsest levels with D_k up to this use the small-level tile
+constexpr int BT_NCOL = 1;           // restricted tile: vertical pixel pairs (32 x 16 tiles)
+constexpr int BT_RTX = RCfg<1, 32, BT_NCOL>::TX;   // restricted tile width (256 threads)
+constexpr int BT_AUX = 128;          // shared bytes before the scratch of non-TMA tiles (mbarrier)
 constexpr long long BT_WAIT_LIMIT = 4000000000LL;   // ~2 s at 2 GHz
 constexpr long long BT_TEST_WAIT_LIMIT = 2000000LL; // ~1 ms (MSBM_FLAG_TEST_TIMEOUT)
+
+enum BStageType { BS_COPY = 0, BS_PYR, BS_COARSE, BS_FULL, BS_STATS, BS_RESTR };
 
 struct BLevel {
     int W, H, Dk, pitch;
     uint8_t *L, *R;          // image origins in the apron buffers
     int16_t *d;              // maps of levels >= 1
     float *c;
+    int2 *rstat;             // right-window statistics plane (levels below the coarsest)
+    int rspitch;
     int sx, zblock;          // full-range tiling (coarsest level only)
-    int tiles_x;             // tiles across for this level's matching stage
+};
+
+struct BStage {
+    int type;                // BStageType
+    int arg;                 // BS_PYR: fused group; BS_COARSE / BS_FULL / BS_RESTR: level
+    int tiles_x, ntiles;     // tiles across (per image for BS_PYR) and in total
 };
 
 struct BPair {
-    int W, H, D, K, nh, r;
+    int W, H, D, K, nh, r, nst;
+    BStage st[BT_MAXS];
+    PyrFuseArgs pf[BT_MAXG];           // fused pyramid groups (group 0 reads the caller's images)
+    int pf_nby[BT_MAXG];               // tile rows of each group's coarsest level
+    int sfirst[BT_MAXK + 1], stx[BT_MAXK];   // statistics stage: first tile and tiles across per level
     BLevel lv[BT_MAXK];
 };
 
 struct BMaps {               // TMA descriptors of one (pair, level), 64-byte aligned
-    CUtensorMap mRL, mR128, mR256, mF256, mFL;
+    CUtensorMap mRL, mR128, mR256, mF256, mFL, mS128, mS256;
 };
 
 struct BIO {                 // per-run caller pointers of one pair
@@ -89,7 +117,7 @@ struct BatchArgs {
     int nseg;
     long long total;
     int *head;               // queue counter
-    int *done;               // [pair * 2 * BT_MAXK + stage] finished tiles
+    int *done;               // [pair * BT_MAXS + stage] finished tiles
     unsigned long long *evals;
     int *err;
     int withhold;            // test hook: never publish completion of stage 0
@@ -106,72 +134,132 @@ __device__ __forceinline__ void fence_proxy_async_global() {
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
+// The non-TMA tiles are called out of line so that each keeps its own register allocation
+// inside the persistent kernel's 128-register budget.
+template <int F>
+__device__ __noinline__ void pyr_item(const PyrFuseArgs &pf, const uint8_t *src, size_t spitch, int bx, int by,
+                                      int img, int nbx, int nby, uint8_t *sm) {
+    pyr_fused_tile<F>(pf, src, spitch, bx, by, img, nbx, nby, sm);
+}
+
 template <int NH>
-__device__ bool run_match(const BatchArgs &a, const BPair &P, const BMaps *mp, const BIO &io, int stage,
-                          int tile, uint8_t *smem, uint32_t &parity) {
+__device__ __noinline__ void stats_item(const BLevel &l, int bx, int by, uint8_t *sm) {
+    stats_tile<NH>(l.R, l.pitch, l.W, l.H, l.rstat, l.rspitch, bx, by, sm);
+}
+
+template <int NH>
+__device__ __noinline__ void coarse_item(const BLevel &l, int16_t *d_out, float *c_out, unsigned long long *evals,
+                                         int bx, int by, uint8_t *sm) {
+    coarse_tile<NH>(l.L, l.R, l.pitch, l.W, l.H, l.Dk, d_out, c_out, evals, bx, by, sm);
+}
+
+template <int NH, bool FULL>
+__device__ bool run_item(const BatchArgs &a, const BPair &P, const BMaps *mp, const BIO &io, const BStage &S,
+                         int tile, uint8_t *smem, uint32_t &parity) {
     const int K = P.K;
-    if (stage == K) {                                    // coarsest full search
-        const int k = K - 1;
-        const BLevel &l = P.lv[k];
+    if (S.type == BS_PYR) {
+        const PyrFuseArgs &pf = P.pf[S.arg];
+        const int per = S.ntiles / 2, img = tile / per, t = tile - img * per;
+        const int by = t / S.tiles_x, bx = t - by * S.tiles_x;
+        const uint8_t *src = S.arg == 0 ? (img ? io.R : io.L) : pf.src[img];
+        const size_t spitch = S.arg == 0 ? io.pitch : pf.spitch;
+        switch (pf.F) {
+            case 1: pyr_item<1>(pf, src, spitch, bx, by, img, S.tiles_x, P.pf_nby[S.arg], smem + BT_AUX); break;
+            case 2: pyr_item<2>(pf, src, spitch, bx, by, img, S.tiles_x, P.pf_nby[S.arg], smem + BT_AUX); break;
+            default: pyr_item<3>(pf, src, spitch, bx, by, img, S.tiles_x, P.pf_nby[S.arg], smem + BT_AUX); break;
+        }
+        return true;
+    }
+    if (S.type == BS_STATS) {
+        int k = 0;
+        while (k + 1 < K - 1 && tile >= P.sfirst[k + 1]) ++k;
+        const int t = tile - P.sfirst[k], by = t / P.stx[k], bx = t - by * P.stx[k];
+        stats_item<NH>(P.lv[k], bx, by, smem + BT_AUX);
+        return true;
+    }
+    const int k = S.arg;
+    const BLevel &l = P.lv[k];
+    int16_t *d_out = k == 0 ? io.d : l.d;
+    float *c_out = k == 0 ? io.c : l.c;
+    const int by = tile / S.tiles_x, bx = tile - by * S.tiles_x;
+    if (S.type == BS_COARSE) {
+        coarse_item<NH>(l, d_out, c_out, a.evals, bx, by, smem + BT_AUX);
+        return true;
+    }
+    if constexpr (FULL) {
+      if (S.type == BS_FULL) {
         FullTileArgs t = {};   // no gating in the batch: mask / tile flags stay NULL
         t.W = l.W; t.H = l.H; t.Dk = l.Dk; t.zblock = l.zblock;
-        t.d_out = k == 0 ? io.d : l.d;
-        t.c_out = k == 0 ? io.c : l.c;
+        t.d_out = d_out; t.c_out = c_out;
         t.evals = a.evals; t.err = a.err; t.force_timeout = 0;
-        const int bx = tile % l.tiles_x, by = tile / l.tiles_x;
         if (l.sx == 1) return full_tile<NH, 1, BT_ZC>(t, &mp[k].mFL, &mp[k].mF256, bx, by, smem, parity);
         return full_tile<NH, 2, BT_ZC>(t, &mp[k].mFL, &mp[k].mF256, bx, by, smem, parity);
+      }
     }
-    const int k = K - 2 - (stage - K - 1);              // restricted level
-    const BLevel &l = P.lv[k];
     RestrTileArgs t = {};
     t.Limg = l.L; t.Rimg = l.R; t.pitch = l.pitch;
     t.W = l.W; t.H = l.H; t.Dk = l.Dk; t.r = P.r;
     t.prior = P.lv[k + 1].d; t.Wp = P.lv[k + 1].W; t.Hp = P.lv[k + 1].H;
-    t.d_out = k == 0 ? io.d : l.d;
-    t.c_out = k == 0 ? io.c : l.c;
+    t.d_out = d_out; t.c_out = c_out;
     t.evals = a.evals; t.err = a.err; t.force_timeout = 0;
-    const int bx = tile % l.tiles_x, by = tile / l.tiles_x;
+    const BMaps &m = mp[k];
     switch (P.r) {
-        case 0: return restr_tile<NH, 1>(t, &mp[k].mRL, &mp[k].mR128, &mp[k].mR256, nullptr, nullptr, bx, by, smem, parity);
-        case 1: return restr_tile<NH, 3>(t, &mp[k].mRL, &mp[k].mR128, &mp[k].mR256, nullptr, nullptr, bx, by, smem, parity);
-        case 2: return restr_tile<NH, 5>(t, &mp[k].mRL, &mp[k].mR128, &mp[k].mR256, nullptr, nullptr, bx, by, smem, parity);
-        default: return restr_tile<NH, 7>(t, &mp[k].mRL, &mp[k].mR128, &mp[k].mR256, nullptr, nullptr, bx, by, smem, parity);
+        case 0: return restr_tile<NH, 1, 32, BT_NCOL, true>(t, &m.mRL, &m.mR128, &m.mR256, &m.mS128, &m.mS256, bx, by, smem, parity);
+        case 1: return restr_tile<NH, 3, 32, BT_NCOL, true>(t, &m.mRL, &m.mR128, &m.mR256, &m.mS128, &m.mS256, bx, by, smem, parity);
+        case 2: return restr_tile<NH, 5, 32, BT_NCOL, true>(t, &m.mRL, &m.mR128, &m.mR256, &m.mS128, &m.mS256, bx, by, smem, parity);
+        default: return restr_tile<NH, 7, 32, BT_NCOL, true>(t, &m.mRL, &m.mR128, &m.mR256, &m.mS128, &m.mS256, bx, by, smem, parity);
     }
 }
 
-__global__ void __launch_bounds__(BT_THREADS, 2) batch_kernel(const __grid_constant__ BatchArgs a) {
+template <bool FULL>
+__global__ void __launch_bounds__(BT_THREADS, FULL ? BT_CTAS_FULL : BT_CTAS_LEAN)
+    batch_kernel(const __grid_constant__ BatchArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ long long item_s;
+    __shared__ int seg_s;
     __shared__ int ok_s;
     const int tid = threadIdx.x;
+    // thread 0 reserves the CTA's next item while the current one runs (the atomic's latency
+    // hides behind the work); items are still taken in increasing order, and the smallest
+    // unfinished item is always one a CTA is working on, so reservations cannot deadlock
+    long long next = 0;
+    int last_seg = -1;       // thread 0: segment of the previous item (its dependency already met)
     if (tid == 0) {
         mbar_init(reinterpret_cast<uint64_t *>(smem), 1);
         fence_mbar_init();
+        seg_s = 0;
+        next = atomicAdd(a.head, 1);
     }
     uint32_t parity = 0;
     for (;;) {
         __syncthreads();   // the previous item is finished with shared memory
         if (tid == 0) {
-            long long it = a.total;
-            if (*reinterpret_cast<volatile int *>(a.err) == 0) it = atomicAdd(a.head, 1);
+            const long long it = next;
             item_s = it;
+            if (it < a.total) next = atomicAdd(a.head, 1);
+            // segment of this item: the last segment whose start is <= it.  Items are handed
+            // out in increasing order, so this CTA's segment only moves forward.
+            int sgi = seg_s;
+            while (sgi + 1 < a.nseg && a.segs[sgi + 1].start <= it) ++sgi;
+            seg_s = sgi;
         }
         __syncthreads();
         const long long it = item_s;
         if (it >= a.total) break;
-        // segment of this item: the last segment whose start is <= it
-        int lo = 0, hi = a.nseg - 1;
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (a.segs[mid].start <= it) lo = mid; else hi = mid - 1;
-        }
-        const BSeg sg = a.segs[lo];
+        const BSeg sg = a.segs[seg_s];
         const int tile = static_cast<int>(it - sg.start);
         if (tid == 0) {
             int ok = 1;
-            if (sg.stage > 0) {
-                const int *cnt = a.done + sg.pair * 2 * BT_MAXK + sg.stage - 1;
+            // a new segment: stop if another CTA recorded an error, else wait for the pair's
+            // previous stage (later items of the same segment find it complete)
+            if (seg_s != last_seg) {
+                last_seg = seg_s;
+                if (*reinterpret_cast<volatile int *>(a.err) != 0) ok = 0;
+            } else {
+                ok = 2;
+            }
+            if (ok == 1 && sg.stage > 0) {
+                const int *cnt = a.done + sg.pair * BT_MAXS + sg.stage - 1;
                 const long long t0 = clock64();
                 while (ld_acquire(cnt) < sg.need) {
                     if (clock64() - t0 > a.wait_limit) {
@@ -184,55 +272,53 @@ __global__ void __launch_bounds__(BT_THREADS, 2) batch_kernel(const __grid_const
             }
             ok_s = ok;
         }
-        __syncthreads();
+        __syncthreads();   // orders thread 0's acquire before every thread's reads
         if (!ok_s) break;
-        __threadfence();
         const BPair &P = a.pairs[sg.pair];
         const BIO io = a.io[sg.pair];
+        const BStage S = P.st[sg.stage];
         bool ok = true;
-        if (sg.stage < P.K) {
-            // copy (stage 0) or reduce (stage k): BT_BAND apron rows of level `stage`
-            const BLevel &d = P.lv[sg.stage];
+        if (S.type == BS_COPY) {
+            // level-0 copy (K = 1): BT_BAND apron rows
+            const BLevel &d = P.lv[0];
             const int quads = (d.W + 2 * APX + 3) / 4;
             const int y0 = tile * BT_BAND - APY;
             const int nrow = min(BT_BAND, d.H + APY - y0);
             for (int i = tid; i < 2 * nrow * quads; i += BT_THREADS) {
                 const int img = i / (nrow * quads), j = i - img * nrow * quads;
                 const int Y = y0 + j / quads, X0 = (j % quads) * 4 - APX;
-                uint8_t *dst = img ? d.R : d.L;
-                if (sg.stage == 0)
-                    copy_quad(img ? io.R : io.L, io.pitch, d.W, d.H, dst, d.pitch, X0, Y);
-                else {
-                    const BLevel &s = P.lv[sg.stage - 1];
-                    reduce_quad(img ? s.R : s.L, s.pitch, dst, d.pitch, d.W, d.H, X0, Y);
-                }
+                copy_quad(img ? io.R : io.L, io.pitch, d.W, d.H, img ? d.R : d.L, d.pitch, X0, Y);
             }
         } else {
             const BMaps *mp = a.maps + sg.pair * BT_MAXK;
             switch (P.nh) {
-                case 1: ok = run_match<1>(a, P, mp, io, sg.stage, tile, smem, parity); break;
-                case 2: ok = run_match<2>(a, P, mp, io, sg.stage, tile, smem, parity); break;
-                case 3: ok = run_match<3>(a, P, mp, io, sg.stage, tile, smem, parity); break;
-                default: ok = run_match<4>(a, P, mp, io, sg.stage, tile, smem, parity); break;
+                case 1: ok = run_item<1, FULL>(a, P, mp, io, S, tile, smem, parity); break;
+                case 2: ok = run_item<2, FULL>(a, P, mp, io, S, tile, smem, parity); break;
+                case 3: ok = run_item<3, FULL>(a, P, mp, io, S, tile, smem, parity); break;
+                default: ok = run_item<4, FULL>(a, P, mp, io, S, tile, smem, parity); break;
             }
         }
         (void)ok;   // a failed wait has set the error word; the loop head then stops
         __syncthreads();   // every thread's stores of this item are issued
         if (tid == 0) {
             __threadfence();
-            if (!(a.withhold && sg.stage == 0)) atomicAdd(a.done + sg.pair * 2 * BT_MAXK + sg.stage, 1);
+            if (!(a.withhold && sg.stage == 0)) atomicAdd(a.done + sg.pair * BT_MAXS + sg.stage, 1);
         }
     }
 }
 
-size_t batch_smem_bytes() {
-    size_t m = 0;
-    m = std::max(m, FullCfg<BT_MAX_NH, 2, BT_ZC>::BYTES);
-    m = std::max(m, FullCfg<BT_MAX_NH, 1, BT_ZC>::BYTES);
-    m = std::max(m, RCfg<BT_MAX_NH>::BYTES);
-    for (size_t b : {FullCfg<1, 2, BT_ZC>::BYTES, FullCfg<2, 2, BT_ZC>::BYTES, FullCfg<3, 2, BT_ZC>::BYTES,
-                     RCfg<1>::BYTES, RCfg<2>::BYTES, RCfg<3>::BYTES})
+size_t batch_smem_bytes(bool full) {
+    size_t m = BT_AUX + (size_t)PF_SMEM;
+    for (size_t b : {RCfg<1, 32, BT_NCOL, true>::BYTES, RCfg<2, 32, BT_NCOL, true>::BYTES,
+                     RCfg<3, 32, BT_NCOL, true>::BYTES, RCfg<BT_MAX_NH, 32, BT_NCOL, true>::BYTES,
+                     BT_AUX + StatsCfg<1>::BYTES, BT_AUX + StatsCfg<2>::BYTES, BT_AUX + StatsCfg<3>::BYTES,
+                     BT_AUX + StatsCfg<BT_MAX_NH>::BYTES, BT_AUX + CoarseCfg<1>::BYTES, BT_AUX + CoarseCfg<2>::BYTES,
+                     BT_AUX + CoarseCfg<3>::BYTES, BT_AUX + CoarseCfg<BT_MAX_NH>::BYTES})
         m = std::max(m, b);
+    if (full)
+        for (size_t b : {FullCfg<1, 2, BT_ZC>::BYTES, FullCfg<2, 2, BT_ZC>::BYTES, FullCfg<3, 2, BT_ZC>::BYTES,
+                         FullCfg<BT_MAX_NH, 2, BT_ZC>::BYTES, FullCfg<BT_MAX_NH, 1, BT_ZC>::BYTES})
+            m = std::max(m, b);
     return m;
 }
 
@@ -266,6 +352,19 @@ bool encode_b(CUtensorMap *m, uint8_t *base, int pitch, int rows, int bw, int bh
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// 2-D map over a plane of 8-byte entries: `rows` rows of `pitch` entries.
+bool encode_b64(CUtensorMap *m, void *base, int pitch, int rows, int bw, int bh) {
+    EncodeFn fn = encode_fn_b();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)pitch, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)pitch * 8};
+    cuuint32_t box[2] = {(cuuint32_t)bw, (cuuint32_t)bh};
+    cuuint32_t es[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 inline msbm_status cst(cudaError_t e) {
     return e == cudaSuccess ? MSBM_OK : (e == cudaErrorMemoryAllocation ? MSBM_ERR_OOM : MSBM_ERR_CUDA);
 }
@@ -292,6 +391,7 @@ struct msbm_batch {
     int grid = 0;
     size_t smem = 0;
     bool withhold = false;
+    bool full = false;           // some pair's coarsest level uses the full-range tile
     bool io_uploaded = false;
     cudaGraphExec_t exec = nullptr;
 };
@@ -365,17 +465,71 @@ msbm_status msbm_batch_create(const msbm_params *pairs, int32_t n_pairs, const i
                 dalloc(reinterpret_cast<void **>(&l.d), (size_t)W * H * sizeof(int16_t));
                 dalloc(reinterpret_cast<void **>(&l.c), (size_t)W * H * sizeof(float));
             }
+            l.rspitch = (W + 15) / 16 * 16;
+            if (k < P.K - 1) dalloc(reinterpret_cast<void **>(&l.rstat), (size_t)l.rspitch * H * sizeof(int2));
             l.sx = full_sx ? full_sx[i] : (W >= 512 ? 2 : 1);
             l.zblock = full_zblock ? full_zblock[i] : 0;
-            l.tiles_x = (k == P.K - 1) ? (W + 32 * l.sx - 1) / (32 * l.sx) : (W + BT_RTX - 1) / BT_RTX;
             BMaps &m = maps[(size_t)i * BT_MAXK + k];
             enc_ok = enc_ok && encode_b(&m.mRL, buf, l.pitch, rows, BT_RTX + 32, rowsR) &&
                      encode_b(&m.mR128, buf + bytes, l.pitch, rows, 128, rowsR) &&
                      encode_b(&m.mR256, buf + bytes, l.pitch, rows, 256, rowsR) &&
                      encode_b(&m.mF256, buf + bytes, l.pitch, rows, 256, rowsF) &&
                      encode_b(&m.mFL, buf, l.pitch, rows, 32 * l.sx + 32, rowsF);
+            if (l.rstat)
+                enc_ok = enc_ok && encode_b64(&m.mS128, l.rstat, l.rspitch, H, 128, RT_TY) &&
+                         encode_b64(&m.mS256, l.rstat, l.rspitch, H, 256, RT_TY);
             W = (W + 1) / 2;
             H = (H + 1) / 2;
+        }
+        if (e != cudaSuccess) break;
+        // the pair's stage table
+        auto add = [&](int type, int arg, int tx, int nt) {
+            BStage &S = P.st[P.nst++];
+            S.type = type; S.arg = arg; S.tiles_x = tx; S.ntiles = nt;
+        };
+        const int K = P.K;
+        if (K == 1) {
+            add(BS_COPY, 0, 1, (P.lv[0].H + 2 * APY + BT_BAND - 1) / BT_BAND);
+        } else {
+            for (int s0 = 0, g = 0; s0 < K - 1; s0 += PF_MAXF, ++g) {
+                PyrFuseArgs &f = P.pf[g];
+                f.F = std::min(PF_MAXF, K - 1 - s0);
+                f.write_src = s0 == 0;
+                f.src[0] = P.lv[s0].L;
+                f.src[1] = P.lv[s0].R;
+                f.spitch = (size_t)P.lv[s0].pitch;
+                for (int j = 0; j <= f.F; ++j) {
+                    const BLevel &l = P.lv[s0 + j];
+                    f.W[j] = l.W; f.H[j] = l.H;
+                    f.dst[j][0] = l.L; f.dst[j][1] = l.R;
+                    f.dpitch[j] = l.pitch;
+                }
+                const int tx = (f.W[f.F] + PF_TX - 1) / PF_TX, ty = (f.H[f.F] + PF_TY - 1) / PF_TY;
+                P.pf_nby[g] = ty;
+                add(BS_PYR, g, tx, 2 * tx * ty);
+            }
+        }
+        {
+            const BLevel &l = P.lv[K - 1];
+            if (l.Dk <= BT_COARSE_DK) {
+                const int tx = (l.W + CO_TX - 1) / CO_TX;
+                add(BS_COARSE, K - 1, tx, tx * ((l.H + CO_TY - 1) / CO_TY));
+            } else {
+                const int tx = (l.W + 32 * l.sx - 1) / (32 * l.sx);
+                add(BS_FULL, K - 1, tx, tx * ((l.H + 7) / 8));
+            }
+        }
+        if (K >= 2) {
+            P.sfirst[0] = 0;
+            for (int k = 0; k < K - 1; ++k) {
+                P.stx[k] = (P.lv[k].W + ST_TX - 1) / ST_TX;
+                P.sfirst[k + 1] = P.sfirst[k] + P.stx[k] * ((P.lv[k].H + ST_TY - 1) / ST_TY);
+            }
+            add(BS_STATS, 0, 1, P.sfirst[K - 1]);
+        }
+        for (int k = K - 2; k >= 0; --k) {
+            const int tx = (P.lv[k].W + BT_RTX - 1) / BT_RTX;
+            add(BS_RESTR, k, tx, tx * ((P.lv[k].H + RT_TY - 1) / RT_TY));
         }
     }
     if (e != cudaSuccess || !enc_ok) {
@@ -386,28 +540,22 @@ msbm_status msbm_batch_create(const msbm_params *pairs, int32_t n_pairs, const i
     // stage-major segment list; within a stage, larger stages first
     std::vector<BSeg> segs;
     int max_stages = 0;
-    for (auto &P : b->pairs) max_stages = std::max(max_stages, 2 * P.K);
-    auto ntiles = [](const BPair &P, int s) {
-        if (s < P.K) return (P.lv[s].H + 2 * APY + BT_BAND - 1) / BT_BAND;
-        const int k = s == P.K ? P.K - 1 : P.K - 2 - (s - P.K - 1);
-        const int th = s == P.K ? 8 : RT_TY;   // full-range tiles are 8 rows, restricted 16
-        return P.lv[k].tiles_x * ((P.lv[k].H + th - 1) / th);
-    };
+    for (auto &P : b->pairs) max_stages = std::max(max_stages, P.nst);
     long long pos = 0;
     for (int s = 0; s < max_stages; ++s) {
         std::vector<int> idx;
         for (int i = 0; i < n_pairs; ++i)
-            if (s < 2 * b->pairs[i].K) idx.push_back(i);
+            if (s < b->pairs[i].nst) idx.push_back(i);
         std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
-            return ntiles(b->pairs[x], s) > ntiles(b->pairs[y], s);
+            return b->pairs[x].st[s].ntiles > b->pairs[y].st[s].ntiles;
         });
         for (int i : idx) {
             BSeg g;
             g.start = pos;
             g.pair = i;
             g.stage = s;
-            g.ntiles = ntiles(b->pairs[i], s);
-            g.need = s > 0 ? ntiles(b->pairs[i], s - 1) : 0;
+            g.ntiles = b->pairs[i].st[s].ntiles;
+            g.need = s > 0 ? b->pairs[i].st[s - 1].ntiles : 0;
             pos += g.ntiles;
             segs.push_back(g);
         }
@@ -419,7 +567,7 @@ msbm_status msbm_batch_create(const msbm_params *pairs, int32_t n_pairs, const i
     dalloc(reinterpret_cast<void **>(&b->d_io), sizeof(BIO) * n_pairs);
     dalloc(reinterpret_cast<void **>(&b->d_segs), sizeof(BSeg) * segs.size());
     dalloc(reinterpret_cast<void **>(&b->d_head), sizeof(int));
-    dalloc(reinterpret_cast<void **>(&b->d_done), sizeof(int) * n_pairs * 2 * BT_MAXK);
+    dalloc(reinterpret_cast<void **>(&b->d_done), sizeof(int) * n_pairs * BT_MAXS);
     dalloc(reinterpret_cast<void **>(&b->d_err), sizeof(int));
     dalloc(reinterpret_cast<void **>(&b->d_evals), sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemcpy(b->d_pairs, b->pairs.data(), sizeof(BPair) * n_pairs, cudaMemcpyHostToDevice);
@@ -427,11 +575,15 @@ msbm_status msbm_batch_create(const msbm_params *pairs, int32_t n_pairs, const i
     if (e == cudaSuccess) e = cudaMemcpy(b->d_segs, segs.data(), sizeof(BSeg) * segs.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(b->d_evals, 0, sizeof(unsigned long long));
-    b->smem = batch_smem_bytes();
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+    b->full = false;
+    for (auto &P : b->pairs)
+        for (int s = 0; s < P.nst; ++s) b->full = b->full || P.st[s].type == BS_FULL;
+    b->smem = batch_smem_bytes(b->full);
+    const void *kern = b->full ? reinterpret_cast<const void *>(batch_kernel<true>)
+                               : reinterpret_cast<const void *>(batch_kernel<false>);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
     int occ = 0;
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel, BT_THREADS, b->smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, BT_THREADS, b->smem);
     if (e == cudaSuccess && occ < 1) e = cudaErrorInvalidConfiguration;
     if (e != cudaSuccess) {
         msbm_status s = cst(e);
@@ -453,9 +605,12 @@ static msbm_status batch_enqueue(msbm_batch *b, cudaStream_t st) {
     a.withhold = b->withhold ? 1 : 0;
     a.wait_limit = b->withhold ? BT_TEST_WAIT_LIMIT : BT_WAIT_LIMIT;
     cudaError_t e = cudaMemsetAsync(b->d_head, 0, sizeof(int), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_done, 0, sizeof(int) * b->n * 2 * BT_MAXK, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_done, 0, sizeof(int) * b->n * BT_MAXS, st);
     if (e == cudaSuccess) {
-        batch_kernel<<<b->grid, BT_THREADS, b->smem, st>>>(a);
+        if (b->full)
+            batch_kernel<true><<<b->grid, BT_THREADS, b->smem, st>>>(a);
+        else
+            batch_kernel<false><<<b->grid, BT_THREADS, b->smem, st>>>(a);
         e = cudaGetLastError();
     }
     return cst(e);

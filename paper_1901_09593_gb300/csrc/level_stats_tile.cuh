@@ -1,0 +1,104 @@
+// level_stats_tile.cuh -- one 64 x 32 tile of a right-window statistics plane, shared by
+// the standalone launch (level_stats.cu) and the batched persistent kernel (batch.cu): for
+// every pixel (y, x), S = sum of the (2n+1)^2 window (clamp-to-edge) and rsqrt(N * sum I^2 -
+// S^2), or 0 for a flat window (Sec. III-A, Eq. 1-4 terms of the right window).  The image
+// rows are staged in shared memory (coordinates clamped to the image), vertical window sums
+// slide down 8-row groups of each column, horizontal sums slide along 8-column segments of
+// each row, and the tile leaves in coalesced stores.  All sums are exact integers.
+#pragma once
+
+#include <math.h>
+
+#include "msbm_device.cuh"
+
+namespace msbm {
+
+constexpr int ST_TX = 64, ST_TY = 32;
+
+template <int NH>
+struct StatsCfg {
+    static constexpr int SC = ST_TX + 2 * NH, SR = ST_TY + 2 * NH;   // staged columns, rows
+    static constexpr int VP = SC + 1;                                 // packed-sum row stride (words)
+    static constexpr size_t OFF_VP = (SR * SC + 15) / 16 * 16;
+    static constexpr size_t OFF_SO = OFF_VP + (size_t)ST_TY * VP * 4;
+    static constexpr size_t BYTES = (OFF_SO + (size_t)ST_TY * ST_TX * 8 + 15) / 16 * 16;
+};
+
+// Tile (bx, by) of the plane out (opitch entries per row) of the W x H image R (pitch bytes).
+// sm: StatsCfg<NH>::BYTES bytes, 16-aligned.  blockDim.x == 256.
+template <int NH>
+__device__ void stats_tile(const uint8_t *__restrict__ R, int pitch, int W, int H, int2 *__restrict__ out,
+                           int opitch, int bx, int by, uint8_t *sm) {
+    constexpr int WIN = 2 * NH + 1, N = WIN * WIN;
+    using C = StatsCfg<NH>;
+    constexpr int SC = C::SC, SR = C::SR, VP = C::VP;
+    uint8_t (*sb)[SC] = reinterpret_cast<uint8_t (*)[SC]>(sm);
+    uint32_t (*vp)[VP] = reinterpret_cast<uint32_t (*)[VP]>(sm + C::OFF_VP);   // q | s << 20 per column window
+    int2 (*so)[ST_TX] = reinterpret_cast<int2 (*)[ST_TX]>(sm + C::OFF_SO);
+    const int x0 = bx * ST_TX, y0 = by * ST_TY, tid = threadIdx.x;
+    {
+        constexpr int T = (SR * SC + 255) / 256;
+        uint8_t v[T];
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const int i = tid + 256 * t, r = i / SC, c = i - r * SC;
+            const int yy = min(max(y0 - NH + r, 0), H - 1), xx = min(max(x0 - NH + c, 0), W - 1);
+            v[t] = i < SR * SC ? __ldg(R + (ptrdiff_t)yy * pitch + xx) : 0;
+        }
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const int i = tid + 256 * t;
+            if (i < SR * SC) sb[i / SC][i % SC] = v[t];
+        }
+    }
+    __syncthreads();
+    // vertical: column c, rows 8g .. 8g+7
+    for (int i = tid; i < SC * (ST_TY / 8); i += 256) {
+        const int g = i / SC, c = i - g * SC;
+        uint32_t s = 0, q = 0;
+#pragma unroll
+        for (int t = 0; t < WIN; ++t) {
+            const uint32_t v = sb[8 * g + t][c];
+            s += v;
+            q += v * v;
+        }
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            vp[8 * g + r][c] = q | (s << 20);      // s < 4096, q < 2^20 for windows up to 13 x 13
+            if (r < 7) {
+                const uint32_t a = sb[8 * g + r + WIN][c], b = sb[8 * g + r][c];
+                s += a - b;
+                q += a * a - b * b;
+            }
+        }
+    }
+    __syncthreads();
+    // horizontal: row r, columns 8g .. 8g+7 (256 items)
+    {
+        const int r = tid >> 3, g = tid & 7;
+        const uint32_t *row = &vp[r][8 * g];
+        int s = 0, q = 0;
+#pragma unroll
+        for (int j = 0; j < WIN; ++j) {
+            s += static_cast<int>(row[j] >> 20);
+            q += static_cast<int>(row[j] & 0xFFFFFu);
+        }
+#pragma unroll
+        for (int x = 0; x < 8; ++x) {
+            const int V = N * q - s * s;
+            so[r][8 * g + x] = make_int2(s, V > 0 ? __float_as_int(rsqrtf(static_cast<float>(V))) : 0);
+            if (x < 7) {
+                s += static_cast<int>(row[x + WIN] >> 20) - static_cast<int>(row[x] >> 20);
+                q += static_cast<int>(row[x + WIN] & 0xFFFFFu) - static_cast<int>(row[x] & 0xFFFFFu);
+            }
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < ST_TX * ST_TY / 256; ++t) {
+        const int i = tid + 256 * t, r = i / ST_TX, c = i % ST_TX;
+        if (y0 + r < H && x0 + c < W) out[(size_t)(y0 + r) * opitch + x0 + c] = so[r][c];
+    }
+}
+
+}  // namespace msbm

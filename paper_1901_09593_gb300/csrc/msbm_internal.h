@@ -90,7 +90,6 @@ struct RestrArgs {
 
 cudaError_t launch_apron_copy(const uint8_t *L, const uint8_t *R, size_t spitch, const LevelBuf &lv,
                               cudaStream_t st);
-cudaError_t launch_pyr_reduce(const LevelBuf &src, const LevelBuf &dst, cudaStream_t st);
 
 // Fused pyramid launch: levels s+1 .. s+F from level s (index 0 below is level s).
 constexpr int PF_MAXF = 3;

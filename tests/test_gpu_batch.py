@@ -70,6 +70,20 @@ def test_mixed_batch_equals_single_pair_path():
         np.testing.assert_array_equal(d2[i].cpu().numpy(), d[i].cpu().numpy())
 
 
+def test_batch_with_large_coarsest_range_uses_full_range_tiles():
+    # coarsest levels above 64 candidates select the batch kernel build with the full-range
+    # tile (tile width and z-block from the caller); maps still equal the single-pair path
+    from paper_1901_09593_gb300 import Batch
+    specs = [(300, 60, 160, 1, 5, 2), (240, 100, 300, 2, 7, 2), (96, 64, 24, 2, 5, 1)]
+    Ls, Rs = _pairs(specs, 11)
+    b = Batch(specs, [2, 1, 1], [64, 0, 32])
+    d, c = b.run(Ls, Rs)
+    b.sync()
+    for i, spec in enumerate(specs):
+        dr, cr = _context_result(spec, Ls[i], Rs[i])
+        _same_maps(d[i].cpu().numpy(), c[i].cpu().numpy(), dr, cr, f"pair {i}")
+
+
 def test_scene_batch_matches_oracle_on_levels():
     from paper_1901_09593_gb300 import Batch
     import torch
