@@ -170,6 +170,28 @@ def stage_work(name, spec, levels_wh, evals_by_level):
     return "alu", evals_by_level[k] * ops_per_eval_restricted(spec.window), "op"
 
 
+# DRAM bytes (read + write) per launch from one ncu capture of a kernel
+# (profiles/<kernel>_bench_1400x1000.md), valid while the sources it was taken on are
+# unchanged: the key is a SHA-256 prefix of those files.
+MEASURED_TRAFFIC = {
+    "restricted_level0": {"files": ["zncc_restricted.cu", "zncc_restricted_tile.cuh", "msbm_device.cuh",
+                                    "msbm_internal.h"],
+                          "sha256_16": "9673084a80ac06f2", "bytes": 14760448},
+}
+
+
+def measured_traffic(kernel):
+    import hashlib
+    rec = MEASURED_TRAFFIC.get(kernel)
+    if rec is None:
+        return None
+    h = hashlib.sha256()
+    for f in rec["files"]:
+        with open(os.path.join(ROOT, "paper_1901_09593_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return rec["bytes"] if h.hexdigest()[:16] == rec["sha256_16"] else None
+
+
 def full_evals(w, h, dk):
     return sum(min(dk - 1, x) + 1 for x in range(w)) * h
 
@@ -506,7 +528,7 @@ def run_gpu(args):
         ach = dom["work"] / (dom["ms"] * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Top/s", "frac": ach / peak}
     roof["kernel"] = dom["kernel"]
-    roof["traffic"] = None
+    roof["traffic"] = measured_traffic(dom["kernel"])
     roof["peak_source"] = ("MEASURED_PEAKS.json hbm_gbs" if dom["bound"] == "hbm" and peaks else
                            f"nominal {sms} SMs x 128 lanes x {sm_max:.0f} MHz")
 
