@@ -60,6 +60,8 @@ def _load():
             lib.oracle_selective_median.argtypes = [P, P, i, i, d, P]
             lib.oracle_disparity_full.argtypes = [P, P, i, i, i, i, i, i, d, d, i, P, P, P]
             lib.oracle_disparity_full.restype = ll
+            lib.oracle_level_half_width.argtypes = [i, i]
+            lib.oracle_level_half_width.restype = i
             lib.oracle_max_threads.restype = i
             lib.oracle_set_threads.argtypes = [i]
             _lib = lib
@@ -199,6 +201,12 @@ def softargmax_bwd(left, right, n: int, ndisp: int, T: float, eps: float, g_d):
 # --- gated steps of the full method (alpha refinement, beta fallback, selective median) ---
 ALPHA_REFINE, BETA_FALLBACK, SELECTIVE_MEDIAN = 1, 2, 4
 FULL_METHOD = ALPHA_REFINE | BETA_FALLBACK | SELECTIVE_MEDIAN
+WINDOW_HALVING = 8     # per-level block size halving (Sec. III)
+
+
+def level_half_width(n0: int, k: int) -> int:
+    """Window half-width at level k with per-level halving: max(1, n0 >> k)."""
+    return int(_load().oracle_level_half_width(n0, k))
 
 
 def bicubic_at(cost, cy: float, cx: float) -> float:

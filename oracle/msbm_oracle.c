@@ -468,12 +468,22 @@ void oracle_selective_median(const int16_t *d_in, const double *C, int W, int H,
         }
 }
 
+/* Window half-width at level k when the block size halves per level (Sec. III: the
+ * matching block size decreases by a factor of 2 at every pyramid level; Sec. IV gives the
+ * block of the full-resolution level): n_k = max(1, n_0 >> k), i.e. windows 2 n_k + 1. */
+int oracle_level_half_width(int n0, int k) {
+    int n = n0 >> k;
+    return n < 1 ? 1 : n;
+}
+
 /* The full method of Sec. III (Fig. 1): coarsest WTA, then (flags & 1) alpha refinement;
  * at each finer level the beta-gated search (flags & 2; else the restricted branch only),
- * then (flags & 4) the selective median.  Outputs as oracle_disparity: all levels, level 0
- * first; d_all holds each level's final (post-median) map, C_all its cost (the median
- * changes d only), C2_all the second-best cost.  Returns the evaluation count (alpha
- * refinement counts its 3x3 x candidates evaluations), or -1 on bad arguments. */
+ * then (flags & 4) the selective median.  flags & 8: level k matches with half-width
+ * oracle_level_half_width(w / 2, k) instead of w / 2 at every level.  Outputs as
+ * oracle_disparity: all levels, level 0 first; d_all holds each level's final
+ * (post-median) map, C_all its cost (the median changes d only), C2_all the second-best
+ * cost.  Returns the evaluation count (alpha refinement counts its 3x3 x candidates
+ * evaluations), or -1 on bad arguments. */
 long long oracle_disparity_full(const uint8_t *L, const uint8_t *R, int W, int H, int D, int K,
                                 int w, int r, double alpha, double beta, int flags, int16_t *d_all,
                                 double *C_all, double *C2_all) {
@@ -490,10 +500,12 @@ long long oracle_disparity_full(const uint8_t *L, const uint8_t *R, int W, int H
     size_t o = 0;
     for (int k = 0; k < K; ++k) { int a, b; oracle_level_size(W, H, k, &a, &b); off[k] = o; o += (size_t)a * b; }
     long long evals = 0;
+    const int n0 = n;
     for (int k = K - 1; k >= 0; --k) {
         int Wk, Hk, Wp = 0, Hp = 0;
         oracle_level_size(W, H, k, &Wk, &Hk);
         int Dk = oracle_level_disp(D, k);
+        n = (flags & 8) ? oracle_level_half_width(n0, k) : n0;
         int16_t *dk = d_all + off[k];
         double *ck = C_all + off[k], *c2k = C2_all + off[k];
         if (k == K - 1) {

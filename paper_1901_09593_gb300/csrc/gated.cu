@@ -51,8 +51,11 @@ __global__ void beta_gate_kernel(const float *__restrict__ Cc, int Wc, int Hc, i
         }
         fb = !(s > beta);
         mask[(size_t)y * W + x] = fb ? 1 : 0;
-        if (fb) atomicOr(tile_flags + (y / tile_h) * tiles_x + x / tile_w, 1);
     }
+    // one flag write per warp and tile: a warp's 32 columns of one row lie in one tile
+    // (tile_w is a multiple of 32 and blocks start on multiples of 32)
+    if (__any_sync(0xFFFFFFFFu, fb) && (threadIdx.x & 31) == 0 && y < H)
+        tile_flags[(y / tile_h) * tiles_x + (blockIdx.x * blockDim.x) / tile_w] = 1;
 }
 
 // Alpha refinement on a 16 x 8 tile.  E(q, z), the ZNCC of every pixel q of the tile's

@@ -21,7 +21,8 @@ struct StatsCfg {
     static constexpr int VP = SC + 1;                                 // packed-sum row stride (words)
     static constexpr size_t OFF_VP = (SR * SC + 15) / 16 * 16;
     static constexpr size_t OFF_SO = OFF_VP + (size_t)ST_TY * VP * 4;
-    static constexpr size_t BYTES = (OFF_SO + (size_t)ST_TY * ST_TX * 8 + 15) / 16 * 16;
+    static constexpr int SOP = ST_TX + 1;                            // output row stride (entries)
+    static constexpr size_t BYTES = (OFF_SO + (size_t)ST_TY * SOP * 8 + 15) / 16 * 16;
 };
 
 // Tile (bx, by) of the plane out (opitch entries per row) of the W x H image R (pitch bytes).
@@ -34,7 +35,7 @@ __device__ void stats_tile(const uint8_t *__restrict__ R, int pitch, int W, int 
     constexpr int SC = C::SC, SR = C::SR, VP = C::VP;
     uint8_t (*sb)[SC] = reinterpret_cast<uint8_t (*)[SC]>(sm);
     uint32_t (*vp)[VP] = reinterpret_cast<uint32_t (*)[VP]>(sm + C::OFF_VP);   // q | s << 20 per column window
-    int2 (*so)[ST_TX] = reinterpret_cast<int2 (*)[ST_TX]>(sm + C::OFF_SO);
+    int2 (*so)[C::SOP] = reinterpret_cast<int2 (*)[C::SOP]>(sm + C::OFF_SO);
     const int x0 = bx * ST_TX, y0 = by * ST_TY, tid = threadIdx.x;
     {
         constexpr int T = (SR * SC + 255) / 256;
@@ -73,9 +74,10 @@ __device__ void stats_tile(const uint8_t *__restrict__ R, int pitch, int W, int 
         }
     }
     __syncthreads();
-    // horizontal: row r, columns 8g .. 8g+7 (256 items)
+    // horizontal: row r, columns 8g .. 8g+7 (256 items; the odd packed-sum row stride and the
+    // padded output stride keep a warp's 32 rows on distinct banks)
     {
-        const int r = tid >> 3, g = tid & 7;
+        const int r = tid & 31, g = tid >> 5;      // a warp: one segment of 32 rows
         const uint32_t *row = &vp[r][8 * g];
         int s = 0, q = 0;
 #pragma unroll

@@ -153,3 +153,39 @@ def test_selective_median_improves_the_planted_scene(oracle_mod):
     med = oracle_mod.disparity_full(sc.left, sc.right, s.max_disp, s.levels, s.window, s.radius, 0.9, 0.9,
                                     oracle_mod.SELECTIVE_MEDIAN)
     assert scenes.bad_rate(med["d"][0], sc.gt, sc.mask) <= scenes.bad_rate(plain["d"][0], sc.gt, sc.mask)
+
+
+def test_window_halving_rule_by_hand(oracle_mod):
+    # Sec. III: the block size halves at every level; Sec. IV: 11x11 at full resolution.
+    # Half-widths n_k = max(1, n_0 >> k): windows 11, 5, 3, 3, ...
+    table = {5: [5, 2, 1, 1, 1], 3: [3, 1, 1, 1], 1: [1, 1, 1], 6: [6, 3, 1, 1], 4: [4, 2, 1, 1]}
+    for n0, expect in table.items():
+        assert [oracle_mod.level_half_width(n0, k) for k in range(len(expect))] == expect
+    assert [2 * oracle_mod.level_half_width(5, k) + 1 for k in range(4)] == [11, 5, 3, 3]
+
+
+def test_window_halving_composes_per_level_windows(oracle_mod):
+    sc = scenes.make_pair(scenes.SPECS["small_320x240"], 7)
+    a, b = sc.left[:72, :150].copy(), sc.right[:72, :150].copy()
+    D, K, w, r = 40, 3, 11, 2
+    full = oracle_mod.disparity_full(a, b, D, K, w, r, 0.9, 0.9, oracle_mod.WINDOW_HALVING)
+    pa, pb = oracle_mod.pyramid(a, K), oracle_mod.pyramid(b, K)
+    prior = None
+    evals = 0
+    for k in range(K - 1, -1, -1):
+        n = max(1, (w // 2) >> k)
+        dk = oracle_mod.level_disp(D, k)
+        if prior is None:
+            d, c, c2, ev = oracle_mod.match_level(pa[k], pb[k], n, dk)
+        else:
+            d, c, c2, ev = oracle_mod.match_level(pa[k], pb[k], n, dk, r, prior)
+        np.testing.assert_array_equal(full["d"][k], d)
+        np.testing.assert_array_equal(full["C"][k], c)
+        prior, evals = d, evals + ev
+    assert full["evals"] == evals
+    # one level: halving changes nothing; without the flag every level uses w
+    one = oracle_mod.disparity_full(a, b, D, 1, w, r, 0.9, 0.9, oracle_mod.WINDOW_HALVING)
+    np.testing.assert_array_equal(one["d"][0], oracle_mod.disparity(a, b, D, 1, w, r)["d"][0])
+    plain = oracle_mod.disparity_full(a, b, D, K, w, r, 0.9, 0.9, 0)
+    np.testing.assert_array_equal(plain["d"][0], oracle_mod.disparity(a, b, D, K, w, r)["d"][0])
+    assert not np.array_equal(plain["d"][K - 1], full["d"][K - 1])
