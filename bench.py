@@ -468,7 +468,9 @@ def run_gpu(args):
     # -- the gated steps of the full method on the same pair (Sec. III-B/C/D)
     methods = {}
     for name, fl in (("selective_median", _lib.MSBM_FLAG_SELECTIVE_MEDIAN),
-                     ("full_method", _lib.MSBM_FLAGS_FULL_METHOD)):
+                     ("full_method", _lib.MSBM_FLAGS_FULL_METHOD),
+                     ("window_halving", _lib.MSBM_FLAG_WINDOW_HALVING),
+                     ("full_method_window_halving", _lib.MSBM_FLAGS_FULL_METHOD | _lib.MSBM_FLAG_WINDOW_HALVING)):
         cx = Context(W, H, spec.max_disp, spec.levels, spec.window, spec.radius, fl, alpha=0.9, beta=0.9)
         dm = torch.empty_like(d)
         cm = torch.empty_like(c)

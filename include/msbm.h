@@ -65,13 +65,18 @@ typedef enum msbm_status {
 #define MSBM_FLAG_BETA_FALLBACK 8u
 #define MSBM_FLAG_SELECTIVE_MEDIAN 16u
 #define MSBM_FLAGS_FULL_METHOD (MSBM_FLAG_ALPHA_REFINE | MSBM_FLAG_BETA_FALLBACK | MSBM_FLAG_SELECTIVE_MEDIAN)
+/* Per-level block size (Sec. III: the matching block size halves at every pyramid level):
+ * `window` is level 0's; level k matches with half-width n_k = max(1, n_0 >> k), i.e.
+ * windows 2 n_k + 1 (11, 5, 3, 3, ... for the paper's 11 x 11). */
+#define MSBM_FLAG_WINDOW_HALVING 32u
 
 /* Problem statement (Sec. III; window and pyramid depth as in Sec. IV). */
 typedef struct msbm_params {
     int32_t width, height; /* level-0 size, 1..16384 each                                  */
     int32_t max_disp;      /* D, 1..4096: level-0 candidates 0..D-1                        */
     int32_t levels;        /* K, 1..12; K = 1 is flat full-range block matching             */
-    int32_t window;        /* odd window side 2n+1, 3..13 (int32-exact sums up to 13x13)   */
+    int32_t window;        /* odd window side 2n+1, 3..13 (int32-exact sums up to 13x13);
+                              level 0's with MSBM_FLAG_WINDOW_HALVING                      */
     int32_t radius;        /* r, 0..16: refinement candidates dhat-r .. dhat+r              */
     uint32_t flags;        /* MSBM_FLAG_*                                                   */
     float alpha;           /* threshold of ALPHA_REFINE and SELECTIVE_MEDIAN (paper: 0.9)  */

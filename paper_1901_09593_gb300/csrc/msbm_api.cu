@@ -109,7 +109,8 @@ msbm_status validate(const msbm_params *p) {
     if (p->levels < 1 || p->levels > 12) return MSBM_ERR_INVALID_ARG;
     if (p->window < 3 || p->window > 13 || (p->window & 1) == 0) return MSBM_ERR_INVALID_ARG;
     if (p->radius < 0 || p->radius > 16) return MSBM_ERR_INVALID_ARG;
-    if (p->flags & ~(MSBM_FLAG_NO_GRAPH | MSBM_FLAG_TEST_TIMEOUT | MSBM_FLAGS_FULL_METHOD)) return MSBM_ERR_INVALID_ARG;
+    if (p->flags & ~(MSBM_FLAG_NO_GRAPH | MSBM_FLAG_TEST_TIMEOUT | MSBM_FLAGS_FULL_METHOD | MSBM_FLAG_WINDOW_HALVING))
+        return MSBM_ERR_INVALID_ARG;
     if ((p->flags & (MSBM_FLAG_ALPHA_REFINE | MSBM_FLAG_SELECTIVE_MEDIAN)) && !(p->alpha > -2.f && p->alpha < 2.f))
         return MSBM_ERR_INVALID_ARG;
     if ((p->flags & MSBM_FLAG_BETA_FALLBACK) && !(p->beta > -2.f && p->beta < 2.f)) return MSBM_ERR_INVALID_ARG;
@@ -184,6 +185,18 @@ msbm_status enqueue_pyramid(msbm_ctx *c, const uint8_t *L, const uint8_t *R, siz
     return cuda_status(e);
 }
 
+// Statistics planes of levels 0 .. n-1: one launch per run of levels with the same window.
+cudaError_t launch_stats_levels(msbm_ctx *c, int n, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    for (int k0 = 0; e == cudaSuccess && k0 < n;) {
+        int k1 = k0 + 1;
+        while (k1 < n && c->lv[k1].nh == c->lv[k0].nh) ++k1;
+        e = launch_right_stats(c->lv.data() + k0, k1 - k0, c->lv[k0].nh, st);
+        k0 = k1;
+    }
+    return e;
+}
+
 // stats_ready: the level's right-window statistics plane is already computed in stream order.
 msbm_status enqueue_level(msbm_ctx *c, int k, const int16_t *prior, int16_t *d, float *cost,
                           cudaStream_t st, const uint8_t *mask = nullptr, const int *tile_flags = nullptr,
@@ -192,7 +205,7 @@ msbm_status enqueue_level(msbm_ctx *c, int k, const int16_t *prior, int16_t *d, 
     const int force = (c->p.flags & MSBM_FLAG_TEST_TIMEOUT) ? 1 : 0;
     cudaError_t e;
     if (!prior && !mask && l.coarse) {
-        e = launch_zncc_coarse(l, c->nh, d, cost, c->d_evals, st);
+        e = launch_zncc_coarse(l, l.nh, d, cost, c->d_evals, st);
     } else if (!prior) {
         FullArgs a;
         memset(&a, 0, sizeof(a));
@@ -203,7 +216,7 @@ msbm_status enqueue_level(msbm_ctx *c, int k, const int16_t *prior, int16_t *d, 
         a.t.tiles_x = (l.W + 32 * l.full_sx - 1) / (32 * l.full_sx);
         a.t.d_out = d; a.t.c_out = cost;
         a.t.evals = c->d_evals; a.t.err = c->d_err; a.t.force_timeout = force;
-        e = launch_zncc_full(a, c->nh, l.full_sx, st);
+        e = launch_zncc_full(a, l.nh, l.full_sx, st);
     } else {
         RestrArgs a;
         memset(&a, 0, sizeof(a));
@@ -218,8 +231,8 @@ msbm_status enqueue_level(msbm_ctx *c, int k, const int16_t *prior, int16_t *d, 
         a.t.prior = prior; a.t.Wp = (l.W + 1) / 2; a.t.Hp = (l.H + 1) / 2;
         a.t.d_out = d; a.t.c_out = cost;
         a.t.evals = c->d_evals; a.t.err = c->d_err; a.t.force_timeout = force;
-        e = stats_ready ? cudaSuccess : launch_right_stats(&l, 1, c->nh, st);
-        if (e == cudaSuccess) e = launch_zncc_restricted(a, c->nh, st);
+        e = stats_ready ? cudaSuccess : launch_right_stats(&l, 1, l.nh, st);
+        if (e == cudaSuccess) e = launch_zncc_restricted(a, l.nh, st);
     }
     return cuda_status(e);
 }
@@ -254,7 +267,7 @@ msbm_status enqueue_match(msbm_ctx *c, int k, int16_t *d, float *cost, cudaStrea
     if (k == K - 1) {
         s = enqueue_level(c, k, nullptr, dk, ck, st);
         if (s == MSBM_OK && (f & MSBM_FLAG_ALPHA_REFINE))
-            s = cuda_status(launch_alpha_refine(l, c->nh, c->p.alpha, dk, ck, c->d_evals, st));
+            s = cuda_status(launch_alpha_refine(l, l.nh, c->p.alpha, dk, ck, c->d_evals, st));
         return s;
     }
     const int16_t *prior = c->lv[k + 1].d;
@@ -277,7 +290,7 @@ msbm_status enqueue_all(msbm_ctx *c, const uint8_t *L, const uint8_t *R, size_t 
     if (s == MSBM_OK && K >= 2) {
         cudaError_t e = cudaEventRecord(c->ev_fork, st);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0);
-        if (e == cudaSuccess) e = launch_right_stats(c->lv.data(), K - 1, c->nh, c->side_stream);
+        if (e == cudaSuccess) e = launch_stats_levels(c, K - 1, c->side_stream);
         if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->side_stream);
         s = cuda_status(e);
     }
@@ -326,7 +339,6 @@ msbm_status msbm_create(const msbm_params *params, void *cuda_stream, msbm_ctx *
     c->device = dev;
     c->num_sms = prop.multiProcessorCount;
     c->stream = static_cast<cudaStream_t>(cuda_stream);
-    const int rowsT = 8 + 2 * c->nh;   // staged rows of the full-range tile
     cudaError_t e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
@@ -340,6 +352,8 @@ msbm_status msbm_create(const msbm_params *params, void *cuda_stream, msbm_ctx *
         LevelBuf l;
         l.W = W; l.H = H;
         l.Dk = (int)(((long)params->max_disp + (1L << k) - 1) >> k);
+        l.nh = (params->flags & MSBM_FLAG_WINDOW_HALVING) ? std::max(1, c->nh >> k) : c->nh;
+        const int rowsT = 8 + 2 * l.nh;    // staged rows of the full-range tile
         l.pitch = (W + 2 * APX + 127) / 128 * 128;
         l.rows = H + 2 * APY;
         size_t bytes = (size_t)l.pitch * l.rows;
@@ -365,7 +379,7 @@ msbm_status msbm_create(const msbm_params *params, void *cuda_stream, msbm_ctx *
         l.full_sx = choose_sx(W, H, c->num_sms);
         l.coarse = zncc_coarse_fits(W, H, c->num_sms);
         if (e == cudaSuccess) {
-            const int rowsR = 16 + 2 * c->nh;
+            const int rowsR = 16 + 2 * l.nh;
             bool ok = encode_u8(&l.tmFL, l.base[0], l.pitch, l.rows, 32 * l.full_sx + 32, rowsT) &&
                       encode_u8(&l.tmR256, l.base[1], l.pitch, l.rows, 256, rowsT) &&
                       encode_u8(&l.tmRL, l.base[0], l.pitch, l.rows, 64, rowsR) &&
@@ -375,8 +389,8 @@ msbm_status msbm_create(const msbm_params *params, void *cuda_stream, msbm_ctx *
                       encode_u64(&l.tmS256, l.rstat, l.rspitch, H, 256, 16);
             if (!ok) { c->lv.push_back(l); free_ctx(c); return MSBM_ERR_UNSUPPORTED; }
         }
-        if (e == cudaSuccess) e = zncc_full_prepare(c->nh, l.full_sx);
-        if (e == cudaSuccess) e = zncc_restricted_prepare(c->nh);
+        if (e == cudaSuccess) e = zncc_full_prepare(l.nh, l.full_sx);
+        if (e == cudaSuccess) e = zncc_restricted_prepare(l.nh);
         c->lv.push_back(l);
         W = (W + 1) / 2;
         H = (H + 1) / 2;
@@ -419,9 +433,9 @@ msbm_status msbm_set_level_tuning(msbm_ctx *ctx, int32_t level, int32_t sx, int3
     if (!ctx || level < 0 || level >= ctx->p.levels) return MSBM_ERR_INVALID_ARG;
     if ((sx != 1 && sx != 2 && sx != 4) || zblock < 0 || zblock % 32 != 0) return MSBM_ERR_INVALID_ARG;
     LevelBuf &l = ctx->lv[level];
-    const int rowsT = 8 + 2 * ctx->nh;
+    const int rowsT = 8 + 2 * l.nh;
     if (!encode_u8(&l.tmFL, l.base[0], l.pitch, l.rows, 32 * sx + 32, rowsT)) return MSBM_ERR_UNSUPPORTED;
-    cudaError_t e = zncc_full_prepare(ctx->nh, sx);
+    cudaError_t e = zncc_full_prepare(l.nh, sx);
     if (e != cudaSuccess) return cuda_status(e);
     l.full_sx = sx;
     l.full_zblock = zblock;
@@ -453,7 +467,7 @@ msbm_status msbm_match_level(msbm_ctx *ctx, int32_t level, const int16_t *d_prio
 
 msbm_status msbm_alpha_refine(msbm_ctx *ctx, int32_t level, int16_t *d, float *cost) {
     if (!ctx || level < 0 || level >= ctx->p.levels || !d || !cost) return MSBM_ERR_INVALID_ARG;
-    return cuda_status(launch_alpha_refine(ctx->lv[level], ctx->nh, ctx->p.alpha, d, cost, ctx->d_evals, ctx->stream));
+    return cuda_status(launch_alpha_refine(ctx->lv[level], ctx->lv[level].nh, ctx->p.alpha, d, cost, ctx->d_evals, ctx->stream));
 }
 
 msbm_status msbm_selective_median(msbm_ctx *ctx, int32_t level, const int16_t *d_in, const float *cost,
@@ -568,7 +582,7 @@ msbm_status msbm_profile_disparity(msbm_ctx *ctx, const uint8_t *d_left, const u
     int i = 0;
     if (s == MSBM_OK) s = cuda_status(cudaEventRecord(ev[i++], st));
     if (s == MSBM_OK) s = enqueue_pyramid(ctx, d_left, d_right, pitch_bytes, st);
-    if (s == MSBM_OK && K >= 2) s = cuda_status(launch_right_stats(ctx->lv.data(), K - 1, ctx->nh, st));
+    if (s == MSBM_OK && K >= 2) s = cuda_status(launch_stats_levels(ctx, K - 1, st));
     if (s == MSBM_OK) s = cuda_status(cudaEventRecord(ev[i++], st));
     for (int k = K - 1; s == MSBM_OK && k >= 0; --k) {
         s = enqueue_match(ctx, k, d_out, cost_out, st, true);

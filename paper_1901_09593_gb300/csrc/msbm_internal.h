@@ -15,6 +15,7 @@ namespace msbm {
 // tensor maps the ZNCC kernels stage tiles with.
 struct LevelBuf {
     int W = 0, H = 0, Dk = 0;
+    int nh = 0;                  // window half-width matched at this level
     int pitch = 0;               // bytes per buffer row (multiple of 128)
     int rows = 0;                // H + 2*APY
     uint8_t *base[2] = {nullptr, nullptr};  // buffer starts: image pixel (-APY, -APX)

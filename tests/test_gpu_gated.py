@@ -112,3 +112,32 @@ def test_gated_pass_beats_flat_bad_rate_on_benchmark_pair(flags_name):
     bad_h = scenes.bad_rate(host(d), sc.gt, sc.mask)
     bad_f = scenes.bad_rate(host(df), sc.gt, sc.mask)
     assert bad_h <= bad_f, (bad_h, bad_f)
+
+
+def test_window_halving_levels_match_oracle():
+    # per-level block size halving (Sec. III): level k matches with half-width max(1, n >> k)
+    from paper_1901_09593_gb300 import Context, _lib
+    sc = scenes.make_pair(scenes.SPECS["small_320x240"], 8)
+    s = sc.spec
+    K, win = 3, 11
+    flags = _lib.MSBM_FLAG_WINDOW_HALVING
+    ctx = Context(s.width, s.height, s.max_disp, K, win, s.radius, flags)
+    ctx.pyramid(dev(sc.left), dev(sc.right))
+    ref = oracle.disparity_full(sc.left, sc.right, s.max_disp, K, win, s.radius, ALPHA, BETA,
+                                oracle.WINDOW_HALVING)
+    pa, pb = oracle.pyramid(sc.left, K), oracle.pyramid(sc.right, K)
+    for k in range(K - 1, -1, -1):
+        n = oracle.level_half_width(win // 2, k)
+        dk = oracle.level_disp(s.max_disp, k)
+        if k == K - 1:
+            d, c = ctx.match_level(k)
+            do, co, c2o, _ = oracle.match_level(pa[k], pb[k], n, dk)
+        else:
+            prior = ref["d"][k + 1]
+            d, c = ctx.match_level(k, dev(prior))
+            do, co, c2o, _ = oracle.match_level(pa[k], pb[k], n, dk, s.radius, prior)
+        compare_level(host(d), host(c), do, co, c2o, f"halving level {k} (n={n})")
+    d, c = ctx.disparity(dev(sc.left), dev(sc.right))
+    ctx.sync()
+    assert (host(d) == ref["d"][0]).mean() > 0.99
+    assert ctx.eval_count() > 0
