@@ -163,7 +163,7 @@ msbm_status msbm_level_result(msbm_ctx *ctx, int32_t level, int16_t *d_out, floa
  *                and the right-window statistics planes of levels 0 .. K-2 (one launch; the
  *                pass itself runs that launch beside the coarsest level's search),
  *   [1]          full search at level K-1 (+ alpha refinement when enabled),
- *   [2 .. K]     levels K-2 .. 0: restricted search (+ beta gate and gated full search,
+ *   [2 .. K]     levels K-2 .. 0: restricted search (+ beta gate and the fallback pixels' full search,
  *                + selective median, when enabled).
  * n_stages must be K + 1.  Results equal msbm_disparity's. */
 msbm_status msbm_profile_disparity(msbm_ctx *ctx, const uint8_t *d_left, const uint8_t *d_right,

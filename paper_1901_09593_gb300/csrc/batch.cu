@@ -188,7 +188,7 @@ __device__ bool run_item(const BatchArgs &a, const BPair &P, const BMaps *mp, co
     }
     if constexpr (FULL) {
       if (S.type == BS_FULL) {
-        FullTileArgs t = {};   // no gating in the batch: mask / tile flags stay NULL
+        FullTileArgs t = {};
         t.W = l.W; t.H = l.H; t.Dk = l.Dk; t.zblock = l.zblock;
         t.d_out = d_out; t.c_out = c_out;
         t.evals = a.evals; t.err = a.err; t.force_timeout = 0;

@@ -2,9 +2,8 @@
 // Eq. 8-9, Sec. III-D), each a small kernel around the matching kernels:
 //  * beta gate (Sec. III-C): the cost prior C_hat^k = BI(C^{k+1}) -- bicubic (Catmull-Rom)
 //    upsampling with fine pixel (y, x) at coarse coordinates (y/2, x/2), clamp-to-edge --
-//    and the fallback mask C_hat <= beta, plus one flag per full-range tile that holds a
-//    fallback pixel (the gated full-range pass then runs only those tiles and writes only
-//    the fallback pixels);
+//    and the fallback mask C_hat <= beta (the fallback pixels' full-range search is
+//    zncc_sparse.cu);
 //  * alpha refinement (Eq. 5-7) at the coarsest level: for a pixel with C' <= alpha, the
 //    average of the ZNCC over its 3 x 3 neighbourhood (neighbours inside the image) for
 //    every admissible candidate z <= min(D_k - 1, x), and its argmax / max;
@@ -32,30 +31,23 @@ __device__ __forceinline__ void cr_weights(int i, float w[4], int &base) {
 }
 
 __global__ void beta_gate_kernel(const float *__restrict__ Cc, int Wc, int Hc, int W, int H, float beta,
-                                 uint8_t *mask, int *tile_flags, int tile_w, int tile_h, int tiles_x) {
+                                 uint8_t *mask) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
-    bool fb = false;
-    if (x < W && y < H) {
-        float wy[4], wx[4];
-        int by, bx;
-        cr_weights(y, wy, by);
-        cr_weights(x, wx, bx);
-        float s = 0.f;
+    if (x >= W || y >= H) return;
+    float wy[4], wx[4];
+    int by, bx;
+    cr_weights(y, wy, by);
+    cr_weights(x, wx, bx);
+    float s = 0.f;
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            const int yy = min(max(by - 1 + a, 0), Hc - 1);
-            float r = 0.f;
+    for (int a = 0; a < 4; ++a) {
+        const int yy = min(max(by - 1 + a, 0), Hc - 1);
+        float r = 0.f;
 #pragma unroll
-            for (int b = 0; b < 4; ++b) r = fmaf(wx[b], __ldg(Cc + (size_t)yy * Wc + min(max(bx - 1 + b, 0), Wc - 1)), r);
-            s = fmaf(wy[a], r, s);
-        }
-        fb = !(s > beta);
-        mask[(size_t)y * W + x] = fb ? 1 : 0;
+        for (int b = 0; b < 4; ++b) r = fmaf(wx[b], __ldg(Cc + (size_t)yy * Wc + min(max(bx - 1 + b, 0), Wc - 1)), r);
+        s = fmaf(wy[a], r, s);
     }
-    // one flag write per warp and tile: a warp's 32 columns of one row lie in one tile
-    // (tile_w is a multiple of 32 and blocks start on multiples of 32)
-    if (__any_sync(0xFFFFFFFFu, fb) && (threadIdx.x & 31) == 0 && y < H)
-        tile_flags[(y / tile_h) * tiles_x + (blockIdx.x * blockDim.x) / tile_w] = 1;
+    mask[(size_t)y * W + x] = !(s > beta) ? 1 : 0;
 }
 
 // Alpha refinement on a 16 x 8 tile.  E(q, z), the ZNCC of every pixel q of the tile's
@@ -254,12 +246,9 @@ selective_median_kernel(const int16_t *__restrict__ d_in, const float *__restric
 }  // namespace
 
 cudaError_t launch_beta_gate(const float *Cc, int Wc, int Hc, int W, int H, float beta, uint8_t *mask,
-                             int *tile_flags, int tile_w, int tile_h, cudaStream_t st) {
-    const int tiles_x = (W + tile_w - 1) / tile_w, tiles_y = (H + tile_h - 1) / tile_h;
-    cudaError_t e = cudaMemsetAsync(tile_flags, 0, sizeof(int) * tiles_x * tiles_y, st);
-    if (e != cudaSuccess) return e;
+                             cudaStream_t st) {
     dim3 blk(32, 8), grd((W + 31) / 32, (H + 7) / 8);
-    beta_gate_kernel<<<grd, blk, 0, st>>>(Cc, Wc, Hc, W, H, beta, mask, tile_flags, tile_w, tile_h, tiles_x);
+    beta_gate_kernel<<<grd, blk, 0, st>>>(Cc, Wc, Hc, W, H, beta, mask);
     return cudaGetLastError();
 }
 

@@ -134,7 +134,6 @@ void free_ctx(msbm_ctx *c) {
         cudaFree(l.c);
         cudaFree(l.dtmp);
         cudaFree(l.mask);
-        cudaFree(l.tile_flags);
         cudaFree(l.rstat);
     }
     cudaFree(c->c0);
@@ -199,12 +198,11 @@ cudaError_t launch_stats_levels(msbm_ctx *c, int n, cudaStream_t st) {
 
 // stats_ready: the level's right-window statistics plane is already computed in stream order.
 msbm_status enqueue_level(msbm_ctx *c, int k, const int16_t *prior, int16_t *d, float *cost,
-                          cudaStream_t st, const uint8_t *mask = nullptr, const int *tile_flags = nullptr,
-                          const uint8_t *skip = nullptr, bool stats_ready = false) {
+                          cudaStream_t st, const uint8_t *skip = nullptr, bool stats_ready = false) {
     const LevelBuf &l = c->lv[k];
     const int force = (c->p.flags & MSBM_FLAG_TEST_TIMEOUT) ? 1 : 0;
     cudaError_t e;
-    if (!prior && !mask && l.coarse) {
+    if (!prior && l.coarse) {
         e = launch_zncc_coarse(l, l.nh, d, cost, c->d_evals, st);
     } else if (!prior) {
         FullArgs a;
@@ -212,8 +210,6 @@ msbm_status enqueue_level(msbm_ctx *c, int k, const int16_t *prior, int16_t *d, 
         a.tmL = l.tmFL;
         a.tmR = l.tmR256;
         a.t.W = l.W; a.t.H = l.H; a.t.Dk = l.Dk; a.t.zblock = l.full_zblock;
-        a.t.mask = mask; a.t.tile_flags = tile_flags;
-        a.t.tiles_x = (l.W + 32 * l.full_sx - 1) / (32 * l.full_sx);
         a.t.d_out = d; a.t.c_out = cost;
         a.t.evals = c->d_evals; a.t.err = c->d_err; a.t.force_timeout = force;
         e = launch_zncc_full(a, l.nh, l.full_sx, st);
@@ -238,18 +234,18 @@ msbm_status enqueue_level(msbm_ctx *c, int k, const int16_t *prior, int16_t *d, 
 }
 
 // Eq. 8-9 with both branches at level k: gate from the coarser cost, restricted search for
-// every pixel (fallback pixels are not counted), then the full search over the flagged
-// tiles writing the fallback pixels.
+// every pixel (fallback pixels are not counted), then the full search of the fallback
+// pixels only (zncc_sparse.cu), overwriting them.
 msbm_status enqueue_level_beta(msbm_ctx *c, int k, const int16_t *prior, const float *cprior, int16_t *d,
                                float *cost, cudaStream_t st, bool stats_ready = false) {
     LevelBuf &l = c->lv[k];
     const LevelBuf &lp = c->lv[k + 1];
-    cudaError_t e = launch_beta_gate(cprior, lp.W, lp.H, l.W, l.H, c->p.beta, l.mask, l.tile_flags,
-                                     32 * l.full_sx, 8, st);
+    cudaError_t e = launch_beta_gate(cprior, lp.W, lp.H, l.W, l.H, c->p.beta, l.mask, st);
     if (e != cudaSuccess) return cuda_status(e);
-    msbm_status s = enqueue_level(c, k, prior, d, cost, st, nullptr, nullptr, l.mask, stats_ready);
+    msbm_status s = enqueue_level(c, k, prior, d, cost, st, l.mask, stats_ready);
     if (s != MSBM_OK) return s;
-    return enqueue_level(c, k, nullptr, d, cost, st, l.mask, l.tile_flags);
+    // the restricted search above left the level's statistics plane in stream order
+    return cuda_status(launch_zncc_sparse(l, l.nh, d, cost, c->d_evals, st));
 }
 
 // Level k of the pass with the gated steps the context's flags select: the full-range
@@ -276,7 +272,7 @@ msbm_status enqueue_match(msbm_ctx *c, int k, int16_t *d, float *cost, cudaStrea
     if (f & MSBM_FLAG_BETA_FALLBACK)
         s = enqueue_level_beta(c, k, prior, c->lv[k + 1].c, dm, ck, st, stats_ready);
     else
-        s = enqueue_level(c, k, prior, dm, ck, st, nullptr, nullptr, nullptr, stats_ready);
+        s = enqueue_level(c, k, prior, dm, ck, st, nullptr, stats_ready);
     if (s == MSBM_OK && med) s = cuda_status(launch_selective_median(dm, ck, l.W, l.H, c->p.alpha, dk, st));
     return s;
 }
@@ -370,12 +366,8 @@ msbm_status msbm_create(const msbm_params *params, void *cuda_stream, msbm_ctx *
         const bool finer = k < params->levels - 1;
         if (e == cudaSuccess && finer && (params->flags & MSBM_FLAG_SELECTIVE_MEDIAN))
             e = cudaMalloc(&l.dtmp, (size_t)W * H * sizeof(int16_t));
-        if (e == cudaSuccess && finer && (params->flags & MSBM_FLAG_BETA_FALLBACK)) {
-            const int sx = choose_sx(W, H, c->num_sms);
-            const long tiles = (long)((W + 32 * sx - 1) / (32 * sx)) * ((H + 7) / 8);
+        if (e == cudaSuccess && finer && (params->flags & MSBM_FLAG_BETA_FALLBACK))
             e = cudaMalloc(&l.mask, (size_t)W * H);
-            if (e == cudaSuccess) e = cudaMalloc(&l.tile_flags, sizeof(int) * tiles);
-        }
         l.full_sx = choose_sx(W, H, c->num_sms);
         l.coarse = zncc_coarse_fits(W, H, c->num_sms);
         if (e == cudaSuccess) {

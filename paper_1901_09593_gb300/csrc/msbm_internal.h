@@ -23,7 +23,6 @@ struct LevelBuf {
     float *c = nullptr;          // this level's cost map (levels >= 1)
     int16_t *dtmp = nullptr;     // pre-median disparity map (SELECTIVE_MEDIAN)
     uint8_t *mask = nullptr;     // fallback mask (BETA_FALLBACK)
-    int *tile_flags = nullptr;   // full-range tiles holding a fallback pixel (BETA_FALLBACK)
     int2 *rstat = nullptr;       // right-window statistics plane {S, bits(rsqrt(V)) or 0}: H rows
     int rspitch = 0;             // of rspitch entries (a multiple of 16), one per pixel
     // TMA maps over the apron buffers.  Full-range tile (8 + 2n rows high):
@@ -46,11 +45,6 @@ struct LevelBuf {
 struct FullTileArgs {
     int W, H, Dk;
     int zblock;          // candidates staged per pass (multiple of 32; 0 = the tile's maximum)
-    // gated pass (beta fallback): only tiles whose flag is set run, only masked pixels are
-    // written and counted; both NULL for the ordinary full-range search
-    const uint8_t *mask;
-    const int *tile_flags;
-    int tiles_x;
     int16_t *d_out;
     float *c_out;
     unsigned long long *evals;
@@ -66,7 +60,7 @@ struct FullArgs {
 
 // Per-tile arguments of the restricted ZNCC tile (zncc_restricted_tile.cuh).
 struct RestrTileArgs {
-    const uint8_t *skip; // NULL, or pixels a later gated pass overwrites (not counted here)
+    const uint8_t *skip; // NULL, or pixels the fallback search overwrites (not counted here)
     const uint8_t *Limg; // level image origins (apron buffers), for the wide-span path
     const uint8_t *Rimg;
     int pitch;
@@ -106,13 +100,16 @@ struct PyrFuseArgs {
 cudaError_t launch_pyr_fused(const PyrFuseArgs &a, cudaStream_t st);
 cudaError_t launch_level_extract(const LevelBuf &lv, int which, uint8_t *out, cudaStream_t st);
 cudaError_t launch_zncc_full(const FullArgs &a, int nh, int sx, cudaStream_t st);
+// Full-range search of the pixels in l.mask only (beta fallback); needs l.rstat computed.
+cudaError_t launch_zncc_sparse(const LevelBuf &l, int nh, int16_t *d, float *c, unsigned long long *evals,
+                               cudaStream_t st);
 // Small-level full-range search (one thread per pixel); fits: the full-range tiles of a
 // W x H level would not fill the GPU.
 bool zncc_coarse_fits(int W, int H, int sms);
 cudaError_t launch_zncc_coarse(const LevelBuf &l, int nh, int16_t *d, float *c, unsigned long long *evals,
                                cudaStream_t st);
 cudaError_t launch_beta_gate(const float *Cc, int Wc, int Hc, int W, int H, float beta, uint8_t *mask,
-                             int *tile_flags, int tile_w, int tile_h, cudaStream_t st);
+                             cudaStream_t st);
 cudaError_t launch_alpha_refine(const LevelBuf &l, int nh, float alpha, int16_t *d, float *C,
                                 unsigned long long *evals, cudaStream_t st);
 cudaError_t launch_selective_median(const int16_t *d_in, const float *C, int W, int H, float alpha, int16_t *d_out,

@@ -263,7 +263,6 @@ __device__ bool full_tile(const FullTileArgs &a, const CUtensorMap *tmL, const C
     const int Dk = a.Dk;
     const int ZBmax = (a.zblock > 0 && a.zblock <= C::ZB) ? (a.zblock & ~31) : C::ZB;
     const bool force_to = a.force_timeout != 0;
-    if (a.tile_flags && a.tile_flags[by * a.tiles_x + bx] == 0) return true;   // no fallback pixel here
 
     // ---- left tile: image columns [x0 - 16, x0 + TX + 16), rows [y0 - n, y0 + TY + n)
     if (tid == 0) {
@@ -325,7 +324,6 @@ __device__ bool full_tile(const FullTileArgs &a, const CUtensorMap *tmL, const C
         int ry = i / TX, px = i - ry * TX;
         int x = x0 + px, y = y0 + ry;
         if (x >= a.W || y >= a.H) continue;
-        if (a.mask && !a.mask[(size_t)y * a.W + x]) continue;
         unsigned long long k = best[i];
         int z = static_cast<int>(0xFFFFFFFFu - static_cast<uint32_t>(k & 0xFFFFFFFFull));
         float sc = float_from_order_key(static_cast<uint32_t>(k >> 32));

@@ -19,21 +19,21 @@ constexpr int ZC = 32;     // candidates per chunk
 
 // Rows y0 .. y0 + ROWS - 1 and columns x0 .. x0 + NCOLS - 1 of an image (clamp-to-edge) into
 // shared bytes with row stride STRIDE (zero from column NCOLS on).  Every thread's loads are
-// issued before its first store.  blockDim.x == 256.
-template <int ROWS, int NCOLS, int STRIDE>
+// issued before its first store.  blockDim.x == NT.
+template <int ROWS, int NCOLS, int STRIDE, int NT = 256>
 __device__ __forceinline__ void stage_rows(uint8_t *dst, const uint8_t *img, int pitch, int W, int H, int y0,
                                            int x0) {
-    constexpr int NB = ROWS * STRIDE, T = (NB + 255) / 256;
+    constexpr int NB = ROWS * STRIDE, T = (NB + NT - 1) / NT;
     uint8_t v[T];
 #pragma unroll
     for (int t = 0; t < T; ++t) {
-        const int i = threadIdx.x + 256 * t, r = i / STRIDE, c = i - r * STRIDE;
+        const int i = threadIdx.x + NT * t, r = i / STRIDE, c = i - r * STRIDE;
         const int yy = min(max(y0 + r, 0), H - 1), xx = min(max(x0 + c, 0), W - 1);
         v[t] = (i < NB && c < NCOLS) ? __ldg(img + (ptrdiff_t)yy * pitch + xx) : 0;
     }
 #pragma unroll
     for (int t = 0; t < T; ++t) {
-        const int i = threadIdx.x + 256 * t;
+        const int i = threadIdx.x + NT * t;
         if (i < NB) dst[i] = v[t];
     }
 }
