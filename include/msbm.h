@@ -146,8 +146,10 @@ msbm_status msbm_match_level_beta(msbm_ctx *ctx, int32_t level, const int16_t *d
 msbm_status msbm_disparity(msbm_ctx *ctx, const uint8_t *d_left, const uint8_t *d_right,
                            size_t pitch_bytes, int16_t *d_out, float *cost_out);
 
-/* Same pass on HOST buffers: copies the images in, runs, copies the maps out, and waits.
- * Pinned host memory gives asynchronous copies; pageable memory works but is slower. */
+/* Same pass on HOST buffers, waiting for the result.  When all given buffers are page-locked
+ * (cudaHostAlloc / cudaHostRegister, e.g. torch pin_memory) the kernels read the images and
+ * write the maps through their device-mapped addresses, so the transfers overlap the pass;
+ * otherwise the images are copied in and the maps copied out through staging buffers. */
 msbm_status msbm_disparity_host(msbm_ctx *ctx, const uint8_t *h_left, const uint8_t *h_right,
                                 size_t pitch_bytes, int16_t *h_d, float *h_cost);
 

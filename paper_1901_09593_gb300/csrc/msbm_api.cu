@@ -40,6 +40,11 @@ struct msbm_ctx {
     const void *gkey[4] = {nullptr, nullptr, nullptr, nullptr};
     size_t gpitch = 0;
     int graph_kernels = 0;       // kernel nodes of the captured pass graph
+    int *h_err = nullptr;        // page-locked copy of d_err read by msbm_sync
+    // msbm_disparity_host: the last host buffers seen and their device-mapped addresses
+    // (NULL: not page-locked)
+    const void *host_seen[4] = {nullptr, nullptr, nullptr, nullptr};
+    void *host_mapped[4] = {nullptr, nullptr, nullptr, nullptr};
     // level-0 cost when the caller passes none but a gated step needs one
     float *c0 = nullptr;
     // device staging of msbm_disparity_host
@@ -138,6 +143,7 @@ void free_ctx(msbm_ctx *c) {
     }
     cudaFree(c->c0);
     cudaFree(c->d_err);
+    cudaFreeHost(c->h_err);
     cudaFree(c->d_evals);
     cudaFree(c->hL);
     cudaFree(c->hR);
@@ -340,6 +346,7 @@ msbm_status msbm_create(const msbm_params *params, void *cuda_stream, msbm_ctx *
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost(&c->h_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_evals, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(c->d_evals, 0, sizeof(unsigned long long));
@@ -527,6 +534,34 @@ msbm_status msbm_disparity_host(msbm_ctx *ctx, const uint8_t *h_left, const uint
     if (!ctx || !h_left || !h_right || !h_d || pitch_bytes < (size_t)ctx->p.width)
         return MSBM_ERR_INVALID_ARG;
     const size_t W = ctx->p.width, H = ctx->p.height;
+    // page-locked host buffers are device-addressable: the pass reads the images and writes
+    // the maps across the host link itself (no staging copies, transfers overlap the kernels)
+    void *mapped[4] = {nullptr, nullptr, nullptr, nullptr};
+    const void *hp[4] = {h_left, h_right, h_d, h_cost};
+    bool zero_copy = true;
+    for (int i = 0; i < 4 && zero_copy; ++i) {
+        if (!hp[i]) continue;
+        if (hp[i] == ctx->host_seen[i] && ctx->host_mapped[i]) {    // same buffer as last call
+            mapped[i] = ctx->host_mapped[i];
+            continue;
+        }
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, hp[i]) != cudaSuccess || at.type != cudaMemoryTypeHost || !at.devicePointer) {
+            cudaGetLastError();
+            zero_copy = false;
+        } else {
+            mapped[i] = at.devicePointer;
+        }
+        ctx->host_seen[i] = hp[i];
+        ctx->host_mapped[i] = mapped[i];
+    }
+    if (zero_copy) {
+        msbm_status s = msbm_disparity(ctx, static_cast<const uint8_t *>(mapped[0]),
+                                       static_cast<const uint8_t *>(mapped[1]), pitch_bytes,
+                                       static_cast<int16_t *>(mapped[2]), static_cast<float *>(mapped[3]));
+        if (s != MSBM_OK) return s;
+        return msbm_sync(ctx);
+    }
     cudaError_t e = cudaSuccess;
     if (!ctx->hL) {
         e = cudaMalloc(&ctx->hL, W * H);
@@ -536,8 +571,14 @@ msbm_status msbm_disparity_host(msbm_ctx *ctx, const uint8_t *h_left, const uint
         if (e != cudaSuccess) return cuda_status(e);
     }
     cudaStream_t st = ctx->stream;
-    e = cudaMemcpy2DAsync(ctx->hL, W, h_left, pitch_bytes, W, H, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpy2DAsync(ctx->hR, W, h_right, pitch_bytes, W, H, cudaMemcpyHostToDevice, st);
+    if (pitch_bytes == W) {      // dense rows: one linear copy per image
+        e = cudaMemcpyAsync(ctx->hL, h_left, W * H, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->hR, h_right, W * H, cudaMemcpyHostToDevice, st);
+    } else {
+        e = cudaMemcpy2DAsync(ctx->hL, W, h_left, pitch_bytes, W, H, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(ctx->hR, W, h_right, pitch_bytes, W, H, cudaMemcpyHostToDevice, st);
+    }
     if (e != cudaSuccess) return cuda_status(e);
     msbm_status s = msbm_disparity(ctx, ctx->hL, ctx->hR, W, ctx->hd, h_cost ? ctx->hc : nullptr);
     if (s != MSBM_OK) return s;
@@ -596,11 +637,11 @@ msbm_status msbm_pass_kernel_count(const msbm_ctx *ctx, int32_t *count) {
 
 msbm_status msbm_sync(msbm_ctx *ctx) {
     if (!ctx) return MSBM_ERR_INVALID_ARG;
-    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    // the error word rides the stream to page-locked host memory: one wait, no extra round trip
+    cudaError_t e = cudaMemcpyAsync(ctx->h_err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return MSBM_ERR_CUDA;
-    int err = 0;
-    e = cudaMemcpy(&err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return MSBM_ERR_CUDA;
+    const int err = *ctx->h_err;
     if (err != 0) {
         cudaMemset(ctx->d_err, 0, sizeof(int));
         return static_cast<msbm_status>(err);

@@ -181,7 +181,8 @@ class Context:
 
     def disparity_host(self, left: np.ndarray, right: np.ndarray, d_out: np.ndarray | None = None,
                        cost_out: np.ndarray | None = None):
-        """Whole pass on host arrays (copies in, runs, copies out, waits)."""
+        """Whole pass on host arrays, waiting for the result (page-locked arrays are read and
+        written by the kernels directly; others go through staging copies)."""
         self._bind_stream()
         for a, nm in ((left, "left"), (right, "right")):
             if a.dtype != np.uint8 or a.shape != (self.height, self.width) or a.strides[1] != 1:
@@ -190,11 +191,14 @@ class Context:
             raise ValueError("left and right must share a row pitch")
         if d_out is None:
             d_out = np.empty((self.height, self.width), np.int16)
+        if d_out.dtype != np.int16 or d_out.shape != (self.height, self.width) or not d_out.flags.c_contiguous:
+            raise ValueError(f"d_out must be a dense int16 ({self.height}, {self.width}) array")
+        if cost_out is not None and (cost_out.dtype != np.float32 or cost_out.shape != (self.height, self.width)
+                                     or not cost_out.flags.c_contiguous):
+            raise ValueError(f"cost_out must be a dense float32 ({self.height}, {self.width}) array")
         _lib.check(self._lib.msbm_disparity_host(
-            self._ctx, left.ctypes.data_as(ctypes.c_void_p), right.ctypes.data_as(ctypes.c_void_p),
-            left.strides[0], d_out.ctypes.data_as(ctypes.c_void_p),
-            cost_out.ctypes.data_as(ctypes.c_void_p) if cost_out is not None else None),
-            "msbm_disparity_host")
+            self._ctx, left.ctypes.data, right.ctypes.data, left.strides[0], d_out.ctypes.data,
+            cost_out.ctypes.data if cost_out is not None else None), "msbm_disparity_host")
         return d_out, cost_out
 
     def profile_disparity(self, left, right, d_out, cost_out):

@@ -162,6 +162,18 @@ def test_end_to_end_small(name, seed):
     ctx.disparity_host(sc.left, sc.right, hd, hc)
     np.testing.assert_array_equal(hd, d)
     np.testing.assert_array_equal(hc, c)
+    # page-locked buffers: the kernels read and write host memory directly (twice: the
+    # second call reuses the cached mappings); a mix falls back to staging copies
+    import torch
+    pl, pr = torch.from_numpy(sc.left).pin_memory(), torch.from_numpy(sc.right).pin_memory()
+    pd, pc = torch.zeros(d.shape, dtype=torch.int16).pin_memory(), torch.zeros(c.shape).pin_memory()
+    for _ in range(2):
+        ctx.disparity_host(pl.numpy(), pr.numpy(), pd.numpy(), pc.numpy())
+        np.testing.assert_array_equal(pd.numpy(), d)
+        np.testing.assert_array_equal(pc.numpy(), c)
+    hd2 = np.zeros_like(d)
+    ctx.disparity_host(pl.numpy(), pr.numpy(), hd2, None)
+    np.testing.assert_array_equal(hd2, d)
 
 
 def test_k1_equals_full_level():
