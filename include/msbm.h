@@ -227,8 +227,8 @@ msbm_status msbm_batch_destroy(msbm_batch *b);
  *           (ac, bc centred on their window means, clamp-to-edge reads), for the admissible
  *           candidates 0 <= z <= min(ndisp - 1, x);
  *   p_z    = softmax_z(rho_z / temperature);   d_soft = sum_z z p_z.
- * The cost volume is never stored.  window: odd 3..9; ndisp 1..256 with batch * ndisp
- * <= 65535; temperature > 0;
+ * The cost volume is never stored.  window: odd 3..9; ndisp 1..256; batch 1..65535;
+ * temperature > 0;
  * eps >= 0 (1e-6 * window^2 is the default used by the Python binding).
  * Forward writes d_soft, and the softmax statistics m_out (max of rho_z * log2(e) / T) and
  * l_out (sum of 2^(rho_z log2(e)/T - m)) that the backward reuses. */
@@ -238,7 +238,7 @@ msbm_status msbm_zncc_softargmax_fwd(const float *d_left, const float *d_right, 
                                      float *l_out, void *cuda_stream);
 
 /* Bytes of device workspace msbm_zncc_softargmax_bwd needs (0 for invalid sizes): the
- * per-(pixel, z) coefficient volume, its box-filtered copy and six per-pixel arrays. */
+ * per-(pixel, z) coefficient volume and six per-pixel arrays. */
 size_t msbm_zncc_softargmax_workspace_bytes(int32_t batch, int32_t height, int32_t width,
                                             int32_t window, int32_t ndisp);
 

@@ -21,9 +21,10 @@
 // where A_z = box filter over the window of alpha(p, z) = g_rho / s, and per pixel / right
 // centre r:  beta(p) = sum_z g_rho rho / (Saa + eps),  zeta(p) = sum_z alpha mb(p - z),
 // delta(r) = sum_z g_rho rho / (Sbb + eps) and er(r) = sum_z alpha ma at p = r + z.
-// Positions outside the image are folded into the clamped edge pixel.  Four kernels:
-// coefficients (recomputes rho and the window statistics), the box filter of the alpha
-// volume, and the two gathers.  Everything is FP32.
+// Positions outside the image are folded into the clamped edge pixel.  Two kernels: the
+// coefficients (recomputes rho and the window statistics, writes the alpha volume) and the
+// gradients (box filter of alpha per tile and candidate, both gathers; the box-filtered
+// volume is never stored).  Everything is FP32.
 #include <math.h>
 
 #include "msbm.h"
@@ -213,7 +214,13 @@ __global__ void __launch_bounds__(256) sa_bwd_coef_kernel(const SaArgs a) {
     for (int i = tid; i < 2 * SA_TY * RSW; i += SA_TX * SA_TY) accD[i] = 0.f;
     sa_stage<NH>(a, a.L + b * plane, a.R + b * plane, x0, y0, Lt, Rt, st, RTP, RSW);
     const int tx = threadIdx.x, ty = threadIdx.y, x = x0 + tx, y = y0 + ty;
-    if (x < a.W && y < a.H) {
+    // a warp is one tile row; when all its in-image lanes walk the same candidates, lane l at
+    // z and lane l+1 at z+1 are the only writers of a right centre, so ordered plain updates
+    // (one __syncwarp per candidate) replace the shared atomics
+    const bool inside = x < a.W && y < a.H;
+    const unsigned am = __ballot_sync(0xFFFFFFFFu, inside);
+    const bool lockstep = __ballot_sync(0xFFFFFFFFu, inside && min(a.ndisp - 1, x) == a.ndisp - 1) == am;
+    if (inside) {
         const size_t p = b * plane + (size_t)y * a.W + x;
         const float g = a.g[p], d = a.dsoft[p], m2 = a.m2[p], invl = 1.f / a.l[p];
         float beta = 0.f, zeta = 0.f, ma = 0.f, rsa = 0.f;
@@ -227,8 +234,14 @@ __global__ void __launch_bounds__(256) sa_bwd_coef_kernel(const SaArgs a) {
             const float al = grho * rsa * rsb;
             beta = fmaf(grho * rho, rsa * rsa, beta);
             zeta = fmaf(al, mb, zeta);
-            atomicAdd(accDrow - z, grho * rho * rsb * rsb);
-            atomicAdd(accErow - z, al * ma);
+            if (lockstep) {
+                accDrow[-z] += grho * rho * rsb * rsb;
+                accErow[-z] += al * ma;
+                __syncwarp(am);
+            } else {
+                atomicAdd(accDrow - z, grho * rho * rsb * rsb);
+                atomicAdd(accErow - z, al * ma);
+            }
             alpha[(size_t)z * plane] = al;
             zmax = z;
         });
@@ -250,86 +263,154 @@ __global__ void __launch_bounds__(256) sa_bwd_coef_kernel(const SaArgs a) {
     }
 }
 
-// A_z over the clamp-extended domain: A[b][z][Y][X], Y in [0, H+2n), X in [0, W+2n), the
-// sum of alpha(b, z) over the (2n+1)^2 image pixels around (Y-n, X-n) (zero outside).
-template <int NH>
-__global__ void __launch_bounds__(256) sa_box_kernel(const SaArgs a, float *A) {
-    constexpr int WIN = 2 * NH + 1;
-    __shared__ float tile[SA_TY + 2 * NH][SA_TX + 2 * NH];
-    __shared__ float hs[SA_TY + 2 * NH][SA_TX];
-    const int bz = blockIdx.z;                       // b * ndisp + z
-    const int Wp = a.W + 2 * NH, Hp = a.H + 2 * NH;
-    const int X0 = blockIdx.x * SA_TX, Y0 = blockIdx.y * SA_TY;
-    const float *al = a.alpha + (size_t)bz * a.H * a.W;
-    const int tid = threadIdx.y * SA_TX + threadIdx.x;
-    for (int i = tid; i < (SA_TY + 2 * NH) * (SA_TX + 2 * NH); i += SA_TX * SA_TY) {
-        int t = i / (SA_TX + 2 * NH), u = i - t * (SA_TX + 2 * NH);
-        // tile (t, u) <-> image (Y0 - 2n + t, X0 - 2n + u)
-        int yy = Y0 - 2 * NH + t, xx = X0 - 2 * NH + u;
-        tile[t][u] = (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W) ? al[(size_t)yy * a.W + xx] : 0.f;
-    }
-    __syncthreads();
-    for (int i = tid; i < (SA_TY + 2 * NH) * SA_TX; i += SA_TX * SA_TY) {
-        int t = i / SA_TX, u = i - t * SA_TX;
-        float s = 0.f;
-#pragma unroll
-        for (int j = 0; j < WIN; ++j) s += tile[t][u + j];
-        hs[t][u] = s;
-    }
-    __syncthreads();
-    const int X = X0 + threadIdx.x, Y = Y0 + threadIdx.y;
-    if (X >= Wp || Y >= Hp) return;
-    float s = 0.f;
-#pragma unroll
-    for (int i = 0; i < WIN; ++i) s += hs[threadIdx.y + i][threadIdx.x];
-    A[(size_t)bz * Hp * Wp + (size_t)Y * Wp + X] = s;
-}
+// Both image gradients over the clamp-extended domain (Y in [0, H+2n), X in [0, W+2n); image
+// position q = (Y-n, X-n), folded into the clamped edge pixel by atomicAdd).  Per 32 x 32
+// tile (each thread a column of 4 positions) and candidate z the CTA box-filters alpha(b, z)
+// in shared memory:
+//   A_z(Y, X) = sum of alpha(b, z) over the (2n+1)^2 image pixels around (Y-n, X-n)
+// (zero outside the image; horizontal sums, then a vertical sliding sum), then
+//   gL(Y, X)     += R(q - z) A_z(Y, X)                      (z <= X; A_z is 0 beyond)
+//   gR(Y, X - z) += L(q)     A_z(Y, X)                      (X - z >= 0)
+// with R(q - z) read from the tile's right rows staged once, and gR accumulated in a shared
+// row buffer spanning the tile and the ndisp - 1 columns to its left, flushed once per tile.
+// The box terms of both gradients (zeta, beta, ma / er, delta, mb) are added for the tile's
+// own positions.  The A volume is never stored.
+constexpr int SG_TY = 32, SG_PER = SG_TY / 8;     // tile rows, rows per thread
 
-// Gathers over the clamp-extended domain, folded into the edge pixel by atomicAdd.
-template <int NH, bool LEFT>
-__global__ void __launch_bounds__(256) sa_grad_kernel(const SaArgs a, const float *A, float *gout) {
-    constexpr int WIN = 2 * NH + 1;
+template <int NH>
+struct SgCfg {
+    static constexpr int TR = SG_TY + 2 * NH, TC = SA_TX + 2 * NH;
+    static constexpr int TCP = TC + 1, HSP = SA_TX + 1;
+    static size_t bytes(int ndisp) {
+        const size_t aw = SA_TX + ndisp - 1;
+        return sizeof(float) * ((size_t)TR * TCP + (size_t)TR * HSP + 2 * (size_t)SG_TY * aw);
+    }
+};
+
+template <int NH>
+__global__ void __launch_bounds__(256) sa_grad_kernel(const SaArgs a, float *gL, float *gR) {
+    using C = SgCfg<NH>;
+    constexpr int WIN = 2 * NH + 1, TR = C::TR, TC = C::TC, TCP = C::TCP, HSP = C::HSP;
+    extern __shared__ float sm[];
+    float *tile = sm;                                 // [TR][TCP]
+    float *hs = tile + TR * TCP;                      // [TR][HSP]
+    const int AW = SA_TX + a.ndisp - 1;               // column c <-> extended X0 - (ndisp-1) + c
+    float *Rs = hs + TR * HSP;                        // [SG_TY][AW]: R at row q_y, column X - n - z
+    float *accR = Rs + SG_TY * AW;                    // [SG_TY][AW]
     const int b = blockIdx.z;
     const int Wp = a.W + 2 * NH, Hp = a.H + 2 * NH;
-    const int X = blockIdx.x * SA_TX + threadIdx.x, Y = blockIdx.y * SA_TY + threadIdx.y;
-    if (X >= Wp || Y >= Hp) return;
-    const int qy = Y - NH, qx = X - NH;                  // image coordinates (may lie outside)
+    const int X0 = blockIdx.x * SA_TX, Y0 = blockIdx.y * SG_TY;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * SA_TX + tx;
     const size_t plane = (size_t)a.H * a.W;
-    const int cy = clampi(qy, 0, a.H - 1);
     const float *Lb = a.L + b * plane, *Rb = a.R + b * plane;
-    const float *Ab = A + (size_t)b * a.ndisp * Hp * Wp + (size_t)Y * Wp;
-    float val = 0.f;
-    if (LEFT) {
-        const int zm = min(a.ndisp - 1, qx + NH);
-        for (int z = 0; z <= zm; ++z)
-            val = fmaf(Rb[(size_t)cy * a.W + clampi(qx - z, 0, a.W - 1)], Ab[(size_t)z * Hp * Wp + X], val);
-    } else {
-        for (int z = 0; z < a.ndisp; ++z) {
-            const int xx = X + z;                       // extended column of q' + z
-            if (xx >= Wp) break;
-            val = fmaf(Lb[(size_t)cy * a.W + clampi(qx + z, 0, a.W - 1)], Ab[(size_t)z * Hp * Wp + xx], val);
+    for (int r = ty; r < SG_TY; r += 8)
+        for (int c = tx; c < AW; c += SA_TX) {
+            const int cy = clampi(Y0 + r - NH, 0, a.H - 1);
+            const int xx = clampi(X0 - (a.ndisp - 1) + c - NH, 0, a.W - 1);
+            Rs[r * AW + c] = Rb[(size_t)cy * a.W + xx];
+            accR[r * AW + c] = 0.f;
+        }
+    const int X = X0 + tx, qx = X - NH;
+    const int r0 = SG_PER * ty;                       // this thread's first tile row
+    float Lq[SG_PER], gl[SG_PER];
+#pragma unroll
+    for (int k = 0; k < SG_PER; ++k) {
+        const int cy = clampi(Y0 + r0 + k - NH, 0, a.H - 1);
+        Lq[k] = Lb[(size_t)cy * a.W + clampi(qx, 0, a.W - 1)];
+        gl[k] = 0.f;
+    }
+    const bool colin = X < Wp;
+    // this thread's tile elements (t, u) = (ty + 8i, tx + 32j) <-> image (Y0 - 2n + t, X0 - 2n + u);
+    // the next candidate's are loaded into registers while the current one is processed
+    constexpr int NI = (TR + 7) / 8, NJ = (TC + SA_TX - 1) / SA_TX;
+    int off[NI][NJ];                                  // element offset in an alpha plane, or -1
+#pragma unroll
+    for (int i = 0; i < NI; ++i)
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+            const int t = ty + 8 * i, u = tx + SA_TX * j;
+            const int yy = Y0 - 2 * NH + t, xx = X0 - 2 * NH + u;
+            off[i][j] = (t < TR && u < TC && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W) ? yy * a.W + xx : -1;
+        }
+    float nxt[NI][NJ];
+    const float *al0 = a.alpha + (size_t)b * a.ndisp * plane;
+#pragma unroll
+    for (int i = 0; i < NI; ++i)
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) nxt[i][j] = off[i][j] >= 0 ? __ldg(al0 + off[i][j]) : 0.f;
+    for (int z = 0; z < a.ndisp; ++z) {
+        __syncthreads();   // the previous candidate's tile and sums are consumed
+#pragma unroll
+        for (int i = 0; i < NI; ++i)
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) {
+                const int t = ty + 8 * i, u = tx + SA_TX * j;
+                if (t < TR && u < TC) tile[t * TCP + u] = nxt[i][j];
+            }
+        if (z + 1 < a.ndisp) {
+            const float *al = al0 + (size_t)(z + 1) * plane;
+#pragma unroll
+            for (int i = 0; i < NI; ++i)
+#pragma unroll
+                for (int j = 0; j < NJ; ++j) nxt[i][j] = off[i][j] >= 0 ? __ldg(al + off[i][j]) : 0.f;
+        }
+        __syncthreads();
+        for (int t = ty; t < TR; t += 8) {
+            float s = 0.f;
+#pragma unroll
+            for (int j = 0; j < WIN; ++j) s += tile[t * TCP + tx + j];
+            hs[t * HSP + tx] = s;
+        }
+        __syncthreads();
+        if (colin && z <= X) {
+            float A = 0.f;
+#pragma unroll
+            for (int i = 0; i < WIN; ++i) A += hs[(r0 + i) * HSP + tx];
+            const int c = tx + a.ndisp - 1 - z;       // column of extended X - z
+#pragma unroll
+            for (int k = 0; k < SG_PER; ++k) {
+                if (k > 0) A += hs[(r0 + k + WIN - 1) * HSP + tx] - hs[(r0 + k - 1) * HSP + tx];
+                gl[k] = fmaf(Rs[(r0 + k) * AW + c], A, gl[k]);
+                accR[(r0 + k) * AW + c] += Lq[k] * A;
+            }
         }
     }
-    // box sums over the image pixels whose window covers q
-    const float *s1 = (LEFT ? a.zeta : a.er) + b * plane;
-    const float *s2 = (LEFT ? a.beta : a.delta) + b * plane;
-    const float *mm = (LEFT ? a.ma : a.mb) + b * plane;
-    float b1 = 0.f, b2 = 0.f, b3 = 0.f;
-    for (int i = -NH; i <= NH; ++i) {
-        const int yy = qy + i;
-        if (yy < 0 || yy >= a.H) continue;
-        for (int j = -NH; j <= NH; ++j) {
-            const int xx = qx + j;
-            if (xx < 0 || xx >= a.W) continue;
-            const size_t o = (size_t)yy * a.W + xx;
-            b1 += s1[o];
-            b2 += s2[o];
-            b3 = fmaf(s2[o], mm[o], b3);
+    __syncthreads();
+    const float *zeta = a.zeta + b * plane, *beta = a.beta + b * plane, *ma = a.ma + b * plane;
+    const float *er = a.er + b * plane, *delta = a.delta + b * plane, *mb = a.mb + b * plane;
+#pragma unroll
+    for (int k = 0; k < SG_PER; ++k) {
+        const int Y = Y0 + r0 + k, qy = Y - NH;
+        if (!colin || Y >= Hp) continue;
+        // box terms over the image pixels whose window covers q
+        float l1 = 0.f, l2 = 0.f, l3 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f;
+        for (int i = -NH; i <= NH; ++i) {
+            const int yy = qy + i;
+            if (yy < 0 || yy >= a.H) continue;
+            for (int j = -NH; j <= NH; ++j) {
+                const int xx = qx + j;
+                if (xx < 0 || xx >= a.W) continue;
+                const size_t o = (size_t)yy * a.W + xx;
+                l1 += zeta[o];
+                l2 += beta[o];
+                l3 = fmaf(beta[o], ma[o], l3);
+                q1 += er[o];
+                q2 += delta[o];
+                q3 = fmaf(delta[o], mb[o], q3);
+            }
         }
+        const size_t o = (size_t)clampi(qy, 0, a.H - 1) * a.W + clampi(qx, 0, a.W - 1);
+        atomicAdd(gL + b * plane + o, gl[k] + l3 - l1 - Lq[k] * l2);
+        accR[(r0 + k) * AW + tx + a.ndisp - 1] += q3 - q1 - Rb[o] * q2;
     }
-    const float own = (LEFT ? Lb : Rb)[(size_t)cy * a.W + clampi(qx, 0, a.W - 1)];
-    val += b3 - b1 - own * b2;
-    atomicAdd(gout + b * plane + (size_t)cy * a.W + clampi(qx, 0, a.W - 1), val);
+    __syncthreads();
+    float *gRb = gR + b * plane;
+    for (int i = tid; i < SG_TY * AW; i += SA_TX * 8) {
+        const int r = i / AW, c = i - r * AW;
+        const int Xe = X0 - (a.ndisp - 1) + c, Ye = Y0 + r;
+        if (Xe < 0 || Xe >= Wp || Ye >= Hp || accR[i] == 0.f) continue;
+        atomicAdd(gRb + (size_t)clampi(Ye - NH, 0, a.H - 1) * a.W + clampi(Xe - NH, 0, a.W - 1), accR[i]);
+    }
 }
 
 size_t sa_fwd_smem(int nh, int ndisp, bool bwd) {
@@ -341,7 +422,7 @@ size_t sa_fwd_smem(int nh, int ndisp, bool bwd) {
 }
 
 template <int NH>
-cudaError_t sa_run(const SaArgs &a, bool bwd, float *A, float *gL, float *gR, cudaStream_t st) {
+cudaError_t sa_run(const SaArgs &a, bool bwd, float *gL, float *gR, cudaStream_t st) {
     dim3 blk(SA_TX, SA_TY);
     dim3 grd((a.W + SA_TX - 1) / SA_TX, (a.H + SA_TY - 1) / SA_TY, a.B);
     size_t smem = sa_fwd_smem(NH, a.ndisp, bwd);
@@ -357,22 +438,20 @@ cudaError_t sa_run(const SaArgs &a, bool bwd, float *A, float *gL, float *gR, cu
     sa_bwd_coef_kernel<NH><<<grd, blk, smem, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int Wp = a.W + 2 * NH, Hp = a.H + 2 * NH;
-    dim3 gbox((Wp + SA_TX - 1) / SA_TX, (Hp + SA_TY - 1) / SA_TY, a.B * a.ndisp);
-    sa_box_kernel<NH><<<gbox, blk, 0, st>>>(a, A);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    dim3 gext((Wp + SA_TX - 1) / SA_TX, (Hp + SA_TY - 1) / SA_TY, a.B);
-    sa_grad_kernel<NH, true><<<gext, blk, 0, st>>>(a, A, gL);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    sa_grad_kernel<NH, false><<<gext, blk, 0, st>>>(a, A, gR);
+    dim3 gext((Wp + SA_TX - 1) / SA_TX, (Hp + SG_TY - 1) / SG_TY, a.B);
+    const size_t gsm = SgCfg<NH>::bytes(a.ndisp);
+    e = cudaFuncSetAttribute(sa_grad_kernel<NH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
+    if (e != cudaSuccess) return e;
+    sa_grad_kernel<NH><<<gext, blk, gsm, st>>>(a, gL, gR);
     return cudaGetLastError();
 }
 
-cudaError_t sa_dispatch(int nh, const SaArgs &a, bool bwd, float *A, float *gL, float *gR, cudaStream_t st) {
+cudaError_t sa_dispatch(int nh, const SaArgs &a, bool bwd, float *gL, float *gR, cudaStream_t st) {
     switch (nh) {
-        case 1: return sa_run<1>(a, bwd, A, gL, gR, st);
-        case 2: return sa_run<2>(a, bwd, A, gL, gR, st);
-        case 3: return sa_run<3>(a, bwd, A, gL, gR, st);
-        case 4: return sa_run<4>(a, bwd, A, gL, gR, st);
+        case 1: return sa_run<1>(a, bwd, gL, gR, st);
+        case 2: return sa_run<2>(a, bwd, gL, gR, st);
+        case 3: return sa_run<3>(a, bwd, gL, gR, st);
+        case 4: return sa_run<4>(a, bwd, gL, gR, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -383,23 +462,21 @@ msbm_status sa_validate(const float *L, const float *R, int B, int H, int W, int
     if (B < 1 || B > 65535 || H < 1 || H > 16384 || W < 1 || W > 16384) return MSBM_ERR_INVALID_ARG;
     if (window < 3 || window > 9 || (window & 1) == 0) return MSBM_ERR_INVALID_ARG;
     if (ndisp < 1 || ndisp > 256) return MSBM_ERR_INVALID_ARG;
-    if ((long)B * ndisp > 65535) return MSBM_ERR_INVALID_ARG;   // box-filter grid z extent
     if (!(T > 0.f) || !(eps >= 0.f) || !isfinite(T) || !isfinite(eps)) return MSBM_ERR_INVALID_ARG;
     return MSBM_OK;
 }
 
 struct SaWorkspace {
-    size_t alpha, A, arrays, total;
+    size_t alpha, arrays, total;
 };
 
 SaWorkspace sa_workspace(int B, int H, int W, int window, int ndisp) {
-    const int nh = window / 2;
+    (void)window;
     SaWorkspace w;
     auto al = [](size_t v) { return (v + 255) / 256 * 256; };
     w.alpha = al((size_t)B * ndisp * H * W * sizeof(float));
-    w.A = al((size_t)B * ndisp * (H + 2 * nh) * (W + 2 * nh) * sizeof(float));
     w.arrays = al((size_t)B * H * W * sizeof(float));
-    w.total = w.alpha + w.A + 6 * w.arrays;
+    w.total = w.alpha + 6 * w.arrays;
     return w;
 }
 
@@ -422,7 +499,7 @@ msbm_status msbm_zncc_softargmax_fwd(const float *d_left, const float *d_right, 
     a.B = batch; a.H = height; a.W = width; a.ndisp = ndisp;
     a.invT2 = LOG2E / temperature; a.invT = 1.f / temperature; a.eps = eps;
     a.dsoft = d_soft; a.m2 = m_out; a.l = l_out;
-    cudaError_t e = sa_dispatch(window / 2, a, false, nullptr, nullptr, nullptr, static_cast<cudaStream_t>(cuda_stream));
+    cudaError_t e = sa_dispatch(window / 2, a, false, nullptr, nullptr, static_cast<cudaStream_t>(cuda_stream));
     return e == cudaSuccess ? MSBM_OK : MSBM_ERR_CUDA;
 }
 
@@ -452,8 +529,7 @@ msbm_status msbm_zncc_softargmax_bwd(const float *d_left, const float *d_right, 
     a.dsoft = const_cast<float *>(d_soft); a.m2 = const_cast<float *>(m_in); a.l = const_cast<float *>(l_in);
     a.g = g_d;
     a.alpha = reinterpret_cast<float *>(ws);
-    float *A = reinterpret_cast<float *>(ws + w.alpha);
-    float *arr = reinterpret_cast<float *>(ws + w.alpha + w.A);
+    float *arr = reinterpret_cast<float *>(ws + w.alpha);
     const size_t na = w.arrays / sizeof(float);
     a.zeta = arr; a.beta = arr + na; a.ma = arr + 2 * na; a.mb = arr + 3 * na; a.delta = arr + 4 * na;
     a.er = arr + 5 * na;
@@ -461,7 +537,7 @@ msbm_status msbm_zncc_softargmax_bwd(const float *d_left, const float *d_right, 
     cudaError_t e = cudaMemsetAsync(a.delta, 0, 2 * w.arrays, st);   // delta and er accumulate
     if (e == cudaSuccess) e = cudaMemsetAsync(g_left, 0, plane_bytes, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(g_right, 0, plane_bytes, st);
-    if (e == cudaSuccess) e = sa_dispatch(window / 2, a, true, A, g_left, g_right, st);
+    if (e == cudaSuccess) e = sa_dispatch(window / 2, a, true, g_left, g_right, st);
     return e == cudaSuccess ? MSBM_OK : MSBM_ERR_CUDA;
 }
 
