@@ -30,13 +30,19 @@ constexpr int PF_TX = 16, PF_TY = 8;
 // bytes plus the widest horizontal-pass buffer (85 rows x 76 16-bit sums)
 constexpr int PF_SMEM = 30 * 1024;
 
-// (i, step) -> (row, column) walk of a rows x n grid without a division per step
+// (i, step) -> (row, column) walk of a rows x n grid without a division per step.  The two
+// quotients at construction use IEEE single-precision division, exact here: for
+// 0 <= a, b < 2^16 the correctly rounded a / b truncates to floor(a / b).
+__device__ __forceinline__ int small_div(int a, int b) {
+    return __float2int_rz(__fdiv_rn(static_cast<float>(a), static_cast<float>(b)));
+}
+
 struct GridWalk {
     int r, c, dr, dc, n;
     __device__ GridWalk(int i0, int step, int n_) : n(n_) {
-        r = i0 / n;
+        r = small_div(i0, n);
         c = i0 - r * n;
-        dr = step / n;
+        dr = small_div(step, n);
         dc = step - dr * n;
     }
     __device__ void next() {
@@ -116,30 +122,41 @@ __device__ void pyr_fused_tile(const PyrFuseArgs &a, const uint8_t *src, size_t 
         const int op = org[j - 1], sp = str[j - 1], Wp = a.W[j - 1], Hp = a.H[j - 1];
         const int nq = str[j] / 4;                        // column quads of level j
         const int fhi = min(op + sp, Wp) - 1;             // last column the fast path may read
-        // horizontal: ny[j-1] rows x nq quads -> 16-bit sums, 4 per thread
+        // horizontal: ny[j-1] rows x nq quads -> 16-bit sums, 4 per thread.  Whether a quad's
+        // 11 input bytes lie inside the staged row and the image depends on its column only:
+        // quads mlo .. mhi take the word path, the few others (region edges, image borders)
+        // the clamped byte path, in a loop of their own so that no warp runs both.
         {
-            const int n = ny[j - 1] * nq;
-            GridWalk g(tid, 256, nq);
-            for (int i = tid; i < n; i += 256, g.next()) {
-                const int x = org[j] + 4 * g.c;           // first output column
-                const uint8_t *row = Pp + g.r * sp;       // column X at row[X - op]
-                uint32_t o01, o23;
-                if (2 * x - 2 >= op && 2 * x + 8 <= fhi) {
-                    const int s0 = 2 * x - 2 - op;        // even
-                    const uint32_t *wr = reinterpret_cast<const uint32_t *>(row) + (s0 >> 2);
-                    const int sh = (s0 & 3) * 8;          // 0 or 16
+            const int mlo = max(0, (op + 2 - 2 * org[j] + 7) >> 3);          // 2x - 2 >= op
+            const int mhi = min(nq - 1, (fhi - 8 - 2 * org[j]) >> 3);         // 2x + 8 <= fhi
+            const int nf = max(0, mhi - mlo + 1);
+            uint2 *t2 = reinterpret_cast<uint2 *>(tmpb);
+            if (nf > 0) {
+                const int n = ny[j - 1] * nf;
+                GridWalk g(tid, 256, nf);
+                for (int i = tid; i < n; i += 256, g.next()) {
+                    const int m = mlo + g.c, x = org[j] + 4 * m;     // first output column
+                    const int s0 = 2 * x - 2 - op;                   // even
+                    const uint32_t *wr = reinterpret_cast<const uint32_t *>(Pp + g.r * sp) + (s0 >> 2);
+                    const int sh = (s0 & 3) * 8;                     // 0 or 16
                     const uint32_t r0 = wr[0], r1 = wr[1], r2 = wr[2];
                     const uint32_t r3 = sh ? wr[3] : 0u;
                     const uint32_t a0 = __funnelshift_r(r0, r1, sh), a1 = __funnelshift_r(r1, r2, sh),
                                    a2 = __funnelshift_r(r2, r3, sh);
-                    constexpr uint32_t K = 0x04060401u;   // weights 1, 4, 6, 4 of taps 0..3
+                    constexpr uint32_t K = 0x04060401u;              // weights 1, 4, 6, 4 of taps 0..3
                     const uint32_t v0 = dp4a_u8(a0, K, a1 & 0xFFu);
                     const uint32_t v1 = dp4a_u8(__funnelshift_r(a0, a1, 16), K, (a1 >> 16) & 0xFFu);
                     const uint32_t v2 = dp4a_u8(a1, K, a2 & 0xFFu);
                     const uint32_t v3 = dp4a_u8(__funnelshift_r(a1, a2, 16), K, (a2 >> 16) & 0xFFu);
-                    o01 = v0 | (v1 << 16);
-                    o23 = v2 | (v3 << 16);
-                } else {
+                    t2[g.r * nq + m] = make_uint2(v0 | (v1 << 16), v2 | (v3 << 16));
+                }
+            }
+            if (nf < nq) {
+                const int ns = nq - nf, n = ny[j - 1] * ns;
+                GridWalk g(tid, 256, ns);
+                for (int i = tid; i < n; i += 256, g.next()) {
+                    const int m = g.c < mlo ? g.c : g.c + nf, x = org[j] + 4 * m;
+                    const uint8_t *row = Pp + g.r * sp;              // column X at row[X - op]
                     uint32_t v[4];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
@@ -150,10 +167,8 @@ __device__ void pyr_fused_tile(const PyrFuseArgs &a, const uint8_t *src, size_t 
                                   c4 = min(x2 + 4, Wp - 1 - op);
                         v[q] = row[c0] + 4u * row[c1] + 6u * row[c2] + 4u * row[c3] + row[c4];
                     }
-                    o01 = v[0] | (v[1] << 16);
-                    o23 = v[2] | (v[3] << 16);
+                    t2[g.r * nq + m] = make_uint2(v[0] | (v[1] << 16), v[2] | (v[3] << 16));
                 }
-                reinterpret_cast<uint2 *>(tmpb)[g.r * nq + g.c] = make_uint2(o01, o23);
             }
         }
         __syncthreads();
