@@ -192,6 +192,16 @@ def measured_traffic(kernel):
     return rec["bytes"] if h.hexdigest()[:16] == rec["sha256_16"] else None
 
 
+def equal_or_better(methods, flat_fps, flat_bad1):
+    """The fastest measured hierarchical method whose bad-1 rate is at most flat matching's."""
+    ok = [(v["frames_per_s"], k, v) for k, v in methods.items() if v.get("bad1", 1.0) <= flat_bad1]
+    if not ok:
+        return None
+    f, k, v = max(ok)
+    return {"method": k, "frames_per_s": f, "bad1": v["bad1"], "flat_frames_per_s": flat_fps,
+            "flat_bad1": flat_bad1, "speedup": f / flat_fps}
+
+
 def full_evals(w, h, dk):
     return sum(min(dk - 1, x) + 1 for x in range(w)) * h
 
@@ -252,6 +262,44 @@ def run_reference(args):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def bench_large(args, dev, flush, stream):
+    """The large, hard pair (2880x1984, D = 640, K = 5, 9x9, r = 3, gain 1.2 / offset -10):
+    hierarchical (plain and with the selective median) and flat full-range matching."""
+    import numpy as np
+    import torch
+
+    from paper_1901_09593_gb300 import Context, _lib, scenes
+    spec = scenes.SPECS["large_2880x1984"]
+    sc = scenes.make_pair(spec, 0)
+    L = torch.from_numpy(sc.left).to(dev)
+    R = torch.from_numpy(sc.right).to(dev)
+    res = {"workload": "large_2880x1984: 2880x1984 uint8 pair, D=640, K=5, 9x9 window, r=3"}
+    for name, levels, flags in (("hierarchical", spec.levels, 0),
+                                ("selective_median", spec.levels, _lib.MSBM_FLAG_SELECTIVE_MEDIAN),
+                                ("flat", 1, 0)):
+        ctx = Context(spec.width, spec.height, spec.max_disp, levels, spec.window, spec.radius, flags)
+        d = torch.empty((spec.height, spec.width), dtype=torch.int16, device=dev)
+        c = torch.empty((spec.height, spec.width), dtype=torch.float32, device=dev)
+        for _ in range(3):
+            ctx.disparity(L, R, d, c)
+        ctx.sync()
+        steps = 5 if levels == 1 else max(5, min(args.steps, 30))
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for e0, e1 in ev:
+            flush.zero_()
+            e0.record(stream)
+            ctx.disparity(L, R, d, c)
+            e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = statistics.median(e0.elapsed_time(e1) for e0, e1 in ev)
+        dh = d.cpu().numpy()
+        res[name] = {"frames_per_s": 1e3 / ms, "ms_per_frame": ms,
+                     "bad1": scenes.bad_rate(dh, sc.gt, sc.mask, 1.0), "bad2": scenes.bad_rate(dh, sc.gt, sc.mask, 2.0)}
+        ctx.close()
+    res["hier_over_flat_speedup"] = res["hierarchical"]["frames_per_s"] / res["flat"]["frames_per_s"]
+    return res
 
 
 def bench_batch(args, dev, flush, stream):
@@ -518,8 +566,16 @@ def run_gpu(args):
         stages.append({"kernel": nm, "ms": round(t, 5), "share": None, "bound": bound,
                        "work": amount, "work_unit": unit})
     tot = sum(stage_ms)
+    hbm_peak = (peaks or {}).get("hbm_gbs") or 6800.0
+    alu_peak = alu_peak_tops(sms, sm_max)
     for s_ in stages:
         s_["share"] = round(s_["ms"] / tot, 4) if tot > 0 else None
+        # achieved fraction of the stage's roofline (algorithmic work / event-timed duration)
+        if s_["ms"] > 0:
+            if s_["bound"] == "hbm":
+                s_["roofline_frac"] = round(s_["work"] / (s_["ms"] * 1e-3) / 1e9 / hbm_peak, 4)
+            else:
+                s_["roofline_frac"] = round(s_["work"] / (s_["ms"] * 1e-3) / 1e12 / alu_peak, 4)
     dom = max(stages, key=lambda s_: s_["ms"])
     if dom["bound"] == "hbm":
         peak = (peaks or {}).get("hbm_gbs") or 6800.0
@@ -561,6 +617,7 @@ def run_gpu(args):
     if rank == 0 and not args.no_additions:
         additions["batching"] = bench_batch(args, dev, flush, stream)
         additions["differentiable"] = bench_diff(args, dev, flush, stream)
+        additions["large_pair"] = bench_large(args, dev, flush, stream)
 
     launches_per_step = ctx.pass_kernel_count()
     line = {
@@ -585,6 +642,8 @@ def run_gpu(args):
                  "gpix_disp_per_s": flat_evals * flat_fps / 1e9, "evals_per_frame": flat_evals,
                  "bad1": bad1_f, "bad2": bad2_f, "steps": fsteps},
         "hier_over_flat_speedup": fps / world / flat_fps,
+        # the hierarchical method at a bad-pixel rate equal to or better than flat matching's
+        "hier_vs_flat_equal_or_better_bad_rate": equal_or_better(methods, flat_fps, bad1_f),
         "methods": methods,
         "roofline": roof,
         "stages": stages,
