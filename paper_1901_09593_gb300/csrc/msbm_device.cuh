@@ -21,13 +21,6 @@ constexpr int DEV_ERR_TIMEOUT = 5;
 // Limit, in clock64 cycles, of a bounded mbarrier wait (about 1 s at 2 GHz).
 constexpr long long WAIT_LIMIT_CYCLES = 2000000000LL;
 
-struct LevelDev {
-    const uint8_t *L;  // apron buffer origin = image pixel (0, 0)
-    const uint8_t *R;
-    int pitch;         // bytes per buffer row
-    int W, H, Dk;
-};
-
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }

@@ -119,6 +119,5 @@ cudaError_t zncc_full_prepare(int nh, int sx);
 cudaError_t launch_right_stats(const LevelBuf *lv, int n, int nh, cudaStream_t st);
 cudaError_t zncc_restricted_prepare(int nh);
 cudaError_t launch_zncc_restricted(const RestrArgs &a, int nh, cudaStream_t st);
-size_t zncc_full_smem_bytes(int nh, int sx);
 
 }  // namespace msbm

@@ -56,15 +56,6 @@ cudaError_t full_dispatch(const FullArgs *a, int nh, int sx, cudaStream_t st) {
 
 }  // namespace
 
-size_t zncc_full_smem_bytes(int nh, int sx) {
-    (void)nh;
-    // upper bound over the instantiations (used for capacity checks)
-    switch (sx) {
-        case 1: return FullCfg<6, 1, 4>::BYTES;
-        case 2: return FullCfg<6, 2, 4>::BYTES;
-        default: return FullCfg<6, 4, 4>::BYTES;
-    }
-}
 
 cudaError_t launch_zncc_full(const FullArgs &a, int nh, int sx, cudaStream_t st) {
     return full_dispatch(&a, nh, sx, st);
