@@ -45,6 +45,8 @@ __global__ void __launch_bounds__(SP_THREADS) zncc_sparse_kernel(const uint8_t *
     __shared__ int2 sS[SP_S + SP_ZCH - 1];         // plane entries of the chunk's right windows
     __shared__ int list[SP_S];
     __shared__ unsigned long long best[SP_S];
+    __shared__ uint32_t sLw[SP_S][WIN][NW];        // each masked pixel's packed left window
+    __shared__ int2 sLa[SP_S];                     // and its {Sa, bits(rsqrt(Va)) or 0}
     __shared__ int nlist;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int x0 = blockIdx.x * SP_S, y = blockIdx.y;
@@ -67,6 +69,16 @@ __global__ void __launch_bounds__(SP_THREADS) zncc_sparse_kernel(const uint8_t *
     const int n = nlist;
     if (n == 0) return;
     region::stage_rows<WIN, SLW, SLW, SP_THREADS>(sL, L, pitch, W, H, y - NH, x0 - NH);
+    __syncthreads();
+    // one thread packs each masked pixel's left window once for all lanes and chunks
+    for (int e = tid; e < n; e += SP_THREADS) {
+        uint32_t Lw[WIN][NW];
+        sLa[e] = region::pack_left<NH, SLW>(sL, 0, list[e], Lw);
+#pragma unroll
+        for (int i = 0; i < WIN; ++i)
+#pragma unroll
+            for (int k = 0; k < NW; ++k) sLw[e][i][k] = Lw[i][k];
+    }
     // the segment's largest admissible candidate
     const int zmax_seg = min(Dk - 1, min(x0 + SP_S, W) - 1);
     for (int z0 = 0; z0 <= zmax_seg; z0 += SP_ZCH) {
@@ -104,20 +116,30 @@ __global__ void __launch_bounds__(SP_THREADS) zncc_sparse_kernel(const uint8_t *
                 const int zmax = min(Dk - 1, x);
                 if (z0 <= zmax) {
                     uint32_t Lw[WIN][NW];
-                    const int2 la = region::pack_left<NH, SLW>(sL, 0, px, Lw);
-                    // groups of 4 candidates z0 + 4g .. z0 + 4g + 3
+#pragma unroll
+                    for (int i = 0; i < WIN; ++i)
+#pragma unroll
+                        for (int kk = 0; kk < NW; ++kk) Lw[i][kk] = sLw[e][i][kk];
+                    const int2 la = sLa[e];
+                    // groups of 4 candidates z0 + 4g .. z0 + 4g + 3; the lane keeps its best
+                    // (score, z) with a strict compare in ascending z, so ties keep the smallest
+                    float bs = -INFINITY;
+                    int bz = -1;
                     for (int g = sl; 4 * g < SP_ZCH && z0 + 4 * g <= zmax; g += lpe) {
                         const int um = px + SP_ZCH - 4 - 4 * g;      // staged column of candidate z0 + 4g + 3
                         uint32_t sab[4];
                         region::sab4<NH, SRWW>(sR, 0, um, Lw, sab);
 #pragma unroll
-                        for (int o = 0; o < 4; ++o) {
+                        for (int o = 3; o >= 0; --o) {               // ascending z
                             const int z = z0 + 4 * g + 3 - o;
-                            if (z > zmax) continue;
-                            const unsigned long long kk = wta_key(region::rho_of<NH>(sab[o], la, sS[um + o]), z);
-                            k = kk > k ? kk : k;
+                            const float r = region::rho_of<NH>(sab[o], la, sS[um + o]);
+                            if (z <= zmax && r > bs) {
+                                bs = r;
+                                bz = z;
+                            }
                         }
                     }
+                    if (bz >= 0) k = wta_key(bs, bz);
                 }
             }
             for (int sh = lpe / 2; sh > 0; sh >>= 1) {
