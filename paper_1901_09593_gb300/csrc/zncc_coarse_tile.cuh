@@ -3,8 +3,8 @@
 // shared by the standalone launch (zncc_coarse.cu) and the batched persistent kernel
 // (batch.cu).  One thread owns one pixel of a 32 x 8 tile and walks the candidates 4 at a
 // time (zncc_region.cuh): the CTA stages the tile's left rows once and, per 32-candidate
-// chunk, the right rows and their window statistics.  WTA on the 64-bit (ordered rho, ~z)
-// key: exact ties keep the smallest z.
+// chunk, the right rows and their window statistics.  WTA in ascending z with a strict
+// compare: exact ties keep the smallest z.
 #pragma once
 
 #include <math.h>
@@ -56,7 +56,10 @@ __device__ void coarse_tile(const uint8_t *L, const uint8_t *R, int pitch, int W
     const int2 la = region::pack_left<NH, SLW>(sL, pr, pc, Lw);
     const int zmax = min(Dk - 1, x);
     const int zmax_tile = min(Dk - 1, min(x0 + CO_TX, W) - 1);
-    unsigned long long best = 0ull;
+    // the thread walks its candidates in ascending z and keeps the first maximum (strict
+    // compare): the best score with the smallest z among exact ties
+    float bs = -INFINITY;
+    int bz = 0;
     for (int z0 = 0; z0 <= zmax_tile; z0 += ZC) {
         __syncthreads();      // the previous chunk's rows and statistics are consumed
         region::stage_rows<SLH, SRW, SRWW * 4>(reinterpret_cast<uint8_t *>(sR), R, pitch, W, H, y0 - NH,
@@ -69,19 +72,21 @@ __device__ void coarse_tile(const uint8_t *L, const uint8_t *R, int pitch, int W
             uint32_t sab[4];
             region::sab4<NH, SRWW>(sR, pr, um, Lw, sab);
 #pragma unroll
-            for (int o = 0; o < 4; ++o) {
+            for (int o = 3; o >= 0; --o) {               // ascending z
                 const int z = z0 + 4 * g + 3 - o;
-                if (z > zmax) continue;
-                const unsigned long long k = wta_key(region::rho_of<NH>(sab[o], la, stR[pr * SU + um + o]), z);
-                best = k > best ? k : best;
+                const float r = region::rho_of<NH>(sab[o], la, stR[pr * SU + um + o]);
+                if (z <= zmax && r > bs) {
+                    bs = r;
+                    bz = z;
+                }
             }
         }
     }
     const bool in = x < W && y < H;
     if (in) {
         const size_t p = (size_t)y * W + x;
-        d_out[p] = static_cast<int16_t>(0xFFFFFFFFu - static_cast<uint32_t>(best & 0xFFFFFFFFull));
-        if (c_out) c_out[p] = fminf(1.f, fmaxf(-1.f, float_from_order_key(static_cast<uint32_t>(best >> 32))));
+        d_out[p] = static_cast<int16_t>(bz);
+        if (c_out) c_out[p] = fminf(1.f, fmaxf(-1.f, bs));
     }
     if (evals) {
         const unsigned cnt = __reduce_add_sync(0xFFFFFFFFu, in ? static_cast<unsigned>(zmax + 1) : 0u);
