@@ -2,7 +2,9 @@
 // the standalone launch (level_stats.cu) and the batched persistent kernel (batch.cu): for
 // every pixel (y, x), S = sum of the (2n+1)^2 window (clamp-to-edge) and rsqrt(N * sum I^2 -
 // S^2), or 0 for a flat window (Sec. III-A, Eq. 1-4 terms of the right window).  The image
-// rows are staged in shared memory (coordinates clamped to the image), vertical window sums
+// rows are staged in shared memory with word loads from the level's apron buffer (whose
+// replicated border makes the clamp-to-edge windows of every image pixel plain reads; words
+// past the apron feed only pixels outside the image and stay zero), vertical window sums
 // slide down 8-row groups of each column, horizontal sums slide along 8-column segments of
 // each row, and the tile leaves in coalesced stores.  All sums are exact integers.
 #pragma once
@@ -17,41 +19,48 @@ constexpr int ST_TX = 64, ST_TY = 32;
 
 template <int NH>
 struct StatsCfg {
-    static constexpr int SC = ST_TX + 2 * NH, SR = ST_TY + 2 * NH;   // staged columns, rows
+    static constexpr int SC = ST_TX + 2 * NH, SR = ST_TY + 2 * NH;   // window columns, staged rows
+    static constexpr int XO = 4 * ((NH + 3) / 4);                     // staged columns start XO early
+    static constexpr int SB = ST_TX + 2 * XO;                         // staged row bytes (word multiple)
     static constexpr int VP = SC + 1;                                 // packed-sum row stride (words)
-    static constexpr size_t OFF_VP = (SR * SC + 15) / 16 * 16;
+    static constexpr size_t OFF_VP = (SR * SB + 15) / 16 * 16;
     static constexpr size_t OFF_SO = OFF_VP + (size_t)ST_TY * VP * 4;
     static constexpr int SOP = ST_TX + 1;                            // output row stride (entries)
     static constexpr size_t BYTES = (OFF_SO + (size_t)ST_TY * SOP * 8 + 15) / 16 * 16;
 };
 
-// Tile (bx, by) of the plane out (opitch entries per row) of the W x H image R (pitch bytes).
-// sm: StatsCfg<NH>::BYTES bytes, 16-aligned.  blockDim.x == 256.
+// Tile (bx, by) of the plane out (opitch entries per row) of the W x H image R (pitch bytes):
+// R is the image origin of an apron buffer (APY rows and APX columns of replicated border,
+// 4-byte aligned rows).  sm: StatsCfg<NH>::BYTES bytes, 16-aligned.  blockDim.x == 256.
 template <int NH>
 __device__ void stats_tile(const uint8_t *__restrict__ R, int pitch, int W, int H, int2 *__restrict__ out,
                            int opitch, int bx, int by, uint8_t *sm) {
     constexpr int WIN = 2 * NH + 1, N = WIN * WIN;
     using C = StatsCfg<NH>;
-    constexpr int SC = C::SC, SR = C::SR, VP = C::VP;
-    uint8_t (*sb)[SC] = reinterpret_cast<uint8_t (*)[SC]>(sm);
+    constexpr int SC = C::SC, SR = C::SR, VP = C::VP, XO = C::XO, SB = C::SB;
+    static_assert(NH <= APY && XO <= APX, "windows inside the apron");
     uint32_t (*vp)[VP] = reinterpret_cast<uint32_t (*)[VP]>(sm + C::OFF_VP);   // q | s << 20 per column window
     int2 (*so)[C::SOP] = reinterpret_cast<int2 (*)[C::SOP]>(sm + C::OFF_SO);
     const int x0 = bx * ST_TX, y0 = by * ST_TY, tid = threadIdx.x;
     {
-        constexpr int T = (SR * SC + 255) / 256;
-        uint8_t v[T];
+        constexpr int NWR = SB / 4, NWT = SR * NWR, T = (NWT + 255) / 256;
+        uint32_t v[T];
 #pragma unroll
         for (int t = 0; t < T; ++t) {
-            const int i = tid + 256 * t, r = i / SC, c = i - r * SC;
-            const int yy = min(max(y0 - NH + r, 0), H - 1), xx = min(max(x0 - NH + c, 0), W - 1);
-            v[t] = i < SR * SC ? __ldg(R + (ptrdiff_t)yy * pitch + xx) : 0;
+            const int i = tid + 256 * t, r = i / NWR, w = i - r * NWR;
+            const int Y = y0 - NH + r, X = x0 - XO + 4 * w;
+            v[t] = (i < NWT && Y < H + APY && X + 3 < W + APX)
+                       ? __ldg(reinterpret_cast<const uint32_t *>(R + (ptrdiff_t)Y * pitch + X))
+                       : 0u;
         }
 #pragma unroll
         for (int t = 0; t < T; ++t) {
             const int i = tid + 256 * t;
-            if (i < SR * SC) sb[i / SC][i % SC] = v[t];
+            if (i < NWT) reinterpret_cast<uint32_t *>(sm)[i] = v[t];
         }
     }
+    // window column c of the old layout (image column x0 - NH + c) is staged byte c + XO - NH
+    const uint8_t *sb = sm + (XO - NH);
     __syncthreads();
     // vertical: column c, rows 8g .. 8g+7
     for (int i = tid; i < SC * (ST_TY / 8); i += 256) {
@@ -59,7 +68,7 @@ __device__ void stats_tile(const uint8_t *__restrict__ R, int pitch, int W, int 
         uint32_t s = 0, q = 0;
 #pragma unroll
         for (int t = 0; t < WIN; ++t) {
-            const uint32_t v = sb[8 * g + t][c];
+            const uint32_t v = sb[(8 * g + t) * SB + c];
             s += v;
             q += v * v;
         }
@@ -67,7 +76,7 @@ __device__ void stats_tile(const uint8_t *__restrict__ R, int pitch, int W, int 
         for (int r = 0; r < 8; ++r) {
             vp[8 * g + r][c] = q | (s << 20);      // s < 4096, q < 2^20 for windows up to 13 x 13
             if (r < 7) {
-                const uint32_t a = sb[8 * g + r + WIN][c], b = sb[8 * g + r][c];
+                const uint32_t a = sb[(8 * g + r + WIN) * SB + c], b = sb[(8 * g + r) * SB + c];
                 s += a - b;
                 q += a * a - b * b;
             }

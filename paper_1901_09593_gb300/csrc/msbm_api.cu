@@ -30,8 +30,10 @@ struct msbm_ctx {
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;
     // second stream of the pass: the statistics planes, beside the coarsest level's search
+    // and the coarser restricted levels; ev_stat[k]: level k's plane is written
     cudaStream_t side_stream = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_stat[12] = {};
     std::vector<LevelBuf> lv;
     int *d_err = nullptr;
     unsigned long long *d_evals = nullptr;
@@ -152,7 +154,8 @@ void free_ctx(msbm_ctx *c) {
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->side_stream) cudaStreamDestroy(c->side_stream);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
-    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    for (cudaEvent_t ev : c->ev_stat)
+        if (ev) cudaEventDestroy(ev);
     delete c;
 }
 
@@ -287,17 +290,20 @@ msbm_status enqueue_all(msbm_ctx *c, const uint8_t *L, const uint8_t *R, size_t 
                         float *cost, cudaStream_t st) {
     msbm_status s = enqueue_pyramid(c, L, R, pitch, st);
     const int K = c->p.levels;
-    // fork: the statistics planes of levels 0 .. K-2 on the side stream, beside the coarsest
-    // level's full-range search; join before the first restricted level
+    // fork: the statistics planes of levels K-2 .. 0, coarsest first, on the side stream,
+    // beside the coarsest level's full-range search and the coarser restricted levels; each
+    // restricted level joins on its own plane only
     if (s == MSBM_OK && K >= 2) {
         cudaError_t e = cudaEventRecord(c->ev_fork, st);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0);
-        if (e == cudaSuccess) e = launch_stats_levels(c, K - 1, c->side_stream);
-        if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->side_stream);
+        for (int k = K - 2; e == cudaSuccess && k >= 0; --k) {
+            e = launch_right_stats(&c->lv[k], 1, c->lv[k].nh, c->side_stream);
+            if (e == cudaSuccess) e = cudaEventRecord(c->ev_stat[k], c->side_stream);
+        }
         s = cuda_status(e);
     }
     for (int k = K - 1; s == MSBM_OK && k >= 0; --k) {
-        if (k == K - 2) s = cuda_status(cudaStreamWaitEvent(st, c->ev_join, 0));
+        if (k <= K - 2) s = cuda_status(cudaStreamWaitEvent(st, c->ev_stat[k], 0));
         if (s == MSBM_OK) s = enqueue_match(c, k, d, cost, st, true);
     }
     return s;
@@ -344,7 +350,8 @@ msbm_status msbm_create(const msbm_params *params, void *cuda_stream, msbm_ctx *
     cudaError_t e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+    for (int k = 0; e == cudaSuccess && k < params->levels; ++k)
+        e = cudaEventCreateWithFlags(&c->ev_stat[k], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMallocHost(&c->h_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_evals, sizeof(unsigned long long));

@@ -63,19 +63,25 @@ cudaError_t launch_apron_copy(const uint8_t *L, const uint8_t *R, size_t spitch,
 }
 
 // ---- fused pyramid: levels s+1 .. s+F (F <= PF_MAXF) in one launch (pyramid_fused.cuh) ----
+// The launch has one CTA per tile and image (a few hundred on the benchmark sizes), so each
+// CTA runs PF_NT threads to keep its serial chain of passes short (measured: 512 beats 256
+// and 1024 on the 1400 x 1000 and 2880 x 1984 pairs).
+constexpr int PF_NT = 512;
+
 template <int F>
-__global__ void __launch_bounds__(256) pyr_fused_kernel(const __grid_constant__ PyrFuseArgs a) {
+__global__ void __launch_bounds__(PF_NT) pyr_fused_kernel(const __grid_constant__ PyrFuseArgs a) {
     __shared__ __align__(16) uint8_t sm[PF_SMEM];
-    pyr_fused_tile<F>(a, a.src[blockIdx.z], a.spitch, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x, gridDim.y, sm);
+    pyr_fused_tile<F, PF_NT>(a, a.src[blockIdx.z], a.spitch, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x,
+                             gridDim.y, sm);
 }
 
 cudaError_t launch_pyr_fused(const PyrFuseArgs &a, cudaStream_t st) {
     if (a.F < 1 || a.F > PF_MAXF) return cudaErrorInvalidValue;
     dim3 grd((a.W[a.F] + PF_TX - 1) / PF_TX, (a.H[a.F] + PF_TY - 1) / PF_TY, 2);
     switch (a.F) {
-        case 1: pyr_fused_kernel<1><<<grd, 256, 0, st>>>(a); break;
-        case 2: pyr_fused_kernel<2><<<grd, 256, 0, st>>>(a); break;
-        default: pyr_fused_kernel<3><<<grd, 256, 0, st>>>(a); break;
+        case 1: pyr_fused_kernel<1><<<grd, PF_NT, 0, st>>>(a); break;
+        case 2: pyr_fused_kernel<2><<<grd, PF_NT, 0, st>>>(a); break;
+        default: pyr_fused_kernel<3><<<grd, PF_NT, 0, st>>>(a); break;
     }
     return cudaGetLastError();
 }

@@ -2,7 +2,8 @@
 // (Sec. III-A, Eq. 1-4; design in zncc_coarse_tile.cuh), normally at the coarsest pyramid
 // level.  The full-range tile kernel (zncc_full.cu) is built for throughput on large searches;
 // on a level of a few ten thousand pixels its 32 x 8 tiles leave most SMs idle and each CTA
-// runs a long serial chain, while here one thread owns one pixel.
+// runs a long serial chain, while here 32 x 2 pixel tiles with four threads per pixel (each
+// taking every fourth group of 4 candidates) spread the level over many short CTAs.
 #include <math.h>
 
 #include "msbm_device.cuh"
@@ -13,17 +14,19 @@ namespace msbm {
 
 namespace {
 
+constexpr int SA_TY = 2;    // tile rows; 8 / SA_TY threads per pixel (measured: 2 beats 4 and 8)
+
 template <int NH>
 __global__ void __launch_bounds__(256) zncc_coarse_kernel(const uint8_t *L, const uint8_t *R, int pitch, int W,
                                                           int H, int Dk, int16_t *d_out, float *c_out,
                                                           unsigned long long *evals) {
-    __shared__ __align__(16) uint8_t sm[CoarseCfg<NH>::BYTES];
-    coarse_tile<NH>(L, R, pitch, W, H, Dk, d_out, c_out, evals, blockIdx.x, blockIdx.y, sm);
+    __shared__ __align__(16) uint8_t sm[CoarseCfg<NH, SA_TY>::BYTES];
+    coarse_tile<NH, SA_TY>(L, R, pitch, W, H, Dk, d_out, c_out, evals, blockIdx.x, blockIdx.y, sm);
 }
 
 template <int NH>
 cudaError_t coarse_launch(const LevelBuf &l, int16_t *d, float *c, unsigned long long *evals, cudaStream_t st) {
-    dim3 grd((l.W + CO_TX - 1) / CO_TX, (l.H + CO_TY - 1) / CO_TY);
+    dim3 grd((l.W + CO_TX - 1) / CO_TX, (l.H + SA_TY - 1) / SA_TY);
     zncc_coarse_kernel<NH><<<grd, 256, 0, st>>>(l.img(0), l.img(1), l.pitch, l.W, l.H, l.Dk, d, c, evals);
     return cudaGetLastError();
 }
