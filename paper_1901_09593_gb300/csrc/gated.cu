@@ -191,56 +191,100 @@ constexpr int MED_SW = MED_TX + 2 * MED_R, MED_SH = MED_TY + 2 * MED_R;
 constexpr int MED_NONE = 0x7FFF;     // a neighbour that does not vote (outside, or cost <= alpha)
 
 // Eq. 10 on a 32 x 8 tile: the 5 x 5 neighbourhood (inside the image) is staged in shared
-// memory as voting disparities (cost > alpha) or MED_NONE; a pixel with cost <= alpha sorts
-// its 24 neighbours (it does not vote itself) with a merge-exchange network, so the voters
-// come first in ascending order, and takes the lower median of the voters.
+// memory as voting disparities (cost > alpha) or MED_NONE (costs and disparities are loaded
+// together, one round trip).  The tile's pixels with cost <=
+// alpha and at least one voter are compacted into a list (warp ballots, one prefix over the
+// warps), so the sorting work goes to as few warps as there are such pixels / 32 instead of
+// to every warp that holds one: each listed pixel's thread sorts its 24 neighbours (the pixel
+// does not vote itself) with a merge-exchange network, so the voters come first in ascending
+// order, and takes the lower median of the voters.  Every other pixel keeps its disparity.
 __global__ void __launch_bounds__(MED_TX * MED_TY)
 selective_median_kernel(const int16_t *__restrict__ d_in, const float *__restrict__ C, int W, int H, float alpha,
                         int16_t *d_out) {
+    constexpr int NT = MED_TX * MED_TY, NWARP = NT / 32;
+    constexpr int NB = (2 * MED_R + 1) * (2 * MED_R + 1) - 1;
     __shared__ int16_t sv[MED_SH][MED_SW];
+    __shared__ uint8_t job[NT];                 // tile pixels to sort, compacted
+    __shared__ int wcount[NWARP];
     const int x0 = blockIdx.x * MED_TX, y0 = blockIdx.y * MED_TY;
-    const int tid = threadIdx.y * MED_TX + threadIdx.x;
-    for (int i = tid; i < MED_SH * MED_SW; i += MED_TX * MED_TY) {
-        const int yy = y0 - MED_R + i / MED_SW, xx = x0 - MED_R + i % MED_SW;
-        int v = MED_NONE;
-        if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
-            const size_t p = (size_t)yy * W + xx;
-            if (__ldg(C + p) > alpha) v = __ldg(d_in + p);
+    const int tid = threadIdx.y * MED_TX + threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    {
+        // cost and disparity of every staged position are requested together (one round trip)
+        constexpr int NS = MED_SH * MED_SW, T = (NS + NT - 1) / NT;
+        float cv[T];
+        int dv[T];
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const int i = tid + NT * t, yy = y0 - MED_R + i / MED_SW, xx = x0 - MED_R + i % MED_SW;
+            cv[t] = 0.f;
+            dv[t] = MED_NONE;
+            if (i < NS && yy >= 0 && yy < H && xx >= 0 && xx < W) {
+                const size_t p = (size_t)yy * W + xx;
+                cv[t] = __ldg(C + p);
+                dv[t] = __ldg(d_in + p);
+            }
         }
-        sv[i / MED_SW][i % MED_SW] = static_cast<int16_t>(v);
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const int i = tid + NT * t;
+            if (i < NS) sv[i / MED_SW][i % MED_SW] = static_cast<int16_t>(cv[t] > alpha ? dv[t] : MED_NONE);
+        }
     }
     __syncthreads();
+    // a voting pixel (cost > alpha) keeps its disparity, read back from the staged tile; a
+    // pixel with cost <= alpha takes the median when some neighbour votes, else keeps its own
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
-    if (x >= W || y >= H) return;
-    const size_t o = (size_t)y * W + x;
-    int out = d_in[o];
-    if (!(C[o] > alpha)) {
-        constexpr int NB = (2 * MED_R + 1) * (2 * MED_R + 1) - 1;
-        int v[NB], cnt = 0;
+    const bool in = x < W && y < H;
+    const int centre = sv[threadIdx.y + MED_R][threadIdx.x + MED_R];
+    bool need = false;
+    if (in && centre == MED_NONE) {
 #pragma unroll
-        for (int m = 0, k = 0; m <= 2 * MED_R; ++m)
+        for (int m = 0; m <= 2 * MED_R; ++m)
 #pragma unroll
-            for (int q = 0; q <= 2 * MED_R; ++q) {
-                if (m == MED_R && q == MED_R) continue;
-                v[k] = sv[threadIdx.y + m][threadIdx.x + q];
-                cnt += v[k] != MED_NONE;
-                ++k;
-            }
-        if (cnt > 0) {
-            constexpr MergeExchange<NB> net;
-#pragma unroll
-            for (int c = 0; c < net.M; ++c) {
-                const int lo = min(v[net.a[c]], v[net.b[c]]), hi = max(v[net.a[c]], v[net.b[c]]);
-                v[net.a[c]] = lo;
-                v[net.b[c]] = hi;
-            }
-            const int want = (cnt - 1) / 2;       // at most NB / 2 - 1
-#pragma unroll
-            for (int i = 0; i < NB / 2; ++i)
-                if (i == want) out = v[i];
-        }
+            for (int q = 0; q <= 2 * MED_R; ++q)
+                if (!(m == MED_R && q == MED_R)) need |= sv[threadIdx.y + m][threadIdx.x + q] != MED_NONE;
     }
-    d_out[o] = static_cast<int16_t>(out);
+    if (in && !need) {
+        const size_t o = (size_t)y * W + x;
+        d_out[o] = centre != MED_NONE ? static_cast<int16_t>(centre) : d_in[o];
+    }
+    const unsigned bal = __ballot_sync(0xFFFFFFFFu, need);
+    if (lane == 0) wcount[warp] = __popc(bal);
+    __syncthreads();
+    int base = 0, njob = 0;
+#pragma unroll
+    for (int w = 0; w < NWARP; ++w) {
+        const int c = wcount[w];
+        base += w < warp ? c : 0;
+        njob += c;
+    }
+    if (need) job[base + __popc(bal & ((1u << lane) - 1u))] = static_cast<uint8_t>(tid);
+    __syncthreads();
+    if (tid >= njob) return;
+    const int t = job[tid], tx = t % MED_TX, ty = t / MED_TX;
+    int v[NB], cnt = 0;
+#pragma unroll
+    for (int m = 0, k = 0; m <= 2 * MED_R; ++m)
+#pragma unroll
+        for (int q = 0; q <= 2 * MED_R; ++q) {
+            if (m == MED_R && q == MED_R) continue;
+            v[k] = sv[ty + m][tx + q];
+            cnt += v[k] != MED_NONE;
+            ++k;
+        }
+    constexpr MergeExchange<NB> net;
+#pragma unroll
+    for (int c = 0; c < net.M; ++c) {
+        const int lo = min(v[net.a[c]], v[net.b[c]]), hi = max(v[net.a[c]], v[net.b[c]]);
+        v[net.a[c]] = lo;
+        v[net.b[c]] = hi;
+    }
+    const int want = (cnt - 1) / 2;       // at most NB / 2 - 1
+    int out = v[0];
+#pragma unroll
+    for (int i = 1; i < NB / 2; ++i)
+        if (i == want) out = v[i];
+    d_out[(size_t)(y0 + ty) * W + x0 + tx] = static_cast<int16_t>(out);
 }
 
 }  // namespace

@@ -55,7 +55,9 @@ __device__ void coarse_tile(const uint8_t *L, const uint8_t *R, int pitch, int W
     const int x0 = bx * CO_TX, y0 = by * TY;
     const int x = x0 + pc, y = y0 + pr;
     if (tid == 0) evsum = 0ull;
-    region::stage_rows<SLH, SLW, SLW>(sL, L, pitch, W, H, y0 - NH, x0 - NH);
+    // the left rows and the first chunk's right rows in one round trip
+    region::stage_rows2<SLH, SLW, SLW, SLH, SRW, SRWW * 4>(sL, L, y0 - NH, x0 - NH, reinterpret_cast<uint8_t *>(sR),
+                                                           R, y0 - NH, x0 - (ZC - 1) - NH, pitch, W, H);
     __syncthreads();
     uint32_t Lw[WIN][NW];
     const int2 la = region::pack_left<NH, SLW>(sL, pr, pc, Lw);
@@ -66,10 +68,12 @@ __device__ void coarse_tile(const uint8_t *L, const uint8_t *R, int pitch, int W
     float bs = -INFINITY;
     int bz = 0;
     for (int z0 = 0; z0 <= zmax_tile; z0 += ZC) {
-        __syncthreads();      // the previous chunk's rows and statistics are consumed
-        region::stage_rows<SLH, SRW, SRWW * 4>(reinterpret_cast<uint8_t *>(sR), R, pitch, W, H, y0 - NH,
-                                                x0 - (z0 + ZC - 1) - NH);
-        __syncthreads();
+        if (z0 > 0) {
+            __syncthreads();      // the previous chunk's rows and statistics are consumed
+            region::stage_rows<SLH, SRW, SRWW * 4>(reinterpret_cast<uint8_t *>(sR), R, pitch, W, H, y0 - NH,
+                                                    x0 - (z0 + ZC - 1) - NH);
+            __syncthreads();
+        }
         region::window_stats<NH, TY, SU, SRWW * 4>(reinterpret_cast<const uint8_t *>(sR), vs, vq, stR);
 #pragma unroll 1
         for (int g = zs; g < ZC / 4 && z0 + 4 * g <= zmax; g += ZS) {

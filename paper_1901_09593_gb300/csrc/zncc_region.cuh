@@ -38,6 +38,38 @@ __device__ __forceinline__ void stage_rows(uint8_t *dst, const uint8_t *img, int
     }
 }
 
+// Two stage_rows calls in one round trip: every load of both regions is issued before the
+// first store.  blockDim.x == NT.
+template <int ROWS_A, int NCOLS_A, int STRIDE_A, int ROWS_B, int NCOLS_B, int STRIDE_B, int NT = 256>
+__device__ __forceinline__ void stage_rows2(uint8_t *dstA, const uint8_t *imgA, int yA, int xA, uint8_t *dstB,
+                                            const uint8_t *imgB, int yB, int xB, int pitch, int W, int H) {
+    constexpr int NA = ROWS_A * STRIDE_A, TA = (NA + NT - 1) / NT;
+    constexpr int NB = ROWS_B * STRIDE_B, TB = (NB + NT - 1) / NT;
+    uint8_t va[TA], vb[TB];
+#pragma unroll
+    for (int t = 0; t < TA; ++t) {
+        const int i = threadIdx.x + NT * t, r = i / STRIDE_A, c = i - r * STRIDE_A;
+        const int yy = min(max(yA + r, 0), H - 1), xx = min(max(xA + c, 0), W - 1);
+        va[t] = (i < NA && c < NCOLS_A) ? __ldg(imgA + (ptrdiff_t)yy * pitch + xx) : 0;
+    }
+#pragma unroll
+    for (int t = 0; t < TB; ++t) {
+        const int i = threadIdx.x + NT * t, r = i / STRIDE_B, c = i - r * STRIDE_B;
+        const int yy = min(max(yB + r, 0), H - 1), xx = min(max(xB + c, 0), W - 1);
+        vb[t] = (i < NB && c < NCOLS_B) ? __ldg(imgB + (ptrdiff_t)yy * pitch + xx) : 0;
+    }
+#pragma unroll
+    for (int t = 0; t < TA; ++t) {
+        const int i = threadIdx.x + NT * t;
+        if (i < NA) dstA[i] = va[t];
+    }
+#pragma unroll
+    for (int t = 0; t < TB; ++t) {
+        const int i = threadIdx.x + NT * t;
+        if (i < NB) dstB[i] = vb[t];
+    }
+}
+
 // Window statistics of staged rows s (row stride STRIDE bytes): for r < OR, u < OU,
 // st[r * OU + u] = {S, bits(rsqrt(N Q - S^2)) or 0} of rows r .. r+2n, columns u .. u+2n.
 // vs, vq: OR x (OU + 2n) scratch.  Ends with a barrier.
