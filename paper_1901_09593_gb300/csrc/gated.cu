@@ -186,30 +186,33 @@ struct MergeExchange {
     }
 };
 
-constexpr int MED_TX = 32, MED_TY = 8, MED_R = 2;
+constexpr int MED_TX = 32, MED_TY = 32, MED_R = 2;   // tile; 256 threads of 4 pixels each
+constexpr int MED_RPT = 4;                             // rows per thread (stride MED_TY / MED_RPT)
 constexpr int MED_SW = MED_TX + 2 * MED_R, MED_SH = MED_TY + 2 * MED_R;
 constexpr int MED_NONE = 0x7FFF;     // a neighbour that does not vote (outside, or cost <= alpha)
 
-// Eq. 10 on a 32 x 8 tile: the 5 x 5 neighbourhood (inside the image) is staged in shared
-// memory as voting disparities (cost > alpha) or MED_NONE (costs and disparities are loaded
-// together, one round trip).  The tile's pixels with cost <=
-// alpha and at least one voter are compacted into a list (warp ballots, one prefix over the
-// warps), so the sorting work goes to as few warps as there are such pixels / 32 instead of
-// to every warp that holds one: each listed pixel's thread sorts its 24 neighbours (the pixel
-// does not vote itself) with a merge-exchange network, so the voters come first in ascending
-// order, and takes the lower median of the voters.  Every other pixel keeps its disparity.
-__global__ void __launch_bounds__(MED_TX * MED_TY)
+// Eq. 10 on a 32 x 32 tile (256 threads, 4 pixels each, so one wave of CTAs covers a level
+// of the benchmark sizes): the 5 x 5 neighbourhood (inside the image) is staged in shared
+// memory as voting disparities (cost > alpha) or MED_NONE, costs and disparities loaded
+// together (one round trip).  A voting pixel keeps its disparity; the tile's pixels with cost
+// <= alpha and at least one voter are collected in a list (warp-aggregated shared atomics),
+// and the CTA's threads sort them: each job sorts the pixel's 24 neighbours (the pixel does
+// not vote itself) with a merge-exchange network, so the voters come first in ascending
+// order, and takes the lower median of the voters.  A pixel with cost <= alpha and no voter
+// keeps its disparity.
+__global__ void __launch_bounds__(256)
 selective_median_kernel(const int16_t *__restrict__ d_in, const float *__restrict__ C, int W, int H, float alpha,
                         int16_t *d_out) {
-    constexpr int NT = MED_TX * MED_TY, NWARP = NT / 32;
-    constexpr int NB = (2 * MED_R + 1) * (2 * MED_R + 1) - 1;
+    constexpr int NT = 256, NB = (2 * MED_R + 1) * (2 * MED_R + 1) - 1, RS = MED_TY / MED_RPT;
+    static_assert(MED_TX * RS == NT && MED_SW <= 64, "median tile");
     __shared__ int16_t sv[MED_SH][MED_SW];
-    __shared__ uint8_t job[NT];                 // tile pixels to sort, compacted
-    __shared__ int wcount[NWARP];
+    __shared__ uint16_t job[MED_TX * MED_TY];   // tile pixels to sort
+    __shared__ unsigned long long vmask[MED_SH];
+    __shared__ int njob_s;
     const int x0 = blockIdx.x * MED_TX, y0 = blockIdx.y * MED_TY;
-    const int tid = threadIdx.y * MED_TX + threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, tx = tid % MED_TX, ty = tid / MED_TX;
+    if (tid == 0) njob_s = 0;
     {
-        // cost and disparity of every staged position are requested together (one round trip)
         constexpr int NS = MED_SH * MED_SW, T = (NS + NT - 1) / NT;
         float cv[T];
         int dv[T];
@@ -231,60 +234,66 @@ selective_median_kernel(const int16_t *__restrict__ d_in, const float *__restric
         }
     }
     __syncthreads();
-    // a voting pixel (cost > alpha) keeps its disparity, read back from the staged tile; a
-    // pixel with cost <= alpha takes the median when some neighbour votes, else keeps its own
-    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
-    const bool in = x < W && y < H;
-    const int centre = sv[threadIdx.y + MED_R][threadIdx.x + MED_R];
-    bool need = false;
-    if (in && centre == MED_NONE) {
-#pragma unroll
-        for (int m = 0; m <= 2 * MED_R; ++m)
-#pragma unroll
-            for (int q = 0; q <= 2 * MED_R; ++q)
-                if (!(m == MED_R && q == MED_R)) need |= sv[threadIdx.y + m][threadIdx.x + q] != MED_NONE;
+    // voter bitmask of every staged row (bit c: column c votes), one ballot pair per row
+    for (int r = tid >> 5; r < MED_SH; r += NT / 32) {
+        const unsigned lo = __ballot_sync(0xFFFFFFFFu, sv[r][lane] != MED_NONE);
+        const unsigned hi = __ballot_sync(0xFFFFFFFFu, lane + 32 < MED_SW && sv[r][min(lane + 32, MED_SW - 1)] != MED_NONE);
+        if (lane == 0) vmask[r] = static_cast<unsigned long long>(lo) | (static_cast<unsigned long long>(hi) << 32);
     }
-    if (in && !need) {
-        const size_t o = (size_t)y * W + x;
-        d_out[o] = centre != MED_NONE ? static_cast<int16_t>(centre) : d_in[o];
-    }
-    const unsigned bal = __ballot_sync(0xFFFFFFFFu, need);
-    if (lane == 0) wcount[warp] = __popc(bal);
     __syncthreads();
-    int base = 0, njob = 0;
+    const int x = x0 + tx;
 #pragma unroll
-    for (int w = 0; w < NWARP; ++w) {
-        const int c = wcount[w];
-        base += w < warp ? c : 0;
-        njob += c;
-    }
-    if (need) job[base + __popc(bal & ((1u << lane) - 1u))] = static_cast<uint8_t>(tid);
-    __syncthreads();
-    if (tid >= njob) return;
-    const int t = job[tid], tx = t % MED_TX, ty = t / MED_TX;
-    int v[NB], cnt = 0;
+    for (int j = 0; j < MED_RPT; ++j) {
+        const int ry = ty + RS * j, y = y0 + ry;
+        const bool in = x < W && y < H;
+        const int centre = sv[ry + MED_R][tx + MED_R];
+        bool need = false;
+        if (in && centre == MED_NONE) {
+            // some voter among the 24 neighbours (the centre itself does not vote)
+            unsigned long long any = 0;
 #pragma unroll
-    for (int m = 0, k = 0; m <= 2 * MED_R; ++m)
-#pragma unroll
-        for (int q = 0; q <= 2 * MED_R; ++q) {
-            if (m == MED_R && q == MED_R) continue;
-            v[k] = sv[ty + m][tx + q];
-            cnt += v[k] != MED_NONE;
-            ++k;
+            for (int m = 0; m <= 2 * MED_R; ++m) any |= vmask[ry + m] >> tx;
+            need = (any & ((1ull << (2 * MED_R + 1)) - 1ull)) != 0;
         }
-    constexpr MergeExchange<NB> net;
-#pragma unroll
-    for (int c = 0; c < net.M; ++c) {
-        const int lo = min(v[net.a[c]], v[net.b[c]]), hi = max(v[net.a[c]], v[net.b[c]]);
-        v[net.a[c]] = lo;
-        v[net.b[c]] = hi;
+        if (in && !need) {
+            const size_t o = (size_t)y * W + x;
+            d_out[o] = centre != MED_NONE ? static_cast<int16_t>(centre) : d_in[o];
+        }
+        // collect the pixels to sort: one shared atomic per warp and row
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, need);
+        int first = 0;
+        if (lane == 0 && bal) first = atomicAdd(&njob_s, __popc(bal));
+        first = __shfl_sync(0xFFFFFFFFu, first, 0);
+        if (need) job[first + __popc(bal & ((1u << lane) - 1u))] = static_cast<uint16_t>(ry * MED_TX + tx);
     }
-    const int want = (cnt - 1) / 2;       // at most NB / 2 - 1
-    int out = v[0];
+    __syncthreads();
+    const int njob = njob_s;
+    for (int k = tid; k < njob; k += NT) {
+        const int t = job[k], jx = t % MED_TX, jy = t / MED_TX;
+        int v[NB], cnt = 0;
 #pragma unroll
-    for (int i = 1; i < NB / 2; ++i)
-        if (i == want) out = v[i];
-    d_out[(size_t)(y0 + ty) * W + x0 + tx] = static_cast<int16_t>(out);
+        for (int m = 0, i = 0; m <= 2 * MED_R; ++m)
+#pragma unroll
+            for (int q = 0; q <= 2 * MED_R; ++q) {
+                if (m == MED_R && q == MED_R) continue;
+                v[i] = sv[jy + m][jx + q];
+                cnt += v[i] != MED_NONE;
+                ++i;
+            }
+        constexpr MergeExchange<NB> net;
+#pragma unroll
+        for (int c = 0; c < net.M; ++c) {
+            const int lo = min(v[net.a[c]], v[net.b[c]]), hi = max(v[net.a[c]], v[net.b[c]]);
+            v[net.a[c]] = lo;
+            v[net.b[c]] = hi;
+        }
+        const int want = (cnt - 1) / 2;       // at most NB / 2 - 1
+        int out = v[0];
+#pragma unroll
+        for (int i = 1; i < NB / 2; ++i)
+            if (i == want) out = v[i];
+        d_out[(size_t)(y0 + jy) * W + x0 + jx] = static_cast<int16_t>(out);
+    }
 }
 
 }  // namespace
@@ -319,8 +328,8 @@ cudaError_t launch_alpha_refine(const LevelBuf &l, int nh, float alpha, int16_t 
 
 cudaError_t launch_selective_median(const int16_t *d_in, const float *C, int W, int H, float alpha, int16_t *d_out,
                                     cudaStream_t st) {
-    dim3 blk(MED_TX, MED_TY), grd((W + MED_TX - 1) / MED_TX, (H + MED_TY - 1) / MED_TY);
-    selective_median_kernel<<<grd, blk, 0, st>>>(d_in, C, W, H, alpha, d_out);
+    dim3 grd((W + MED_TX - 1) / MED_TX, (H + MED_TY - 1) / MED_TY);
+    selective_median_kernel<<<grd, 256, 0, st>>>(d_in, C, W, H, alpha, d_out);
     return cudaGetLastError();
 }
 

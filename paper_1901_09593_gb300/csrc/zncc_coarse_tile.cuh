@@ -21,13 +21,14 @@ constexpr int CO_TX = 32, CO_TY = 8;
 template <int NH, int TY = CO_TY>
 struct CoarseCfg {
     static constexpr int SLW = CO_TX + 2 * NH, SLH = TY + 2 * NH;      // staged left region
+    static constexpr int SLP = (SLW + 3) / 4 * 4 + 4;                   // its row stride: whole words + 1
     static constexpr int SU = CO_TX + region::ZC - 1;                   // right window columns per chunk
     static constexpr int SRW = SU + 2 * NH;                             // staged right columns per chunk
     static constexpr int SRWW = (SRW + 3) / 4 + 2;                      // words per staged right row
     static constexpr size_t al(size_t v) { return (v + 15) / 16 * 16; }
     static constexpr size_t OFF_SR = 16;                                // [0,16): evaluation sum
     static constexpr size_t OFF_SL = OFF_SR + al((size_t)SLH * SRWW * 4);
-    static constexpr size_t OFF_VS = OFF_SL + al((size_t)SLH * SLW);
+    static constexpr size_t OFF_VS = OFF_SL + al((size_t)SLH * SLP);
     static constexpr size_t OFF_VQ = OFF_VS + al((size_t)TY * SRW * 4);
     static constexpr size_t OFF_ST = OFF_VQ + al((size_t)TY * SRW * 4);
     static constexpr size_t BYTES = OFF_ST + al((size_t)TY * SU * 8);
@@ -44,7 +45,7 @@ __device__ void coarse_tile(const uint8_t *L, const uint8_t *R, int pitch, int W
     constexpr int ZS = 256 / (CO_TX * TY);         // threads per pixel
     static_assert(ZS * CO_TX * TY == 256 && (ZS & (ZS - 1)) == 0, "tile shape");
     constexpr int WIN = 2 * NH + 1, NW = (WIN + 3) / 4;
-    constexpr int SLW = C::SLW, SLH = C::SLH, SU = C::SU, SRW = C::SRW, SRWW = C::SRWW;
+    constexpr int SLW = C::SLW, SLP = C::SLP, SLH = C::SLH, SU = C::SU, SRW = C::SRW, SRWW = C::SRWW;
     unsigned long long &evsum = *reinterpret_cast<unsigned long long *>(sm);
     uint32_t *sR = reinterpret_cast<uint32_t *>(sm + C::OFF_SR);
     uint8_t *sL = sm + C::OFF_SL;
@@ -56,11 +57,11 @@ __device__ void coarse_tile(const uint8_t *L, const uint8_t *R, int pitch, int W
     const int x = x0 + pc, y = y0 + pr;
     if (tid == 0) evsum = 0ull;
     // the left rows and the first chunk's right rows in one round trip
-    region::stage_rows2<SLH, SLW, SLW, SLH, SRW, SRWW * 4>(sL, L, y0 - NH, x0 - NH, reinterpret_cast<uint8_t *>(sR),
+    region::stage_rows2<SLH, SLW, SLP, SLH, SRW, SRWW * 4>(sL, L, y0 - NH, x0 - NH, reinterpret_cast<uint8_t *>(sR),
                                                            R, y0 - NH, x0 - (ZC - 1) - NH, pitch, W, H);
     __syncthreads();
     uint32_t Lw[WIN][NW];
-    const int2 la = region::pack_left<NH, SLW>(sL, pr, pc, Lw);
+    const int2 la = region::pack_left_w<NH, SLP>(sL, pr, pc, Lw);
     const int zmax = min(Dk - 1, x);
     const int zmax_tile = min(Dk - 1, min(x0 + CO_TX, W) - 1);
     // the thread walks its candidates in ascending z and keeps the first maximum (strict

@@ -125,6 +125,35 @@ __device__ __forceinline__ int2 pack_left(const uint8_t *s, int r, int c, uint32
     return make_int2(static_cast<int>(a), V > 0 ? __float_as_int(rsqrtf(static_cast<float>(V))) : 0);
 }
 
+// pack_left on rows staged with a word-multiple stride that leaves at least one readable
+// word past each window: whole-word loads and funnel shifts instead of byte loads.
+template <int NH, int STRIDE>
+__device__ __forceinline__ int2 pack_left_w(const uint8_t *s, int r, int c,
+                                            uint32_t (&Lw)[2 * NH + 1][(2 * NH + 4) / 4]) {
+    constexpr int WIN = 2 * NH + 1, N = WIN * WIN, NW = (WIN + 3) / 4;
+    constexpr uint32_t LAST = (WIN % 4 == 0) ? 0xFFFFFFFFu : ((1u << (8 * (WIN % 4))) - 1u);
+    static_assert(STRIDE % 4 == 0, "word stride");
+    const int w0 = c >> 2, sh = 8 * (c & 3);
+    uint32_t a = 0, q = 0;
+#pragma unroll
+    for (int i = 0; i < WIN; ++i) {
+        const uint32_t *row = reinterpret_cast<const uint32_t *>(s + (r + i) * STRIDE) + w0;
+        uint32_t raw[NW + 1];
+#pragma unroll
+        for (int k = 0; k <= NW; ++k) raw[k] = row[k];
+#pragma unroll
+        for (int k = 0; k < NW; ++k) {
+            uint32_t w = __funnelshift_r(raw[k], raw[k + 1], sh);
+            if (k == NW - 1) w &= LAST;
+            Lw[i][k] = w;
+            a = dp4a_u8(w, 0x01010101u, a);
+            q = dp4a_u8(w, w, q);
+        }
+    }
+    const int V = N * static_cast<int>(q) - static_cast<int>(a) * static_cast<int>(a);
+    return make_int2(static_cast<int>(a), V > 0 ? __float_as_int(rsqrtf(static_cast<float>(V))) : 0);
+}
+
 // Sab of the packed left window with the 4 right windows whose top-left bytes are staged at
 // columns um + o (o = 0..3), row r, of word-staged rows sR (WSTRIDE words per row; each row
 // readable 2 words past its last window byte).
