@@ -63,10 +63,9 @@ cudaError_t launch_apron_copy(const uint8_t *L, const uint8_t *R, size_t spitch,
 }
 
 // ---- fused pyramid: levels s+1 .. s+F (F <= PF_MAXF) in one launch (pyramid_fused.cuh) ----
-// The launch has one CTA per tile and image (a few hundred on the benchmark sizes), so each
-// CTA runs PF_NT threads to keep its serial chain of passes short (measured: 512 beats 256
-// and 1024 on the 1400 x 1000 and 2880 x 1984 pairs).
-constexpr int PF_NT = 512;
+// One CTA of PF_NT threads per tile and image (measured with 16 x 4 tiles: 256 threads
+// beat 512 on the 2880 x 1984 pair and match it on the 1400 x 1000 pair).
+constexpr int PF_NT = 256;
 
 template <int F>
 __global__ void __launch_bounds__(PF_NT) pyr_fused_kernel(const __grid_constant__ PyrFuseArgs a) {

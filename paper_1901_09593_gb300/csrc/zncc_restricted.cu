@@ -14,8 +14,16 @@ using namespace tiles;
 constexpr int SA_QX = 32;    // threads per tile row; tile width SA_QX pixels
 constexpr int SA_NCOL = 1;
 
+// Minimum CTAs per SM the register allocation must allow.  Up to 9 x 9 windows run four
+// CTAs per SM (64 registers): for r = 3 at 7 x 7 that costs 20 spilled bytes instead of 78
+// registers (3 CTAs per SM), at 9 x 9 196 bytes instead of 99 registers (2 CTAs per SM), and
+// level 0 of the 2880 x 1984 pair (9 x 9, r = 3) went 190 -> 150 us (three CTAs per SM at 80
+// registers: 156 us).  Without a minimum the compiler may also take more registers for smaller
+// groups.  Larger windows keep two CTAs per SM.
+constexpr int restr_min_ctas(int nh) { return nh <= 4 ? 4 : 2; }
+
 template <int NH, int G>
-__global__ void __launch_bounds__(SA_QX * 8) zncc_restricted_kernel(const __grid_constant__ RestrArgs a) {
+__global__ void __launch_bounds__(SA_QX * 8, restr_min_ctas(NH)) zncc_restricted_kernel(const __grid_constant__ RestrArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
     if (threadIdx.x == 0) {
         mbar_init(reinterpret_cast<uint64_t *>(smem), 1);
