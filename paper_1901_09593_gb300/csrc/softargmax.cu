@@ -198,8 +198,11 @@ __global__ void __launch_bounds__(256) sa_fwd_kernel(const SaArgs a) {
     a.l[p] = l;
 }
 
+// Two CTAs per SM: at 7 x 7 the unconstrained build took 148 registers (one CTA per SM);
+// at 128 registers a few hundred bytes spill and forward + backward of the 8 x 640 x 480,
+// 64-candidate workload went 2.58 -> 2.29 ms.
 template <int NH>
-__global__ void __launch_bounds__(256) sa_bwd_coef_kernel(const SaArgs a) {
+__global__ void __launch_bounds__(256, 2) sa_bwd_coef_kernel(const SaArgs a) {
     using C = SaCfg<NH>;
     extern __shared__ float sm[];
     const int RTP = SA_TX + a.ndisp - 1 + 2 * NH, RSW = SA_TX + a.ndisp - 1;
