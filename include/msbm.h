@@ -162,8 +162,9 @@ msbm_status msbm_level_result(msbm_ctx *ctx, int32_t level, int16_t *d_out, floa
  * before the first kernel and after each stage on the context's stream, wait, and write
  * each stage's milliseconds to stage_ms in launch order:
  *   [0]          the pyramid (level-0 copy and reduces to levels 1 .. K-1, fused launches)
- *                and the right-window statistics planes of levels 0 .. K-2 (one launch; the
- *                pass itself runs that launch beside the coarsest level's search),
+ *                and the right-window statistics planes of levels 0 .. K-2 (one launch here;
+ *                the pass itself runs one launch per level on a second stream, beside the
+ *                coarsest level's search and the coarser restricted levels),
  *   [1]          full search at level K-1 (+ alpha refinement when enabled),
  *   [2 .. K]     levels K-2 .. 0: restricted search (+ beta gate and the fallback pixels' full search,
  *                + selective median, when enabled).
