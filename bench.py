@@ -176,7 +176,7 @@ def stage_work(name, spec, levels_wh, evals_by_level):
 MEASURED_TRAFFIC = {
     "restricted_level0": {"files": ["zncc_restricted.cu", "zncc_restricted_tile.cuh", "msbm_device.cuh",
                                     "msbm_internal.h"],
-                          "sha256_16": "8fe4496d728e0f69", "bytes": 14760704},
+                          "sha256_16": "64b37b125a1afb87", "bytes": 14739968},
 }
 
 
@@ -231,6 +231,25 @@ def time_oracle(sc, budget_s: float, min_runs: int = 1):
         if runs >= min_runs and el >= budget_s:
             break
     return runs, el, oracle.max_threads()
+
+
+def oracle_side_samples(sc, cores: int) -> dict:
+    """One flat (K = 1) oracle frame on all host cores and one hierarchical frame on one
+    core, for context beside the baseline (a few seconds in all)."""
+    import oracle
+    s = sc.spec
+    t0 = time.perf_counter()
+    oracle.disparity(sc.left, sc.right, s.max_disp, 1, s.window, s.radius)
+    flat_s = time.perf_counter() - t0
+    oracle.set_threads(1)
+    try:
+        t0 = time.perf_counter()
+        oracle.disparity(sc.left, sc.right, s.max_disp, s.levels, s.window, s.radius)
+        one_s = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(cores)
+    return {"flat_frames_per_s": 1.0 / flat_s, "hier_one_core_frames_per_s": 1.0 / one_s,
+            "side_samples": "one flat K = 1 frame on all cores; one hierarchical frame on one core"}
 
 
 def run_reference(args):
@@ -612,6 +631,7 @@ def run_gpu(args):
         cpu = {"kind": "oracle", "value": runs / el, "unit": "frames/s", "cores": cores,
                "sample": f"{runs} full-frame hierarchical passes of the {W}x{H} pair "
                          f"(FP64 C oracle, OpenMP over rows), {el:.1f} s"}
+        cpu.update(oracle_side_samples(sc, cores))
 
     additions = {}
     if rank == 0 and not args.no_additions:

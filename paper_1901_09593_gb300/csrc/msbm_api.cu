@@ -385,14 +385,14 @@ msbm_status msbm_create(const msbm_params *params, void *cuda_stream, msbm_ctx *
         l.full_sx = choose_sx(W, H, c->num_sms);
         l.coarse = zncc_coarse_fits(W, H, c->num_sms);
         if (e == cudaSuccess) {
-            const int rowsR = 16 + 2 * l.nh;
+            const int rowsR = restr_tile_rows() + 2 * l.nh;
             bool ok = encode_u8(&l.tmFL, l.base[0], l.pitch, l.rows, 32 * l.full_sx + 32, rowsT) &&
                       encode_u8(&l.tmR256, l.base[1], l.pitch, l.rows, 256, rowsT) &&
                       encode_u8(&l.tmRL, l.base[0], l.pitch, l.rows, 64, rowsR) &&
                       encode_u8(&l.tmRR128, l.base[1], l.pitch, l.rows, 128, rowsR) &&
                       encode_u8(&l.tmRR256, l.base[1], l.pitch, l.rows, 256, rowsR) &&
-                      encode_u64(&l.tmS128, l.rstat, l.rspitch, H, 128, 16) &&
-                      encode_u64(&l.tmS256, l.rstat, l.rspitch, H, 256, 16);
+                      encode_u64(&l.tmS128, l.rstat, l.rspitch, H, 128, restr_tile_rows()) &&
+                      encode_u64(&l.tmS256, l.rstat, l.rspitch, H, 256, restr_tile_rows());
             if (!ok) { c->lv.push_back(l); free_ctx(c); return MSBM_ERR_UNSUPPORTED; }
         }
         if (e == cudaSuccess) e = zncc_full_prepare(l.nh, l.full_sx);

@@ -28,10 +28,10 @@ struct LevelBuf {
     // TMA maps over the apron buffers.  Full-range tile (8 + 2n rows high):
     //   tmFL   : left,  32*SX + 32 bytes wide, SX per level
     //   tmR256 : right, 256 bytes wide
-    // Restricted tile (16 + 2n rows high):
+    // Restricted tile (restr_tile_rows() + 2n rows high):
     //   tmRL   : left,  64 bytes wide
     //   tmRR128, tmRR256 : right, 128 / 256 bytes wide (narrow / wide candidate spans)
-    //   tmS128, tmS256   : statistics plane, 128 / 256 entries wide, 16 rows
+    //   tmS128, tmS256   : statistics plane, 128 / 256 entries wide, restr_tile_rows() rows
     CUtensorMap tmFL, tmR256, tmRL, tmRR128, tmRR256, tmS128, tmS256;
     int full_sx = 4;             // full-range tile width 32*full_sx at this level
     int full_zblock = 0;         // full-range z-block (0 = the tile's maximum)
@@ -75,11 +75,11 @@ struct RestrTileArgs {
 };
 
 struct RestrArgs {
-    CUtensorMap tmL;     // box {64, 16 + 2n} over the left apron buffer
-    CUtensorMap tmR128;  // box {128, 16 + 2n} over the right apron buffer
-    CUtensorMap tmR256;  // box {256, 16 + 2n} over the right apron buffer
-    CUtensorMap tmS128;  // box {128, 16} over the right statistics plane
-    CUtensorMap tmS256;  // box {256, 16} over the right statistics plane
+    CUtensorMap tmL;     // box {64, ty + 2n} over the left apron buffer, ty = restr_tile_rows()
+    CUtensorMap tmR128;  // box {128, ty + 2n} over the right apron buffer
+    CUtensorMap tmR256;  // box {256, ty + 2n} over the right apron buffer
+    CUtensorMap tmS128;  // box {128, ty} over the right statistics plane
+    CUtensorMap tmS256;  // box {256, ty} over the right statistics plane
     RestrTileArgs t;
 };
 
@@ -118,6 +118,8 @@ cudaError_t zncc_full_prepare(int nh, int sx);
 // Right-window statistics planes of n consecutive levels (lv[0 .. n-1]) in one launch.
 cudaError_t launch_right_stats(const LevelBuf *lv, int n, int nh, cudaStream_t st);
 cudaError_t zncc_restricted_prepare(int nh);
+// Rows of the standalone restricted kernel's tile (its TMA boxes are rows + 2n high).
+int restr_tile_rows();
 cudaError_t launch_zncc_restricted(const RestrArgs &a, int nh, cudaStream_t st);
 
 }  // namespace msbm

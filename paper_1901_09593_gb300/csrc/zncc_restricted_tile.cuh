@@ -5,7 +5,7 @@
 // paper's "3 comparisons per pixel" is r = 1), clipped to 0 .. min(D_k - 1, x); dhat is
 // first clamped into that range (a no-op for priors produced by the coarser level).
 //
-// Design (per CTA: a (NCOL*QX) x 16 pixel tile of QX x 8 threads; each thread owns an
+// Design (per CTA: a (NCOL*QX) x TY pixel tile, TY = 16 or 8, of QX x TY/2 threads; each thread owns an
 // NCOL x 2 block of pixels, NCOL = 2 (2 x 2 blocks) or 1 (vertical pairs)):
 //  * The pixels of a block aligned to even coordinates share one prior cell, hence one
 //    candidate span (up to the per-pixel clip at x, handled by masking).
@@ -36,16 +36,17 @@
 namespace msbm {
 namespace tiles {
 
-constexpr int RT_TY = 16;      // tile height (pixels)
+constexpr int RT_TY = 16;      // default tile height (pixels)
 
-template <int NH, int QX = 32, int NCOL = 2, bool PLANE = false>
+template <int NH, int QX = 32, int NCOL = 2, bool PLANE = false, int TY = RT_TY>
 struct RCfg {
+    static_assert(TY == 8 || TY == 16, "tile height");
     static constexpr int TX = NCOL * QX;         // tile width (pixels)
-    static constexpr int THREADS = QX * 8;
+    static constexpr int THREADS = QX * (TY / 2);
     static constexpr int WIN = 2 * NH + 1;
     static constexpr int N = WIN * WIN;
     static constexpr int NW = (WIN + 3) / 4;     // words per packed window row
-    static constexpr int ROWS = RT_TY + 2 * NH;  // staged rows
+    static constexpr int ROWS = TY + 2 * NH;     // staged rows
     static constexpr int LBOX = TX + 32;         // left box: image columns x0-16 .. x0+TX+16
     static constexpr uint32_t LASTMASK =
         (WIN % 4 == 0) ? 0xFFFFFFFFu : ((1u << (8 * (WIN % 4))) - 1u);
@@ -55,28 +56,28 @@ struct RCfg {
     static constexpr size_t PAD_R = 128;         // readable slack before the right span
     static constexpr size_t OFF_SR = OFF_SL + al((size_t)ROWS * LBOX) + PAD_R;
     static constexpr size_t OFF_TMP = OFF_SR + al((size_t)(ROWS + 1) * 256);
-    static constexpr size_t OFF_STR = OFF_TMP + (size_t)RT_TY * 256 * 4;
+    static constexpr size_t OFF_STR = OFF_TMP + (size_t)TY * 256 * 4;
     // plane mode stages the span's entries of the level's statistics plane at OFF_TMP instead
     static constexpr size_t OFF_SS = OFF_TMP;
-    static constexpr size_t BYTES = PLANE ? OFF_SS + (size_t)RT_TY * 256 * 8 : OFF_STR + (size_t)RT_TY * 256 * 8;
+    static constexpr size_t BYTES = PLANE ? OFF_SS + (size_t)TY * 256 * 8 : OFF_STR + (size_t)TY * 256 * 8;
 };
 
 __device__ __forceinline__ uint32_t fsr(uint32_t lo, uint32_t hi, int bytes) {
     return __funnelshift_r(lo, hi, 8 * bytes);
 }
 
-// Restricted WTA of one (NCOL*QX) x 16 tile (bx, by) by the calling CTA (blockDim.x = QX*8).
+// Restricted WTA of one (NCOL*QX) x TY tile (bx, by) by the calling CTA (blockDim.x = QX*TY/2).
 // `smem` holds RCfg::BYTES bytes, 128-aligned; its first 8 bytes are an mbarrier the caller
 // has initialised (count 1) and `parity` is its next phase parity, advanced here.  tmL is a
 // (NCOL*QX + 32)-byte-wide box over the left apron buffer, tmR128/tmR256 128/256-byte boxes
 // over the right one.  PLANE: the right-window statistics are staged by TMA from the level's
 // statistics plane (tmS128 / tmS256: 128 / 256 x 16 boxes of 8-byte entries) instead of being
 // built in the CTA.  Returns false if a bounded wait gave up (the error word is then set).
-template <int NH, int G, int QX = 32, int NCOL = 2, bool PLANE = false>
+template <int NH, int G, int QX = 32, int NCOL = 2, bool PLANE = false, int TY = RT_TY>
 __device__ bool restr_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const CUtensorMap *tmR128,
                            const CUtensorMap *tmR256, const CUtensorMap *tmS128, const CUtensorMap *tmS256,
                            int bx, int by, uint8_t *smem, uint32_t &parity) {
-    using C = RCfg<NH, QX, NCOL, PLANE>;
+    using C = RCfg<NH, QX, NCOL, PLANE, TY>;
     constexpr int RT_TX = C::TX, RT_THREADS = C::THREADS;
     constexpr int ROWS = C::ROWS, WIN = C::WIN, NW = C::NW;
     // right bytes one row of a candidate group needs for both columns: G + WIN, plus up to
@@ -93,12 +94,12 @@ __device__ bool restr_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const
     unsigned long long &evsum = *reinterpret_cast<unsigned long long *>(smem + 32);
     uint8_t *sL = smem + C::OFF_SL;                       // [ROWS][LBOX]
     uint8_t *sR = smem + C::OFF_SR;                       // [ROWS + 1][64|128|256] + slack before
-    uint32_t *tmpV = reinterpret_cast<uint32_t *>(smem + C::OFF_TMP);   // [RT_TY][256] packed (Q | S << 20)
-    int2 *stR = reinterpret_cast<int2 *>(smem + C::OFF_STR);           // [RT_TY][256] {Sb, bits(rsqrt(Vb))}
-    const int2 *stS = reinterpret_cast<const int2 *>(smem + C::OFF_SS);  // plane mode: [RT_TY][128|256]
+    uint32_t *tmpV = reinterpret_cast<uint32_t *>(smem + C::OFF_TMP);   // [TY][256] packed (Q | S << 20)
+    int2 *stR = reinterpret_cast<int2 *>(smem + C::OFF_STR);           // [TY][256] {Sb, bits(rsqrt(Vb))}
+    const int2 *stS = reinterpret_cast<const int2 *>(smem + C::OFF_SS);  // plane mode: [TY][128|256]
 
     const int tid = threadIdx.x, qx = tid % QX, qy = tid / QX;
-    const int x0 = bx * RT_TX, y0 = by * RT_TY;
+    const int x0 = bx * RT_TX, y0 = by * TY;
     const int xa = x0 + NCOL * qx, ya = y0 + 2 * qy;    // top-left pixel of this thread's block
     const int Dk = a.Dk;
     bool colv[NCOL];
@@ -166,7 +167,7 @@ __device__ bool restr_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const
         mode_s = mode;
         xs_s = xs;
         uint32_t bytes = ROWS * C::LBOX + (mode == 1 ? ROWS * 128 : (mode == 2 ? ROWS * 256 : 0));
-        if (PLANE) bytes += mode == 1 ? RT_TY * 128 * 8 : (mode == 2 ? RT_TY * 256 * 8 : 0);
+        if (PLANE) bytes += mode == 1 ? TY * 128 * 8 : (mode == 2 ? TY * 256 * 8 : 0);
         fence_proxy_async_smem();
         mbar_arrive_expect_tx(&bar, bytes);
         tma_load_2d(sL, tmL, &bar, x0 - 16 + APX, y0 - NH + APY);
@@ -186,7 +187,7 @@ __device__ bool restr_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const
     if (!PLANE && mode != 0) {
         // vertical window sums of every (output row, span column), spread over all threads
         const int cols = SW + 2 * NH;
-        for (int i = tid; i < RT_TY * cols; i += RT_THREADS) {
+        for (int i = tid; i < TY * cols; i += RT_THREADS) {
             const int ry = i / cols, c = i - ry * cols;
             const uint8_t *p = sR + ry * rst + rs + c + soff;
             uint32_t s = 0, q = 0;
@@ -200,7 +201,7 @@ __device__ bool restr_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const
         }
         __syncthreads();
         // horizontal sums, then rsqrt of the window variance
-        for (int i = tid; i < RT_TY * SW; i += RT_THREADS) {
+        for (int i = tid; i < TY * SW; i += RT_THREADS) {
             const int ry = i / SW, v = i - ry * SW;
             int s = 0, q = 0;
 #pragma unroll
