@@ -191,15 +191,15 @@ constexpr int MED_RPT = 4;                             // rows per thread (strid
 constexpr int MED_SW = MED_TX + 2 * MED_R, MED_SH = MED_TY + 2 * MED_R;
 constexpr int MED_NONE = 0x7FFF;     // a neighbour that does not vote (outside, or cost <= alpha)
 
-// Eq. 10 on a 32 x 32 tile (256 threads, 4 pixels each, so one wave of CTAs covers a level
-// of the benchmark sizes): the 5 x 5 neighbourhood (inside the image) is staged in shared
-// memory as voting disparities (cost > alpha) or MED_NONE, costs and disparities loaded
-// together (one round trip).  A voting pixel keeps its disparity; the tile's pixels with cost
-// <= alpha and at least one voter are collected in a list (warp-aggregated shared atomics),
-// and the CTA's threads sort them: each job sorts the pixel's 24 neighbours (the pixel does
-// not vote itself) with a merge-exchange network, so the voters come first in ascending
-// order, and takes the lower median of the voters.  A pixel with cost <= alpha and no voter
-// keeps its disparity.
+// Eq. 10 on a 32 x 32 tile (256 threads, 4 pixels each, which amortises the staged halo and
+// the per-CTA barriers over four times the pixels of a 32 x 8 tile): the 5 x 5 neighbourhood
+// (inside the image) is staged in shared memory as voting disparities (cost > alpha) or
+// MED_NONE, costs and disparities loaded together (one round trip).  A voting pixel keeps
+// its disparity; the tile's pixels with cost <= alpha and at least one voter are collected in
+// a list (warp-aggregated shared atomics), and the CTA's threads sort them: each job sorts
+// the pixel's 24 neighbours (the pixel does not vote itself) with a merge-exchange network,
+// so the voters come first in ascending order, and takes the lower median of the voters.  A
+// pixel with cost <= alpha and no voter keeps its disparity.
 __global__ void __launch_bounds__(256)
 selective_median_kernel(const int16_t *__restrict__ d_in, const float *__restrict__ C, int W, int H, float alpha,
                         int16_t *d_out) {
