@@ -146,10 +146,11 @@ msbm_status msbm_match_level_beta(msbm_ctx *ctx, int32_t level, const int16_t *d
 msbm_status msbm_disparity(msbm_ctx *ctx, const uint8_t *d_left, const uint8_t *d_right,
                            size_t pitch_bytes, int16_t *d_out, float *cost_out);
 
-/* Same pass on HOST buffers, waiting for the result.  When all given buffers are page-locked
- * (cudaHostAlloc / cudaHostRegister, e.g. torch pin_memory) the kernels read the images and
- * write the maps through their device-mapped addresses, so the transfers overlap the pass;
- * otherwise the images are copied in and the maps copied out through staging buffers. */
+/* Same pass on HOST buffers, waiting for the result: the images are copied into device
+ * staging buffers (owned by the context, allocated on the first call), the pass runs on them
+ * and the maps are copied back, all on the context's stream.  Page-locked buffers
+ * (cudaHostAlloc / cudaHostRegister, e.g. torch pin_memory) make the copies asynchronous
+ * DMA transfers; pageable ones work too, at the driver's pageable-copy speed. */
 msbm_status msbm_disparity_host(msbm_ctx *ctx, const uint8_t *h_left, const uint8_t *h_right,
                                 size_t pitch_bytes, int16_t *h_d, float *h_cost);
 

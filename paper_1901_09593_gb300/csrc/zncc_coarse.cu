@@ -14,20 +14,21 @@ namespace msbm {
 
 namespace {
 
-constexpr int SA_TY = 2;    // tile rows; 8 / SA_TY threads per pixel (measured: 2 beats 4 and 8)
+constexpr int SA_NT = 256;       // threads per CTA (128 measured the same)
+constexpr int SA_TY = SA_NT / 128;  // tile rows: 2, four threads per pixel (measured: beats 4 and 8 rows)
 
 template <int NH>
-__global__ void __launch_bounds__(256) zncc_coarse_kernel(const uint8_t *L, const uint8_t *R, int pitch, int W,
+__global__ void __launch_bounds__(SA_NT) zncc_coarse_kernel(const uint8_t *L, const uint8_t *R, int pitch, int W,
                                                           int H, int Dk, int16_t *d_out, float *c_out,
                                                           unsigned long long *evals) {
     __shared__ __align__(16) uint8_t sm[CoarseCfg<NH, SA_TY>::BYTES];
-    coarse_tile<NH, SA_TY>(L, R, pitch, W, H, Dk, d_out, c_out, evals, blockIdx.x, blockIdx.y, sm);
+    coarse_tile<NH, SA_TY, SA_NT>(L, R, pitch, W, H, Dk, d_out, c_out, evals, blockIdx.x, blockIdx.y, sm);
 }
 
 template <int NH>
 cudaError_t coarse_launch(const LevelBuf &l, int16_t *d, float *c, unsigned long long *evals, cudaStream_t st) {
     dim3 grd((l.W + CO_TX - 1) / CO_TX, (l.H + SA_TY - 1) / SA_TY);
-    zncc_coarse_kernel<NH><<<grd, 256, 0, st>>>(l.img(0), l.img(1), l.pitch, l.W, l.H, l.Dk, d, c, evals);
+    zncc_coarse_kernel<NH><<<grd, SA_NT, 0, st>>>(l.img(0), l.img(1), l.pitch, l.W, l.H, l.Dk, d, c, evals);
     return cudaGetLastError();
 }
 

@@ -35,15 +35,15 @@ struct CoarseCfg {
 };
 
 // Tile (bx, by) of 32 x TY pixels of a W x H level (apron buffers L, R with `pitch`).  sm:
-// CoarseCfg<NH, TY>::BYTES bytes, 16-aligned.  blockDim.x == 256 == 32 * TY * ZS.  evals (may
+// CoarseCfg<NH, TY>::BYTES bytes, 16-aligned.  blockDim.x == NT == 32 * TY * ZS.  evals (may
 // be NULL) gains the tile's evaluations.
-template <int NH, int TY = CO_TY>
+template <int NH, int TY = CO_TY, int NT = 256>
 __device__ void coarse_tile(const uint8_t *L, const uint8_t *R, int pitch, int W, int H, int Dk, int16_t *d_out,
                             float *c_out, unsigned long long *evals, int bx, int by, uint8_t *sm) {
     using region::ZC;
     using C = CoarseCfg<NH, TY>;
-    constexpr int ZS = 256 / (CO_TX * TY);         // threads per pixel
-    static_assert(ZS * CO_TX * TY == 256 && (ZS & (ZS - 1)) == 0, "tile shape");
+    constexpr int ZS = NT / (CO_TX * TY);          // threads per pixel
+    static_assert(ZS * CO_TX * TY == NT && (ZS & (ZS - 1)) == 0, "tile shape");
     constexpr int WIN = 2 * NH + 1, NW = (WIN + 3) / 4;
     constexpr int SLW = C::SLW, SLP = C::SLP, SLH = C::SLH, SU = C::SU, SRW = C::SRW, SRWW = C::SRWW;
     unsigned long long &evsum = *reinterpret_cast<unsigned long long *>(sm);
@@ -57,7 +57,7 @@ __device__ void coarse_tile(const uint8_t *L, const uint8_t *R, int pitch, int W
     const int x = x0 + pc, y = y0 + pr;
     if (tid == 0) evsum = 0ull;
     // the left rows and the first chunk's right rows in one round trip
-    region::stage_rows2<SLH, SLW, SLP, SLH, SRW, SRWW * 4>(sL, L, y0 - NH, x0 - NH, reinterpret_cast<uint8_t *>(sR),
+    region::stage_rows2<SLH, SLW, SLP, SLH, SRW, SRWW * 4, NT>(sL, L, y0 - NH, x0 - NH, reinterpret_cast<uint8_t *>(sR),
                                                            R, y0 - NH, x0 - (ZC - 1) - NH, pitch, W, H);
     __syncthreads();
     uint32_t Lw[WIN][NW];
@@ -71,11 +71,11 @@ __device__ void coarse_tile(const uint8_t *L, const uint8_t *R, int pitch, int W
     for (int z0 = 0; z0 <= zmax_tile; z0 += ZC) {
         if (z0 > 0) {
             __syncthreads();      // the previous chunk's rows and statistics are consumed
-            region::stage_rows<SLH, SRW, SRWW * 4>(reinterpret_cast<uint8_t *>(sR), R, pitch, W, H, y0 - NH,
+            region::stage_rows<SLH, SRW, SRWW * 4, NT>(reinterpret_cast<uint8_t *>(sR), R, pitch, W, H, y0 - NH,
                                                     x0 - (z0 + ZC - 1) - NH);
             __syncthreads();
         }
-        region::window_stats<NH, TY, SU, SRWW * 4>(reinterpret_cast<const uint8_t *>(sR), vs, vq, stR);
+        region::window_stats<NH, TY, SU, SRWW * 4, NT>(reinterpret_cast<const uint8_t *>(sR), vs, vq, stR);
 #pragma unroll 1
         for (int g = zs; g < ZC / 4 && z0 + 4 * g <= zmax; g += ZS) {
             const int um = pc + ZC - 4 - 4 * g;       // staged column of candidate z0 + 4g + 3

@@ -72,11 +72,11 @@ __device__ __forceinline__ void stage_rows2(uint8_t *dstA, const uint8_t *imgA, 
 
 // Window statistics of staged rows s (row stride STRIDE bytes): for r < OR, u < OU,
 // st[r * OU + u] = {S, bits(rsqrt(N Q - S^2)) or 0} of rows r .. r+2n, columns u .. u+2n.
-// vs, vq: OR x (OU + 2n) scratch.  Ends with a barrier.
-template <int NH, int OR, int OU, int STRIDE>
+// vs, vq: OR x (OU + 2n) scratch.  Ends with a barrier.  blockDim.x == NT.
+template <int NH, int OR, int OU, int STRIDE, int NT = 256>
 __device__ __forceinline__ void window_stats(const uint8_t *s, int *vs, int *vq, int2 *st) {
     constexpr int WIN = 2 * NH + 1, N = WIN * WIN, VC = OU + 2 * NH;
-    for (int i = threadIdx.x; i < OR * VC; i += 256) {
+    for (int i = threadIdx.x; i < OR * VC; i += NT) {
         const int r = i / VC, c = i - r * VC;
         int a = 0, q = 0;
 #pragma unroll
@@ -89,7 +89,7 @@ __device__ __forceinline__ void window_stats(const uint8_t *s, int *vs, int *vq,
         vq[i] = q;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < OR * OU; i += 256) {
+    for (int i = threadIdx.x; i < OR * OU; i += NT) {
         const int r = i / OU, u = i - r * OU;
         int a = 0, q = 0;
 #pragma unroll

@@ -181,8 +181,8 @@ class Context:
 
     def disparity_host(self, left: np.ndarray, right: np.ndarray, d_out: np.ndarray | None = None,
                        cost_out: np.ndarray | None = None):
-        """Whole pass on host arrays, waiting for the result (page-locked arrays are read and
-        written by the kernels directly; others go through staging copies)."""
+        """Whole pass on host arrays, waiting for the result: the images are copied into device
+        staging buffers and the maps copied back (asynchronous DMA for page-locked arrays)."""
         self._bind_stream()
         for a, nm in ((left, "left"), (right, "right")):
             if a.dtype != np.uint8 or a.shape != (self.height, self.width) or a.strides[1] != 1:

@@ -162,8 +162,8 @@ def test_end_to_end_small(name, seed):
     ctx.disparity_host(sc.left, sc.right, hd, hc)
     np.testing.assert_array_equal(hd, d)
     np.testing.assert_array_equal(hc, c)
-    # page-locked buffers: the kernels read and write host memory directly (twice: the
-    # second call reuses the cached mappings); a mix falls back to staging copies
+    # page-locked buffers (asynchronous staging copies), twice in a row, and a mix of
+    # page-locked and pageable buffers
     import torch
     pl, pr = torch.from_numpy(sc.left).pin_memory(), torch.from_numpy(sc.right).pin_memory()
     pd, pc = torch.zeros(d.shape, dtype=torch.int16).pin_memory(), torch.zeros(c.shape).pin_memory()
