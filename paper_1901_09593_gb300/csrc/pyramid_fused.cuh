@@ -208,7 +208,6 @@ __device__ void pyr_fused_tile(const PyrFuseArgs &a, const uint8_t *src, size_t 
     using G = PyrGeom<F>;
     const int tid = threadIdx.x;
     int lox[F + 1], loy[F + 1];
-    (void)nbx;
     lox[F] = bx * PF_TX;
     loy[F] = by * PF_TY;
 #pragma unroll
