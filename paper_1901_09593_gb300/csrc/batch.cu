@@ -7,7 +7,7 @@
 //   coarsest level   full-range search at level K-1 (Eq. 3-4): the small-level tile
 //                    (zncc_coarse_tile.cuh) for D_k <= 64, else the full-range tile
 //   statistics       right-window statistics planes of levels 0 .. K-2 (level_stats_tile.cuh)
-//   restricted       level K-2 .. 0 (Eq. 8-9), 32 x 16 tiles of vertical pixel pairs reading
+//   restricted       level K-2 .. 0 (Eq. 8-9), 32 x 8 tiles of vertical pixel pairs reading
 //                    the level's statistics plane (zncc_restricted_tile.cuh, plane mode)
 // Stage s of a pair needs every tile of stage s-1 of the same pair.  The host lays the
 // (pair, stage) segments out stage-major (stage 0 of every pair, then stage 1, ...), which is
@@ -51,17 +51,20 @@ using namespace tiles;
 constexpr int BT_MAXK = 12;
 constexpr int BT_MAXG = (BT_MAXK + PF_MAXF - 2) / PF_MAXF;   // fused pyramid groups
 constexpr int BT_MAXS = BT_MAXG + 2 + BT_MAXK;              // stages per pair
-constexpr int BT_THREADS = 256;
-// Two builds of the kernel: with the full-range tile (its 128-register, ~57 KB footprint
-// allows 2 CTAs per SM) for batches whose coarsest levels exceed BT_COARSE_DK candidates, and
-// without it (64 registers: 4 CTAs per SM) otherwise.
-constexpr int BT_CTAS_FULL = 2, BT_CTAS_LEAN = 4;
+constexpr int BT_THREADS = 128;
+// Two builds of the kernel: with the full-range tile (128 registers; its ~57 KB footprint
+// allows 3 CTAs per SM) for batches whose coarsest levels exceed BT_COARSE_DK candidates, and
+// without it (64 registers: 8 CTAs per SM) otherwise.  128-thread CTAs (restricted items on
+// 32 x 8 tiles) give each SM twice the independent CTAs of 256-thread ones.
+constexpr int BT_CTAS_FULL = 4, BT_CTAS_LEAN = 8;
 constexpr int BT_BAND = 16;          // apron rows per copy item (K = 1)
 constexpr int BT_MAX_NH = 4;         // windows up to 9 x 9
 constexpr int BT_ZC = 4;             // candidates per lane chunk in batched full-range tiles
 constexpr int BT_COARSE_DK = 64;     // coarsest levels with D_k up to this use the small-level tile
-constexpr int BT_NCOL = 1;           // restricted tile: vertical pixel pairs (32 x 16 tiles)
-constexpr int BT_RTX = RCfg<1, 32, BT_NCOL>::TX;   // restricted tile width (256 threads)
+constexpr int BT_NCOL = 1;           // restricted tile: vertical pixel pairs
+constexpr int BT_RTY = 8;            // restricted tile rows (32 x 8 tiles, 128 threads)
+constexpr int BT_CO_TY = 4;          // small-level full-range tile rows (one thread per pixel)
+constexpr int BT_RTX = RCfg<1, 32, BT_NCOL, true, BT_RTY>::TX;   // restricted tile width
 constexpr int BT_AUX = 128;          // shared bytes before the scratch of non-TMA tiles (mbarrier)
 constexpr long long BT_WAIT_LIMIT = 4000000000LL;   // ~2 s at 2 GHz
 constexpr long long BT_TEST_WAIT_LIMIT = 2000000LL; // ~1 ms (MSBM_FLAG_TEST_TIMEOUT)
@@ -139,18 +142,18 @@ __device__ __forceinline__ void fence_proxy_async_global() {
 template <int F>
 __device__ __noinline__ void pyr_item(const PyrFuseArgs &pf, const uint8_t *src, size_t spitch, int bx, int by,
                                       int img, int nbx, int nby, uint8_t *sm) {
-    pyr_fused_tile<F>(pf, src, spitch, bx, by, img, nbx, nby, sm);
+    pyr_fused_tile<F, BT_THREADS>(pf, src, spitch, bx, by, img, nbx, nby, sm);
 }
 
 template <int NH>
 __device__ __noinline__ void stats_item(const BLevel &l, int bx, int by, uint8_t *sm) {
-    stats_tile<NH>(l.R, l.pitch, l.W, l.H, l.rstat, l.rspitch, bx, by, sm);
+    stats_tile<NH, BT_THREADS>(l.R, l.pitch, l.W, l.H, l.rstat, l.rspitch, bx, by, sm);
 }
 
 template <int NH>
 __device__ __noinline__ void coarse_item(const BLevel &l, int16_t *d_out, float *c_out, unsigned long long *evals,
                                          int bx, int by, uint8_t *sm) {
-    coarse_tile<NH>(l.L, l.R, l.pitch, l.W, l.H, l.Dk, d_out, c_out, evals, bx, by, sm);
+    coarse_tile<NH, BT_CO_TY, BT_THREADS>(l.L, l.R, l.pitch, l.W, l.H, l.Dk, d_out, c_out, evals, bx, by, sm);
 }
 
 template <int NH, bool FULL>
@@ -204,10 +207,10 @@ __device__ bool run_item(const BatchArgs &a, const BPair &P, const BMaps *mp, co
     t.evals = a.evals; t.err = a.err; t.force_timeout = 0;
     const BMaps &m = mp[k];
     switch (P.r) {
-        case 0: return restr_tile<NH, 1, 32, BT_NCOL, true>(t, &m.mRL, &m.mR128, &m.mR256, &m.mS128, &m.mS256, bx, by, smem, parity);
-        case 1: return restr_tile<NH, 3, 32, BT_NCOL, true>(t, &m.mRL, &m.mR128, &m.mR256, &m.mS128, &m.mS256, bx, by, smem, parity);
-        case 2: return restr_tile<NH, 5, 32, BT_NCOL, true>(t, &m.mRL, &m.mR128, &m.mR256, &m.mS128, &m.mS256, bx, by, smem, parity);
-        default: return restr_tile<NH, 7, 32, BT_NCOL, true>(t, &m.mRL, &m.mR128, &m.mR256, &m.mS128, &m.mS256, bx, by, smem, parity);
+        case 0: return restr_tile<NH, 1, 32, BT_NCOL, true, BT_RTY>(t, &m.mRL, &m.mR128, &m.mR256, &m.mS128, &m.mS256, bx, by, smem, parity);
+        case 1: return restr_tile<NH, 3, 32, BT_NCOL, true, BT_RTY>(t, &m.mRL, &m.mR128, &m.mR256, &m.mS128, &m.mS256, bx, by, smem, parity);
+        case 2: return restr_tile<NH, 5, 32, BT_NCOL, true, BT_RTY>(t, &m.mRL, &m.mR128, &m.mR256, &m.mS128, &m.mS256, bx, by, smem, parity);
+        default: return restr_tile<NH, 7, 32, BT_NCOL, true, BT_RTY>(t, &m.mRL, &m.mR128, &m.mR256, &m.mS128, &m.mS256, bx, by, smem, parity);
     }
 }
 
@@ -309,11 +312,12 @@ __global__ void __launch_bounds__(BT_THREADS, FULL ? BT_CTAS_FULL : BT_CTAS_LEAN
 
 size_t batch_smem_bytes(bool full) {
     size_t m = BT_AUX + (size_t)PF_SMEM;
-    for (size_t b : {RCfg<1, 32, BT_NCOL, true>::BYTES, RCfg<2, 32, BT_NCOL, true>::BYTES,
-                     RCfg<3, 32, BT_NCOL, true>::BYTES, RCfg<BT_MAX_NH, 32, BT_NCOL, true>::BYTES,
+    for (size_t b : {RCfg<1, 32, BT_NCOL, true, BT_RTY>::BYTES, RCfg<2, 32, BT_NCOL, true, BT_RTY>::BYTES,
+                     RCfg<3, 32, BT_NCOL, true, BT_RTY>::BYTES, RCfg<BT_MAX_NH, 32, BT_NCOL, true, BT_RTY>::BYTES,
                      BT_AUX + StatsCfg<1>::BYTES, BT_AUX + StatsCfg<2>::BYTES, BT_AUX + StatsCfg<3>::BYTES,
-                     BT_AUX + StatsCfg<BT_MAX_NH>::BYTES, BT_AUX + CoarseCfg<1>::BYTES, BT_AUX + CoarseCfg<2>::BYTES,
-                     BT_AUX + CoarseCfg<3>::BYTES, BT_AUX + CoarseCfg<BT_MAX_NH>::BYTES})
+                     BT_AUX + StatsCfg<BT_MAX_NH>::BYTES, BT_AUX + CoarseCfg<1, BT_CO_TY>::BYTES,
+                     BT_AUX + CoarseCfg<2, BT_CO_TY>::BYTES, BT_AUX + CoarseCfg<3, BT_CO_TY>::BYTES,
+                     BT_AUX + CoarseCfg<BT_MAX_NH, BT_CO_TY>::BYTES})
         m = std::max(m, b);
     if (full)
         for (size_t b : {FullCfg<1, 2, BT_ZC>::BYTES, FullCfg<2, 2, BT_ZC>::BYTES, FullCfg<3, 2, BT_ZC>::BYTES,
@@ -447,7 +451,7 @@ msbm_status msbm_batch_create(const msbm_params *pairs, int32_t n_pairs, const i
         memset(&P, 0, sizeof(P));
         P.W = p.width; P.H = p.height; P.D = p.max_disp; P.K = p.levels; P.nh = p.window / 2; P.r = p.radius;
         int W = p.width, H = p.height;
-        const int rowsF = 8 + 2 * P.nh, rowsR = RT_TY + 2 * P.nh;
+        const int rowsF = 8 + 2 * P.nh, rowsR = BT_RTY + 2 * P.nh;
         for (int k = 0; k < P.K && e == cudaSuccess; ++k) {
             BLevel &l = P.lv[k];
             l.W = W; l.H = H;
@@ -476,8 +480,8 @@ msbm_status msbm_batch_create(const msbm_params *pairs, int32_t n_pairs, const i
                      encode_b(&m.mF256, buf + bytes, l.pitch, rows, 256, rowsF) &&
                      encode_b(&m.mFL, buf, l.pitch, rows, 32 * l.sx + 32, rowsF);
             if (l.rstat)
-                enc_ok = enc_ok && encode_b64(&m.mS128, l.rstat, l.rspitch, H, 128, RT_TY) &&
-                         encode_b64(&m.mS256, l.rstat, l.rspitch, H, 256, RT_TY);
+                enc_ok = enc_ok && encode_b64(&m.mS128, l.rstat, l.rspitch, H, 128, BT_RTY) &&
+                         encode_b64(&m.mS256, l.rstat, l.rspitch, H, 256, BT_RTY);
             W = (W + 1) / 2;
             H = (H + 1) / 2;
         }
@@ -513,7 +517,7 @@ msbm_status msbm_batch_create(const msbm_params *pairs, int32_t n_pairs, const i
             const BLevel &l = P.lv[K - 1];
             if (l.Dk <= BT_COARSE_DK) {
                 const int tx = (l.W + CO_TX - 1) / CO_TX;
-                add(BS_COARSE, K - 1, tx, tx * ((l.H + CO_TY - 1) / CO_TY));
+                add(BS_COARSE, K - 1, tx, tx * ((l.H + BT_CO_TY - 1) / BT_CO_TY));
             } else {
                 const int tx = (l.W + 32 * l.sx - 1) / (32 * l.sx);
                 add(BS_FULL, K - 1, tx, tx * ((l.H + 7) / 8));
@@ -529,7 +533,7 @@ msbm_status msbm_batch_create(const msbm_params *pairs, int32_t n_pairs, const i
         }
         for (int k = K - 2; k >= 0; --k) {
             const int tx = (P.lv[k].W + BT_RTX - 1) / BT_RTX;
-            add(BS_RESTR, k, tx, tx * ((P.lv[k].H + RT_TY - 1) / RT_TY));
+            add(BS_RESTR, k, tx, tx * ((P.lv[k].H + BT_RTY - 1) / BT_RTY));
         }
     }
     if (e != cudaSuccess || !enc_ok) {

@@ -31,23 +31,24 @@ struct StatsCfg {
 
 // Tile (bx, by) of the plane out (opitch entries per row) of the W x H image R (pitch bytes):
 // R is the image origin of an apron buffer (APY rows and APX columns of replicated border,
-// 4-byte aligned rows).  sm: StatsCfg<NH>::BYTES bytes, 16-aligned.  blockDim.x == 256.
-template <int NH>
+// 4-byte aligned rows).  sm: StatsCfg<NH>::BYTES bytes, 16-aligned.  blockDim.x == NT.
+template <int NH, int NT = 256>
 __device__ void stats_tile(const uint8_t *__restrict__ R, int pitch, int W, int H, int2 *__restrict__ out,
                            int opitch, int bx, int by, uint8_t *sm) {
     constexpr int WIN = 2 * NH + 1, N = WIN * WIN;
     using C = StatsCfg<NH>;
     constexpr int SC = C::SC, SR = C::SR, VP = C::VP, XO = C::XO, SB = C::SB;
     static_assert(NH <= APY && XO <= APX, "windows inside the apron");
+    static_assert(NT % 32 == 0 && 256 % NT == 0, "thread count");
     uint32_t (*vp)[VP] = reinterpret_cast<uint32_t (*)[VP]>(sm + C::OFF_VP);   // q | s << 20 per column window
     int2 (*so)[C::SOP] = reinterpret_cast<int2 (*)[C::SOP]>(sm + C::OFF_SO);
     const int x0 = bx * ST_TX, y0 = by * ST_TY, tid = threadIdx.x;
     {
-        constexpr int NWR = SB / 4, NWT = SR * NWR, T = (NWT + 255) / 256;
+        constexpr int NWR = SB / 4, NWT = SR * NWR, T = (NWT + NT - 1) / NT;
         uint32_t v[T];
 #pragma unroll
         for (int t = 0; t < T; ++t) {
-            const int i = tid + 256 * t, r = i / NWR, w = i - r * NWR;
+            const int i = tid + NT * t, r = i / NWR, w = i - r * NWR;
             const int Y = y0 - NH + r, X = x0 - XO + 4 * w;
             v[t] = (i < NWT && Y < H + APY && X + 3 < W + APX)
                        ? __ldg(reinterpret_cast<const uint32_t *>(R + (ptrdiff_t)Y * pitch + X))
@@ -55,7 +56,7 @@ __device__ void stats_tile(const uint8_t *__restrict__ R, int pitch, int W, int 
         }
 #pragma unroll
         for (int t = 0; t < T; ++t) {
-            const int i = tid + 256 * t;
+            const int i = tid + NT * t;
             if (i < NWT) reinterpret_cast<uint32_t *>(sm)[i] = v[t];
         }
     }
@@ -63,7 +64,7 @@ __device__ void stats_tile(const uint8_t *__restrict__ R, int pitch, int W, int 
     const uint8_t *sb = sm + (XO - NH);
     __syncthreads();
     // vertical: column c, rows 8g .. 8g+7
-    for (int i = tid; i < SC * (ST_TY / 8); i += 256) {
+    for (int i = tid; i < SC * (ST_TY / 8); i += NT) {
         const int g = i / SC, c = i - g * SC;
         uint32_t s = 0, q = 0;
 #pragma unroll
@@ -85,8 +86,8 @@ __device__ void stats_tile(const uint8_t *__restrict__ R, int pitch, int W, int 
     __syncthreads();
     // horizontal: row r, columns 8g .. 8g+7 (256 items; the odd packed-sum row stride and the
     // padded output stride keep a warp's 32 rows on distinct banks)
-    {
-        const int r = tid & 31, g = tid >> 5;      // a warp: one segment of 32 rows
+    for (int g = tid >> 5; g < 8; g += NT / 32) {
+        const int r = tid & 31;                    // a warp: one segment of 32 rows
         const uint32_t *row = &vp[r][8 * g];
         int s = 0, q = 0;
 #pragma unroll
@@ -106,8 +107,8 @@ __device__ void stats_tile(const uint8_t *__restrict__ R, int pitch, int W, int 
     }
     __syncthreads();
 #pragma unroll
-    for (int t = 0; t < ST_TX * ST_TY / 256; ++t) {
-        const int i = tid + 256 * t, r = i / ST_TX, c = i % ST_TX;
+    for (int t = 0; t < ST_TX * ST_TY / NT; ++t) {
+        const int i = tid + NT * t, r = i / ST_TX, c = i % ST_TX;
         if (y0 + r < H && x0 + c < W) out[(size_t)(y0 + r) * opitch + x0 + c] = so[r][c];
     }
 }
