@@ -93,6 +93,40 @@ def test_candidate_count_identity(oracle_mod):
     assert evf == sum(min(dk - 1, x) + 1 for x in range(33)) * 21
 
 
+def test_exact_ties_go_to_the_smallest_candidate(oracle_mod):
+    # Tie-break reading: among candidates with equal rho the smallest z wins.  Exact ties
+    # built two ways: (1) a flat left window has rho = 0 for every candidate; (2) a right
+    # image periodic along rows with period 4 and a left image equal to it shifted by 1
+    # column give byte-identical right windows at z = 1, 5, 9, ..., so rho = 1 exactly at
+    # each of them.
+    rng = np.random.default_rng(31)
+    h, w, n, dk = 12, 40, 1, 16
+    tile = rng.integers(0, 256, (h, 4)).astype(np.uint8)
+    b = np.tile(tile, (1, w // 4))
+    a = np.roll(b, 1, axis=1)
+    a[:, :8] = 77                                            # flat left windows for x <= 6
+    d, c, c2, _ = oracle_mod.match_level(a, b, n, dk)
+    flat = np.zeros((h, w), bool)
+    flat[:, :7] = True
+    assert np.all(d[flat] == 0) and np.all(c[flat] == 0.0)
+    assert np.all(c2[:, 1:7] == 0.0)                         # every candidate ties at 0
+    per = np.zeros((h, w), bool)
+    per[:, 8 + n:w - n] = True                               # left window periodic and inside the image
+    assert np.all(d[per] == 1) and np.all(c[per] == 1.0) and np.all(c2[per] == 1.0)
+    # restricted branch (dhat = 2 * prior): the span decides which of the tied candidates remain
+    prior = np.zeros(((h + 1) // 2, (w + 1) // 2), np.int16)
+    prior[:] = 2                                             # dhat = 4, r = 2: span 2 .. 6 holds z = 5 only
+    d, c, _, _ = oracle_mod.match_level(a, b, n, dk, 2, prior)
+    assert np.all(d[per] == 5) and np.all(c[per] == 1.0)
+    prior[:] = 1                                             # dhat = 2, r = 4: span 0 .. 6 holds z = 1 and 5
+    d, c, c2, _ = oracle_mod.match_level(a, b, n, dk, 4, prior)
+    assert np.all(d[per] == 1) and np.all(c2[per] == 1.0)
+    prior[:] = 3                                             # dhat = 6, r = 1: span 5 .. 7, flat pixels clip it
+    d, _, _, _ = oracle_mod.match_level(a, b, n, dk, 1, prior)
+    assert np.all(d[per] == 5)
+    assert np.all(d[:, 6] == 5) and np.all(d[:, 1:5] == np.arange(1, 5) - 1)
+
+
 def _interior_one_region(sc, n):
     """Left pixels whose whole window lies in one region with one disparity, is visible,
     and whose matched right window lies inside the image: there the warped right window is
@@ -140,18 +174,22 @@ def test_k1_is_flat_matching(oracle_mod):
     assert out["evals"] == ev
 
 
-def test_hierarchy_composes_levels_and_priors_are_admissible(oracle_mod):
+@pytest.mark.parametrize("D", [32, 27])
+def test_hierarchy_composes_levels_and_priors_are_admissible(oracle_mod, D):
+    # D = 27 is not a multiple of 2^(K-1): the levels search D_k = ceil(D / 2^k) = 27, 14, 7
+    # candidates (Sec. III), written out here rather than taken from the oracle
     sc = scenes.make_pair(scenes.SPECS["small_320x240"], 4)
     a, b = sc.left[:100, :200].copy(), sc.right[:100, :200].copy()
-    D, K, w, r = 32, 3, 5, 2
+    K, w, r = 3, 5, 2
+    dks = [D, (D + 1) // 2, (D + 3) // 4]
     out = oracle_mod.disparity(a, b, D, K, w, r)
     pa, pb = oracle_mod.pyramid(a, K), oracle_mod.pyramid(b, K)
-    d, c, c2, ev = oracle_mod.match_level(pa[K - 1], pb[K - 1], w // 2, oracle_mod.level_disp(D, K - 1))
+    d, c, c2, ev = oracle_mod.match_level(pa[K - 1], pb[K - 1], w // 2, dks[K - 1])
     np.testing.assert_array_equal(out["d"][K - 1], d)
     total = ev
     for k in range(K - 2, -1, -1):
         prior = out["d"][k + 1]
-        dk = oracle_mod.level_disp(D, k)
+        dk = dks[k]
         hk, wk = pa[k].shape
         yy, xx = np.mgrid[0:hk, 0:wk]
         dh = 2 * prior[yy // 2, xx // 2].astype(np.int64)
