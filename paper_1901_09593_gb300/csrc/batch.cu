@@ -2,7 +2,7 @@
 // levels in one persistent launch (the hierarchical pass of Sec. III, Fig. 1, per pair).
 //
 // Work queue.  Each pair's pass is a chain of stages (the host's per-pair stage table):
-//   pyramid          fused groups of up to 3 reduce levels (pyramid_fused.cuh), 16 x 8 tiles
+//   pyramid          fused groups of up to 3 reduce levels (pyramid_fused.cuh), 16 x 4 tiles
 //                    of the group's coarsest level per image; a plain band copy when K = 1
 //   coarsest level   full-range search at level K-1 (Eq. 3-4): the small-level tile
 //                    (zncc_coarse_tile.cuh) for D_k <= 64, else the full-range tile
@@ -54,8 +54,9 @@ constexpr int BT_MAXS = BT_MAXG + 2 + BT_MAXK;              // stages per pair
 constexpr int BT_THREADS = 128;
 // Two builds of the kernel: with the full-range tile (128 registers; its ~57 KB footprint
 // allows 3 CTAs per SM) for batches whose coarsest levels exceed BT_COARSE_DK candidates, and
-// without it (64 registers: 8 CTAs per SM) otherwise.  128-thread CTAs (restricted items on
-// 32 x 8 tiles) give each SM twice the independent CTAs of 256-thread ones.
+// without it (64 registers; up to 8 CTAs per SM, 7 by the statistics tile's shared memory)
+// otherwise.  128-thread CTAs (restricted items on 32 x 8 tiles) give each SM about twice the
+// independent CTAs of 256-thread ones.
 constexpr int BT_CTAS_FULL = 4, BT_CTAS_LEAN = 8;
 constexpr int BT_BAND = 16;          // apron rows per copy item (K = 1)
 constexpr int BT_MAX_NH = 4;         // windows up to 9 x 9
