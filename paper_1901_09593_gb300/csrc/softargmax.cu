@@ -459,12 +459,16 @@ cudaError_t sa_dispatch(int nh, const SaArgs &a, bool bwd, float *gL, float *gR,
     }
 }
 
+bool sa_sizes_ok(int B, int H, int W, int window, int ndisp) {
+    if (B < 1 || B > 65535 || H < 1 || H > 16384 || W < 1 || W > 16384) return false;
+    if (window < 3 || window > 9 || (window & 1) == 0) return false;
+    return ndisp >= 1 && ndisp <= 256;
+}
+
 msbm_status sa_validate(const float *L, const float *R, int B, int H, int W, int window, int ndisp, float T,
                         float eps) {
     if (!L || !R) return MSBM_ERR_INVALID_ARG;
-    if (B < 1 || B > 65535 || H < 1 || H > 16384 || W < 1 || W > 16384) return MSBM_ERR_INVALID_ARG;
-    if (window < 3 || window > 9 || (window & 1) == 0) return MSBM_ERR_INVALID_ARG;
-    if (ndisp < 1 || ndisp > 256) return MSBM_ERR_INVALID_ARG;
+    if (!sa_sizes_ok(B, H, W, window, ndisp)) return MSBM_ERR_INVALID_ARG;
     if (!(T > 0.f) || !(eps >= 0.f) || !isfinite(T) || !isfinite(eps)) return MSBM_ERR_INVALID_ARG;
     return MSBM_OK;
 }
@@ -508,7 +512,7 @@ msbm_status msbm_zncc_softargmax_fwd(const float *d_left, const float *d_right, 
 
 size_t msbm_zncc_softargmax_workspace_bytes(int32_t batch, int32_t height, int32_t width, int32_t window,
                                             int32_t ndisp) {
-    if (batch < 1 || height < 1 || width < 1 || window < 3 || ndisp < 1) return 0;
+    if (!sa_sizes_ok(batch, height, width, window, ndisp)) return 0;
     return sa_workspace(batch, height, width, window, ndisp).total;
 }
 

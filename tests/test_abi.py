@@ -92,3 +92,96 @@ def test_context_fails_loudly_when_library_missing(tmp_path):
             _lib.load(str(tmp_path / "missing.so"))
     finally:
         _lib._lib = saved
+
+
+def _no_gpu():
+    torch = pytest.importorskip("torch")
+    return not torch.cuda.is_available()
+
+
+# non-null placeholders: these calls reject their arguments before touching any pointer
+_FAKE = ctypes.c_void_p(4096)
+
+
+@pytest.mark.parametrize("field,value", [
+    ("width", 0), ("height", 16385), ("max_disp", 0), ("max_disp", 4097), ("levels", 0),
+    ("levels", 13), ("window", 11), ("window", 6), ("radius", 17), ("flags", 4)])
+def test_batch_create_rejects_bad_pair_params(lib, field, value):
+    from paper_1901_09593_gb300 import _lib
+    pairs = (_lib.msbm_params * 3)(*[_lib.msbm_params(64 + 32 * i, 48, 16, 2, 5, 2, 0) for i in range(3)])
+    setattr(pairs[1], field, value)
+    out = ctypes.c_void_p(123)
+    assert lib.msbm_batch_create(pairs, 3, None, None, None, ctypes.byref(out)) == _lib.MSBM_ERR_INVALID_ARG
+    assert out.value is None
+
+
+def test_batch_create_rejects_bad_counts_and_tuning(lib):
+    from paper_1901_09593_gb300 import _lib
+    pairs = (_lib.msbm_params * 2)(*[_lib.msbm_params(64, 48, 16, 2, 5, 2, 0) for _ in range(2)])
+    out = ctypes.c_void_p()
+    bad = _lib.MSBM_ERR_INVALID_ARG
+    assert lib.msbm_batch_create(pairs, 0, None, None, None, ctypes.byref(out)) == bad
+    assert lib.msbm_batch_create(pairs, 4097, None, None, None, ctypes.byref(out)) == bad
+    assert lib.msbm_batch_create(None, 2, None, None, None, ctypes.byref(out)) == bad
+    assert lib.msbm_batch_create(pairs, 2, None, None, None, None) == bad
+    sx = (ctypes.c_int32 * 2)(1, 3)
+    assert lib.msbm_batch_create(pairs, 2, sx, None, None, ctypes.byref(out)) == bad
+    zb = (ctypes.c_int32 * 2)(0, 48)
+    assert lib.msbm_batch_create(pairs, 2, None, zb, None, ctypes.byref(out)) == bad
+    if _no_gpu():
+        ok_sx, ok_zb = (ctypes.c_int32 * 2)(1, 2), (ctypes.c_int32 * 2)(0, 64)
+        assert lib.msbm_batch_create(pairs, 2, ok_sx, ok_zb, None, ctypes.byref(out)) == _lib.MSBM_ERR_UNSUPPORTED
+    assert lib.msbm_batch_destroy(None) == _lib.MSBM_OK
+
+
+def test_softargmax_workspace_bytes_formula_and_invalid_sizes(lib):
+    # the backward's workspace: one float per (image, pixel, candidate) and six floats per
+    # pixel, each part rounded up to 256 bytes
+    al = lambda v: (v + 255) // 256 * 256
+    for b, h, w, win, nd in [(1, 5, 9, 3, 4), (8, 480, 640, 5, 64), (2, 7, 13, 9, 256)]:
+        want = al(b * nd * h * w * 4) + 6 * al(b * h * w * 4)
+        assert lib.msbm_zncc_softargmax_workspace_bytes(b, h, w, win, nd) == want
+    for args in [(0, 5, 9, 3, 4), (65536, 5, 9, 3, 4), (1, 0, 9, 3, 4), (1, 5, 16385, 3, 4),
+                 (1, 5, 9, 1, 4), (1, 5, 9, 4, 4), (1, 5, 9, 11, 4), (1, 5, 9, 3, 0), (1, 5, 9, 3, 257)]:
+        assert lib.msbm_zncc_softargmax_workspace_bytes(*args) == 0, args
+
+
+@pytest.mark.parametrize("change", ["null_left", "batch", "height", "window_even", "window_big", "ndisp",
+                                    "temperature", "temperature_nan", "eps", "null_out"])
+def test_softargmax_rejects_bad_arguments_before_device_work(lib, change):
+    from paper_1901_09593_gb300 import _lib
+    a = dict(L=_FAKE, R=_FAKE, B=2, H=16, W=24, win=5, nd=8, T=0.1, eps=1e-6, out=_FAKE)
+    a.update({"null_left": {"L": None}, "batch": {"B": 0}, "height": {"H": 16385}, "window_even": {"win": 4},
+              "window_big": {"win": 11}, "ndisp": {"nd": 257}, "temperature": {"T": 0.0},
+              "temperature_nan": {"T": float("nan")}, "eps": {"eps": -1.0}, "null_out": {"out": None}}[change])
+    st = lib.msbm_zncc_softargmax_fwd(a["L"], a["R"], a["B"], a["H"], a["W"], a["win"], a["nd"], a["T"], a["eps"],
+                                      a["out"], _FAKE, _FAKE, None)
+    assert st == _lib.MSBM_ERR_INVALID_ARG
+    st = lib.msbm_zncc_softargmax_bwd(a["L"], a["R"], a["B"], a["H"], a["W"], a["win"], a["nd"], a["T"], a["eps"],
+                                      _FAKE, _FAKE, _FAKE, _FAKE, a["out"], _FAKE, _FAKE, 1 << 30, None)
+    assert st == _lib.MSBM_ERR_INVALID_ARG
+
+
+def test_softargmax_backward_checks_its_workspace(lib):
+    from paper_1901_09593_gb300 import _lib
+    need = lib.msbm_zncc_softargmax_workspace_bytes(1, 8, 16, 3, 4)
+    args = [_FAKE, _FAKE, 1, 8, 16, 3, 4, 0.1, 0.0, _FAKE, _FAKE, _FAKE, _FAKE, _FAKE, _FAKE]
+    assert lib.msbm_zncc_softargmax_bwd(*args, None, need, None) == _lib.MSBM_ERR_INVALID_ARG
+    assert lib.msbm_zncc_softargmax_bwd(*args, _FAKE, need - 1, None) == _lib.MSBM_ERR_INVALID_ARG
+    assert lib.msbm_zncc_softargmax_bwd(*args, ctypes.c_void_p(4096 + 128), need, None) == _lib.MSBM_ERR_ALIGNMENT
+
+
+def test_noalloc_rejects_bad_arguments_and_oversized_images_before_device_work(lib):
+    from paper_1901_09593_gb300 import _lib
+    f = lib.msbm_flat_disparity_noalloc
+    bad = _lib.MSBM_ERR_INVALID_ARG
+    assert f(None, _FAKE, 64, 64, 48, 16, 5, _FAKE, None, None, None) == bad
+    assert f(_FAKE, _FAKE, 64, 64, 48, 16, 5, None, None, None, None) == bad
+    assert f(_FAKE, _FAKE, 63, 64, 48, 16, 5, _FAKE, None, None, None) == bad       # pitch < width
+    assert f(_FAKE, _FAKE, 64, 64, 48, 0, 5, _FAKE, None, None, None) == bad
+    assert f(_FAKE, _FAKE, 64, 64, 48, 4097, 5, _FAKE, None, None, None) == bad
+    assert f(_FAKE, _FAKE, 64, 64, 48, 16, 15, _FAKE, None, None, None) == bad
+    assert f(_FAKE, _FAKE, 64, 64, 48, 16, 4, _FAKE, None, None, None) == bad
+    assert f(_FAKE, _FAKE, 16385, 16385, 48, 16, 5, _FAKE, None, None, None) == bad
+    # two apron buffers of round_up(W + 32, 128) x (H + 16) bytes must fit the 16 MiB array
+    assert f(_FAKE, _FAKE, 4096, 4096, 2160, 64, 5, _FAKE, None, None, None) == _lib.MSBM_ERR_UNSUPPORTED
