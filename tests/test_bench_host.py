@@ -71,3 +71,12 @@ def test_measured_traffic_only_for_recorded_kernels():
     rec = bench.MEASURED_TRAFFIC["restricted_level0"]
     got = bench.measured_traffic("restricted_level0")
     assert got is None or got == rec["bytes"]
+
+
+def test_reference_rows_bound_the_reference_run():
+    # whole frames while they fit the budget
+    assert bench.reference_rows(1000, 4, 0.2, 100, 150.0) == 1000
+    # otherwise a band from the top, a multiple of 2^(K-1) rows, sized to the budget
+    rows = bench.reference_rows(1000, 4, 0.2, 2000, 150.0)
+    assert rows % 8 == 0 and rows <= 1000 * 150.0 / (2000 * 0.2) and rows > 1000 * 150.0 / (2000 * 0.2) - 8
+    assert bench.reference_rows(1000, 4, 5.0, 10000, 1.0) == 8
