@@ -124,9 +124,10 @@ def test_selective_median_matches_numpy(oracle_mod):
 
 
 def test_full_method_driver_composes_the_steps(oracle_mod):
+    # alpha and beta differ here so that a gate fed the other threshold shows
     sc = scenes.make_pair(scenes.SPECS["small_320x240"], 6)
     a, b = sc.left[:96, :160].copy(), sc.right[:96, :160].copy()
-    D, K, w, r, al, be = 32, 3, 5, 2, 0.9, 0.9
+    D, K, w, r, al, be = 32, 3, 5, 2, 0.8, 0.9
     plain = oracle_mod.disparity(a, b, D, K, w, r)
     f0 = oracle_mod.disparity_full(a, b, D, K, w, r, al, be, 0)
     for k in range(K):
@@ -134,16 +135,28 @@ def test_full_method_driver_composes_the_steps(oracle_mod):
     assert f0["evals"] == plain["evals"]
     full = oracle_mod.disparity_full(a, b, D, K, w, r, al, be, oracle_mod.FULL_METHOD)
     pa, pb = oracle_mod.pyramid(a, K), oracle_mod.pyramid(b, K)
-    d, c, c2, _ = oracle_mod.match_level(pa[K - 1], pb[K - 1], w // 2, oracle_mod.level_disp(D, K - 1))
-    d, c, c2, _ = oracle_mod.alpha_refine(pa[K - 1], pb[K - 1], w // 2, oracle_mod.level_disp(D, K - 1), al, d, c, c2)
+    dkc = oracle_mod.level_disp(D, K - 1)
+    d, c, c2, evals = oracle_mod.match_level(pa[K - 1], pb[K - 1], w // 2, dkc)
+    d, c, c2, refined = oracle_mod.alpha_refine(pa[K - 1], pb[K - 1], w // 2, dkc, al, d, c, c2)
+    assert 0 < refined.sum() < refined.size
+    # alpha refinement evaluates every candidate of the pixel at each neighbour inside the image
+    hk, wk = refined.shape
+    for y, x in zip(*np.nonzero(refined)):
+        nb = sum(1 for m in range(y - 1, y + 2) for q in range(x - 1, x + 2) if 0 <= m < hk and 0 <= q < wk)
+        evals += nb * (min(dkc - 1, x) + 1)
     np.testing.assert_array_equal(full["d"][K - 1], d)
+    between = 0
     for k in range(K - 2, -1, -1):
-        dk, ck, c2k, _, _, _ = oracle_mod.match_level_beta(pa[k], pb[k], w // 2, oracle_mod.level_disp(D, k), r,
-                                                           d, c, be)
+        dk, ck, c2k, ev, _, chat = oracle_mod.match_level_beta(pa[k], pb[k], w // 2, oracle_mod.level_disp(D, k), r,
+                                                               d, c, be)
+        evals += ev
+        between += int(np.sum((ck > al) & (ck <= be))) + int(np.sum((chat > al) & (chat <= be)))
         d = oracle_mod.selective_median(dk, ck, al)
         c = ck
         np.testing.assert_array_equal(full["d"][k], d)
         np.testing.assert_array_equal(full["C"][k], c)
+    assert between > 0                     # the two thresholds select different pixels
+    assert full["evals"] == evals
 
 
 def test_selective_median_improves_the_planted_scene(oracle_mod):

@@ -78,6 +78,15 @@ MUTANTS = [
     ("median_3x3", "3 x 3 median neighbourhood", "for (int m = y - 2; m <= y + 2; ++m)\n                for (int q = x - 2; q <= x + 2; ++q)",
      "for (int m = y - 1; m <= y + 1; ++m)\n                for (int q = x - 1; q <= x + 1; ++q)", 0),
     ("halving_shift", "window halves one level early", "int n = n0 >> k;", "int n = n0 >> (k + 1);", 0),
+    ("beta_axes", "cost prior sampled with x and y swapped", "oracle_bicubic_at(Cprior, Wp, Hp, 0.5 * y, 0.5 * x)",
+     "oracle_bicubic_at(Cprior, Wp, Hp, 0.5 * x, 0.5 * y)", 0),
+    # the full method's driver (Fig. 1 with the gates)
+    ("full_median_beta", "median gated by beta", "oracle_selective_median(dk, ck, Wk, Hk, alpha, tmp);",
+     "oracle_selective_median(dk, ck, Wk, Hk, beta, tmp);", 0),
+    ("full_gate_alpha", "fallback gated by alpha", "beta, dk, ck, c2k, NULL, NULL);", "alpha, dk, ck, c2k, NULL, NULL);", 0),
+    ("full_alpha_evals", "alpha evaluations counted as full 3 x 3", "cnt *= (x > 0) + 1 + (x < Wk - 1);", "cnt *= 3;", 0),
+    ("full_no_halving", "window halving flag ignored", "n = (flags & 8) ? oracle_level_half_width(n0, k) : n0;",
+     "n = n0;", 0),
 ]
 
 
