@@ -65,6 +65,15 @@ MUTANTS = [
      "double db = ac[t] / sq - r_ * bc[t] / (Saa + eps);", 0),
     ("bwd_right_column", "right gradient sent to x + z", "gB[(long)yy * W + clampi(x - z + j, 0, W - 1)]",
      "gB[(long)yy * W + clampi(x + j, 0, W - 1)]", 0),
+    ("sa_fwd_inadmissible", "soft-argmax over candidates past the left border",
+     "int zmax = ndisp - 1 < x ? ndisp - 1 : x;", "int zmax = ndisp - 1;", 0),
+    ("sa_bwd_inadmissible", "backward over candidates past the left border",
+     "int zmax = ndisp - 1 < x ? ndisp - 1 : x;", "int zmax = ndisp - 1;", 1),
+    ("sa_mean_biased", "window mean over N - 1", "ma /= N; mb /= N;", "ma /= N - 1; mb /= N - 1;", 0),
+    ("bwd_p_without_T", "backward softmax without the temperature", "double p = exp(rho[z] / T - m) / s;",
+     "double p = exp(rho[z] - m) / s;", 0),
+    ("bwd_left_mirrored", "left gradient sent to the mirrored window column",
+     "gA[(long)yy * W + clampi(x + j, 0, W - 1)] += grho * da;", "gA[(long)yy * W + clampi(x - j, 0, W - 1)] += grho * da;", 0),
     # gated steps (Sec. III-B, III-C, III-D)
     ("cubic_kernel", "cubic kernel with a = -3/4", "if (t < 1.0) return (1.5 * t - 2.5) * t * t + 1.0;",
      "if (t < 1.0) return (1.25 * t - 2.25) * t * t + 1.0;", 0),
