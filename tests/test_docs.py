@@ -1,0 +1,39 @@
+"""The design notes' file map names only files that exist (CPU)."""
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+PKG = os.path.join(ROOT, "paper_1901_09593_gb300")
+
+
+def _file_map_paths():
+    txt = open(os.path.join(ROOT, "DESIGN.md"), encoding="utf-8").read()
+    sec = txt[txt.index("## 14."):]
+    return sorted(set(re.findall(r"`([A-Za-z0-9_./*-]+\.(?:py|cu|cuh|h|c|md|txt))`", sec)))
+
+
+def _exists(p):
+    for base in (ROOT, PKG, os.path.join(PKG, "csrc")):
+        full = os.path.join(base, p)
+        if "*" in p:
+            import glob
+            if glob.glob(full):
+                return True
+        elif os.path.exists(full):
+            return True
+    return False
+
+
+def test_file_map_names_existing_files():
+    paths = _file_map_paths()
+    assert len(paths) > 20
+    missing = [p for p in paths if not _exists(p)]
+    assert not missing, missing
+
+
+def test_every_source_file_is_in_the_file_map():
+    named = " ".join(_file_map_paths())
+    srcs = [f for f in os.listdir(os.path.join(PKG, "csrc")) if f.endswith((".cu", ".cuh", ".h"))]
+    srcs += [f for f in os.listdir(PKG) if f.endswith(".py") and f != "__init__.py"]
+    unnamed = [f for f in srcs if f not in named]
+    assert not unnamed, unnamed
