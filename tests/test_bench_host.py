@@ -80,3 +80,17 @@ def test_reference_rows_bound_the_reference_run():
     rows = bench.reference_rows(1000, 4, 0.2, 2000, 150.0)
     assert rows % 8 == 0 and rows <= 1000 * 150.0 / (2000 * 0.2) and rows > 1000 * 150.0 / (2000 * 0.2) - 8
     assert bench.reference_rows(1000, 4, 5.0, 10000, 1.0) == 8
+
+
+def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
+    # under torchrun every rank but 0 exits at once, printing nothing
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setenv("LOCAL_RANK", "1")
+    assert bench.main(["--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "3"]) == 0
+    assert capsys.readouterr().out == ""
+
+
+def test_warmup_below_three_is_refused():
+    with pytest.raises(SystemExit):
+        bench.main(["--warmup", "2"])
