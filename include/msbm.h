@@ -40,7 +40,8 @@ extern "C" {
 typedef enum msbm_status {
     MSBM_OK = 0,
     MSBM_ERR_INVALID_ARG = 1,   /* a size, pointer or parameter is out of range */
-    MSBM_ERR_ALIGNMENT = 2,     /* reserved: no entry point currently requires alignment */
+    MSBM_ERR_ALIGNMENT = 2,     /* a buffer misses its required alignment (the soft-argmax
+                                   backward's workspace, 256 bytes) */
     MSBM_ERR_OOM = 3,           /* device or host allocation failed */
     MSBM_ERR_CUDA = 4,          /* a CUDA runtime call or launch failed */
     MSBM_ERR_TIMEOUT = 5,       /* a bounded device wait gave up (see MSBM_FLAG_TEST_TIMEOUT) */
