@@ -105,28 +105,3 @@ def __getattr__(name):
             _FN = _make_function()
         return _FN
     raise AttributeError(name)
-
-
-def smoke_check() -> None:
-    """Tiny forward + backward on cuda:0 against the FP64 oracle (used by smoke())."""
-    import numpy as np
-    import oracle
-    torch = _torch()
-    rng = np.random.default_rng(0)
-    L = rng.random((1, 12, 40))
-    R = rng.random((1, 12, 40))
-    win, nd, T = 5, 8, 0.05
-    eps = default_eps(win)
-    lt = torch.tensor(L, dtype=torch.float32, device="cuda", requires_grad=True)
-    rt = torch.tensor(R, dtype=torch.float32, device="cuda", requires_grad=True)
-    fn = __getattr__("ZnccSoftArgmax")
-    d = fn.apply(lt, rt, win, nd, T, eps)
-    g = rng.standard_normal(L.shape)
-    d.backward(torch.tensor(g, dtype=torch.float32, device="cuda"))
-    ref = oracle.softargmax_fwd(L.astype(np.float32).astype(np.float64), R.astype(np.float32).astype(np.float64),
-                                win // 2, nd, T, eps)
-    gl, gr = oracle.softargmax_bwd(L.astype(np.float32).astype(np.float64),
-                                   R.astype(np.float32).astype(np.float64), win // 2, nd, T, eps, g)
-    assert np.abs(d.detach().cpu().numpy() - ref).max() < 1e-3
-    rel = np.abs(lt.grad.cpu().numpy() - gl).max() / max(np.abs(gl).max(), 1e-12)
-    assert rel < 1e-2, rel

@@ -1,4 +1,5 @@
-"""The design notes' file map names only files that exist (CPU)."""
+"""Repository layout rules (CPU): the design notes' file map names only files that exist and
+covers every source; the product package never uses the oracle."""
 import os
 import re
 
@@ -37,3 +38,17 @@ def test_every_source_file_is_in_the_file_map():
     srcs += [f for f in os.listdir(PKG) if f.endswith(".py") and f != "__init__.py"]
     unnamed = [f for f in srcs if f not in named]
     assert not unnamed, unnamed
+
+
+def test_product_package_never_uses_the_oracle():
+    # the oracle is test infrastructure: nothing under the package imports, loads or builds it
+    hits = []
+    for dirpath, _, files in os.walk(PKG):
+        if "_build" in dirpath or "__pycache__" in dirpath:
+            continue
+        for fn in files:
+            if fn.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, fn), encoding="utf-8").read()
+                if re.search(r"^\s*(import oracle|from oracle\b)|liboracle|msbm_oracle", txt, re.M):
+                    hits.append(fn)
+    assert not hits, hits
