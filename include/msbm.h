@@ -80,8 +80,10 @@ typedef struct msbm_params {
                               level 0's with MSBM_FLAG_WINDOW_HALVING                      */
     int32_t radius;        /* r, 0..16: refinement candidates dhat-r .. dhat+r              */
     uint32_t flags;        /* MSBM_FLAG_*                                                   */
-    float alpha;           /* threshold of ALPHA_REFINE and SELECTIVE_MEDIAN (paper: 0.9)  */
-    float beta;            /* threshold of BETA_FALLBACK (paper: 0.9)                      */
+    float alpha;           /* threshold of ALPHA_REFINE and SELECTIVE_MEDIAN (paper: 0.9);
+                              inside (-2, 2) when either flag is set (NaN is rejected)     */
+    float beta;            /* threshold of BETA_FALLBACK (paper: 0.9); inside (-2, 2) when
+                              that flag is set                                             */
 } msbm_params;
 
 typedef struct msbm_ctx msbm_ctx;

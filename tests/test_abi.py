@@ -185,3 +185,19 @@ def test_noalloc_rejects_bad_arguments_and_oversized_images_before_device_work(l
     assert f(_FAKE, _FAKE, 16385, 16385, 48, 16, 5, _FAKE, None, None, None) == bad
     # two apron buffers of round_up(W + 32, 128) x (H + 16) bytes must fit the 16 MiB array
     assert f(_FAKE, _FAKE, 4096, 4096, 2160, 64, 5, _FAKE, None, None, None) == _lib.MSBM_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("flags,alpha,beta,ok", [
+    (4, float("nan"), 0.9, False), (16, 2.0, 0.9, False), (8, 0.9, -2.5, False), (8, 0.9, float("nan"), False),
+    (0, float("nan"), float("nan"), True), (28, 0.9, 0.9, True), (4, -1.99, 5.0, True)])
+def test_create_checks_the_thresholds_its_flags_use(lib, flags, alpha, beta, ok):
+    from paper_1901_09593_gb300 import _lib
+    p = _lib.msbm_params(64, 48, 16, 2, 5, 2, flags, alpha, beta)
+    out = ctypes.c_void_p()
+    st = lib.msbm_create(ctypes.byref(p), None, ctypes.byref(out))
+    if not ok:
+        assert st == _lib.MSBM_ERR_INVALID_ARG
+    else:
+        assert st != _lib.MSBM_ERR_INVALID_ARG
+        if st == _lib.MSBM_OK:
+            lib.msbm_destroy(out)
