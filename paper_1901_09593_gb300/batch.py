@@ -16,6 +16,13 @@ def _torch():
     return torch
 
 
+def _same(a, b) -> bool:
+    """Same list of the same tensor objects (or both None)."""
+    if a is None or b is None:
+        return a is b
+    return len(a) == len(b) and all(x is y for x, y in zip(a, b))
+
+
 class Batch:
     """specs: iterable of (width, height, max_disp, levels, window, radius)."""
 
@@ -67,6 +74,8 @@ class Batch:
             raise ValueError(f"expected {n} pairs")
         if d_outs is None:
             d_outs, cost_outs = self.alloc_outputs(with_cost=True)
+        else:
+            self._check_outs(d_outs, cost_outs)
         for i, (w, h, *_r) in enumerate(self.specs):
             for t, nm in ((lefts[i], "left"), (rights[i], "right")):
                 if not t.is_cuda or t.dtype != torch.uint8 or tuple(t.shape) != (h, w) or t.stride(1) != 1:
@@ -82,6 +91,26 @@ class Batch:
         _lib.check(self._lib.msbm_batch_run(self._b, L, R, pitch, D, C), "msbm_batch_run")
         self._keep = (lefts, rights, d_outs, cost_outs)
         return d_outs, cost_outs
+
+    def _check_outs(self, d_outs, cost_outs):
+        """The caller's output maps: dense CUDA tensors of each pair's level-0 size (the C ABI
+        takes bare pointers).  The tensors of the previous call are not checked again."""
+        torch = _torch()
+        last = getattr(self, "_outs_ok", None)
+        if last is not None and _same(last[0], d_outs) and _same(last[1], cost_outs):
+            return
+        n = len(self.specs)
+        if len(d_outs) != n or (cost_outs is not None and len(cost_outs) != n):
+            raise ValueError(f"expected {n} output maps")
+        for i, (w, h, *_r) in enumerate(self.specs):
+            outs = [(d_outs[i], torch.int16, "d_outs")]
+            if cost_outs is not None and cost_outs[i] is not None:
+                outs.append((cost_outs[i], torch.float32, "cost_outs"))
+            for t, dt, nm in outs:
+                if (not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dt or t.shape != (h, w)
+                        or not t.is_contiguous()):
+                    raise ValueError(f"{nm}[{i}] must be a dense CUDA {dt} ({h}, {w}) tensor")
+        self._outs_ok = (list(d_outs), None if cost_outs is None else list(cost_outs))
 
     def sync(self):
         _lib.check(self._lib.msbm_batch_sync(self._b), "msbm_batch_sync")

@@ -23,6 +23,16 @@ def _stream_ptr(device) -> int:
     return int(torch.cuda.current_stream(device).cuda_stream)
 
 
+def _check_map(t, w: int, h: int, dtype, name: str) -> None:
+    """A dense (h, w) CUDA tensor of `dtype`: the C ABI takes such maps as bare pointers and
+    cannot check their size."""
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dtype:
+        raise TypeError(f"{name} must be a CUDA {dtype} tensor")
+    if t.shape != (h, w) or not t.is_contiguous():
+        raise ValueError(f"{name} must be a dense ({h}, {w}) tensor")
+
+
 def _check_image(t, w: int, h: int, name: str) -> int:
     torch = _torch()
     if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.uint8:
@@ -48,6 +58,7 @@ class Context:
                                              ctypes.c_void_p(_stream_ptr(self.device)),
                                              ctypes.byref(self._ctx)), "msbm_create")
         self.width, self.height, self.levels = width, height, levels
+        self._outs_ok = (None, None)     # the caller's output tensors last checked
 
     # -- lifetime ---------------------------------------------------------------------
     def close(self) -> None:
@@ -66,6 +77,18 @@ class Context:
 
     def __exit__(self, *exc):
         self.close()
+
+    def _check_outs(self, d_out, cost_out) -> None:
+        """Level-0 output maps given by the caller; the tensors of the previous call are not
+        checked again (repeated calls with the same outputs stay cheap)."""
+        if d_out is self._outs_ok[0] and cost_out is self._outs_ok[1]:
+            return
+        torch = _torch()
+        if d_out is not None:
+            _check_map(d_out, self.width, self.height, torch.int16, "d_out")
+        if cost_out is not None:
+            _check_map(cost_out, self.width, self.height, torch.float32, "cost_out")
+        self._outs_ok = (d_out, cost_out)
 
     def _bind_stream(self) -> None:
         _lib.check(self._lib.msbm_set_stream(self._ctx, ctypes.c_void_p(_stream_ptr(self.device))))
@@ -133,6 +156,10 @@ class Context:
 
     def alpha_refine(self, level: int, d, cost) -> None:
         """Eq. 5-7 in place on (d, cost) of `level` (pyramid from pyramid())."""
+        torch = _torch()
+        w, h, _ = self.level_shape(level)
+        _check_map(d, w, h, torch.int16, "d")
+        _check_map(cost, w, h, torch.float32, "cost")
         self._bind_stream()
         _lib.check(self._lib.msbm_alpha_refine(self._ctx, level, ctypes.c_void_p(d.data_ptr()),
                                                ctypes.c_void_p(cost.data_ptr())), "msbm_alpha_refine")
@@ -140,6 +167,9 @@ class Context:
     def selective_median(self, level: int, d, cost):
         """Eq. 10: returns the filtered map."""
         torch = _torch()
+        w, h, _ = self.level_shape(level)
+        _check_map(d, w, h, torch.int16, "d")
+        _check_map(cost, w, h, torch.float32, "cost")
         self._bind_stream()
         out = torch.empty_like(d)
         _lib.check(self._lib.msbm_selective_median(self._ctx, level, ctypes.c_void_p(d.data_ptr()),
@@ -152,6 +182,8 @@ class Context:
         torch = _torch()
         self._bind_stream()
         w, h, _ = self.level_shape(level)
+        _check_map(prior, (w + 1) // 2, (h + 1) // 2, torch.int16, "prior")
+        _check_map(cost_prior, (w + 1) // 2, (h + 1) // 2, torch.float32, "cost_prior")
         d = torch.empty((h, w), dtype=torch.int16, device=self.device)
         c = torch.empty((h, w), dtype=torch.float32, device=self.device)
         fb = torch.empty((h, w), dtype=torch.uint8, device=self.device)
@@ -168,6 +200,7 @@ class Context:
         pitch = _check_image(left, self.width, self.height, "left")
         if _check_image(right, self.width, self.height, "right") != pitch:
             raise ValueError("left and right must share a row pitch")
+        self._check_outs(d_out, cost_out)
         if d_out is None:
             d_out = torch.empty((self.height, self.width), dtype=torch.int16, device=self.device)
         if cost_out is None and with_cost:
@@ -204,8 +237,14 @@ class Context:
     def profile_disparity(self, left, right, d_out, cost_out):
         """One pass with per-stage CUDA-event timing; returns the list of milliseconds in
         launch order (pyramid, coarsest full search, restricted levels K-2..0)."""
+        torch = _torch()
         self._bind_stream()
         pitch = _check_image(left, self.width, self.height, "left")
+        if _check_image(right, self.width, self.height, "right") != pitch:
+            raise ValueError("left and right must share a row pitch")
+        _check_map(d_out, self.width, self.height, torch.int16, "d_out")
+        if cost_out is not None:
+            _check_map(cost_out, self.width, self.height, torch.float32, "cost_out")
         n = self.levels + 1
         ms = (ctypes.c_float * n)()
         _lib.check(self._lib.msbm_profile_disparity(
