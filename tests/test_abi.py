@@ -201,3 +201,38 @@ def test_create_checks_the_thresholds_its_flags_use(lib, flags, alpha, beta, ok)
         assert st != _lib.MSBM_ERR_INVALID_ARG
         if st == _lib.MSBM_OK:
             lib.msbm_destroy(out)
+
+
+C_CONSUMER = r"""
+#include <stdio.h>
+#include "msbm.h"
+int main(void) {
+    msbm_params p = {64, 48, 16, 2, 5, 2, 0u, 0.9f, 0.9f};
+    msbm_ctx *ctx = NULL;
+    p.window = 4;   /* even: rejected before any device work */
+    msbm_status s = msbm_create(&p, NULL, &ctx);
+    printf("%d %s %d %d\n", msbm_version() >= 10000, msbm_status_string(s), ctx == NULL,
+           (int)msbm_zncc_softargmax_workspace_bytes(1, 8, 16, 3, 4));
+    return s == MSBM_ERR_INVALID_ARG ? 0 : 1;
+}
+"""
+
+
+def test_header_serves_a_plain_c_program(lib, tmp_path):
+    # the boundary is a C ABI: a C11 program includes the header with every warning an error,
+    # links the library and calls it
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if not gcc:
+        pytest.skip("gcc not available")
+    from paper_1901_09593_gb300 import build
+    src, exe = tmp_path / "consumer.c", tmp_path / "consumer"
+    src.write_text(C_CONSUMER)
+    subprocess.check_call([gcc, "-std=c11", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I",
+                           os.path.join(ROOT, "include"), str(src), "-o", str(exe), build.SO,
+                           "-Wl,-rpath," + os.path.dirname(build.SO)])
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
+    want = (8 * 16 * 4 * 4 + 255) // 256 * 256 + 6 * ((8 * 16 * 4 + 255) // 256 * 256)
+    assert r.stdout.split() == ["1", "invalid", "argument", "1", str(want)], r.stdout
