@@ -52,3 +52,16 @@ def test_product_package_never_uses_the_oracle():
                 if re.search(r"^\s*(import oracle|from oracle\b)|liboracle|msbm_oracle", txt, re.M):
                     hits.append(fn)
     assert not hits, hits
+
+
+def test_profile_summaries_give_their_command():
+    # each ncu summary states the command that made it: clocks left alone, committed files only
+    pdir = os.path.join(ROOT, "profiles")
+    names = [f for f in os.listdir(pdir) if f.endswith(".md") and f != "README.md"]
+    assert names
+    index = open(os.path.join(pdir, "README.md"), encoding="utf-8").read()
+    for fn in names:
+        txt = open(os.path.join(pdir, fn), encoding="utf-8").read()
+        assert "ncu " in txt and "--clock-control none" in txt, fn
+        assert "_work" not in txt, fn
+        assert f"`{fn}`" in index, fn
