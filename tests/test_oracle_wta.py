@@ -208,3 +208,10 @@ def test_hierarchical_recovers_noise_free_scene(oracle_mod):
     ok = _interior_one_region(sc, 2)
     rate = np.mean(out["d"][0][ok] == sc.gt[ok])
     assert rate >= 0.95, rate
+
+
+def test_driver_rejects_invalid_arguments(oracle_mod):
+    a = np.zeros((8, 8), np.uint8)
+    for D, K, w, r in ((0, 1, 3, 0), (8, 0, 3, 0), (8, 1, 4, 0), (8, 1, 3, -1)):
+        with pytest.raises(ValueError):
+            oracle_mod.disparity(a, a, D, K, w, r)
