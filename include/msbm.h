@@ -220,6 +220,12 @@ msbm_status msbm_batch_run(msbm_batch *b, const uint8_t *const *d_lefts,
 /* Wait for the stream; return (and clear) a recorded device error (MSBM_ERR_TIMEOUT). */
 msbm_status msbm_batch_sync(msbm_batch *b);
 msbm_status msbm_batch_eval_count(msbm_batch *b, int64_t *count, int32_t reset);
+/* Copy pair `pair`'s map of level `level` (1 <= level < levels) from the last completed
+ * run into caller device buffers (dense W_k x H_k; cost_out may be NULL), on the batch's
+ * stream.  These are the priors the pair's finer levels searched around (Sec. III-C), so
+ * each level of a batched pair can be checked on its own. */
+msbm_status msbm_batch_level_result(msbm_batch *b, int32_t pair, int32_t level, int16_t *d_out,
+                                    float *cost_out);
 /* Queue length, persistent grid size (CTAs) and number of (pair, stage) segments. */
 msbm_status msbm_batch_info(const msbm_batch *b, int64_t *n_items, int32_t *grid,
                             int32_t *n_segments);
@@ -282,9 +288,11 @@ msbm_status msbm_zncc_softargmax_bwd(const float *d_left, const float *d_right, 
  * apron buffers, (round_up(width + 32, 128) * (height + 16) bytes each, rounded up to 256)
  * plus 256 bytes, exceed MSBM_NOALLOC_SCRATCH_BYTES returns MSBM_ERR_UNSUPPORTED before
  * any work is enqueued (2880 x 1984 fits; 4096 x 2160 does not).
- * The first call on each device resolves the array's device address with
- * cudaGetSymbolAddress (with that device current) and sets kernel attributes; make that
- * first call outside any stream capture.  All calls share the one array and it keeps the
+ * Every call resolves the array's device address in the current context with
+ * cudaGetSymbolAddress and sets the kernel's shared-memory attribute (host calls that
+ * allocate nothing), so a context re-created after cudaDeviceReset is served correctly.
+ * The first call on a device may load the library's device code (CUDA's lazy module
+ * loading); make that first call outside any stream capture.  All calls share the one array and it keeps the
  * last call's contents: calls whose work overlaps on the GPU (on different streams, or
  * from different host threads without ordering) race on it and must be serialised by the
  * caller. */

@@ -64,6 +64,7 @@ SIGNATURES = {
     "msbm_batch_run": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], ctypes.c_int),
     "msbm_batch_sync": ([c_void_p], ctypes.c_int),
     "msbm_batch_eval_count": ([c_void_p, P(ctypes.c_int64), c_int32], ctypes.c_int),
+    "msbm_batch_level_result": ([c_void_p, c_int32, c_int32, c_void_p, c_void_p], ctypes.c_int),
     "msbm_batch_info": ([c_void_p, P(ctypes.c_int64), P(c_int32), P(c_int32)], ctypes.c_int),
     "msbm_batch_destroy": ([c_void_p], ctypes.c_int),
     "msbm_zncc_softargmax_fwd": ([c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_int32,

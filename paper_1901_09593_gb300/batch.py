@@ -112,6 +112,18 @@ class Batch:
                     raise ValueError(f"{nm}[{i}] must be a dense CUDA {dt} ({h}, {w}) tensor")
         self._outs_ok = (list(d_outs), None if cost_outs is None else list(cost_outs))
 
+    def level_result(self, pair: int, level: int):
+        """(d, cost) of `pair` at `level` >= 1 from the last run (device tensors)."""
+        torch = _torch()
+        w, h = self.specs[pair][0], self.specs[pair][1]
+        for _ in range(level):
+            w, h = (w + 1) // 2, (h + 1) // 2
+        d = torch.empty((h, w), dtype=torch.int16, device=self.device)
+        c = torch.empty((h, w), dtype=torch.float32, device=self.device)
+        _lib.check(self._lib.msbm_batch_level_result(self._b, int(pair), int(level), ctypes.c_void_p(d.data_ptr()),
+                                                     ctypes.c_void_p(c.data_ptr())), "msbm_batch_level_result")
+        return d, c
+
     def sync(self):
         _lib.check(self._lib.msbm_batch_sync(self._b), "msbm_batch_sync")
 

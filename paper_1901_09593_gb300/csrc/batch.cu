@@ -665,11 +665,13 @@ msbm_status msbm_batch_run(msbm_batch *b, const uint8_t *const *d_lefts, const u
 
 msbm_status msbm_batch_sync(msbm_batch *b) {
     if (!b) return MSBM_ERR_INVALID_ARG;
-    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return MSBM_ERR_CUDA;
     int err = 0;
-    if (cudaMemcpy(&err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return MSBM_ERR_CUDA;
+    if (cudaMemcpyAsync(&err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream) != cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess)
+        return MSBM_ERR_CUDA;
     if (err) {
-        cudaMemset(b->d_err, 0, sizeof(int));
+        // cleared in the batch stream's order (see msbm_sync)
+        if (cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream) != cudaSuccess) return MSBM_ERR_CUDA;
         return static_cast<msbm_status>(err);
     }
     return MSBM_OK;
@@ -677,12 +679,26 @@ msbm_status msbm_batch_sync(msbm_batch *b) {
 
 msbm_status msbm_batch_eval_count(msbm_batch *b, int64_t *count, int32_t reset) {
     if (!b || !count) return MSBM_ERR_INVALID_ARG;
-    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return MSBM_ERR_CUDA;
     unsigned long long v = 0;
-    if (cudaMemcpy(&v, b->d_evals, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return MSBM_ERR_CUDA;
+    if (cudaMemcpyAsync(&v, b->d_evals, sizeof(v), cudaMemcpyDeviceToHost, b->stream) != cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess)
+        return MSBM_ERR_CUDA;
     *count = static_cast<int64_t>(v);
-    if (reset && cudaMemset(b->d_evals, 0, sizeof(v)) != cudaSuccess) return MSBM_ERR_CUDA;
+    if (reset && cudaMemsetAsync(b->d_evals, 0, sizeof(v), b->stream) != cudaSuccess) return MSBM_ERR_CUDA;
     return MSBM_OK;
+}
+
+msbm_status msbm_batch_level_result(msbm_batch *b, int32_t pair, int32_t level, int16_t *d_out,
+                                    float *cost_out) {
+    if (!b || pair < 0 || pair >= b->n || !d_out) return MSBM_ERR_INVALID_ARG;
+    const BPair &P = b->pairs[pair];
+    if (level < 1 || level >= P.K) return MSBM_ERR_INVALID_ARG;
+    const BLevel &l = P.lv[level];
+    const size_t n = (size_t)l.W * l.H;
+    cudaError_t e = cudaMemcpyAsync(d_out, l.d, n * sizeof(int16_t), cudaMemcpyDeviceToDevice, b->stream);
+    if (e == cudaSuccess && cost_out)
+        e = cudaMemcpyAsync(cost_out, l.c, n * sizeof(float), cudaMemcpyDeviceToDevice, b->stream);
+    return cst(e);
 }
 
 msbm_status msbm_batch_info(const msbm_batch *b, int64_t *n_items, int32_t *grid, int32_t *n_segments) {

@@ -622,7 +622,9 @@ msbm_status msbm_sync(msbm_ctx *ctx) {
     if (e != cudaSuccess) return MSBM_ERR_CUDA;
     const int err = *ctx->h_err;
     if (err != 0) {
-        cudaMemset(ctx->d_err, 0, sizeof(int));
+        // cleared in the context stream's order, so it cannot wipe a status that work
+        // enqueued on that stream after this call records
+        if (cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream) != cudaSuccess) return MSBM_ERR_CUDA;
         return static_cast<msbm_status>(err);
     }
     return MSBM_OK;
@@ -630,11 +632,12 @@ msbm_status msbm_sync(msbm_ctx *ctx) {
 
 msbm_status msbm_eval_count(msbm_ctx *ctx, int64_t *count, int32_t reset) {
     if (!ctx || !count) return MSBM_ERR_INVALID_ARG;
-    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return MSBM_ERR_CUDA;
     unsigned long long v = 0;
-    if (cudaMemcpy(&v, ctx->d_evals, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return MSBM_ERR_CUDA;
+    if (cudaMemcpyAsync(&v, ctx->d_evals, sizeof(v), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+        cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+        return MSBM_ERR_CUDA;
     *count = static_cast<int64_t>(v);
-    if (reset && cudaMemset(ctx->d_evals, 0, sizeof(v)) != cudaSuccess) return MSBM_ERR_CUDA;
+    if (reset && cudaMemsetAsync(ctx->d_evals, 0, sizeof(v), ctx->stream) != cudaSuccess) return MSBM_ERR_CUDA;
     return MSBM_OK;
 }
 

@@ -31,9 +31,7 @@ static __device__ __align__(256) uint8_t g_noalloc_scratch[MSBM_NOALLOC_SCRATCH_
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
-uint8_t *g_scratch_ptr[kMaxDevices] = {nullptr};   // device address per device, once set up
-int g_num_sms[kMaxDevices] = {0};
-
+int g_num_sms[kMaxDevices] = {0};   // per device, once its architecture has been checked
 typedef CUresult (*EncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                              const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
                              CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
@@ -64,22 +62,26 @@ bool encode_map(CUtensorMap *m, uint8_t *base, int pitch, int rows, int box_w, i
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// One-time set-up per device, with that device current: resolve the scratch array's
-// device address (host code only sees a stand-in for the symbol) and opt the full-range
-// kernels in to their dynamic shared memory.
-msbm_status setup_device(int dev) {
+// Per-device checks, once: the architecture and the SM count (neither changes while the
+// process lives).
+msbm_status check_device(int dev) {
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (g_scratch_ptr[dev]) return MSBM_OK;
+    if (g_num_sms[dev]) return MSBM_OK;
     cudaDeviceProp prop;
     if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return MSBM_ERR_CUDA;
     if (!(prop.major == 10 && prop.minor == 3) || !encode_entry()) return MSBM_ERR_UNSUPPORTED;
+    g_num_sms[dev] = prop.multiProcessorCount;
+    return MSBM_OK;
+}
+
+// The scratch array's device address in the current context.  Host code only sees a
+// stand-in for the symbol; the address is looked up again on every call (the lookup
+// allocates nothing once the module is loaded), so a context created anew after
+// cudaDeviceReset, where the module may load at another address, gets its own address.
+msbm_status scratch_address(uint8_t **out) {
     void *ptr = nullptr;
     if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return MSBM_ERR_CUDA;
-    for (int nh = 1; nh <= MAX_NH; ++nh)
-        for (int sx = 1; sx <= 4; sx *= 2)
-            if (zncc_full_prepare(nh, sx) != cudaSuccess) return MSBM_ERR_CUDA;
-    g_num_sms[dev] = prop.multiProcessorCount;
-    g_scratch_ptr[dev] = static_cast<uint8_t *>(ptr);
+    *out = static_cast<uint8_t *>(ptr);
     return MSBM_OK;
 }
 
@@ -110,9 +112,11 @@ extern "C" msbm_status msbm_flat_disparity_noalloc(const uint8_t *d_left, const 
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MSBM_ERR_CUDA;
-    msbm_status s = setup_device(dev);
+    msbm_status s = check_device(dev);
     if (s != MSBM_OK) return s;
-    uint8_t *scratch = g_scratch_ptr[dev];
+    uint8_t *scratch = nullptr;
+    s = scratch_address(&scratch);
+    if (s != MSBM_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
 
     LevelBuf lv;
@@ -125,6 +129,9 @@ extern "C" msbm_status msbm_flat_disparity_noalloc(const uint8_t *d_left, const 
     lv.base[1] = scratch + 256 + img_bytes;
     const int nh = window / 2, rowsF = 8 + 2 * nh;
     const int sx = pick_sx(width, height, g_num_sms[dev]);
+    // the kernel's dynamic shared memory opt-in, in the current context (a host-side call
+    // that allocates nothing)
+    if (zncc_full_prepare(nh, sx) != cudaSuccess) return MSBM_ERR_CUDA;
     FullArgs a;
     memset(&a, 0, sizeof(a));
     if (!encode_map(&a.tmL, lv.base[0], pitch, rows, 32 * sx + 32, rowsF) ||

@@ -1,8 +1,12 @@
-"""Batched persistent launch: every pair of a mixed batch must equal the single-pair
-context path (which the parity tests tie to the FP64 oracle) up to the last bit of the
-cost -- the batched restricted tile applies the two rsqrt factors in the other order -- and
-the same disparities except where that rounding splits an exact tie; a sampled oracle
-check is repeated on batch outputs directly.  The dependency-wait
+"""Batched persistent launch against the FP64 oracle, through the C ABI.
+
+Every level of every batched pair is compared element by element with the oracle fed the
+batch's own coarser map as the prior, so both sides search the same candidate sets: costs
+within 1e-4 and disparities equal except where the oracle's best and second-best costs
+differ by less than 1e-4 (counted).  The batch is also compared with the single-pair
+context path: costs within one rounding of the rsqrt order (the batched tile applies the
+two factors in the other order) wherever the disparities agree, and the same disparities
+at every pixel whose prior cell agrees, except at counted near-ties.  The dependency-wait
 timeout path is exercised by withholding the first stage (test hook).  The autotuner's
 choices only change speed."""
 import numpy as np
@@ -10,7 +14,7 @@ import pytest
 
 import oracle
 from paper_1901_09593_gb300 import scenes
-from tests.gpu_util import compare_level
+from tests.gpu_util import TIE_TOL, compare_level
 
 pytestmark = pytest.mark.gpu
 
@@ -22,12 +26,17 @@ def _built():
     oracle.build()
 
 
-def _same_maps(d, c, dr, cr, what):
-    assert np.abs(c - cr).max() <= 1e-6, what
-    assert (d == dr).mean() >= 0.9999, what
+def _levels_of_batch(b, i, spec, d0, c0):
+    """[(d, c)] of pair i, level 0 first (host arrays)."""
+    K = spec[3]
+    out = [(d0.cpu().numpy(), c0.cpu().numpy())]
+    for k in range(1, K):
+        d, c = b.level_result(i, k)
+        out.append((d.cpu().numpy(), c.cpu().numpy()))
+    return out
 
 
-def _context_result(spec, L, R, sx=None, zblock=0):
+def _levels_of_context(spec, L, R, sx=None, zblock=0):
     from paper_1901_09593_gb300 import Context
     w, h, d, k, win, r = spec
     ctx = Context(w, h, d, k, win, r)
@@ -35,7 +44,49 @@ def _context_result(spec, L, R, sx=None, zblock=0):
         ctx.set_level_tuning(k - 1, sx, zblock)
     dd, cc = ctx.disparity(L, R)
     ctx.sync()
-    return dd.cpu().numpy(), cc.cpu().numpy()
+    out = [(dd.cpu().numpy(), cc.cpu().numpy())]
+    for j in range(1, k):
+        dj, cj = ctx.level_result(j)
+        out.append((dj.cpu().numpy(), cj.cpu().numpy()))
+    ctx.close()
+    return out
+
+
+def _check_against_oracle(levels, spec, left, right, what):
+    """Each level vs the oracle given the batch's own coarser map.  Returns (near-tie
+    disagreements, oracle near-tie masks per level)."""
+    w, h, D, K, win, r = spec
+    pa, pb = oracle.pyramid(left, K), oracle.pyramid(right, K)
+    ties, near = 0, [None] * K
+    for k in range(K - 1, -1, -1):
+        dk = oracle.level_disp(D, k)
+        if k == K - 1:
+            do, co, c2, _ = oracle.match_level(pa[k], pb[k], win // 2, dk)
+        else:
+            do, co, c2, _ = oracle.match_level(pa[k], pb[k], win // 2, dk, r, levels[k + 1][0])
+        ties += compare_level(levels[k][0], levels[k][1], do, co, c2, f"{what} level {k}")
+        near[k] = (co - c2) < TIE_TOL
+    return ties, near
+
+
+def _check_against_context(bl, cl, near, what):
+    """Batch vs context path: same disparity wherever the prior cell agrees, except at the
+    oracle's near-ties; costs within 1e-6 wherever the disparities agree."""
+    K = len(bl)
+    for k in range(K - 1, -1, -1):
+        db, cb = bl[k]
+        dc, cc = cl[k]
+        if k == K - 1:
+            same_prior = np.ones(db.shape, bool)
+        else:
+            h, w = db.shape
+            pb, pc = bl[k + 1][0], cl[k + 1][0]
+            yy, xx = np.mgrid[0:h, 0:w]
+            same_prior = pb[yy // 2, xx // 2] == pc[yy // 2, xx // 2]
+        bad = (db != dc) & same_prior & ~near[k]
+        assert not bad.any(), f"{what} level {k}: {int(bad.sum())} disparities differ from the context path"
+        eq = db == dc
+        assert np.abs(cb[eq] - cc[eq]).max(initial=0.0) <= 1e-6, f"{what} level {k}: cost"
 
 
 def _pairs(specs, seed):
@@ -43,45 +94,53 @@ def _pairs(specs, seed):
     rng = np.random.default_rng(seed)
     Ls, Rs = [], []
     for (w, h, *_r) in specs:
-        Ls.append(torch.from_numpy(rng.integers(0, 256, (h, w), dtype=np.uint8)).cuda())
-        Rs.append(torch.from_numpy(rng.integers(0, 256, (h, w), dtype=np.uint8)).cuda())
-    return Ls, Rs
+        Ls.append(rng.integers(0, 256, (h, w), dtype=np.uint8))
+        Rs.append(rng.integers(0, 256, (h, w), dtype=np.uint8))
+    return Ls, Rs, [torch.from_numpy(a).cuda() for a in Ls], [torch.from_numpy(a).cuda() for a in Rs]
 
 
-def test_mixed_batch_equals_single_pair_path():
+def _check_batch(b, specs, Lh, Rh, Ld, Rd, d, c, sx=None, zb=None, context=True):
+    ties = 0
+    for i, spec in enumerate(specs):
+        bl = _levels_of_batch(b, i, spec, d[i], c[i])
+        t, near = _check_against_oracle(bl, spec, Lh[i], Rh[i], f"pair {i} {spec}")
+        ties += t
+        if context:
+            cl = _levels_of_context(spec, Ld[i], Rd[i])
+            _check_against_context(bl, cl, near, f"pair {i} {spec}")
+    return ties
+
+
+def test_mixed_batch_matches_oracle_and_single_pair_path():
     from paper_1901_09593_gb300 import Batch
     specs = [(160, 120, 32, 3, 5, 2), (320, 240, 64, 3, 7, 2), (257, 130, 40, 2, 3, 1), (64, 40, 16, 1, 9, 0),
              (1, 1, 1, 1, 3, 0), (33, 17, 50, 4, 7, 3), (200, 96, 48, 2, 5, 5)]
-    Ls, Rs = _pairs(specs, 0)
+    Lh, Rh, Ls, Rs = _pairs(specs, 0)
     sx = [1, 2, 1, 1, 1, 2, 2]
     zb = [0, 32, 64, 0, 0, 0, 32]
     b = Batch(specs, sx, zb)
     d, c = b.run(Ls, Rs)
     b.sync()
-    n_items = b.info()["items"]
-    assert n_items > 0
-    for i, spec in enumerate(specs):
-        dr, cr = _context_result(spec, Ls[i], Rs[i])
-        _same_maps(d[i].cpu().numpy(), c[i].cpu().numpy(), dr, cr, f"pair {i}")
+    assert b.info()["items"] > 0
+    _check_batch(b, specs, Lh, Rh, Ls, Rs, d, c)
     # a second run with new outputs (pointer table re-upload) gives the same maps
     d2, c2 = b.run(Ls, Rs)
     b.sync()
     for i in range(len(specs)):
         np.testing.assert_array_equal(d2[i].cpu().numpy(), d[i].cpu().numpy())
+        np.testing.assert_array_equal(c2[i].cpu().numpy(), c[i].cpu().numpy())
 
 
 def test_batch_with_large_coarsest_range_uses_full_range_tiles():
     # coarsest levels above 64 candidates select the batch kernel build with the full-range
-    # tile (tile width and z-block from the caller); maps still equal the single-pair path
+    # tile (tile width and z-block from the caller)
     from paper_1901_09593_gb300 import Batch
     specs = [(300, 60, 160, 1, 5, 2), (240, 100, 300, 2, 7, 2), (96, 64, 24, 2, 5, 1)]
-    Ls, Rs = _pairs(specs, 11)
+    Lh, Rh, Ls, Rs = _pairs(specs, 11)
     b = Batch(specs, [2, 1, 1], [64, 0, 32])
     d, c = b.run(Ls, Rs)
     b.sync()
-    for i, spec in enumerate(specs):
-        dr, cr = _context_result(spec, Ls[i], Rs[i])
-        _same_maps(d[i].cpu().numpy(), c[i].cpu().numpy(), dr, cr, f"pair {i}")
+    _check_batch(b, specs, Lh, Rh, Ls, Rs, d, c)
 
 
 def test_scene_batch_matches_oracle_on_levels():
@@ -95,15 +154,12 @@ def test_scene_batch_matches_oracle_on_levels():
     Rs = [torch.from_numpy(s.right).cuda() for s in scs]
     d, c = b.run(Ls, Rs)
     b.sync()
-    for i, sc in enumerate(scs):
-        ref = oracle.disparity(sc.left, sc.right, spec.max_disp, spec.levels, spec.window, spec.radius)
-        dh = d[i].cpu().numpy()
-        assert (dh == ref["d"][0]).mean() > 0.99
-        same = dh == ref["d"][0]
-        assert np.abs(c[i].cpu().numpy()[same] - ref["C"][0][same]).max() <= 1e-4
+    _check_batch(b, specs, [s.left for s in scs], [s.right for s in scs], Ls, Rs, d, c)
 
 
 def test_mixed_size_batch_of_48_benchmark_pairs():
+    # the 48 seeded mixed-size pairs the batch benchmark runs: every level of every pair
+    # against the oracle, and against the single-pair path
     from paper_1901_09593_gb300 import Batch, autotune
     import torch
     specs_s = scenes.make_batch_specs(48, 0)
@@ -117,19 +173,17 @@ def test_mixed_size_batch_of_48_benchmark_pairs():
     d, c = b.run(Ls, Rs)
     b.sync()
     evals = b.eval_count()
-    total = 0
-    for i in (0, 7, 23, 47):
-        dr, cr = _context_result(specs[i], Ls[i], Rs[i])
-        _same_maps(d[i].cpu().numpy(), c[i].cpu().numpy(), dr, cr, f"pair {i}")
+    ties = _check_batch(b, specs, [s.left for s in scs], [s.right for s in scs], Ls, Rs, d, c)
+    npx = sum(w * h for (w, h, *_r) in specs)
+    assert ties <= 1e-3 * npx, ties
     for i, s in enumerate(specs_s):
         bad = scenes.bad_rate(d[i].cpu().numpy(), scs[i].gt, scs[i].mask, 1.0)
         assert bad < 0.25, (i, bad)
-        total += 1
-    assert evals > 0 and total == 48
+    assert evals > 0
 
 
 def test_sampled_oracle_levels_from_batch_output():
-    # the coarsest level of a batched pair checked against the oracle directly
+    # a flat (K = 1) batched pair checked against the oracle directly
     from paper_1901_09593_gb300 import Batch
     import torch
     rng = np.random.default_rng(3)
@@ -146,7 +200,7 @@ def test_sampled_oracle_levels_from_batch_output():
 def test_withheld_dependency_times_out_and_reports():
     from paper_1901_09593_gb300 import Batch, _lib
     specs = [(96, 64, 16, 2, 5, 2), (64, 48, 16, 2, 5, 1)]
-    Ls, Rs = _pairs(specs, 5)
+    Lh, Rh, Ls, Rs = _pairs(specs, 5)
     b = Batch(specs, flags=_lib.MSBM_FLAG_TEST_TIMEOUT)
     b.run(Ls, Rs)
     with pytest.raises(_lib.MsbmError) as ei:
@@ -156,8 +210,7 @@ def test_withheld_dependency_times_out_and_reports():
     ok = Batch(specs)
     d, c = ok.run(Ls, Rs)
     ok.sync()
-    dr, cr = _context_result(specs[0], Ls[0], Rs[0])
-    _same_maps(d[0].cpu().numpy(), c[0].cpu().numpy(), dr, cr, "after timeout")
+    _check_batch(ok, specs, Lh, Rh, Ls, Rs, d, c)
 
 
 def test_autotuner_choices_do_not_change_results():

@@ -2,9 +2,18 @@
 backward) against the FP64 oracle, through the C ABI via the autograd.Function.
 
 The oracle's gradient is itself pinned to FP64 central differences (tests/
-test_oracle_softargmax.py); here the GPU gradient is compared with it element-wise (max
-error relative to the largest gradient magnitude <= 1e-3), and directly with FP64 central
-differences of the oracle's loss along random directions on a 64x48 crop."""
+test_oracle_softargmax.py); here the GPU gradient is compared with it element by element:
+within 1e-3 relative at every element whose magnitude is at least 1 % of the largest, and
+within 1e-5 of the largest magnitude everywhere (FP32 rounding is absolute at the scale of
+the summed terms, so small elements carry large relative error).  The GPU gradient is also
+compared directly with FP64 central differences of the oracle's loss along random
+directions on a 64x48 crop.
+
+Forward bound, derived: the GPU computes rho in FP32 from two-pass window sums of at most
+9 x 9 terms, so |d rho| <= 1e-5 (about N u with u = 2^-24 and N <= 81, rounded up).  With
+p = softmax(rho / T), a perturbation d rho moves d_soft = sum z p_z by
+sum_z (z - d_soft) p_z (d rho_z - sum_w p_w d rho_w) / T, at most
+2 (ndisp - 1) max|d rho| / T."""
 import numpy as np
 import pytest
 
@@ -42,6 +51,23 @@ def rel_err(a, b):
     return np.abs(a - b).max() / max(np.abs(b).max(), 1e-30)
 
 
+DRHO = 1e-5          # FP32 bound on |rho_gpu - rho| (module docstring)
+
+
+def fwd_bound(nd):
+    return 2.0 * (nd - 1) * DRHO / T + 1e-6
+
+
+def check_grad(g, gref, what):
+    """Per element: 1e-3 relative where |gref| >= 1 % of max|gref|; 1e-5 of max|gref| elsewhere."""
+    top = max(np.abs(gref).max(), 1e-30)
+    err = np.abs(g - gref)
+    big = np.abs(gref) >= 1e-2 * top
+    rel = err[big] / np.abs(gref[big])
+    assert rel.max(initial=0.0) <= 1e-3, f"{what}: per-element relative error {rel.max():.3g}"
+    assert err[~big].max(initial=0.0) <= 1e-5 * top, f"{what}: small-element error {err[~big].max() / top:.3g}"
+
+
 @pytest.mark.parametrize("win,nd,h,w", [(3, 4, 5, 9), (5, 8, 12, 40), (7, 16, 20, 64), (9, 12, 16, 37),
                                         (7, 64, 24, 100), (5, 1, 6, 10), (7, 20, 9, 11)])
 def test_forward_and_backward_match_oracle_random(win, nd, h, w):
@@ -54,12 +80,12 @@ def test_forward_and_backward_match_oracle_random(win, nd, h, w):
     Lf, Rf = f32(L), f32(R)
     dref = oracle.softargmax_fwd(Lf, Rf, win // 2, nd, T, eps)
     glr, grr = oracle.softargmax_bwd(Lf, Rf, win // 2, nd, T, eps, g)
-    assert np.abs(d - dref).max() <= 2e-3 + 1e-4 * nd
+    assert np.abs(d - dref).max() <= fwd_bound(nd), np.abs(d - dref).max()
     if nd == 1:
         assert np.all(d == 0) and np.all(gl == 0) and np.all(gr == 0)
         return
-    assert rel_err(gl, glr) <= 1e-3, rel_err(gl, glr)
-    assert rel_err(gr, grr) <= 1e-3, rel_err(gr, grr)
+    check_grad(gl, glr, "dL")
+    check_grad(gr, grr, "dR")
 
 
 def test_scene_crop_64x48_against_central_differences():
@@ -73,7 +99,8 @@ def test_scene_crop_64x48_against_central_differences():
     d, gl, gr = run_gpu(L, R, win, nd, T, eps, wts)
     Lf, Rf = f32(L), f32(R)
     glr, grr = oracle.softargmax_bwd(Lf, Rf, 3, nd, T, eps, wts)
-    assert rel_err(gl, glr) <= 1e-3 and rel_err(gr, grr) <= 1e-3
+    check_grad(gl, glr, "crop dL")
+    check_grad(gr, grr, "crop dR")
 
     def loss(a, b):
         return float((oracle.softargmax_fwd(a, b, 3, nd, T, eps) * wts).sum())
@@ -104,11 +131,10 @@ def test_full_size_batch_forward_and_one_image_backward():
     d = d.detach().cpu().numpy()
     Lf, Rf = f32(L[:1]), f32(R[:1])
     dref = oracle.softargmax_fwd(Lf, Rf, 3, nd, T, eps)
-    assert np.abs(d[:1] - dref).max() <= 1e-2
-    assert np.mean(np.abs(d[:1] - dref) <= 2e-3) > 0.999
+    assert np.abs(d[:1] - dref).max() <= fwd_bound(nd)
     glr, grr = oracle.softargmax_bwd(Lf, Rf, 3, nd, T, eps, g[:1])
-    assert rel_err(lt.grad[:1].cpu().numpy(), glr) <= 1e-3
-    assert rel_err(rt.grad[:1].cpu().numpy(), grr) <= 1e-3
+    check_grad(lt.grad[:1].cpu().numpy(), glr, "640x480 dL")
+    check_grad(rt.grad[:1].cpu().numpy(), grr, "640x480 dR")
     # soft disparities track the scene where the match is clear
     assert np.all(np.isfinite(d))
 
