@@ -1,11 +1,12 @@
-// level_stats.cu -- the window statistics plane of a pyramid level's right image, read by the
-// restricted ZNCC search (Sec. III-C, Eq. 1-4 terms of the right window): for every pixel
-// (y, x), S = sum of the (2n+1)^2 window (clamp-to-edge) and rsqrt(N * sum I^2 - S^2), or
-// 0 for a flat window.  Every right window a restricted candidate reads is one entry, so the
-// matching kernel does no window statistics of its own.
+// level_stats.cu -- the window statistics planes of a pyramid level's two images, read by the
+// restricted ZNCC search (Sec. III-C; the per-window terms of Eq. 2): for every pixel (y, x),
+// S = sum of the (2n+1)^2 window (clamp-to-edge) and rsqrt(N * sum I^2 - S^2), or 0 for a
+// flat window.  Every right window a restricted candidate reads, and every left window, is
+// one entry, so the matching kernel does no window statistics of its own.
 //
-// One launch covers several levels, their 64 x 32 tiles (level_stats_tile.cuh) numbered
-// consecutively.  Bound: a few integer operations and 8 bytes written per pixel.
+// One launch covers several levels and both images, their 64 x 32 tiles
+// (level_stats_tile.cuh) numbered consecutively.  Bound: a few integer operations and 8
+// bytes written per pixel and image.
 #include <math.h>
 #include <string.h>
 
@@ -17,19 +18,19 @@ namespace msbm {
 
 namespace {
 
-constexpr int ST_MAXL = 16;
+constexpr int ST_MAXL = 24;      // planes per launch (two per level)
 
 struct StatsArgs {
     int n;                          // levels in this launch
     int first[ST_MAXL + 1];         // first tile of each level; first[n] = total tiles
     int tiles_x[ST_MAXL];
-    const uint8_t *R[ST_MAXL];      // right image origins (apron buffers)
+    const uint8_t *R[ST_MAXL];      // image origins (apron buffers)
     int pitch[ST_MAXL], W[ST_MAXL], H[ST_MAXL], opitch[ST_MAXL];
     int2 *out[ST_MAXL];
 };
 
 template <int NH>
-__global__ void __launch_bounds__(256) right_stats_kernel(const __grid_constant__ StatsArgs a) {
+__global__ void __launch_bounds__(256) level_stats_kernel(const __grid_constant__ StatsArgs a) {
     __shared__ __align__(16) uint8_t sm[StatsCfg<NH>::BYTES];
     int lv = 0;
     while (lv + 1 < a.n && static_cast<int>(blockIdx.x) >= a.first[lv + 1]) ++lv;
@@ -40,28 +41,30 @@ __global__ void __launch_bounds__(256) right_stats_kernel(const __grid_constant_
 
 template <int NH>
 cudaError_t stats_launch(const StatsArgs &a, cudaStream_t st) {
-    right_stats_kernel<NH><<<a.first[a.n], 256, 0, st>>>(a);
+    level_stats_kernel<NH><<<a.first[a.n], 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_right_stats(const LevelBuf *lv, int n, int nh, cudaStream_t st) {
+cudaError_t launch_level_stats(const LevelBuf *lv, int n, int nh, cudaStream_t st) {
     if (n < 1) return cudaSuccess;
-    if (n > ST_MAXL) return cudaErrorInvalidValue;
+    if (2 * n > ST_MAXL) return cudaErrorInvalidValue;
     StatsArgs a;
     memset(&a, 0, sizeof(a));
-    a.n = n;
-    for (int i = 0; i < n; ++i) {
-        const LevelBuf &l = lv[i];
-        if (!l.rstat) return cudaErrorInvalidValue;
+    a.n = 2 * n;
+    for (int i = 0; i < 2 * n; ++i) {
+        const LevelBuf &l = lv[i / 2];
+        const int which = (i & 1) ? 0 : 1;           // right plane first, then left
+        int2 *out = which ? l.rstat : l.lstat;
+        if (!out) return cudaErrorInvalidValue;
         a.tiles_x[i] = (l.W + ST_TX - 1) / ST_TX;
         a.first[i + 1] = a.first[i] + a.tiles_x[i] * ((l.H + ST_TY - 1) / ST_TY);
-        a.R[i] = l.img(1);
+        a.R[i] = l.img(which);
         a.pitch[i] = l.pitch;
         a.W[i] = l.W;
         a.H[i] = l.H;
-        a.out[i] = l.rstat;
+        a.out[i] = out;
         a.opitch[i] = l.rspitch;
     }
     switch (nh) {

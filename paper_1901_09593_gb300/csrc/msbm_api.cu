@@ -138,6 +138,7 @@ void free_ctx(msbm_ctx *c) {
         cudaFree(l.dtmp);
         cudaFree(l.mask);
         cudaFree(l.rstat);
+        cudaFree(l.lstat);
     }
     cudaFree(c->c0);
     cudaFree(c->d_err);
@@ -195,7 +196,7 @@ cudaError_t launch_stats_levels(msbm_ctx *c, int n, cudaStream_t st) {
     for (int k0 = 0; e == cudaSuccess && k0 < n;) {
         int k1 = k0 + 1;
         while (k1 < n && c->lv[k1].nh == c->lv[k0].nh) ++k1;
-        e = launch_right_stats(c->lv.data() + k0, k1 - k0, c->lv[k0].nh, st);
+        e = launch_level_stats(c->lv.data() + k0, k1 - k0, c->lv[k0].nh, st);
         k0 = k1;
     }
     return e;
@@ -224,16 +225,17 @@ msbm_status enqueue_level(msbm_ctx *c, int k, const int16_t *prior, int16_t *d, 
         a.tmL = l.tmRL;
         a.tmR128 = l.tmRR128;
         a.tmR256 = l.tmRR256;
-        a.tmS128 = l.tmS128;
-        a.tmS256 = l.tmS256;
+        a.tmS = l.tmS128;
+        a.tmSL = l.tmSL;
         a.t.skip = skip;
         a.t.Limg = l.img(0); a.t.Rimg = l.img(1); a.t.pitch = l.pitch;
         a.t.W = l.W; a.t.H = l.H; a.t.Dk = l.Dk; a.t.r = c->p.radius;
         a.t.prior = prior; a.t.Wp = (l.W + 1) / 2; a.t.Hp = (l.H + 1) / 2;
         a.t.d_out = d; a.t.c_out = cost;
         a.t.evals = c->d_evals; a.t.err = c->d_err; a.t.force_timeout = force;
-        e = stats_ready ? cudaSuccess : launch_right_stats(&l, 1, l.nh, st);
-        if (e == cudaSuccess) e = launch_zncc_restricted(a, l.nh, st);
+        a.t.rstat = l.rstat; a.t.rspitch = l.rspitch;
+        e = stats_ready ? cudaSuccess : launch_level_stats(&l, 1, l.nh, st);
+        if (e == cudaSuccess) e = launch_zncc_restricted(a, l.nh, l.rty, st);
     }
     return cuda_status(e);
 }
@@ -293,7 +295,7 @@ msbm_status enqueue_all(msbm_ctx *c, const uint8_t *L, const uint8_t *R, size_t 
         cudaError_t e = cudaEventRecord(c->ev_fork, st);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0);
         for (int k = K - 2; e == cudaSuccess && k >= 0; --k) {
-            e = launch_right_stats(&c->lv[k], 1, c->lv[k].nh, c->side_stream);
+            e = launch_level_stats(&c->lv[k], 1, c->lv[k].nh, c->side_stream);
             if (e == cudaSuccess) e = cudaEventRecord(c->ev_stat[k], c->side_stream);
         }
         s = cuda_status(e);
@@ -373,6 +375,7 @@ msbm_status msbm_create(const msbm_params *params, void *cuda_stream, msbm_ctx *
         if (e == cudaSuccess && k > 0) e = cudaMalloc(&l.c, (size_t)W * H * sizeof(float));
         l.rspitch = (W + 15) / 16 * 16;
         if (e == cudaSuccess) e = cudaMalloc(&l.rstat, (size_t)l.rspitch * H * sizeof(int2));
+        if (e == cudaSuccess) e = cudaMalloc(&l.lstat, (size_t)l.rspitch * H * sizeof(int2));
         const bool finer = k < params->levels - 1;
         if (e == cudaSuccess && finer && (params->flags & MSBM_FLAG_SELECTIVE_MEDIAN))
             e = cudaMalloc(&l.dtmp, (size_t)W * H * sizeof(int16_t));
@@ -380,15 +383,16 @@ msbm_status msbm_create(const msbm_params *params, void *cuda_stream, msbm_ctx *
             e = cudaMalloc(&l.mask, (size_t)W * H);
         l.full_sx = choose_sx(W, H, c->num_sms);
         l.coarse = zncc_coarse_fits(W, H, c->num_sms);
+        l.rty = restr_tile_rows(W, H, c->num_sms);
         if (e == cudaSuccess) {
-            const int rowsR = restr_tile_rows() + 2 * l.nh;
+            const int rowsR = l.rty + 2 * l.nh;
             bool ok = encode_u8(&l.tmFL, l.base[0], l.pitch, l.rows, 32 * l.full_sx + 32, rowsT) &&
                       encode_u8(&l.tmR256, l.base[1], l.pitch, l.rows, 256, rowsT) &&
                       encode_u8(&l.tmRL, l.base[0], l.pitch, l.rows, 64, rowsR) &&
                       encode_u8(&l.tmRR128, l.base[1], l.pitch, l.rows, 128, rowsR) &&
                       encode_u8(&l.tmRR256, l.base[1], l.pitch, l.rows, 256, rowsR) &&
-                      encode_u64(&l.tmS128, l.rstat, l.rspitch, H, 128, restr_tile_rows()) &&
-                      encode_u64(&l.tmS256, l.rstat, l.rspitch, H, 256, restr_tile_rows());
+                      encode_u64(&l.tmS128, l.rstat, l.rspitch, H, 128, l.rty) &&
+                      encode_u64(&l.tmSL, l.lstat, l.rspitch, H, 32, l.rty);
             if (!ok) { c->lv.push_back(l); free_ctx(c); return MSBM_ERR_UNSUPPORTED; }
         }
         if (e == cudaSuccess) e = zncc_full_prepare(l.nh, l.full_sx);

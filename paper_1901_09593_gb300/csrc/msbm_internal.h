@@ -24,15 +24,18 @@ struct LevelBuf {
     int16_t *dtmp = nullptr;     // pre-median disparity map (SELECTIVE_MEDIAN)
     uint8_t *mask = nullptr;     // fallback mask (BETA_FALLBACK)
     int2 *rstat = nullptr;       // right-window statistics plane {S, bits(rsqrt(V)) or 0}: H rows
+    int2 *lstat = nullptr;       // left-window statistics plane, same layout
     int rspitch = 0;             // of rspitch entries (a multiple of 16), one per pixel
+    int rty = 16;                // rows of this level's restricted tile (8 or 16)
     // TMA maps over the apron buffers.  Full-range tile (8 + 2n rows high):
     //   tmFL   : left,  32*SX + 32 bytes wide, SX per level
     //   tmR256 : right, 256 bytes wide
-    // Restricted tile (restr_tile_rows() + 2n rows high):
+    // Restricted tile (rty + 2n rows high):
     //   tmRL   : left,  64 bytes wide
     //   tmRR128, tmRR256 : right, 128 / 256 bytes wide (narrow / wide candidate spans)
-    //   tmS128, tmS256   : statistics plane, 128 / 256 entries wide, restr_tile_rows() rows
-    CUtensorMap tmFL, tmR256, tmRL, tmRR128, tmRR256, tmS128, tmS256;
+    //   tmS128 : right statistics plane, 128 entries wide, rty rows
+    //   tmSL   : left statistics plane, 32 entries wide, rty rows
+    CUtensorMap tmFL, tmR256, tmRL, tmRR128, tmRR256, tmS128, tmSL;
     int full_sx = 4;             // full-range tile width 32*full_sx at this level
     int full_zblock = 0;         // full-range z-block (0 = the tile's maximum)
     bool coarse = false;         // plain full-range search by the small-level kernel
@@ -72,14 +75,18 @@ struct RestrTileArgs {
     unsigned long long *evals;
     int *err;
     int force_timeout;
+    const int2 *rstat;   // the level's right statistics plane (strip tile: wide spans read it
+    int rspitch;         // from global memory)
 };
 
+// Arguments of the standalone restricted kernel (strip tile, zncc_strip_tile.cuh), ty rows
+// per tile (LevelBuf::rty).
 struct RestrArgs {
-    CUtensorMap tmL;     // box {64, ty + 2n} over the left apron buffer, ty = restr_tile_rows()
+    CUtensorMap tmL;     // box {64, ty + 2n} over the left apron buffer
     CUtensorMap tmR128;  // box {128, ty + 2n} over the right apron buffer
     CUtensorMap tmR256;  // box {256, ty + 2n} over the right apron buffer
-    CUtensorMap tmS128;  // box {128, ty} over the right statistics plane
-    CUtensorMap tmS256;  // box {256, ty} over the right statistics plane
+    CUtensorMap tmS;     // box {128, ty} over the right statistics plane
+    CUtensorMap tmSL;    // box {32, ty} over the left statistics plane
     RestrTileArgs t;
 };
 
@@ -115,11 +122,13 @@ cudaError_t launch_alpha_refine(const LevelBuf &l, int nh, float alpha, int16_t 
 cudaError_t launch_selective_median(const int16_t *d_in, const float *C, int W, int H, float alpha, int16_t *d_out,
                                     cudaStream_t st);
 cudaError_t zncc_full_prepare(int nh, int sx);
-// Right-window statistics planes of n consecutive levels (lv[0 .. n-1]) in one launch.
-cudaError_t launch_right_stats(const LevelBuf *lv, int n, int nh, cudaStream_t st);
+// Window statistics planes (left into lstat, right into rstat) of n consecutive levels
+// (lv[0 .. n-1]) in one launch.
+cudaError_t launch_level_stats(const LevelBuf *lv, int n, int nh, cudaStream_t st);
 cudaError_t zncc_restricted_prepare(int nh);
-// Rows of the standalone restricted kernel's tile (its TMA boxes are rows + 2n high).
-int restr_tile_rows();
-cudaError_t launch_zncc_restricted(const RestrArgs &a, int nh, cudaStream_t st);
+// Rows of the standalone restricted kernel's tile at a W x H level (its TMA boxes are
+// rows + 2n high): 16, or 8 where 32 x 16 tiles would give the GPU too few CTAs.
+int restr_tile_rows(int W, int H, int sms);
+cudaError_t launch_zncc_restricted(const RestrArgs &a, int nh, int ty, cudaStream_t st);
 
 }  // namespace msbm

@@ -1,9 +1,9 @@
 // zncc_restricted.cu -- standalone launch of the restricted ZNCC winner-take-all tile
-// (Sec. III-C, Eq. 8-9, first branch; design in zncc_restricted_tile.cuh): one CTA of
-// 128 threads per 32 x 8 tile, each thread a vertical pair of pixels that share a prior
-// cell and the products of their 2n common window rows; right-window statistics from the
-// level's plane (level_stats.cu).
-#include "zncc_restricted_tile.cuh"
+// (Sec. III-C, Eq. 8-9, first branch; design in zncc_strip_tile.cuh): one CTA per 32 x TY
+// tile, each thread a vertical strip of four pixels that share the products of their
+// common window rows; left- and right-window statistics from the level's planes
+// (level_stats.cu).
+#include "zncc_strip_tile.cuh"
 
 namespace msbm {
 
@@ -11,25 +11,11 @@ namespace {
 
 using namespace tiles;
 
-constexpr int SA_QX = 32;    // threads per tile row; tile width SA_QX pixels
-constexpr int SA_NCOL = 1;
+// Minimum CTAs per SM the register allocation must allow (128-thread CTAs at TY = 16).
+constexpr int strip_min_ctas(int nh, int ty) { return (nh <= 4 ? 6 : 3) * (16 / ty); }
 
-// Minimum CTAs per SM the register allocation must allow.  Up to 9 x 9 windows run four
-// CTAs per SM (64 registers): for r = 3 at 7 x 7 that costs 20 spilled bytes instead of 78
-// registers (3 CTAs per SM), at 9 x 9 196 bytes instead of 99 registers (2 CTAs per SM), and
-// level 0 of the 2880 x 1984 pair (9 x 9, r = 3) went 190 -> 150 us (three CTAs per SM at 80
-// registers: 156 us).  Without a minimum the compiler may also take more registers for smaller
-// groups.  Larger windows keep two CTAs per SM.
-constexpr int restr_min_ctas(int nh) { return nh <= 4 ? 4 : 2; }
-
-// Tile height: 32 x 8 tiles of 128 threads, eight CTAs per SM, hide each CTA's latency chain
-// (prior load, span reduction, TMA wait) behind more independent CTAs than 32 x 16 tiles of
-// 256 threads at four per SM (measured: 1400 x 1000 pass 58.3 -> 54.5 us, level 0 28.7 ->
-// 26.6 us; 2880 x 1984 pass 265 -> 248 us), at 1.27x the staged halo rows per pixel.
-constexpr int SA_TY = 8;
-
-template <int NH, int G>
-__global__ void __launch_bounds__(SA_QX * SA_TY / 2, restr_min_ctas(NH) * 16 / SA_TY)
+template <int NH, int G, int TY>
+__global__ void __launch_bounds__(SCfg<NH, TY>::THREADS, strip_min_ctas(NH, TY))
     zncc_restricted_kernel(const __grid_constant__ RestrArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
     if (threadIdx.x == 0) {
@@ -38,49 +24,65 @@ __global__ void __launch_bounds__(SA_QX * SA_TY / 2, restr_min_ctas(NH) * 16 / S
     }
     __syncthreads();
     uint32_t parity = 0;
-    restr_tile<NH, G, SA_QX, SA_NCOL, true, SA_TY>(a.t, &a.tmL, &a.tmR128, &a.tmR256, &a.tmS128, &a.tmS256,
-                                                   blockIdx.x, blockIdx.y, smem, parity);
+    strip_tile<NH, G, TY>(a.t, &a.tmL, &a.tmR128, &a.tmR256, &a.tmS, &a.tmSL, blockIdx.x, blockIdx.y, smem, parity);
 }
 
-template <int NH, int G>
+template <int NH, int G, int TY>
 cudaError_t prepare_t() {
-    using C = RCfg<NH, SA_QX, SA_NCOL, true, SA_TY>;
-    return cudaFuncSetAttribute(zncc_restricted_kernel<NH, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    using C = SCfg<NH, TY>;
+    return cudaFuncSetAttribute(zncc_restricted_kernel<NH, G, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 static_cast<int>(C::BYTES));
 }
 
-template <int NH, int G>
+template <int NH, int G, int TY>
 cudaError_t launch_restr_t(const RestrArgs &a, cudaStream_t st) {
-    using C = RCfg<NH, SA_QX, SA_NCOL, true, SA_TY>;
-    static_assert(C::TX == 32 && C::BYTES <= 227 * 1024, "restricted tile shape");
-    dim3 grd((a.t.W + C::TX - 1) / C::TX, (a.t.H + SA_TY - 1) / SA_TY);
-    zncc_restricted_kernel<NH, G><<<grd, C::THREADS, C::BYTES, st>>>(a);
+    using C = SCfg<NH, TY>;
+    static_assert(C::BYTES <= 227 * 1024, "restricted tile shape");
+    dim3 grd((a.t.W + C::TX - 1) / C::TX, (a.t.H + TY - 1) / TY);
+    zncc_restricted_kernel<NH, G, TY><<<grd, C::THREADS, C::BYTES, st>>>(a);
     return cudaGetLastError();
 }
 
-// G, the candidates a thread evaluates per staged right word group, is 2r + 1 (at most 7)
-template <int NH>
-cudaError_t prepare_nh() {
-    cudaError_t e = prepare_t<NH, 1>();
-    if (e == cudaSuccess) e = prepare_t<NH, 3>();
-    if (e == cudaSuccess) e = prepare_t<NH, 5>();
-    if (e == cudaSuccess) e = prepare_t<NH, 7>();
+// G, the candidates a thread evaluates per group, is 2r + 1 (at most 7; wider radii run
+// several groups)
+template <int NH, int TY>
+cudaError_t prepare_nt() {
+    cudaError_t e = prepare_t<NH, 1, TY>();
+    if (e == cudaSuccess) e = prepare_t<NH, 3, TY>();
+    if (e == cudaSuccess) e = prepare_t<NH, 5, TY>();
+    if (e == cudaSuccess) e = prepare_t<NH, 7, TY>();
     return e;
 }
 
 template <int NH>
-cudaError_t launch_restr_nh(const RestrArgs &a, cudaStream_t st) {
+cudaError_t prepare_nh() {
+    cudaError_t e = prepare_nt<NH, 8>();
+    if (e == cudaSuccess) e = prepare_nt<NH, 16>();
+    return e;
+}
+
+template <int NH, int TY>
+cudaError_t launch_restr_nt(const RestrArgs &a, cudaStream_t st) {
     switch (a.t.r) {
-        case 0: return launch_restr_t<NH, 1>(a, st);
-        case 1: return launch_restr_t<NH, 3>(a, st);
-        case 2: return launch_restr_t<NH, 5>(a, st);
-        default: return launch_restr_t<NH, 7>(a, st);
+        case 0: return launch_restr_t<NH, 1, TY>(a, st);
+        case 1: return launch_restr_t<NH, 3, TY>(a, st);
+        case 2: return launch_restr_t<NH, 5, TY>(a, st);
+        default: return launch_restr_t<NH, 7, TY>(a, st);
     }
+}
+
+template <int NH>
+cudaError_t launch_restr_nh(const RestrArgs &a, int ty, cudaStream_t st) {
+    return ty == 8 ? launch_restr_nt<NH, 8>(a, st) : launch_restr_nt<NH, 16>(a, st);
 }
 
 }  // namespace
 
-int restr_tile_rows() { return SA_TY; }
+int restr_tile_rows(int W, int H, int sms) {
+    // 32 x 16 tiles unless they would give fewer than four CTAs per SM
+    const long ctas = (long)((W + 31) / 32) * ((H + 15) / 16);
+    return ctas >= 4L * sms ? 16 : 8;
+}
 
 cudaError_t zncc_restricted_prepare(int nh) {
     switch (nh) {
@@ -94,14 +96,15 @@ cudaError_t zncc_restricted_prepare(int nh) {
     }
 }
 
-cudaError_t launch_zncc_restricted(const RestrArgs &a, int nh, cudaStream_t st) {
+cudaError_t launch_zncc_restricted(const RestrArgs &a, int nh, int ty, cudaStream_t st) {
+    if (ty != 8 && ty != 16) return cudaErrorInvalidValue;
     switch (nh) {
-        case 1: return launch_restr_nh<1>(a, st);
-        case 2: return launch_restr_nh<2>(a, st);
-        case 3: return launch_restr_nh<3>(a, st);
-        case 4: return launch_restr_nh<4>(a, st);
-        case 5: return launch_restr_nh<5>(a, st);
-        case 6: return launch_restr_nh<6>(a, st);
+        case 1: return launch_restr_nh<1>(a, ty, st);
+        case 2: return launch_restr_nh<2>(a, ty, st);
+        case 3: return launch_restr_nh<3>(a, ty, st);
+        case 4: return launch_restr_nh<4>(a, ty, st);
+        case 5: return launch_restr_nh<5>(a, ty, st);
+        case 6: return launch_restr_nh<6>(a, ty, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -1,0 +1,344 @@
+// zncc_strip_tile.cuh -- the restricted ZNCC winner-take-all tile of the standalone pass
+// (Sec. III-C, Eq. 8-9, first branch).  Each pixel evaluates dhat - r .. dhat + r around the
+// nearest-neighbour upsample dhat = 2 * d^{k+1}(y/2, x/2) of the coarser disparity (the
+// paper's "3 comparisons per pixel" is r = 1), clipped to 0 .. min(D_k - 1, x); dhat is
+// first clamped into that range (a no-op for priors produced by the coarser level).
+//
+// Design (a 32 x TY pixel tile, TY = 8 or 16, of 32 x TY/4 threads; each thread owns a
+// vertical strip of four pixels of one column, which spans two prior cells):
+//  * The CTA reduces the union [zlo, zhi] of its spans; the left tile (a 64-byte box), the
+//    right span [x0 - zhi - n, x1 - zlo + n] (a 128- or 256-byte box), the span's entries of
+//    the level's right statistics plane (128 x TY) and the tile's entries of the left
+//    statistics plane (32 x TY) are staged by TMA on one mbarrier with a bounded wait.  A
+//    span wider than 128 bytes reads its right statistics from global memory; wider than
+//    256 it reads the right image there too.
+//  * The four pixels' windows cover 2n + 4 rows.  For each of those rows the thread aligns
+//    its left window row once (word loads and funnel shifts) and the right bytes of a group
+//    of G consecutive candidates once, extracts the G window offsets, and accumulates
+//    sum a*b with dp4a into running chains: the 2n - 2 rows all four windows share, the
+//    three rows above (chained from them) and the three below, so that each pixel's window
+//    sum costs two dp4a per window row over the strip plus two additions per candidate.
+//    All sums are exact int32 (windows up to 13 x 13); c = N*Sab - Sa*Sb is exact; the only
+//    rounding is rho = float(c) * rsqrt(Vb) * rsqrt(Va).
+//  * A warp whose threads all see one full-width span for both prior cells (the common
+//    case) evaluates its single group without per-candidate span tests.
+//  * WTA in ascending z with a strict compare, so exact ties keep the smallest z.
+// Bound: instruction issue (dp4a, funnel shifts, shared loads); HBM traffic is a few bytes
+// per pixel.
+#pragma once
+
+#include <limits.h>
+#include <math.h>
+
+#include <type_traits>
+
+#include "msbm_device.cuh"
+#include "msbm_internal.h"
+
+namespace msbm {
+namespace tiles {
+
+template <int NH, int TY>
+struct SCfg {
+    static_assert(TY == 8 || TY == 16, "tile height");
+    static constexpr int TX = 32;                // tile width (pixels)
+    static constexpr int THREADS = 32 * (TY / 4);
+    static constexpr int WIN = 2 * NH + 1;
+    static constexpr int N = WIN * WIN;
+    static constexpr int NW = (WIN + 3) / 4;     // words per packed window row
+    static constexpr int ROWS = TY + 2 * NH;     // staged rows
+    static constexpr int SROWS = 4 + 2 * NH;     // rows one strip's windows cover
+    static constexpr int LBOX = 64;              // left box: image columns x0-16 .. x0+48
+    static constexpr uint32_t LASTMASK =
+        (WIN % 4 == 0) ? 0xFFFFFFFFu : ((1u << (8 * (WIN % 4))) - 1u);
+    // shared memory carve (bytes): [0,128) barrier, flag, span scalars, evaluation sum
+    static constexpr size_t al(size_t v) { return (v + 127) / 128 * 128; }
+    static constexpr size_t OFF_SL = 128;
+    static constexpr size_t PAD_R = 128;         // readable slack before the right span
+    static constexpr size_t OFF_SR = OFF_SL + al((size_t)ROWS * LBOX) + PAD_R;
+    static constexpr size_t OFF_SS = OFF_SR + al((size_t)(ROWS + 1) * 256);   // right plane [TY][128]
+    static constexpr size_t OFF_SLS = OFF_SS + (size_t)TY * 128 * 8;          // left plane [TY][32]
+    static constexpr size_t BYTES = OFF_SLS + (size_t)TY * 32 * 8;
+};
+
+__device__ __forceinline__ uint32_t sfsr(uint32_t lo, uint32_t hi, int bytes) {
+    return __funnelshift_r(lo, hi, 8 * bytes);
+}
+
+// One group of G candidates zg .. zg+G-1 for the thread's four pixels (rows 4*qy + p of the
+// staged tile, p = 0..3).  sRrow0: the thread's first staged right row; rst: right row
+// stride; b0: staging column of the window of candidate zg+G-1 (may be slightly negative:
+// the slack before the span).  Adds each pixel's window sums of a*b for the G candidates to
+// P[p][j] (which start at 0).
+template <int NH, int G, int TY>
+__device__ __forceinline__ void strip_sums(const uint8_t *sLrow0, int w0L, int shL, const uint8_t *sRrow0,
+                                           int rst, int b0, uint32_t (&P)[4][G]) {
+    using C = SCfg<NH, TY>;
+    constexpr int WIN = C::WIN, NW = C::NW, SROWS = C::SROWS;
+    constexpr int NWA = (G - 1 + WIN + 3) / 4 + 1;    // aligned words covering the group
+    constexpr int NWL = NWA + 1;                       // raw words loaded per row
+    const int w0 = b0 >> 2, sh = b0 & 3;               // arithmetic shift: floor
+    // chains: M = rows 3 .. 2n (shared by all four windows); T = M + rows 2, 1 (top of
+    // pixels 1, 2); B = M + rows 2n+1, 2n+2 (bottom of pixels 1, 2)
+    uint32_t M[G], T2[G], T12[G], B1[G];
+#pragma unroll
+    for (int j = 0; j < G; ++j) M[j] = 0;
+    // row order: shared rows first, then 2, 1, 0 (chained from M), then 2n+1 .. 2n+3
+#pragma unroll
+    for (int i = 0; i < SROWS; ++i) {
+        // strip row tt: 3 .. 2n, then 2, 1, 0, then 2n+1, 2n+2, 2n+3
+        const int tt = i < 2 * NH - 2 ? 3 + i : (i < 2 * NH + 1 ? 2 - (i - (2 * NH - 2)) : i);
+        // left window row tt of the strip, aligned
+        uint32_t Lw[NW];
+        {
+            const uint32_t *row = reinterpret_cast<const uint32_t *>(sLrow0 + tt * C::LBOX);
+            uint32_t raw[NW + 1];
+#pragma unroll
+            for (int k = 0; k <= NW; ++k) raw[k] = row[w0L + k];
+#pragma unroll
+            for (int k = 0; k < NW; ++k) Lw[k] = sfsr(raw[k], raw[k + 1], shL);
+            Lw[NW - 1] &= C::LASTMASK;
+        }
+        // right bytes of the group, aligned, and the window of each candidate
+        const uint32_t *rrow = reinterpret_cast<const uint32_t *>(sRrow0 + tt * rst);
+        uint32_t raw[NWL], alw[NWA];
+#pragma unroll
+        for (int k = 0; k < NWL; ++k) raw[k] = rrow[w0 + k];
+#pragma unroll
+        for (int k = 0; k < NWA; ++k) alw[k] = sfsr(raw[k], raw[k + 1], sh);
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            const int o = G - 1 - j;                   // window offset of candidate zg + j
+            uint32_t acc;
+            if (tt >= 3 && tt <= 2 * NH) acc = M[j];
+            else if (tt == 2) acc = M[j];
+            else if (tt == 1) acc = T2[j];
+            else if (tt == 0) acc = T12[j];
+            else if (tt == 2 * NH + 1) acc = M[j];
+            else acc = B1[j];                          // rows 2n+2, 2n+3 continue the B chain
+#pragma unroll
+            for (int k = 0; k < NW; ++k) {
+                const uint32_t w = (o & 3) ? sfsr(alw[(o >> 2) + k], alw[(o >> 2) + k + 1], o & 3)
+                                           : alw[(o >> 2) + k];
+                acc = dp4a_u8(Lw[k], w, acc);
+            }
+            if (tt >= 3 && tt <= 2 * NH) M[j] = acc;
+            else if (tt == 2) T2[j] = acc;                  // M + r2        (pixel 2's top)
+            else if (tt == 1) T12[j] = acc;                 // M + r1 + r2   (pixel 1's top)
+            else if (tt == 0) P[0][j] = acc;                // pixel 0: rows 0 .. 2n
+            else if (tt == 2 * NH + 1) {                    // M + r(2n+1)
+                P[1][j] = T12[j] + acc - M[j];              // pixel 1: rows 1 .. 2n+1
+                B1[j] = acc;
+            } else if (tt == 2 * NH + 2) {                  // M + r(2n+1) + r(2n+2)
+                P[2][j] = T2[j] + acc - M[j];               // pixel 2: rows 2 .. 2n+2
+                B1[j] = acc;
+            } else {
+                P[3][j] = acc;                              // pixel 3: rows 3 .. 2n+3
+            }
+        }
+    }
+}
+
+// Restricted WTA of one 32 x TY tile (bx, by) by the calling CTA (blockDim.x = 32 * TY / 4).
+// `smem` holds SCfg::BYTES bytes, 128-aligned; its first 8 bytes are an mbarrier the caller
+// has initialised (count 1) and `parity` is its next phase parity, advanced here.  Returns
+// false if a bounded wait gave up (the error word is then set).
+template <int NH, int G, int TY>
+__device__ bool strip_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const CUtensorMap *tmR128,
+                           const CUtensorMap *tmR256, const CUtensorMap *tmS, const CUtensorMap *tmSL,
+                           int bx, int by, uint8_t *smem, uint32_t &parity) {
+    using C = SCfg<NH, TY>;
+    constexpr int WIN = C::WIN, NW = C::NW;
+    uint64_t &bar = *reinterpret_cast<uint64_t *>(smem);
+    int &flag = *reinterpret_cast<int *>(smem + 8);
+    int &zlo_s = *reinterpret_cast<int *>(smem + 12);
+    int &zhi_s = *reinterpret_cast<int *>(smem + 16);
+    int &mode_s = *reinterpret_cast<int *>(smem + 20);
+    int &xs_s = *reinterpret_cast<int *>(smem + 24);
+    unsigned long long &evsum = *reinterpret_cast<unsigned long long *>(smem + 32);
+    const uint8_t *sL = smem + C::OFF_SL;                               // [ROWS][64]
+    const uint8_t *sR = smem + C::OFF_SR;                               // [ROWS + 1][128|256]
+    const int2 *stS = reinterpret_cast<const int2 *>(smem + C::OFF_SS);   // [TY][128] right plane
+    const int2 *stL = reinterpret_cast<const int2 *>(smem + C::OFF_SLS);  // [TY][32] left plane
+
+    const int tid = threadIdx.x, qx = tid & 31, qy = tid >> 5;
+    const int x0 = bx * C::TX, y0 = by * TY;
+    const int xa = x0 + qx, ya = y0 + 4 * qy;           // the strip: column xa, rows ya .. ya+3
+    const int Dk = a.Dk;
+    const bool colv = xa < a.W;
+    bool rowv[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) rowv[p] = colv && ya + p < a.H;
+    const bool any = rowv[0];
+
+    // candidate spans of the two prior cells (rows ya/2 and ya/2 + 1)
+    int lo_c[2] = {INT_MAX, INT_MAX}, hi_c[2] = {-1, -1};
+    if (any) {
+        const int px = min(xa >> 1, a.Wp - 1);
+        const int zmx = min(Dk - 1, xa);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (!rowv[2 * h]) continue;
+            const int py = min((ya >> 1) + h, a.Hp - 1);
+            const int p2 = 2 * static_cast<int>(a.prior[(size_t)py * a.Wp + px]);
+            const int dh = min(max(p2, 0), zmx);
+            lo_c[h] = max(0, dh - a.r);
+            hi_c[h] = min(zmx, dh + a.r);
+        }
+    }
+    const int lo_u = min(lo_c[0], lo_c[1]), hi_u = max(hi_c[0], hi_c[1]);
+    // a warp takes the check-free path when every strip in it has one full-width span
+    const bool uni_t = !any || (hi_c[0] - lo_c[0] + 1 == G && (!rowv[2] || (lo_c[1] == lo_c[0] && hi_c[1] == hi_c[0])));
+    const bool uni = __all_sync(0xFFFFFFFFu, uni_t);
+    if (tid == 0) {
+        zlo_s = INT_MAX; zhi_s = -1; evsum = 0ull;
+    }
+    __syncthreads();
+    {
+        const int wlo = __reduce_min_sync(0xFFFFFFFFu, lo_u);
+        const int whi = __reduce_max_sync(0xFFFFFFFFu, hi_u);
+        unsigned cnt = 0;
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+            if (rowv[p] && !(a.skip && a.skip[(size_t)(ya + p) * a.W + xa]))
+                cnt += static_cast<unsigned>(hi_c[p >> 1] - lo_c[p >> 1] + 1);
+        const unsigned wcnt = __reduce_add_sync(0xFFFFFFFFu, cnt);
+        if ((tid & 31) == 0) {
+            atomicMin(&zlo_s, wlo);
+            atomicMax(&zhi_s, whi);
+            atomicAdd(&evsum, static_cast<unsigned long long>(wcnt));
+        }
+    }
+    __syncthreads();
+    const int zlo = zlo_s, zhi = zhi_s;
+    const int xlast = min(x0 + C::TX, a.W) - 1;
+    const int rs = x0 - zhi - NH;              // first right column any window reads
+    const int re = xlast - zlo + NH;           // last
+    const int sxs = (x0 - zhi) & ~1;           // first staged right-plane column (even)
+    if (tid == 0) {
+        const int xs = (rs + APX) & ~15;
+        const int width = re + APX + 1 - xs;
+        const int mode = width <= 128 ? 1 : (width <= 256 ? 2 : 0);
+        mode_s = mode;
+        xs_s = xs;
+        uint32_t bytes = C::ROWS * C::LBOX + TY * 32 * 8 + (mode == 1 ? C::ROWS * 128 + TY * 128 * 8
+                                                                      : (mode == 2 ? C::ROWS * 256 : 0));
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&bar, bytes);
+        tma_load_2d(smem + C::OFF_SL, tmL, &bar, x0 - 16 + APX, y0 - NH + APY);
+        tma_load_2d(smem + C::OFF_SLS, tmSL, &bar, x0, y0);
+        if (mode == 1) {
+            tma_load_2d(smem + C::OFF_SR, tmR128, &bar, xs, y0 - NH + APY);
+            tma_load_2d(smem + C::OFF_SS, tmS, &bar, sxs, y0);
+        }
+        if (mode == 2) tma_load_2d(smem + C::OFF_SR, tmR256, &bar, xs, y0 - NH + APY);
+    }
+    if (!tma_batch_wait(&bar, parity, &flag, a.force_timeout != 0, a.err)) return false;
+    parity ^= 1;
+    if (!any) return true;
+    const int mode = mode_s, xs = xs_s;
+    const int soff = APX - xs;                 // staging column of image column X: X + soff
+    const int rst = mode == 1 ? 128 : 256;     // staging row stride (bytes)
+
+    // left windows of the four pixels: {Sa, rsqrt(Va)} from the left plane
+    int Sa[4];
+    float rA[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const int2 e = stL[(4 * qy + p) * 32 + qx];
+        Sa[p] = e.x;
+        rA[p] = __int_as_float(e.y);
+    }
+    float best[4];
+    int bz[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        best[p] = -INFINITY;
+        bz[p] = lo_c[p >> 1];
+    }
+    const int sc = qx + 16 - NH;               // left staging column of xa - n
+    const int w0L = sc >> 2, shL = sc & 3;
+    const uint8_t *sLrow0 = sL + (4 * qy) * C::LBOX;
+    const int2 *gst = a.rstat + (size_t)ya * a.rspitch;   // right plane row ya (global)
+
+    if (mode != 0) {
+        const uint8_t *sRrow0 = sR + (4 * qy) * rst;
+        // the right plane entries of candidate z for pixel p: staged (mode 1) or global
+        auto eval_group = [&](const int zg, auto check_tag) {
+            constexpr bool check = decltype(check_tag)::value;
+            uint32_t P[4][G];
+            const int b0 = xa - (zg + G - 1) - NH + soff;   // >= -(G-1): inside the slack
+            strip_sums<NH, G, TY>(sLrow0, w0L, shL, sRrow0, rst, b0, P);
+#pragma unroll
+            for (int j = 0; j < G; ++j) {
+                const int z = zg + j;
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    if (check && (z < lo_c[p >> 1] || z > hi_c[p >> 1])) continue;
+                    const int2 st = mode == 1 ? stS[(4 * qy + p) * 128 + (xa - z - sxs)]
+                                              : (rowv[p] ? __ldg(gst + (size_t)p * a.rspitch + (xa - z))
+                                                         : make_int2(0, 0));
+                    const int cc = C::N * static_cast<int>(P[p][j]) - Sa[p] * st.x;
+                    const float rho = static_cast<float>(cc) * __int_as_float(st.y);
+                    if (rho > best[p]) {
+                        best[p] = rho;
+                        bz[p] = z;
+                    }
+                }
+            }
+        };
+        if (uni) {
+            eval_group(lo_c[0], std::false_type{});
+        } else {
+            for (int zg = lo_u; zg <= hi_u; zg += G) eval_group(zg, std::true_type{});
+        }
+    } else {
+        // wide span: the right image from global memory (apron buffer, no clamping)
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            if (!rowv[p]) continue;
+            const int y = ya + p;
+            for (int z = lo_c[p >> 1]; z <= hi_c[p >> 1]; ++z) {
+                uint32_t Sab = 0;
+#pragma unroll
+                for (int t = 0; t < WIN; ++t) {
+                    const uint32_t *lrow = reinterpret_cast<const uint32_t *>(sLrow0 + (p + t) * C::LBOX);
+                    const uint8_t *rrow = a.Rimg + (ptrdiff_t)(y - NH + t) * a.pitch + (xa - z - NH);
+#pragma unroll
+                    for (int k = 0; k < NW; ++k) {
+                        uint32_t lw = sfsr(lrow[w0L + k], lrow[w0L + k + 1], shL);
+                        if (k == NW - 1) lw &= C::LASTMASK;
+                        uint32_t w = 0;
+#pragma unroll
+                        for (int b = 0; b < 4; ++b)
+                            if (4 * k + b < WIN) w |= static_cast<uint32_t>(__ldg(rrow + 4 * k + b)) << (8 * b);
+                        Sab = dp4a_u8(lw, w, Sab);
+                    }
+                }
+                const int2 st = __ldg(gst + (size_t)p * a.rspitch + (xa - z));
+                const int cc = C::N * static_cast<int>(Sab) - Sa[p] * st.x;
+                const float rho = static_cast<float>(cc) * __int_as_float(st.y);
+                if (rho > best[p]) {
+                    best[p] = rho;
+                    bz[p] = z;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        if (!rowv[p]) continue;
+        // rsqrt(Va) scales every candidate of the pixel alike: applied once here.  A flat
+        // left window (rA = 0) has c = 0 for every candidate, so the smallest z wins with 0.
+        float rho = best[p] * rA[p];
+        rho = fminf(1.f, fmaxf(-1.f, rho));
+        const size_t o = (size_t)(ya + p) * a.W + xa;
+        a.d_out[o] = static_cast<int16_t>(bz[p]);
+        if (a.c_out) a.c_out[o] = rho;
+    }
+    if (tid == 0 && a.evals) atomicAdd(a.evals, evsum);
+    return true;
+}
+
+}  // namespace tiles
+}  // namespace msbm
