@@ -226,6 +226,7 @@ msbm_status enqueue_level(msbm_ctx *c, int k, const int16_t *prior, int16_t *d, 
         a.tmR128 = l.tmRR128;
         a.tmR256 = l.tmRR256;
         a.tmS = l.tmS128;
+        a.tmS256 = l.tmS256;
         a.tmSL = l.tmSL;
         a.t.skip = skip;
         a.t.Limg = l.img(0); a.t.Rimg = l.img(1); a.t.pitch = l.pitch;
@@ -392,6 +393,7 @@ msbm_status msbm_create(const msbm_params *params, void *cuda_stream, msbm_ctx *
                       encode_u8(&l.tmRR128, l.base[1], l.pitch, l.rows, 128, rowsR) &&
                       encode_u8(&l.tmRR256, l.base[1], l.pitch, l.rows, 256, rowsR) &&
                       encode_u64(&l.tmS128, l.rstat, l.rspitch, H, 128, l.rty) &&
+                      encode_u64(&l.tmS256, l.rstat, l.rspitch, H, 256, l.rty) &&
                       encode_u64(&l.tmSL, l.lstat, l.rspitch, H, 32, l.rty);
             if (!ok) { c->lv.push_back(l); free_ctx(c); return MSBM_ERR_UNSUPPORTED; }
         }

@@ -26,16 +26,16 @@ struct LevelBuf {
     int2 *rstat = nullptr;       // right-window statistics plane {S, bits(rsqrt(V)) or 0}: H rows
     int2 *lstat = nullptr;       // left-window statistics plane, same layout
     int rspitch = 0;             // of rspitch entries (a multiple of 16), one per pixel
-    int rty = 16;                // rows of this level's restricted tile (8 or 16)
+    int rty = 16;                // rows of this level's restricted tile: 16 (strip tile) or 8
     // TMA maps over the apron buffers.  Full-range tile (8 + 2n rows high):
     //   tmFL   : left,  32*SX + 32 bytes wide, SX per level
     //   tmR256 : right, 256 bytes wide
     // Restricted tile (rty + 2n rows high):
     //   tmRL   : left,  64 bytes wide
-    //   tmRR128, tmRR256 : right, 128 / 256 bytes wide (narrow / wide candidate spans)
-    //   tmS128 : right statistics plane, 128 entries wide, rty rows
-    //   tmSL   : left statistics plane, 32 entries wide, rty rows
-    CUtensorMap tmFL, tmR256, tmRL, tmRR128, tmRR256, tmS128, tmSL;
+    //   tmRR128, tmRR256 : right, 128 / 256 bytes wide (the 256-byte box: rty = 8 only)
+    //   tmS128, tmS256 : right statistics plane, 128 / 256 entries wide, rty rows
+    //   tmSL   : left statistics plane, 32 entries wide, rty rows (rty = 16 only)
+    CUtensorMap tmFL, tmR256, tmRL, tmRR128, tmRR256, tmS128, tmS256, tmSL;
     int full_sx = 4;             // full-range tile width 32*full_sx at this level
     int full_zblock = 0;         // full-range z-block (0 = the tile's maximum)
     bool coarse = false;         // plain full-range search by the small-level kernel
@@ -79,14 +79,16 @@ struct RestrTileArgs {
     int rspitch;         // from global memory)
 };
 
-// Arguments of the standalone restricted kernel (strip tile, zncc_strip_tile.cuh), ty rows
-// per tile (LevelBuf::rty).
+// Arguments of the standalone restricted kernels, ty rows per tile (LevelBuf::rty): the
+// strip tile (zncc_strip_tile.cuh) for ty = 16, the vertical-pair tile
+// (zncc_restricted_tile.cuh) for ty = 8.
 struct RestrArgs {
     CUtensorMap tmL;     // box {64, ty + 2n} over the left apron buffer
     CUtensorMap tmR128;  // box {128, ty + 2n} over the right apron buffer
-    CUtensorMap tmR256;  // box {256, ty + 2n} over the right apron buffer
+    CUtensorMap tmR256;  // box {256, ty + 2n} over the right apron buffer (ty = 8)
     CUtensorMap tmS;     // box {128, ty} over the right statistics plane
-    CUtensorMap tmSL;    // box {32, ty} over the left statistics plane
+    CUtensorMap tmS256;  // box {256, ty} over the right statistics plane (ty = 8)
+    CUtensorMap tmSL;    // box {32, ty} over the left statistics plane (ty = 16)
     RestrTileArgs t;
 };
 

@@ -1,8 +1,13 @@
-// zncc_restricted.cu -- standalone launch of the restricted ZNCC winner-take-all tile
-// (Sec. III-C, Eq. 8-9, first branch; design in zncc_strip_tile.cuh): one CTA per 32 x TY
-// tile, each thread a vertical strip of four pixels that share the products of their
-// common window rows; left- and right-window statistics from the level's planes
-// (level_stats.cu).
+// zncc_restricted.cu -- standalone launches of the restricted ZNCC winner-take-all search
+// (Sec. III-C, Eq. 8-9, first branch).  Two tiles, chosen per level by its size:
+//  * large levels: the strip tile (zncc_strip_tile.cuh), one CTA of 128 threads per 32 x 16
+//    tile, each thread a vertical strip of four pixels that share the products of their
+//    common window rows; left- and right-window statistics from the level's planes;
+//  * small levels: the vertical-pair tile (zncc_restricted_tile.cuh), one CTA of 128
+//    threads per 32 x 8 tile, each thread two pixels of one prior cell: twice the CTAs per
+//    pixel, which hides the per-CTA latency chain (prior load, span reduction, TMA wait)
+//    where the level gives the GPU few tiles.
+#include "zncc_restricted_tile.cuh"
 #include "zncc_strip_tile.cuh"
 
 namespace msbm {
@@ -11,11 +16,31 @@ namespace {
 
 using namespace tiles;
 
-// Minimum CTAs per SM the register allocation must allow (128-thread CTAs at TY = 16).
-constexpr int strip_min_ctas(int nh, int ty) { return (nh <= 4 ? 6 : 3) * (16 / ty); }
+// ---- strip tile (32 x 16)
+constexpr int ST_TY = 16;
+// Minimum CTAs per SM the register allocation must allow.
+constexpr int strip_min_ctas(int nh) { return nh <= 4 ? 6 : 3; }
 
-template <int NH, int G, int TY>
-__global__ void __launch_bounds__(SCfg<NH, TY>::THREADS, strip_min_ctas(NH, TY))
+template <int NH, int G>
+__global__ void __launch_bounds__(SCfg<NH, ST_TY>::THREADS, strip_min_ctas(NH))
+    zncc_strip_kernel(const __grid_constant__ RestrArgs a) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    if (threadIdx.x == 0) {
+        mbar_init(reinterpret_cast<uint64_t *>(smem), 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t parity = 0;
+    strip_tile<NH, G, ST_TY>(a.t, &a.tmL, &a.tmR128, &a.tmS, &a.tmSL, blockIdx.x, blockIdx.y, smem, parity);
+}
+
+// ---- vertical-pair tile (32 x 8)
+constexpr int VP_TY = 8;
+// Up to 9 x 9 windows run eight CTAs per SM (64 registers); larger ones four.
+constexpr int pair_min_ctas(int nh) { return nh <= 4 ? 8 : 4; }
+
+template <int NH, int G>
+__global__ void __launch_bounds__(32 * VP_TY / 2, pair_min_ctas(NH))
     zncc_restricted_kernel(const __grid_constant__ RestrArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
     if (threadIdx.x == 0) {
@@ -24,64 +49,63 @@ __global__ void __launch_bounds__(SCfg<NH, TY>::THREADS, strip_min_ctas(NH, TY))
     }
     __syncthreads();
     uint32_t parity = 0;
-    strip_tile<NH, G, TY>(a.t, &a.tmL, &a.tmR128, &a.tmR256, &a.tmS, &a.tmSL, blockIdx.x, blockIdx.y, smem, parity);
+    restr_tile<NH, G, 32, 1, true, VP_TY>(a.t, &a.tmL, &a.tmR128, &a.tmR256, &a.tmS, &a.tmS256, blockIdx.x,
+                                          blockIdx.y, smem, parity);
 }
 
-template <int NH, int G, int TY>
+template <int NH, int G>
 cudaError_t prepare_t() {
-    using C = SCfg<NH, TY>;
-    return cudaFuncSetAttribute(zncc_restricted_kernel<NH, G, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(C::BYTES));
+    cudaError_t e = cudaFuncSetAttribute(zncc_strip_kernel<NH, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(SCfg<NH, ST_TY>::BYTES));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(zncc_restricted_kernel<NH, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(RCfg<NH, 32, 1, true, VP_TY>::BYTES));
+    return e;
 }
 
-template <int NH, int G, int TY>
-cudaError_t launch_restr_t(const RestrArgs &a, cudaStream_t st) {
-    using C = SCfg<NH, TY>;
-    static_assert(C::BYTES <= 227 * 1024, "restricted tile shape");
-    dim3 grd((a.t.W + C::TX - 1) / C::TX, (a.t.H + TY - 1) / TY);
-    zncc_restricted_kernel<NH, G, TY><<<grd, C::THREADS, C::BYTES, st>>>(a);
+template <int NH, int G>
+cudaError_t launch_restr_t(const RestrArgs &a, int ty, cudaStream_t st) {
+    if (ty == ST_TY) {
+        using C = SCfg<NH, ST_TY>;
+        static_assert(C::BYTES <= 227 * 1024, "strip tile shape");
+        dim3 grd((a.t.W + C::TX - 1) / C::TX, (a.t.H + ST_TY - 1) / ST_TY);
+        zncc_strip_kernel<NH, G><<<grd, C::THREADS, C::BYTES, st>>>(a);
+    } else {
+        using C = RCfg<NH, 32, 1, true, VP_TY>;
+        static_assert(C::TX == 32 && C::BYTES <= 227 * 1024, "restricted tile shape");
+        dim3 grd((a.t.W + C::TX - 1) / C::TX, (a.t.H + VP_TY - 1) / VP_TY);
+        zncc_restricted_kernel<NH, G><<<grd, C::THREADS, C::BYTES, st>>>(a);
+    }
     return cudaGetLastError();
 }
 
 // G, the candidates a thread evaluates per group, is 2r + 1 (at most 7; wider radii run
 // several groups)
-template <int NH, int TY>
-cudaError_t prepare_nt() {
-    cudaError_t e = prepare_t<NH, 1, TY>();
-    if (e == cudaSuccess) e = prepare_t<NH, 3, TY>();
-    if (e == cudaSuccess) e = prepare_t<NH, 5, TY>();
-    if (e == cudaSuccess) e = prepare_t<NH, 7, TY>();
-    return e;
-}
-
 template <int NH>
 cudaError_t prepare_nh() {
-    cudaError_t e = prepare_nt<NH, 8>();
-    if (e == cudaSuccess) e = prepare_nt<NH, 16>();
+    cudaError_t e = prepare_t<NH, 1>();
+    if (e == cudaSuccess) e = prepare_t<NH, 3>();
+    if (e == cudaSuccess) e = prepare_t<NH, 5>();
+    if (e == cudaSuccess) e = prepare_t<NH, 7>();
     return e;
-}
-
-template <int NH, int TY>
-cudaError_t launch_restr_nt(const RestrArgs &a, cudaStream_t st) {
-    switch (a.t.r) {
-        case 0: return launch_restr_t<NH, 1, TY>(a, st);
-        case 1: return launch_restr_t<NH, 3, TY>(a, st);
-        case 2: return launch_restr_t<NH, 5, TY>(a, st);
-        default: return launch_restr_t<NH, 7, TY>(a, st);
-    }
 }
 
 template <int NH>
 cudaError_t launch_restr_nh(const RestrArgs &a, int ty, cudaStream_t st) {
-    return ty == 8 ? launch_restr_nt<NH, 8>(a, st) : launch_restr_nt<NH, 16>(a, st);
+    switch (a.t.r) {
+        case 0: return launch_restr_t<NH, 1>(a, ty, st);
+        case 1: return launch_restr_t<NH, 3>(a, ty, st);
+        case 2: return launch_restr_t<NH, 5>(a, ty, st);
+        default: return launch_restr_t<NH, 7>(a, ty, st);
+    }
 }
 
 }  // namespace
 
 int restr_tile_rows(int W, int H, int sms) {
-    // 32 x 16 tiles unless they would give fewer than four CTAs per SM
+    // the strip tile where its 32 x 16 grid gives every SM at least eight CTAs
     const long ctas = (long)((W + 31) / 32) * ((H + 15) / 16);
-    return ctas >= 4L * sms ? 16 : 8;
+    return ctas >= 8L * sms ? ST_TY : VP_TY;
 }
 
 cudaError_t zncc_restricted_prepare(int nh) {
@@ -97,7 +121,7 @@ cudaError_t zncc_restricted_prepare(int nh) {
 }
 
 cudaError_t launch_zncc_restricted(const RestrArgs &a, int nh, int ty, cudaStream_t st) {
-    if (ty != 8 && ty != 16) return cudaErrorInvalidValue;
+    if (ty != ST_TY && ty != VP_TY) return cudaErrorInvalidValue;
     switch (nh) {
         case 1: return launch_restr_nh<1>(a, ty, st);
         case 2: return launch_restr_nh<2>(a, ty, st);

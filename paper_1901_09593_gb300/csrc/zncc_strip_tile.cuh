@@ -7,11 +7,13 @@
 // Design (a 32 x TY pixel tile, TY = 8 or 16, of 32 x TY/4 threads; each thread owns a
 // vertical strip of four pixels of one column, which spans two prior cells):
 //  * The CTA reduces the union [zlo, zhi] of its spans; the left tile (a 64-byte box), the
-//    right span [x0 - zhi - n, x1 - zlo + n] (a 128- or 256-byte box), the span's entries of
-//    the level's right statistics plane (128 x TY) and the tile's entries of the left
-//    statistics plane (32 x TY) are staged by TMA on one mbarrier with a bounded wait.  A
-//    span wider than 128 bytes reads its right statistics from global memory; wider than
-//    256 it reads the right image there too.
+//    right span [x0 - zhi - n, x1 - zlo + n] (a 128-byte box), the span's entries of the
+//    level's right statistics plane (128 x TY) and the tile's entries of the left statistics
+//    plane (32 x TY) are staged by TMA on one mbarrier with a bounded wait.  A union too wide
+//    for 128 bytes (a tile across a large disparity jump) is staged in several passes, each
+//    covering the smallest pending candidate groups of the tile.
+//  * Each thread's candidates are its two prior cells' spans in groups of G, ascending, a
+//    candidate two spans share being evaluated once.
 //  * The four pixels' windows cover 2n + 4 rows.  For each of those rows the thread aligns
 //    its left window row once (word loads and funnel shifts) and the right bytes of a group
 //    of G consecutive candidates once, extracts the G window offsets, and accumulates
@@ -56,7 +58,7 @@ struct SCfg {
     static constexpr size_t OFF_SL = 128;
     static constexpr size_t PAD_R = 128;         // readable slack before the right span
     static constexpr size_t OFF_SR = OFF_SL + al((size_t)ROWS * LBOX) + PAD_R;
-    static constexpr size_t OFF_SS = OFF_SR + al((size_t)(ROWS + 1) * 256);   // right plane [TY][128]
+    static constexpr size_t OFF_SS = OFF_SR + al((size_t)(ROWS + 2) * 128);   // right plane [TY][128]
     static constexpr size_t OFF_SLS = OFF_SS + (size_t)TY * 128 * 8;          // left plane [TY][32]
     static constexpr size_t BYTES = OFF_SLS + (size_t)TY * 32 * 8;
 };
@@ -145,19 +147,21 @@ __device__ __forceinline__ void strip_sums(const uint8_t *sLrow0, int w0L, int s
 // false if a bounded wait gave up (the error word is then set).
 template <int NH, int G, int TY>
 __device__ bool strip_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const CUtensorMap *tmR128,
-                           const CUtensorMap *tmR256, const CUtensorMap *tmS, const CUtensorMap *tmSL,
-                           int bx, int by, uint8_t *smem, uint32_t &parity) {
+                           const CUtensorMap *tmS, const CUtensorMap *tmSL, int bx, int by, uint8_t *smem,
+                           uint32_t &parity) {
     using C = SCfg<NH, TY>;
-    constexpr int WIN = C::WIN, NW = C::NW;
+    // candidates one pass can stage: 32 + ZR + 2n columns plus up to 15 of alignment in 128
+    constexpr int ZR = 128 - C::TX - 2 * NH - 15;
+    static_assert(ZR >= G - 1, "a group must fit one pass");
     uint64_t &bar = *reinterpret_cast<uint64_t *>(smem);
     int &flag = *reinterpret_cast<int *>(smem + 8);
     int &zlo_s = *reinterpret_cast<int *>(smem + 12);
     int &zhi_s = *reinterpret_cast<int *>(smem + 16);
-    int &mode_s = *reinterpret_cast<int *>(smem + 20);
-    int &xs_s = *reinterpret_cast<int *>(smem + 24);
+    int *za_s = reinterpret_cast<int *>(smem + 20);       // [2]: next pass start (alternating)
+    int &xs_s = *reinterpret_cast<int *>(smem + 28);
     unsigned long long &evsum = *reinterpret_cast<unsigned long long *>(smem + 32);
     const uint8_t *sL = smem + C::OFF_SL;                               // [ROWS][64]
-    const uint8_t *sR = smem + C::OFF_SR;                               // [ROWS + 1][128|256]
+    const uint8_t *sR = smem + C::OFF_SR;                               // [ROWS + 1][128]
     const int2 *stS = reinterpret_cast<const int2 *>(smem + C::OFF_SS);   // [TY][128] right plane
     const int2 *stL = reinterpret_cast<const int2 *>(smem + C::OFF_SLS);  // [TY][32] left plane
 
@@ -187,11 +191,18 @@ __device__ bool strip_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const
         }
     }
     const int lo_u = min(lo_c[0], lo_c[1]), hi_u = max(hi_c[0], hi_c[1]);
+    // the thread's groups, ascending: the lower cell's span from its start in steps of G, then
+    // the rest of the other cell's span (candidates a group already covered are not repeated)
+    const bool swap = lo_c[1] < lo_c[0];
+    const int l1 = swap ? lo_c[1] : lo_c[0], h1 = swap ? hi_c[1] : hi_c[0];
+    const int l2 = swap ? lo_c[0] : lo_c[1], h2 = swap ? hi_c[0] : hi_c[1];
+    int next = any ? l1 : INT_MAX, cell = 0;
     // a warp takes the check-free path when every strip in it has one full-width span
     const bool uni_t = !any || (hi_c[0] - lo_c[0] + 1 == G && (!rowv[2] || (lo_c[1] == lo_c[0] && hi_c[1] == hi_c[0])));
-    const bool uni = __all_sync(0xFFFFFFFFu, uni_t);
+    const bool uni_w = __all_sync(0xFFFFFFFFu, uni_t);
     if (tid == 0) {
         zlo_s = INT_MAX; zhi_s = -1; evsum = 0ull;
+        za_s[0] = INT_MAX; za_s[1] = INT_MAX;
     }
     __syncthreads();
     {
@@ -212,43 +223,13 @@ __device__ bool strip_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const
     __syncthreads();
     const int zlo = zlo_s, zhi = zhi_s;
     const int xlast = min(x0 + C::TX, a.W) - 1;
-    const int rs = x0 - zhi - NH;              // first right column any window reads
-    const int re = xlast - zlo + NH;           // last
-    const int sxs = (x0 - zhi) & ~1;           // first staged right-plane column (even)
-    if (tid == 0) {
-        const int xs = (rs + APX) & ~15;
-        const int width = re + APX + 1 - xs;
-        const int mode = width <= 128 ? 1 : (width <= 256 ? 2 : 0);
-        mode_s = mode;
-        xs_s = xs;
-        uint32_t bytes = C::ROWS * C::LBOX + TY * 32 * 8 + (mode == 1 ? C::ROWS * 128 + TY * 128 * 8
-                                                                      : (mode == 2 ? C::ROWS * 256 : 0));
-        fence_proxy_async_smem();
-        mbar_arrive_expect_tx(&bar, bytes);
-        tma_load_2d(smem + C::OFF_SL, tmL, &bar, x0 - 16 + APX, y0 - NH + APY);
-        tma_load_2d(smem + C::OFF_SLS, tmSL, &bar, x0, y0);
-        if (mode == 1) {
-            tma_load_2d(smem + C::OFF_SR, tmR128, &bar, xs, y0 - NH + APY);
-            tma_load_2d(smem + C::OFF_SS, tmS, &bar, sxs, y0);
-        }
-        if (mode == 2) tma_load_2d(smem + C::OFF_SR, tmR256, &bar, xs, y0 - NH + APY);
-    }
-    if (!tma_batch_wait(&bar, parity, &flag, a.force_timeout != 0, a.err)) return false;
-    parity ^= 1;
-    if (!any) return true;
-    const int mode = mode_s, xs = xs_s;
-    const int soff = APX - xs;                 // staging column of image column X: X + soff
-    const int rst = mode == 1 ? 128 : 256;     // staging row stride (bytes)
+    // one pass when the tile's whole candidate union fits the 128-byte staging box
+    const bool single = ((xlast - zlo + NH) + APX + 1 - ((x0 - zhi - NH + APX) & ~15)) <= 128;
+    const bool uni = single && uni_w;
 
-    // left windows of the four pixels: {Sa, rsqrt(Va)} from the left plane
+    // left windows of the four pixels: {Sa, rsqrt(Va)} from the left plane (after the first wait)
     int Sa[4];
     float rA[4];
-#pragma unroll
-    for (int p = 0; p < 4; ++p) {
-        const int2 e = stL[(4 * qy + p) * 32 + qx];
-        Sa[p] = e.x;
-        rA[p] = __int_as_float(e.y);
-    }
     float best[4];
     int bz[4];
 #pragma unroll
@@ -259,25 +240,51 @@ __device__ bool strip_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const
     const int sc = qx + 16 - NH;               // left staging column of xa - n
     const int w0L = sc >> 2, shL = sc & 3;
     const uint8_t *sLrow0 = sL + (4 * qy) * C::LBOX;
-    const int2 *gst = a.rstat + (size_t)ya * a.rspitch;   // right plane row ya (global)
+    const uint8_t *sRrow0 = sR + (4 * qy) * 128;
 
-    if (mode != 0) {
-        const uint8_t *sRrow0 = sR + (4 * qy) * rst;
-        // the right plane entries of candidate z for pixel p: staged (mode 1) or global
+    int za = zlo;
+    for (int pass = 0;; ++pass) {
+        const int zb = single ? zhi : za + ZR;  // candidates staged in this pass: za .. zb
+        const int sxs = (x0 - zb) & ~1;        // first staged right-plane column (even)
+        if (tid == 0) {
+            const int xs = (x0 - zb - NH + APX) & ~15;
+            xs_s = xs;
+            uint32_t bytes = C::ROWS * 128 + TY * 128 * 8;
+            if (pass == 0) bytes += C::ROWS * C::LBOX + TY * 32 * 8;
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&bar, bytes);
+            if (pass == 0) {
+                tma_load_2d(smem + C::OFF_SL, tmL, &bar, x0 - 16 + APX, y0 - NH + APY);
+                tma_load_2d(smem + C::OFF_SLS, tmSL, &bar, x0, y0);
+            }
+            tma_load_2d(smem + C::OFF_SR, tmR128, &bar, xs, y0 - NH + APY);
+            tma_load_2d(smem + C::OFF_SS, tmS, &bar, sxs, y0);
+        }
+        if (!tma_batch_wait(&bar, parity, &flag, a.force_timeout != 0, a.err)) return false;
+        parity ^= 1;
+        if (pass == 0 && any) {
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                const int2 e = stL[(4 * qy + p) * 32 + qx];
+                Sa[p] = e.x;
+                rA[p] = __int_as_float(e.y);
+            }
+        }
+        const int soff = APX - xs_s;           // staging column of image column X: X + soff
+
+        // one group of G candidates zg .. zg+G-1 for the four pixels
         auto eval_group = [&](const int zg, auto check_tag) {
             constexpr bool check = decltype(check_tag)::value;
             uint32_t P[4][G];
             const int b0 = xa - (zg + G - 1) - NH + soff;   // >= -(G-1): inside the slack
-            strip_sums<NH, G, TY>(sLrow0, w0L, shL, sRrow0, rst, b0, P);
+            strip_sums<NH, G, TY>(sLrow0, w0L, shL, sRrow0, 128, b0, P);
 #pragma unroll
             for (int j = 0; j < G; ++j) {
                 const int z = zg + j;
 #pragma unroll
                 for (int p = 0; p < 4; ++p) {
                     if (check && (z < lo_c[p >> 1] || z > hi_c[p >> 1])) continue;
-                    const int2 st = mode == 1 ? stS[(4 * qy + p) * 128 + (xa - z - sxs)]
-                                              : (rowv[p] ? __ldg(gst + (size_t)p * a.rspitch + (xa - z))
-                                                         : make_int2(0, 0));
+                    const int2 st = stS[(4 * qy + p) * 128 + (xa - z - sxs)];
                     const int cc = C::N * static_cast<int>(P[p][j]) - Sa[p] * st.x;
                     const float rho = static_cast<float>(cc) * __int_as_float(st.y);
                     if (rho > best[p]) {
@@ -289,42 +296,34 @@ __device__ bool strip_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const
         };
         if (uni) {
             eval_group(lo_c[0], std::false_type{});
-        } else {
-            for (int zg = lo_u; zg <= hi_u; zg += G) eval_group(zg, std::true_type{});
+            break;
         }
-    } else {
-        // wide span: the right image from global memory (apron buffer, no clamping)
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            if (!rowv[p]) continue;
-            const int y = ya + p;
-            for (int z = lo_c[p >> 1]; z <= hi_c[p >> 1]; ++z) {
-                uint32_t Sab = 0;
-#pragma unroll
-                for (int t = 0; t < WIN; ++t) {
-                    const uint32_t *lrow = reinterpret_cast<const uint32_t *>(sLrow0 + (p + t) * C::LBOX);
-                    const uint8_t *rrow = a.Rimg + (ptrdiff_t)(y - NH + t) * a.pitch + (xa - z - NH);
-#pragma unroll
-                    for (int k = 0; k < NW; ++k) {
-                        uint32_t lw = sfsr(lrow[w0L + k], lrow[w0L + k + 1], shL);
-                        if (k == NW - 1) lw &= C::LASTMASK;
-                        uint32_t w = 0;
-#pragma unroll
-                        for (int b = 0; b < 4; ++b)
-                            if (4 * k + b < WIN) w |= static_cast<uint32_t>(__ldg(rrow + 4 * k + b)) << (8 * b);
-                        Sab = dp4a_u8(lw, w, Sab);
-                    }
-                }
-                const int2 st = __ldg(gst + (size_t)p * a.rspitch + (xa - z));
-                const int cc = C::N * static_cast<int>(Sab) - Sa[p] * st.x;
-                const float rho = static_cast<float>(cc) * __int_as_float(st.y);
-                if (rho > best[p]) {
-                    best[p] = rho;
-                    bz[p] = z;
-                }
+        // groups that fit this pass (all of them in a single pass), in ascending order
+        while (next != INT_MAX && (single || next + G - 1 <= zb)) {
+            eval_group(next, std::true_type{});
+            const int z = next + G;
+            if (cell == 0 && z <= h1) {
+                next = z;
+            } else if (cell == 0 && l2 != INT_MAX && max(l2, z) <= h2) {
+                cell = 1;
+                next = max(l2, z);
+            } else if (cell == 1 && z <= h2) {
+                next = z;
+            } else {
+                next = INT_MAX;
             }
         }
+        if (single) break;
+        // the next pass starts at the smallest pending group; the barrier also keeps the
+        // staged span until every thread is done with it
+        const int wmin = __reduce_min_sync(0xFFFFFFFFu, next);
+        if ((tid & 31) == 0) atomicMin(&za_s[pass & 1], wmin);
+        __syncthreads();
+        za = za_s[pass & 1];
+        if (tid == 0) za_s[(pass + 1) & 1] = INT_MAX;
+        if (za == INT_MAX) break;
     }
+    if (!any) return true;
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
         if (!rowv[p]) continue;
