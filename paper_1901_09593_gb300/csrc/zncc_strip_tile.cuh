@@ -295,7 +295,8 @@ __device__ bool strip_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const
             }
         };
         if (uni) {
-            eval_group(lo_c[0], std::false_type{});
+            // (threads outside the image have no span: INT_MAX would overflow the offsets)
+            if (any) eval_group(lo_c[0], std::false_type{});
             break;
         }
         // groups that fit this pass (all of them in a single pass), in ascending order
