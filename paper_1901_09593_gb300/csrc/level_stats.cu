@@ -52,21 +52,27 @@ cudaError_t launch_level_stats(const LevelBuf *lv, int n, int nh, cudaStream_t s
     if (2 * n > ST_MAXL) return cudaErrorInvalidValue;
     StatsArgs a;
     memset(&a, 0, sizeof(a));
-    a.n = 2 * n;
-    for (int i = 0; i < 2 * n; ++i) {
-        const LevelBuf &l = lv[i / 2];
-        const int which = (i & 1) ? 0 : 1;           // right plane first, then left
-        int2 *out = which ? l.rstat : l.lstat;
-        if (!out) return cudaErrorInvalidValue;
-        a.tiles_x[i] = (l.W + ST_TX - 1) / ST_TX;
-        a.first[i + 1] = a.first[i] + a.tiles_x[i] * ((l.H + ST_TY - 1) / ST_TY);
-        a.R[i] = l.img(which);
-        a.pitch[i] = l.pitch;
-        a.W[i] = l.W;
-        a.H[i] = l.H;
-        a.out[i] = out;
-        a.opitch[i] = l.rspitch;
+    // the right plane of every level; the left plane where the level's restricted search
+    // reads it (the strip tile, rty = 16)
+    int m = 0;
+    for (int i = 0; i < n; ++i) {
+        const LevelBuf &l = lv[i];
+        for (int which = 1; which >= 0; --which) {
+            if (which == 0 && l.rty != 16) continue;
+            int2 *out = which ? l.rstat : l.lstat;
+            if (!out) return cudaErrorInvalidValue;
+            a.tiles_x[m] = (l.W + ST_TX - 1) / ST_TX;
+            a.first[m + 1] = a.first[m] + a.tiles_x[m] * ((l.H + ST_TY - 1) / ST_TY);
+            a.R[m] = l.img(which);
+            a.pitch[m] = l.pitch;
+            a.W[m] = l.W;
+            a.H[m] = l.H;
+            a.out[m] = out;
+            a.opitch[m] = l.rspitch;
+            ++m;
+        }
     }
+    a.n = m;
     switch (nh) {
         case 1: return stats_launch<1>(a, st);
         case 2: return stats_launch<2>(a, st);

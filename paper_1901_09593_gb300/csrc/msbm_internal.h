@@ -124,8 +124,8 @@ cudaError_t launch_alpha_refine(const LevelBuf &l, int nh, float alpha, int16_t 
 cudaError_t launch_selective_median(const int16_t *d_in, const float *C, int W, int H, float alpha, int16_t *d_out,
                                     cudaStream_t st);
 cudaError_t zncc_full_prepare(int nh, int sx);
-// Window statistics planes (left into lstat, right into rstat) of n consecutive levels
-// (lv[0 .. n-1]) in one launch.
+// Window statistics planes of n consecutive levels (lv[0 .. n-1]) in one launch: the right
+// plane (rstat) of each, and the left plane (lstat) of those with rty = 16.
 cudaError_t launch_level_stats(const LevelBuf *lv, int n, int nh, cudaStream_t st);
 cudaError_t zncc_restricted_prepare(int nh);
 // Rows of the standalone restricted kernel's tile at a W x H level (its TMA boxes are

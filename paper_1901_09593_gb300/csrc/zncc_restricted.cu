@@ -55,11 +55,19 @@ __global__ void __launch_bounds__(32 * VP_TY / 2, pair_min_ctas(NH))
 
 template <int NH, int G>
 cudaError_t prepare_t() {
+    // dynamic shared memory opt-in, and the largest shared-memory carveout so that shared
+    // memory does not cap the resident CTAs below what the registers allow
     cudaError_t e = cudaFuncSetAttribute(zncc_strip_kernel<NH, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(SCfg<NH, ST_TY>::BYTES));
     if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(zncc_strip_kernel<NH, G>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess)
         e = cudaFuncSetAttribute(zncc_restricted_kernel<NH, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  static_cast<int>(RCfg<NH, 32, 1, true, VP_TY>::BYTES));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(zncc_restricted_kernel<NH, G>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
     return e;
 }
 

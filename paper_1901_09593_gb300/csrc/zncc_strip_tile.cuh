@@ -155,11 +155,11 @@ __device__ bool strip_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const
     static_assert(ZR >= G - 1, "a group must fit one pass");
     uint64_t &bar = *reinterpret_cast<uint64_t *>(smem);
     int &flag = *reinterpret_cast<int *>(smem + 8);
-    int &zlo_s = *reinterpret_cast<int *>(smem + 12);
-    int &zhi_s = *reinterpret_cast<int *>(smem + 16);
-    int *za_s = reinterpret_cast<int *>(smem + 20);       // [2]: next pass start (alternating)
-    int &xs_s = *reinterpret_cast<int *>(smem + 28);
-    unsigned long long &evsum = *reinterpret_cast<unsigned long long *>(smem + 32);
+    int *za_s = reinterpret_cast<int *>(smem + 16);       // [2]: next pass start (alternating)
+    int &xs_s = *reinterpret_cast<int *>(smem + 24);
+    int *wlo_s = reinterpret_cast<int *>(smem + 32);      // [TY/4] per-warp span union
+    int *whi_s = reinterpret_cast<int *>(smem + 48);
+    unsigned *wcnt_s = reinterpret_cast<unsigned *>(smem + 64);   // [TY/4] per-warp evaluations
     const uint8_t *sL = smem + C::OFF_SL;                               // [ROWS][64]
     const uint8_t *sR = smem + C::OFF_SR;                               // [ROWS + 1][128]
     const int2 *stS = reinterpret_cast<const int2 *>(smem + C::OFF_SS);   // [TY][128] right plane
@@ -200,12 +200,8 @@ __device__ bool strip_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const
     // a warp takes the check-free path when every strip in it has one full-width span
     const bool uni_t = !any || (hi_c[0] - lo_c[0] + 1 == G && (!rowv[2] || (lo_c[1] == lo_c[0] && hi_c[1] == hi_c[0])));
     const bool uni_w = __all_sync(0xFFFFFFFFu, uni_t);
-    if (tid == 0) {
-        zlo_s = INT_MAX; zhi_s = -1; evsum = 0ull;
-        za_s[0] = INT_MAX; za_s[1] = INT_MAX;
-    }
-    __syncthreads();
     {
+        // the tile's span union and evaluation count: one slot per warp, one barrier
         const int wlo = __reduce_min_sync(0xFFFFFFFFu, lo_u);
         const int whi = __reduce_max_sync(0xFFFFFFFFu, hi_u);
         unsigned cnt = 0;
@@ -215,13 +211,19 @@ __device__ bool strip_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const
                 cnt += static_cast<unsigned>(hi_c[p >> 1] - lo_c[p >> 1] + 1);
         const unsigned wcnt = __reduce_add_sync(0xFFFFFFFFu, cnt);
         if ((tid & 31) == 0) {
-            atomicMin(&zlo_s, wlo);
-            atomicMax(&zhi_s, whi);
-            atomicAdd(&evsum, static_cast<unsigned long long>(wcnt));
+            wlo_s[qy] = wlo;
+            whi_s[qy] = whi;
+            wcnt_s[qy] = wcnt;
         }
+        if (tid == 0) za_s[0] = za_s[1] = INT_MAX;   // pass-start slots, first used after a barrier
     }
     __syncthreads();
-    const int zlo = zlo_s, zhi = zhi_s;
+    int zlo = wlo_s[0], zhi = whi_s[0];
+#pragma unroll
+    for (int w = 1; w < TY / 4; ++w) {
+        zlo = min(zlo, wlo_s[w]);
+        zhi = max(zhi, whi_s[w]);
+    }
     const int xlast = min(x0 + C::TX, a.W) - 1;
     // one pass when the tile's whole candidate union fits the 128-byte staging box
     const bool single = ((xlast - zlo + NH) + APX + 1 - ((x0 - zhi - NH + APX) & ~15)) <= 128;
@@ -283,11 +285,14 @@ __device__ bool strip_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const
                 const int z = zg + j;
 #pragma unroll
                 for (int p = 0; p < 4; ++p) {
-                    if (check && (z < lo_c[p >> 1] || z > hi_c[p >> 1])) continue;
+                    // a candidate outside the pixel's span (check path) is read but not
+                    // taken: its entry index stays within -(G-1) .. 127 of the staged row,
+                    // inside this tile's shared memory
+                    const bool ok = !check || (z >= lo_c[p >> 1] && z <= hi_c[p >> 1]);
                     const int2 st = stS[(4 * qy + p) * 128 + (xa - z - sxs)];
                     const int cc = C::N * static_cast<int>(P[p][j]) - Sa[p] * st.x;
                     const float rho = static_cast<float>(cc) * __int_as_float(st.y);
-                    if (rho > best[p]) {
+                    if (ok && rho > best[p]) {
                         best[p] = rho;
                         bz[p] = z;
                     }
@@ -336,7 +341,12 @@ __device__ bool strip_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const
         a.d_out[o] = static_cast<int16_t>(bz[p]);
         if (a.c_out) a.c_out[o] = rho;
     }
-    if (tid == 0 && a.evals) atomicAdd(a.evals, evsum);
+    if (tid == 0 && a.evals) {
+        unsigned long long ev = 0;
+#pragma unroll
+        for (int w = 0; w < TY / 4; ++w) ev += wcnt_s[w];
+        atomicAdd(a.evals, ev);
+    }
     return true;
 }
 
