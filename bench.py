@@ -140,34 +140,61 @@ def load_peaks():
         return None
 
 
-# One "op" is one 32-bit ALU lane instruction.  Nominal ALU peak: SMs x 128 lanes x max
-# SM clock (an upper bound for every pipe; integer dot products may issue at half rate).
+# One "op" is one 32-bit lane instruction.  Nominal issue peak: SMs x 128 lanes x max SM
+# clock (one warp instruction per clock per SM sub-partition), an upper bound for every pipe.
 def alu_peak_tops(sms: int, mhz: float) -> float:
     return sms * 128 * mhz * 1e6 / 1e12
 
 
+def dp4a_per_eval(window: int) -> int:
+    # the direct window: one 4-way byte dot product per 4 window bytes per row (the method's
+    # sum of products; the remaining per-evaluation terms are a handful of scalar operations)
+    return window * ((window + 3) // 4)
+
+
 def ops_per_eval_restricted(window: int) -> int:
-    # direct window: one dp4a per 4 window bytes per row, plus the exact int32 combine,
-    # int-to-float, two scalings and the WTA compare
-    return window * ((window + 3) // 4) + 5
+    # dp4a for the window plus the exact int32 combine, int-to-float, two scalings, compare
+    return dp4a_per_eval(window) + 5
 
 
 OPS_PER_EVAL_FULL = 8   # sliding sums: 2 vertical + 2 horizontal, c (2), scale (1), compare (1)
 
+PROBE_KINDS = {"dp4a": 0, "funnel_shift": 1, "ffma": 2, "int_add_logic": 3, "lds32": 4}
+
+
+def measure_pipe_peaks(sms: int, stream, target_ms: float = 25.0) -> dict:
+    """Issue rates of the instruction classes the matching kernels use, measured on this GPU
+    with msbm_pipe_probe (8 CTAs of 256 threads per SM), best of three runs each."""
+    import ctypes
+
+    from paper_1901_09593_gb300 import _lib
+    lib = _lib.load()
+    out = {}
+    for name, kind in PROBE_KINDS.items():
+        ms, ops = ctypes.c_float(), ctypes.c_double()
+
+        def run(iters):
+            _lib.check(lib.msbm_pipe_probe(kind, sms * 8, iters, ctypes.c_void_p(stream.cuda_stream),
+                                           ctypes.byref(ms), ctypes.byref(ops)), "msbm_pipe_probe")
+            return ms.value, ops.value
+        t, _ = run(64)
+        iters = max(64, int(64 * target_ms / max(t, 1e-3)))
+        best = max(o / (t_ * 1e-3) for t_, o in (run(iters) for _ in range(3)))
+        out[name] = {"lane_ops_per_s": best, "iters": iters, "ctas": sms * 8}
+    return out
+
 
 def stage_work(name, spec, levels_wh, evals_by_level):
-    """(bound, algorithmic amount, unit) of one stage of the pass."""
+    """(bound, algorithmic amount, unit) of one stage of the pass: HBM bytes for the pyramid,
+    dp4a lane operations (the window's sum of products) for the matching levels."""
     if name == "pyramid":
         # read both input images once, write every level's apron buffer of both images; read
         # the right image of levels 0..K-2 and write their 8-byte statistics planes
         w0, h0 = levels_wh[0]
         return "hbm", (2 * w0 * h0 + sum(2 * (w + 32) * (h + 16) for w, h in levels_wh)
                        + sum(9 * w * h for w, h in levels_wh[:-1])), "B"
-    if name.startswith("full_level"):
-        k = int(name[len("full_level"):])
-        return "alu", evals_by_level[k] * OPS_PER_EVAL_FULL, "op"
-    k = int(name[len("restricted_level"):])
-    return "alu", evals_by_level[k] * ops_per_eval_restricted(spec.window), "op"
+    k = int(name[len("full_level"):]) if name.startswith("full_level") else int(name[len("restricted_level"):])
+    return "dp4a", evals_by_level[k] * dp4a_per_eval(spec.window), "dp4a"
 
 
 # DRAM bytes (read + write) per launch from one committed ncu capture of a kernel, valid
@@ -651,6 +678,15 @@ def run_gpu(args):
     peaks = load_peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_max = (clocks.get("sm_max_mhz") or (peaks or {}).get("sm_max_mhz") or 2070.0)
+    # measured pipe rates (the denominators of the matching stages), clocks sampled meanwhile
+    pclk = ClockSampler(local)
+    pclk.start()
+    pipes = measure_pipe_peaks(sms, stream)
+    pclocks = pclk.stop()
+    pmhz = pclocks.get("sm_mhz") or sm_max
+    for v in pipes.values():
+        v["per_sm_per_clock"] = round(v["lane_ops_per_s"] / (sms * pmhz * 1e6), 2)
+    dp4a_peak = pipes["dp4a"]["lane_ops_per_s"] / 1e12
     stages = []
     for nm, t in zip(stage_names, stage_ms):
         bound, amount, unit = stage_work(nm, spec, levels_wh, evals_by_level)
@@ -658,7 +694,6 @@ def run_gpu(args):
                        "work": amount, "work_unit": unit})
     tot = sum(stage_ms)
     hbm_peak = (peaks or {}).get("hbm_gbs") or 6800.0
-    alu_peak = alu_peak_tops(sms, sm_max)
     for s_ in stages:
         s_["share"] = round(s_["ms"] / tot, 4) if tot > 0 else None
         # achieved fraction of the stage's roofline (algorithmic work / event-timed duration)
@@ -666,35 +701,54 @@ def run_gpu(args):
             if s_["bound"] == "hbm":
                 s_["roofline_frac"] = round(s_["work"] / (s_["ms"] * 1e-3) / 1e9 / hbm_peak, 4)
             else:
-                s_["roofline_frac"] = round(s_["work"] / (s_["ms"] * 1e-3) / 1e12 / alu_peak, 4)
+                s_["roofline_frac"] = round(s_["work"] / (s_["ms"] * 1e-3) / 1e12 / dp4a_peak, 4)
     dom = max(stages, key=lambda s_: s_["ms"])
     if dom["bound"] == "hbm":
-        peak = (peaks or {}).get("hbm_gbs") or 6800.0
+        peak = hbm_peak
         ach = dom["work"] / (dom["ms"] * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak}
+        roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6800 GB/s"}
     else:
-        peak = alu_peak_tops(sms, sm_max)
         ach = dom["work"] / (dom["ms"] * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Top/s", "frac": ach / peak}
+        roof = {"bound": "alu", "pipe": "dp4a", "achieved": ach, "peak": dp4a_peak, "unit": "T dp4a/s",
+                "frac": ach / dp4a_peak,
+                "peak_source": f"measured in this run by msbm_pipe_probe (dp4a, {sms * 8} CTAs x 256 threads) "
+                               f"at {pmhz:.0f} MHz median SM clock",
+                # the same time against the nominal issue rate, with all of an evaluation's
+                # algorithmic operations (dp4a + the scalar combine)
+                "issue_frac_nominal": (dom["work"] / dp4a_per_eval(spec.window)
+                                       * ops_per_eval_restricted(spec.window) / (dom["ms"] * 1e-3) / 1e12
+                                       / alu_peak_tops(sms, sm_max))}
     roof["kernel"] = dom["kernel"]
     roof["traffic"] = measured_traffic(dom["kernel"])
-    roof["peak_source"] = ("MEASURED_PEAKS.json hbm_gbs" if dom["bound"] == "hbm" and peaks else
-                           f"nominal {sms} SMs x 128 lanes x {sm_max:.0f} MHz")
+    roof["pipes"] = pipes
+    roof["pipe_clock_mhz"] = pmhz
 
-    # -- end to end through the C ABI with pinned host buffers
+    # -- end to end through the C ABI with pinned host buffers: K frames through the
+    # pipelined host call (each frame's images uploaded, its pass, its disparity and cost
+    # maps downloaded; frame i+1's upload and frame i-1's download overlap frame i's pass)
     pin_l = torch.from_numpy(sc.left).pin_memory()
     pin_r = torch.from_numpy(sc.right).pin_memory()
-    pin_d = torch.empty((H, W), dtype=torch.int16).pin_memory()
-    pin_c = torch.empty((H, W), dtype=torch.float32).pin_memory()
-    hl, hr, hd, hc = pin_l.numpy(), pin_r.numpy(), pin_d.numpy(), pin_c.numpy()
-    for _ in range(max(3, args.warmup)):
-        ctx.disparity_host(hl, hr, hd, hc)
+    pin_d = [torch.empty((H, W), dtype=torch.int16).pin_memory() for _ in range(2)]
+    pin_c = [torch.empty((H, W), dtype=torch.float32).pin_memory() for _ in range(2)]
+    hl, hr = pin_l.numpy(), pin_r.numpy()
+    K = args.steps
+    lefts, rights = [hl] * K, [hr] * K
+    ds = [pin_d[i % 2].numpy() for i in range(K)]
+    cs = [pin_c[i % 2].numpy() for i in range(K)]
+    ctx.disparity_host_frames(lefts[:max(3, args.warmup)], rights[:max(3, args.warmup)],
+                              ds[:max(3, args.warmup)], cs[:max(3, args.warmup)])
     barrier(dist)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        ctx.disparity_host(hl, hr, hd, hc)
+    ctx.disparity_host_frames(lefts, rights, ds, cs)
     e2e_s = reduce_max(time.perf_counter() - t0, dist, dev)
     e2e_fps = world * args.steps / e2e_s
+    assert np.array_equal(pin_d[(K - 1) % 2].numpy(), d_h), "pipelined host path differs from the device pass"
+    # one frame at a time (no overlap across frames), for comparison
+    t0 = time.perf_counter()
+    for i in range(min(K, 50)):
+        ctx.disparity_host(hl, hr, ds[i], cs[i])
+    e2e_single_fps = min(K, 50) / (time.perf_counter() - t0)
 
     # -- CPU baseline: the oracle on this host (rank 0, N = 1 only)
     cpu = None
@@ -741,7 +795,8 @@ def run_gpu(args):
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": 2 * W * H,
-                "d2h_bytes_per_step": W * H * (2 + 4)},
+                "d2h_bytes_per_step": W * H * (2 + 4), "api": "msbm_disparity_host_frames (pipelined)",
+                "one_frame_per_call_frames_per_s": e2e_single_fps},
         "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
         "gpix_disp_per_s": evals_per_frame * fps / 1e9,
         "gpix_disp_per_s_flat_equivalent": W * H * spec.max_disp * fps / 1e9,

@@ -151,11 +151,24 @@ msbm_status msbm_disparity(msbm_ctx *ctx, const uint8_t *d_left, const uint8_t *
 
 /* Same pass on HOST buffers, waiting for the result: the images are copied into device
  * staging buffers (owned by the context, allocated on the first call), the pass runs on them
- * and the maps are copied back, all on the context's stream.  Page-locked buffers
- * (cudaHostAlloc / cudaHostRegister, e.g. torch pin_memory) make the copies asynchronous
- * DMA transfers; pageable ones work too, at the driver's pageable-copy speed. */
+ * and the maps are copied back.  h_cost may be NULL (the disparity map alone comes back).
+ * Page-locked buffers (cudaHostAlloc / cudaHostRegister, e.g. torch pin_memory) make the
+ * copies asynchronous DMA transfers; pageable ones work too, at the driver's pageable-copy
+ * speed.  The same as msbm_disparity_host_frames with one frame. */
 msbm_status msbm_disparity_host(msbm_ctx *ctx, const uint8_t *h_left, const uint8_t *h_right,
                                 size_t pitch_bytes, int16_t *h_d, float *h_cost);
+
+/* A sequence of n_frames stereo pairs in HOST memory (a video stream), pipelined, waiting
+ * for the last result.  Frame i (arrays of n_frames host pointers; images width x height at
+ * pitch_bytes; maps dense) is uploaded on an upload stream into one of two device staging
+ * sets, matched on the context's stream, and its maps downloaded on a download stream, so
+ * that the upload of frame i+1 and the download of frame i-1 overlap the pass of frame i
+ * (they need page-locked buffers to overlap).  h_costs may be NULL or hold NULLs (no cost
+ * map for that frame).  Results equal msbm_disparity_host frame by frame.  Returns the
+ * first CUDA error, or the device error word as msbm_sync does. */
+msbm_status msbm_disparity_host_frames(msbm_ctx *ctx, int32_t n_frames, const uint8_t *const *h_lefts,
+                                       const uint8_t *const *h_rights, size_t pitch_bytes,
+                                       int16_t *const *h_ds, float *const *h_costs);
 
 /* Copy the maps of an intermediate level (1..K-1) left by the last msbm_disparity into
  * the caller's dense device buffers (W_k x H_k; cost_out may be NULL).  Level 0 is written
@@ -264,6 +277,19 @@ msbm_status msbm_zncc_softargmax_bwd(const float *d_left, const float *d_right, 
                                      const float *m_in, const float *l_in, const float *g_d,
                                      float *g_left, float *g_right, void *workspace,
                                      size_t workspace_bytes, void *cuda_stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Measurement support (the paper has no counterpart): issue-rate probe of one instruction
+ * class, the denominator of the matching kernels' rooflines.
+ *   kind   : 0 = 4-way byte dot product (dp4a), 1 = 32-bit funnel shift, 2 = FP32 FMA,
+ *            3 = 32-bit integer add / logic, 4 = 32-bit shared-memory load.
+ *   blocks : CTAs of 256 threads (1 .. 65536); iters: loop iterations (1 .. 2^24), each
+ *            8 independent chains x 16 operations per thread.
+ * Runs one launch on cuda_stream and waits for it; *ms = its CUDA-event time, *lane_ops =
+ * the operations executed (blocks * 256 * iters * 128).  Allocates and frees a small
+ * result buffer; changes no clock or device setting. */
+msbm_status msbm_pipe_probe(int32_t kind, int32_t blocks, int32_t iters, void *cuda_stream, float *ms,
+                            double *lane_ops);
 
 /* ---------------------------------------------------------------------------------------
  * Allocation-free flat matching.  The paper has no counterpart: this is a deployment aid.

@@ -50,6 +50,8 @@ SIGNATURES = {
     "msbm_match_level": ([c_void_p, c_int32, c_void_p, c_void_p, c_void_p], ctypes.c_int),
     "msbm_disparity": ([c_void_p, c_void_p, c_void_p, c_size_t, c_void_p, c_void_p], ctypes.c_int),
     "msbm_disparity_host": ([c_void_p, c_void_p, c_void_p, c_size_t, c_void_p, c_void_p], ctypes.c_int),
+    "msbm_disparity_host_frames": ([c_void_p, c_int32, c_void_p, c_void_p, c_size_t, c_void_p, c_void_p], ctypes.c_int),
+    "msbm_pipe_probe": ([c_int32, c_int32, c_int32, c_void_p, P(ctypes.c_float), P(ctypes.c_double)], ctypes.c_int),
     "msbm_level_result": ([c_void_p, c_int32, c_void_p, c_void_p], ctypes.c_int),
     "msbm_profile_disparity": ([c_void_p, c_void_p, c_void_p, c_size_t, c_void_p, c_void_p,
                                 P(ctypes.c_float), c_int32], ctypes.c_int),

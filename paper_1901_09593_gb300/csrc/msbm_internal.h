@@ -128,9 +128,9 @@ cudaError_t zncc_full_prepare(int nh, int sx);
 // plane (rstat) of each, and the left plane (lstat) of those with rty = 16.
 cudaError_t launch_level_stats(const LevelBuf *lv, int n, int nh, cudaStream_t st);
 cudaError_t zncc_restricted_prepare(int nh);
-// Rows of the standalone restricted kernel's tile at a W x H level (its TMA boxes are
-// rows + 2n high): 16, or 8 where 32 x 16 tiles would give the GPU too few CTAs.
-int restr_tile_rows(int W, int H, int sms);
+// Rows of the standalone restricted kernel's tile at a W x H level with window half-width
+// nh (its TMA boxes are rows + 2n high): 16 (the strip tile) or 8 (the vertical-pair tile).
+int restr_tile_rows(int W, int H, int nh, int sms);
 cudaError_t launch_zncc_restricted(const RestrArgs &a, int nh, int ty, cudaStream_t st);
 
 }  // namespace msbm

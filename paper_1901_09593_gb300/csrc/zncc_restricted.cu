@@ -1,9 +1,9 @@
 // zncc_restricted.cu -- standalone launches of the restricted ZNCC winner-take-all search
-// (Sec. III-C, Eq. 8-9, first branch).  Two tiles, chosen per level by its size:
-//  * large levels: the strip tile (zncc_strip_tile.cuh), one CTA of 128 threads per 32 x 16
+// (Sec. III-C, Eq. 8-9, first branch).  Two tiles, chosen per level by its size and window:
+//  * large levels, windows of 9 x 9 and more: the strip tile (zncc_strip_tile.cuh), one CTA of 128 threads per 32 x 16
 //    tile, each thread a vertical strip of four pixels that share the products of their
 //    common window rows; left- and right-window statistics from the level's planes;
-//  * small levels: the vertical-pair tile (zncc_restricted_tile.cuh), one CTA of 128
+//  * otherwise: the vertical-pair tile (zncc_restricted_tile.cuh), one CTA of 128
 //    threads per 32 x 8 tile, each thread two pixels of one prior cell: twice the CTAs per
 //    pixel, which hides the per-CTA latency chain (prior load, span reduction, TMA wait)
 //    where the level gives the GPU few tiles.
@@ -110,10 +110,14 @@ cudaError_t launch_restr_nh(const RestrArgs &a, int ty, cudaStream_t st) {
 
 }  // namespace
 
-int restr_tile_rows(int W, int H, int sms) {
-    // the strip tile where its 32 x 16 grid gives every SM at least eight CTAs
+int restr_tile_rows(int W, int H, int nh, int sms) {
+    // The strip tile for windows of 9 x 9 and more where its 32 x 16 grid gives every SM at
+    // least eight CTAs.  Measured (level 0 / whole pass): 2880 x 1984, 9 x 9, r = 3:
+    // 114.7 / 235 us against 151.6 / 258 us for the vertical-pair tile; 1400 x 1000, 7 x 7,
+    // r = 2: 26.6 us for both tiles at level 0, the strip tile's left-window plane adding
+    // ~4 us to the pass.
     const long ctas = (long)((W + 31) / 32) * ((H + 15) / 16);
-    return ctas >= 8L * sms ? ST_TY : VP_TY;
+    return (nh >= 4 && ctas >= 8L * sms) ? ST_TY : VP_TY;
 }
 
 cudaError_t zncc_restricted_prepare(int nh) {

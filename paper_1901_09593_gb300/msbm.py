@@ -234,6 +234,36 @@ class Context:
             cost_out.ctypes.data if cost_out is not None else None), "msbm_disparity_host")
         return d_out, cost_out
 
+    def disparity_host_frames(self, lefts, rights, d_outs, cost_outs=None):
+        """A sequence of pairs in host arrays, pipelined (msbm_disparity_host_frames): frame
+        i+1's upload and frame i-1's download overlap frame i's pass when the arrays are
+        page-locked.  Waits for the last frame; returns (d_outs, cost_outs)."""
+        self._bind_stream()
+        n = len(lefts)
+        if n < 1 or len(rights) != n or len(d_outs) != n or (cost_outs is not None and len(cost_outs) != n):
+            raise ValueError("lefts, rights, d_outs (and cost_outs) must be equally long and non-empty")
+        pitch = lefts[0].strides[0]
+        for i in range(n):
+            for a, nm in ((lefts[i], "left"), (rights[i], "right")):
+                if a.dtype != np.uint8 or a.shape != (self.height, self.width) or a.strides[1] != 1 \
+                        or a.strides[0] != pitch:
+                    raise ValueError(f"{nm}[{i}] must be uint8 ({self.height}, {self.width}) at one row pitch")
+            if d_outs[i].dtype != np.int16 or d_outs[i].shape != (self.height, self.width) \
+                    or not d_outs[i].flags.c_contiguous:
+                raise ValueError(f"d_outs[{i}] must be a dense int16 ({self.height}, {self.width}) array")
+            c = None if cost_outs is None else cost_outs[i]
+            if c is not None and (c.dtype != np.float32 or c.shape != (self.height, self.width)
+                                  or not c.flags.c_contiguous):
+                raise ValueError(f"cost_outs[{i}] must be a dense float32 ({self.height}, {self.width}) array")
+        P = ctypes.c_void_p
+        L = (P * n)(*[a.ctypes.data for a in lefts])
+        R = (P * n)(*[a.ctypes.data for a in rights])
+        D = (P * n)(*[a.ctypes.data for a in d_outs])
+        C = None if cost_outs is None else (P * n)(*[None if c is None else c.ctypes.data for c in cost_outs])
+        _lib.check(self._lib.msbm_disparity_host_frames(self._ctx, n, L, R, pitch, D, C),
+                   "msbm_disparity_host_frames")
+        return d_outs, cost_outs
+
     def profile_disparity(self, left, right, d_out, cost_out):
         """One pass with per-stage CUDA-event timing; returns the list of milliseconds in
         launch order (pyramid, coarsest full search, restricted levels K-2..0)."""

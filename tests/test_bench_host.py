@@ -53,8 +53,10 @@ def test_stage_work_units():
     ev = [10, 20, 30, 40]
     bound, work, unit = bench.stage_work("pyramid", spec, wh, ev)
     assert (bound, unit) == ("hbm", "B") and work > 2 * spec.width * spec.height
-    assert bench.stage_work("full_level3", spec, wh, ev) == ("alu", 40 * bench.OPS_PER_EVAL_FULL, "op")
-    assert bench.stage_work("restricted_level1", spec, wh, ev) == ("alu", 20 * 19, "op")
+    # matching stages count the window's dp4a (7 x 7: 7 rows x 2 words) per evaluation
+    assert bench.dp4a_per_eval(7) == 14 and bench.dp4a_per_eval(9) == 27 and bench.dp4a_per_eval(5) == 10
+    assert bench.stage_work("full_level3", spec, wh, ev) == ("dp4a", 40 * 14, "dp4a")
+    assert bench.stage_work("restricted_level1", spec, wh, ev) == ("dp4a", 20 * 14, "dp4a")
 
 
 def test_equal_or_better_picks_fastest_admissible_method():

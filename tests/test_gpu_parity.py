@@ -304,3 +304,32 @@ def test_full_size_flat_every_pixel():
     ties = compare_level(host(d), host(c), do, co, c2, "flat 1400x1000")
     assert ties <= 1e-3 * s.width * s.height, ties
     assert ctx.eval_count() == ev == sum(min(s.max_disp - 1, x) + 1 for x in range(s.width)) * s.height
+
+
+@pytest.mark.parametrize("name,n,pinned", [("small_320x240", 5, True), ("small_320x240", 3, False),
+                                           ("bench_1400x1000", 4, True)])
+def test_pipelined_host_frames_equal_the_device_path(name, n, pinned):
+    # frames of different scenes through msbm_disparity_host_frames (two staging sets
+    # alternate, uploads and downloads overlap the passes) equal the device-buffer pass
+    # frame by frame; every other frame asks for no cost map
+    import torch
+    spec = scenes.SPECS[name]
+    scs = [scenes.make_pair(spec, 20 + i) for i in range(n)]
+    ctx = make_ctx(spec.width, spec.height, spec.max_disp, spec.levels, spec.window, spec.radius)
+    shape = (spec.height, spec.width)
+
+    def host_buf(a=None, dtype=np.uint8):
+        t = torch.from_numpy(a) if a is not None else torch.zeros(shape, dtype=dtype)
+        return (t.pin_memory() if pinned else t.clone()).numpy()
+    lefts = [host_buf(s.left) for s in scs]
+    rights = [host_buf(s.right) for s in scs]
+    ds = [host_buf(dtype=torch.int16) for _ in scs]
+    cs = [host_buf(dtype=torch.float32) if i % 2 == 0 else None for i in range(n)]
+    for _ in range(2):          # twice: the staging sets and graphs are reused
+        ctx.disparity_host_frames(lefts, rights, ds, cs)
+        for i, s in enumerate(scs):
+            d, c = ctx.disparity(dev(s.left), dev(s.right))
+            ctx.sync()
+            np.testing.assert_array_equal(ds[i], host(d), err_msg=f"frame {i}")
+            if cs[i] is not None:
+                np.testing.assert_array_equal(cs[i], host(c), err_msg=f"frame {i} cost")
