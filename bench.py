@@ -221,7 +221,8 @@ def measured_traffic(kernel):
 
 def equal_or_better(methods, flat_fps, flat_bad1):
     """The fastest measured hierarchical method whose bad-1 rate is at most flat matching's."""
-    ok = [(v["frames_per_s"], k, v) for k, v in methods.items() if v.get("bad1", 1.0) <= flat_bad1]
+    ok = [(v["frames_per_s"], k, v) for k, v in methods.items()
+          if "frames_per_s" in v and v.get("bad1", 1.0) <= flat_bad1]
     if not ok:
         return None
     f, k, v = max(ok)
@@ -537,6 +538,10 @@ def _flat_and_methods(args, sc, L, R, d, c, timed, methods):
     spec = sc.spec
     W, H = spec.width, spec.height
     flat = Context(W, H, spec.max_disp, 1, spec.window, spec.radius)
+    # the flat baseline at its autotuned tiling (tile width 32*sx, z-block)
+    from paper_1901_09593_gb300 import autotune
+    tune = autotune.tune_full_level(W, H, spec.max_disp, spec.window)
+    flat.set_level_tuning(0, tune["sx"], tune["zblock"])
     df = torch.empty_like(d)
     cf = torch.empty_like(c)
     fsteps = max(3, min(args.steps, 20))
@@ -571,6 +576,7 @@ def _flat_and_methods(args, sc, L, R, d, c, timed, methods):
                                        for nm, v in zip(cx.stage_names(), zip(*prof))}}
         cx.close()
     flat.close()
+    methods["_flat_tuning"] = {"sx": tune["sx"], "zblock": tune["zblock"]}
     return flat_fps, bad1_f, bad2_f, fsteps
 
 

@@ -8,8 +8,10 @@ namespace {
 
 using namespace tiles;
 
+// Three CTAs per SM: the 7 x 7, 128-column tile takes 168 registers and 68.5 KB of shared
+// memory (its window-statistics temporaries packed one word per column sum).
 template <int NH, int SX, int ZC>
-__global__ void __launch_bounds__(128, 2) zncc_full_kernel(const __grid_constant__ FullArgs a) {
+__global__ void __launch_bounds__(128, 3) zncc_full_kernel(const __grid_constant__ FullArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
     if (threadIdx.x == 0) {
         mbar_init(reinterpret_cast<uint64_t *>(smem), 1);
@@ -25,9 +27,15 @@ cudaError_t launch_full_t(const FullArgs *a, cudaStream_t st) {
     constexpr int ZC = NH <= 4 ? 8 : 4;
     using C = FullCfg<NH, SX, ZC>;
     auto kern = zncc_full_kernel<NH, SX, ZC>;
-    if (!a)  // preparation: opt in to the dynamic shared memory this instantiation needs
-        return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    static_cast<int>(C::BYTES));
+    if (!a) {  // preparation: the dynamic shared memory this instantiation needs, and the
+               // largest carveout so that shared memory does not cap the resident CTAs
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(C::BYTES));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     cudaSharedmemCarveoutMaxShared);
+        return e;
+    }
     dim3 grd((a->t.W + C::TX - 1) / C::TX, (a->t.H + C::TY - 1) / C::TY);
     kern<<<grd, dim3(128), C::BYTES, st>>>(*a);
     return cudaGetLastError();

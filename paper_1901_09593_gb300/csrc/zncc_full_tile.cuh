@@ -66,7 +66,7 @@ struct FullCfg {
     static constexpr size_t OFF_STL = OFF_RF + al((size_t)ROWS * RFP * 4);
     static constexpr size_t OFF_STR = OFF_STL + al((size_t)3 * TY * TX * 4);
     static constexpr size_t OFF_TMP = OFF_STR + al((size_t)TY * SFP * 8);
-    static constexpr size_t OFF_BEST = OFF_TMP + al((size_t)TY * RFP * 8);
+    static constexpr size_t OFF_BEST = OFF_TMP + al((size_t)TY * RFP * 4);
     static constexpr size_t BYTES = OFF_BEST + al((size_t)TY * TX * 8);
 };
 
@@ -192,40 +192,44 @@ __device__ __forceinline__ void full_chunk(const float *Lf, const float *Rf, con
     }
 }
 
-// Window statistics from a widened tile: vertical sliding sums into tmp, then horizontal
-// sums.  Output column v uses tile columns v .. v + 2n.  Writes (S, rsqrt(V)) or, for the
-// left tile, the split (S_hi, S_lo) and rsqrt(V) into three planes.
+// Window statistics from a widened tile: vertical sliding sums into tmp (one word per
+// column sum: q | s << 20, s < 4096 and q < 2^20 for columns of up to 13 bytes), then
+// horizontal sums.  Output column v uses tile columns v .. v + 2n.  Writes (S, rsqrt(V)) or,
+// for the left tile, the split (S_hi, S_lo) and rsqrt(V) into three planes.  All sums are
+// exact integers.
 template <int NH, bool LEFT>
-__device__ __forceinline__ void tile_stats(const float *img, int pitch, int cols_in, float2 *tmp,
+__device__ __forceinline__ void tile_stats(const float *img, int pitch, int cols_in, uint32_t *tmp,
                                            int tmp_pitch, int cols_out, float2 *outR, int outR_pitch,
                                            float *outL, int TXo) {
     constexpr int TY = FT_TY, WIN = 2 * NH + 1, N = WIN * WIN;
     for (int c = threadIdx.x; c < cols_in; c += blockDim.x) {
-        float s = 0.f, q = 0.f;
+        int s = 0, q = 0;
 #pragma unroll
         for (int t = 0; t < WIN; ++t) {
-            float v = img[t * pitch + c];
-            s += v; q = fmaf(v, v, q);
+            const int v = static_cast<int>(img[t * pitch + c]);
+            s += v; q += v * v;
         }
-        tmp[c] = make_float2(s, q);
+        tmp[c] = static_cast<uint32_t>(q) | (static_cast<uint32_t>(s) << 20);
 #pragma unroll 1
         for (int ry = 1; ry < TY; ++ry) {
-            float vn = img[(ry + 2 * NH) * pitch + c], vo = img[(ry - 1) * pitch + c];
-            s = (s + vn) - vo;
-            q = fmaf(-vo, vo, fmaf(vn, vn, q));
-            tmp[ry * tmp_pitch + c] = make_float2(s, q);
+            const int vn = static_cast<int>(img[(ry + 2 * NH) * pitch + c]);
+            const int vo = static_cast<int>(img[(ry - 1) * pitch + c]);
+            s += vn - vo;
+            q += vn * vn - vo * vo;
+            tmp[ry * tmp_pitch + c] = static_cast<uint32_t>(q) | (static_cast<uint32_t>(s) << 20);
         }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < TY * cols_out; i += blockDim.x) {
         int ry = i / cols_out, v = i - ry * cols_out;
-        float s = 0.f, q = 0.f;
+        int si = 0, qi = 0;
 #pragma unroll
         for (int j = 0; j < WIN; ++j) {
-            float2 t = tmp[ry * tmp_pitch + v + j];
-            s += t.x; q += t.y;
+            const uint32_t t = tmp[ry * tmp_pitch + v + j];
+            si += static_cast<int>(t >> 20);
+            qi += static_cast<int>(t & 0xFFFFFu);
         }
-        int si = __float2int_rn(s), qi = __float2int_rn(q);
+        const float s = static_cast<float>(si);
         int V = N * qi - si * si;                      // exact: |N*Q| < 2^31 for n <= 6
         float r = V > 0 ? rsqrtf(static_cast<float>(V)) : 0.f;
         if (LEFT) {
@@ -255,7 +259,7 @@ __device__ bool full_tile(const FullTileArgs &a, const CUtensorMap *tmL, const C
     float *Rf = reinterpret_cast<float *>(smem + C::OFF_RF);
     float *stL = reinterpret_cast<float *>(smem + C::OFF_STL);
     float2 *stR = reinterpret_cast<float2 *>(smem + C::OFF_STR);
-    float2 *tmp = reinterpret_cast<float2 *>(smem + C::OFF_TMP);
+    uint32_t *tmp = reinterpret_cast<uint32_t *>(smem + C::OFF_TMP);
     unsigned long long *best = reinterpret_cast<unsigned long long *>(smem + C::OFF_BEST);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
