@@ -70,6 +70,12 @@ typedef enum msbm_status {
  * `window` is level 0's; level k matches with half-width n_k = max(1, n_0 >> k), i.e.
  * windows 2 n_k + 1 (11, 5, 3, 3, ... for the paper's 11 x 11). */
 #define MSBM_FLAG_WINDOW_HALVING 32u
+/* Batch execution mode (msbm_batch_create, taken from pairs[0].flags): instead of one
+ * persistent launch over the (pair, stage, tile) queue, one launch per group of stages that
+ * share a tile function (pyramid groups, coarsest searches, statistics planes, then each
+ * restricted level from the coarsest down), all pairs' tiles of a group in one grid,
+ * captured in one CUDA graph.  Same results. */
+#define MSBM_FLAG_BATCH_GROUPED 64u
 
 /* Problem statement (Sec. III; window and pyramid depth as in Sec. IV). */
 typedef struct msbm_params {

@@ -26,6 +26,7 @@ MSBM_FLAG_BETA_FALLBACK = 8
 MSBM_FLAG_SELECTIVE_MEDIAN = 16
 MSBM_FLAGS_FULL_METHOD = 28
 MSBM_FLAG_WINDOW_HALVING = 32
+MSBM_FLAG_BATCH_GROUPED = 64
 
 # Every function the header declares, with its ctypes signature.
 c_void_p, c_int32, c_uint32, c_size_t = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_size_t

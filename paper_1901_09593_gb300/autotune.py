@@ -101,3 +101,48 @@ def tune_batch(specs, cache_path: str | None = _CACHE):
         sx.append(memo[key]["sx"])
         zb.append(memo[key]["zblock"])
     return sx, zb
+
+
+def tune_batch_mode(specs, lefts, rights, full_sx=None, full_zblock=None, reps: int = 10,
+                    cache_path: str | None = _CACHE, force: bool = False):
+    """Batch execution mode for a workload: times the persistent launch and the grouped
+    launches (MSBM_FLAG_BATCH_GROUPED) on the caller's pairs with CUDA events and returns
+    {"grouped": bool, "persistent_ms": .., "grouped_ms": ..}, cached by the pairs' shapes.
+    Results never depend on the choice."""
+    import hashlib
+
+    import torch
+
+    from . import _lib
+    from .batch import Batch
+    name = torch.cuda.get_device_name()
+    shape = json.dumps([list(s) for s in specs] + [list(full_sx or []), list(full_zblock or [])])
+    key = f"{name}|batchmode|{hashlib.sha256(shape.encode()).hexdigest()[:16]}"
+    if cache_path and not force:
+        with _lock:
+            hit = _load_cache(cache_path).get(key)
+        if hit:
+            return hit
+    stream = torch.cuda.current_stream()
+    out = {}
+    for nm, flags in (("persistent", 0), ("grouped", _lib.MSBM_FLAG_BATCH_GROUPED)):
+        b = Batch(specs, full_sx, full_zblock, flags=flags)
+        d, c = b.alloc_outputs()
+        for _ in range(3):
+            b.run(lefts, rights, d, c)
+        b.sync()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for e0, e1 in ev:
+            e0.record(stream)
+            b.run(lefts, rights, d, c)
+            e1.record(stream)
+        b.sync()
+        out[nm + "_ms"] = sorted(e0.elapsed_time(e1) for e0, e1 in ev)[reps // 2]
+        b.close()
+    out["grouped"] = out["grouped_ms"] < out["persistent_ms"]
+    if cache_path:
+        with _lock:
+            cache = _load_cache(cache_path)
+            cache[key] = out
+            _save_cache(cache_path, cache)
+    return out

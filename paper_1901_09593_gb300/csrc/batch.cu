@@ -311,6 +311,152 @@ __global__ void __launch_bounds__(BT_THREADS, FULL ? BT_CTAS_FULL : BT_CTAS_LEAN
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Grouped launches (MSBM_FLAG_BATCH_GROUPED).  The same per-pair stage tables, run as one
+// ordinary launch per group of stages that share a tile function and its template
+// parameters (kind, window, tile variant) and a place in the pass order (pyramid groups,
+// coarsest search, statistics planes, then restricted level k from the coarsest down).  A
+// group's CTAs cover the tiles of all its (pair, stage) segments; a CTA finds its segment
+// by binary search over the segments' first blocks.  Stream order between the launches of
+// the captured graph replaces the persistent kernel's completion counters, so there are
+// no device waits besides each tile's own TMA wait, and each tile function keeps the
+// register allocation of a kernel of its own.
+
+struct BGSeg {
+    int start;               // first block of the segment in its launch
+    int pair, stage;
+};
+
+struct BGArgs {
+    const BPair *pairs;
+    const BMaps *maps;       // [pair * BT_MAXK + level]
+    const BIO *io;
+    const BGSeg *segs;       // this launch's segments
+    int nseg;
+    unsigned long long *evals;
+    int *err;
+    int force_timeout;
+};
+
+__device__ __forceinline__ int bg_find(const BGArgs &a, int b) {
+    int lo = 0, hi = a.nseg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.segs[mid].start <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int F>
+__global__ void __launch_bounds__(BT_THREADS) bg_pyr_kernel(const __grid_constant__ BGArgs a) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    const BGSeg sg = a.segs[bg_find(a, blockIdx.x)];
+    const BPair &P = a.pairs[sg.pair];
+    const BIO &io = a.io[sg.pair];
+    const BStage &S = P.st[sg.stage];
+    const PyrFuseArgs &pf = P.pf[S.arg];
+    const int tile = blockIdx.x - sg.start, per = S.ntiles / 2, img = tile / per, t = tile - img * per;
+    const int by = t / S.tiles_x, bx = t - by * S.tiles_x;
+    const uint8_t *src = S.arg == 0 ? (img ? io.R : io.L) : pf.src[img];
+    const size_t spitch = S.arg == 0 ? io.pitch : pf.spitch;
+    pyr_fused_tile<F, BT_THREADS>(pf, src, spitch, bx, by, img, S.tiles_x, P.pf_nby[S.arg], smem);
+}
+
+__global__ void __launch_bounds__(BT_THREADS) bg_copy_kernel(const __grid_constant__ BGArgs a) {
+    const BGSeg sg = a.segs[bg_find(a, blockIdx.x)];
+    const BPair &P = a.pairs[sg.pair];
+    const BIO &io = a.io[sg.pair];
+    const BLevel &d = P.lv[0];
+    const int tile = blockIdx.x - sg.start;
+    const int quads = (d.W + 2 * APX + 3) / 4;
+    const int y0 = tile * BT_BAND - APY;
+    const int nrow = min(BT_BAND, d.H + APY - y0);
+    for (int i = threadIdx.x; i < 2 * nrow * quads; i += BT_THREADS) {
+        const int img = i / (nrow * quads), j = i - img * nrow * quads;
+        const int Y = y0 + j / quads, X0 = (j % quads) * 4 - APX;
+        copy_quad(img ? io.R : io.L, io.pitch, d.W, d.H, img ? d.R : d.L, d.pitch, X0, Y);
+    }
+}
+
+template <int NH>
+__global__ void __launch_bounds__(BT_THREADS) bg_stats_kernel(const __grid_constant__ BGArgs a) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    const BGSeg sg = a.segs[bg_find(a, blockIdx.x)];
+    const BPair &P = a.pairs[sg.pair];
+    const int tile = blockIdx.x - sg.start, K = P.K;
+    int k = 0;
+    while (k + 1 < K - 1 && tile >= P.sfirst[k + 1]) ++k;
+    const int t = tile - P.sfirst[k], by = t / P.stx[k], bx = t - by * P.stx[k];
+    const BLevel &l = P.lv[k];
+    stats_tile<NH, BT_THREADS>(l.R, l.pitch, l.W, l.H, l.rstat, l.rspitch, bx, by, smem);
+}
+
+template <int NH>
+__global__ void __launch_bounds__(BT_THREADS) bg_coarse_kernel(const __grid_constant__ BGArgs a) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    const BGSeg sg = a.segs[bg_find(a, blockIdx.x)];
+    const BPair &P = a.pairs[sg.pair];
+    const BIO &io = a.io[sg.pair];
+    const BStage &S = P.st[sg.stage];
+    const int k = S.arg, tile = blockIdx.x - sg.start;
+    const BLevel &l = P.lv[k];
+    const int by = tile / S.tiles_x, bx = tile - by * S.tiles_x;
+    coarse_tile<NH, BT_CO_TY, BT_THREADS>(l.L, l.R, l.pitch, l.W, l.H, l.Dk, k == 0 ? io.d : l.d,
+                                          k == 0 ? io.c : l.c, a.evals, bx, by, smem);
+}
+
+template <int NH, int SX>
+__global__ void __launch_bounds__(BT_THREADS, 3) bg_full_kernel(const __grid_constant__ BGArgs a) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    if (threadIdx.x == 0) {
+        mbar_init(reinterpret_cast<uint64_t *>(smem), 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const BGSeg sg = a.segs[bg_find(a, blockIdx.x)];
+    const BPair &P = a.pairs[sg.pair];
+    const BIO &io = a.io[sg.pair];
+    const BStage &S = P.st[sg.stage];
+    const int k = S.arg, tile = blockIdx.x - sg.start;
+    const BLevel &l = P.lv[k];
+    FullTileArgs t = {};
+    t.W = l.W; t.H = l.H; t.Dk = l.Dk; t.zblock = l.zblock;
+    t.d_out = k == 0 ? io.d : l.d;
+    t.c_out = k == 0 ? io.c : l.c;
+    t.evals = a.evals; t.err = a.err; t.force_timeout = a.force_timeout;
+    const BMaps &m = a.maps[sg.pair * BT_MAXK + k];
+    uint32_t parity = 0;
+    full_tile<NH, SX, BT_ZC>(t, &m.mFL, &m.mF256, tile % S.tiles_x, tile / S.tiles_x, smem, parity);
+}
+
+template <int NH, int G>
+__global__ void __launch_bounds__(BT_THREADS, 8) bg_restr_kernel(const __grid_constant__ BGArgs a) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    if (threadIdx.x == 0) {
+        mbar_init(reinterpret_cast<uint64_t *>(smem), 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const BGSeg sg = a.segs[bg_find(a, blockIdx.x)];
+    const BPair &P = a.pairs[sg.pair];
+    const BIO &io = a.io[sg.pair];
+    const BStage &S = P.st[sg.stage];
+    const int k = S.arg, tile = blockIdx.x - sg.start;
+    const BLevel &l = P.lv[k];
+    RestrTileArgs t = {};
+    t.Limg = l.L; t.Rimg = l.R; t.pitch = l.pitch;
+    t.W = l.W; t.H = l.H; t.Dk = l.Dk; t.r = P.r;
+    t.prior = P.lv[k + 1].d; t.Wp = P.lv[k + 1].W; t.Hp = P.lv[k + 1].H;
+    t.d_out = k == 0 ? io.d : l.d;
+    t.c_out = k == 0 ? io.c : l.c;
+    t.evals = a.evals; t.err = a.err; t.force_timeout = a.force_timeout;
+    const BMaps &m = a.maps[sg.pair * BT_MAXK + k];
+    uint32_t parity = 0;
+    restr_tile<NH, G, 32, BT_NCOL, true, BT_RTY>(t, &m.mRL, &m.mR128, &m.mR256, &m.mS128, &m.mS256,
+                                                 tile % S.tiles_x, tile / S.tiles_x, smem, parity);
+}
+
 size_t batch_smem_bytes(bool full) {
     size_t m = BT_AUX + (size_t)PF_SMEM;
     for (size_t b : {RCfg<1, 32, BT_NCOL, true, BT_RTY>::BYTES, RCfg<2, 32, BT_NCOL, true, BT_RTY>::BYTES,
@@ -379,6 +525,78 @@ inline msbm_status cst(cudaError_t e) {
 
 using namespace msbm;
 
+namespace msbm {
+namespace {
+
+// One grouped launch: a tile function with its template parameters and its segments.
+struct BGLaunch {
+    int type;                // BStageType
+    int nh, var;             // window half-width; F (pyramid), sx (full), G (restricted)
+    int order;               // place in the pass: pyramid groups, coarsest, statistics, levels
+    int nblocks;
+    int seg0, nseg;          // the launch's segments in the batch's segment array
+    size_t smem;
+};
+
+size_t bg_smem(int type, int nh, int var) {
+    auto pick = [](int h, size_t a1, size_t a2, size_t a3, size_t a4) {
+        return h == 1 ? a1 : (h == 2 ? a2 : (h == 3 ? a3 : a4));
+    };
+    switch (type) {
+        case BS_PYR: return PF_SMEM;
+        case BS_STATS: return pick(nh, StatsCfg<1>::BYTES, StatsCfg<2>::BYTES, StatsCfg<3>::BYTES, StatsCfg<4>::BYTES);
+        case BS_COARSE:
+            return pick(nh, CoarseCfg<1, BT_CO_TY>::BYTES, CoarseCfg<2, BT_CO_TY>::BYTES, CoarseCfg<3, BT_CO_TY>::BYTES,
+                        CoarseCfg<4, BT_CO_TY>::BYTES);
+        case BS_FULL:
+            return var == 1 ? pick(nh, FullCfg<1, 1, BT_ZC>::BYTES, FullCfg<2, 1, BT_ZC>::BYTES, FullCfg<3, 1, BT_ZC>::BYTES,
+                                   FullCfg<4, 1, BT_ZC>::BYTES)
+                            : pick(nh, FullCfg<1, 2, BT_ZC>::BYTES, FullCfg<2, 2, BT_ZC>::BYTES, FullCfg<3, 2, BT_ZC>::BYTES,
+                                   FullCfg<4, 2, BT_ZC>::BYTES);
+        case BS_RESTR:
+            return pick(nh, RCfg<1, 32, BT_NCOL, true, BT_RTY>::BYTES, RCfg<2, 32, BT_NCOL, true, BT_RTY>::BYTES,
+                        RCfg<3, 32, BT_NCOL, true, BT_RTY>::BYTES, RCfg<4, 32, BT_NCOL, true, BT_RTY>::BYTES);
+        default: return 0;
+    }
+}
+
+// The kernel of a grouped launch (host-side function pointer), or nullptr.
+template <int NH>
+const void *bg_kernel_nh(int type, int var) {
+    switch (type) {
+        case BS_STATS: return reinterpret_cast<const void *>(bg_stats_kernel<NH>);
+        case BS_COARSE: return reinterpret_cast<const void *>(bg_coarse_kernel<NH>);
+        case BS_FULL:
+            return var == 1 ? reinterpret_cast<const void *>(bg_full_kernel<NH, 1>)
+                            : reinterpret_cast<const void *>(bg_full_kernel<NH, 2>);
+        case BS_RESTR:
+            switch (var) {
+                case 1: return reinterpret_cast<const void *>(bg_restr_kernel<NH, 1>);
+                case 3: return reinterpret_cast<const void *>(bg_restr_kernel<NH, 3>);
+                case 5: return reinterpret_cast<const void *>(bg_restr_kernel<NH, 5>);
+                default: return reinterpret_cast<const void *>(bg_restr_kernel<NH, 7>);
+            }
+        default: return nullptr;
+    }
+}
+
+const void *bg_kernel(int type, int nh, int var) {
+    if (type == BS_COPY) return reinterpret_cast<const void *>(bg_copy_kernel);
+    if (type == BS_PYR)
+        return var == 1 ? reinterpret_cast<const void *>(bg_pyr_kernel<1>)
+                        : (var == 2 ? reinterpret_cast<const void *>(bg_pyr_kernel<2>)
+                                    : reinterpret_cast<const void *>(bg_pyr_kernel<3>));
+    switch (nh) {
+        case 1: return bg_kernel_nh<1>(type, var);
+        case 2: return bg_kernel_nh<2>(type, var);
+        case 3: return bg_kernel_nh<3>(type, var);
+        default: return bg_kernel_nh<4>(type, var);
+    }
+}
+
+}  // namespace
+}  // namespace msbm
+
 struct msbm_batch {
     int n = 0;
     cudaStream_t stream = nullptr, cap = nullptr;
@@ -399,6 +617,11 @@ struct msbm_batch {
     bool full = false;           // some pair's coarsest level uses the full-range tile
     bool io_uploaded = false;
     cudaGraphExec_t exec = nullptr;
+    // grouped launches (MSBM_FLAG_BATCH_GROUPED)
+    bool grouped = false;
+    std::vector<BGLaunch> launches;
+    BGSeg *d_gsegs = nullptr;
+    int force_timeout = 0;
 };
 
 static void batch_free(msbm_batch *b) {
@@ -422,7 +645,8 @@ msbm_status msbm_batch_create(const msbm_params *pairs, int32_t n_pairs, const i
         if (p.max_disp < 1 || p.max_disp > 4096 || p.levels < 1 || p.levels > BT_MAXK) return MSBM_ERR_INVALID_ARG;
         if (p.window < 3 || p.window > 2 * BT_MAX_NH + 1 || (p.window & 1) == 0) return MSBM_ERR_INVALID_ARG;
         if (p.radius < 0 || p.radius > 16) return MSBM_ERR_INVALID_ARG;
-        if (p.flags & ~(MSBM_FLAG_NO_GRAPH | MSBM_FLAG_TEST_TIMEOUT)) return MSBM_ERR_INVALID_ARG;
+        if (p.flags & ~(MSBM_FLAG_NO_GRAPH | MSBM_FLAG_TEST_TIMEOUT | MSBM_FLAG_BATCH_GROUPED))
+            return MSBM_ERR_INVALID_ARG;
         if (full_sx && full_sx[i] != 1 && full_sx[i] != 2) return MSBM_ERR_INVALID_ARG;
         if (full_zblock && (full_zblock[i] < 0 || full_zblock[i] % 32 != 0)) return MSBM_ERR_INVALID_ARG;
     }
@@ -436,7 +660,9 @@ msbm_status msbm_batch_create(const msbm_params *pairs, int32_t n_pairs, const i
     if (!b) return MSBM_ERR_OOM;
     b->n = n_pairs;
     b->stream = static_cast<cudaStream_t>(cuda_stream);
-    b->withhold = (pairs[0].flags & MSBM_FLAG_TEST_TIMEOUT) != 0;
+    b->grouped = (pairs[0].flags & MSBM_FLAG_BATCH_GROUPED) != 0;
+    b->withhold = !b->grouped && (pairs[0].flags & MSBM_FLAG_TEST_TIMEOUT) != 0;
+    b->force_timeout = b->grouped && (pairs[0].flags & MSBM_FLAG_TEST_TIMEOUT) != 0 ? 1 : 0;
     cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
     auto dalloc = [&](void **p, size_t bytes) {
         if (e == cudaSuccess) e = cudaMalloc(p, bytes);
@@ -567,6 +793,71 @@ msbm_status msbm_batch_create(const msbm_params *pairs, int32_t n_pairs, const i
     }
     b->nseg = (int)segs.size();
     b->total = pos;
+    // grouped launches: (order, type, window, variant) -> segments of that launch
+    std::vector<BGSeg> gsegs;
+    if (b->grouped) {
+        struct Key {
+            int order, type, nh, var;
+            bool operator<(const Key &o) const {
+                if (order != o.order) return order < o.order;
+                if (type != o.type) return type < o.type;
+                if (nh != o.nh) return nh < o.nh;
+                return var < o.var;
+            }
+        };
+        std::vector<std::pair<Key, std::pair<int, int>>> items;   // key -> (pair, stage)
+        for (int i = 0; i < n_pairs; ++i) {
+            const BPair &P = b->pairs[i];
+            for (int st = 0; st < P.nst; ++st) {
+                const BStage &S = P.st[st];
+                Key k{0, S.type, 0, 0};
+                switch (S.type) {
+                    case BS_COPY: k.order = 0; break;
+                    case BS_PYR: k.order = S.arg; k.var = P.pf[S.arg].F; break;
+                    case BS_COARSE: k.order = 100; k.nh = P.nh; break;
+                    case BS_FULL: k.order = 100; k.nh = P.nh; k.var = P.lv[S.arg].sx; break;
+                    case BS_STATS: k.order = 200; k.nh = P.nh; break;
+                    default: k.order = 300 + (BT_MAXK - S.arg); k.nh = P.nh; k.var = std::min(2 * P.r + 1, 7); break;
+                }
+                items.push_back({k, {i, st}});
+            }
+        }
+        std::stable_sort(items.begin(), items.end(),
+                         [](const auto &x, const auto &y) { return x.first < y.first; });
+        for (size_t a0 = 0; a0 < items.size();) {
+            size_t a1 = a0;
+            BGLaunch L;
+            L.type = items[a0].first.type; L.nh = items[a0].first.nh; L.var = items[a0].first.var;
+            L.order = items[a0].first.order;
+            L.seg0 = (int)gsegs.size();
+            int blocks = 0;
+            while (a1 < items.size() && !(items[a0].first < items[a1].first) && !(items[a1].first < items[a0].first)) {
+                BGSeg g;
+                g.start = blocks;
+                g.pair = items[a1].second.first;
+                g.stage = items[a1].second.second;
+                blocks += b->pairs[g.pair].st[g.stage].ntiles;
+                gsegs.push_back(g);
+                ++a1;
+            }
+            L.nseg = (int)gsegs.size() - L.seg0;
+            L.nblocks = blocks;
+            L.smem = bg_smem(L.type, L.nh, L.var);
+            if (L.nblocks > 0) b->launches.push_back(L);
+            a0 = a1;
+        }
+        for (const BGLaunch &L : b->launches) {
+            if (e == cudaSuccess && L.smem > 48 * 1024)
+                e = cudaFuncSetAttribute(bg_kernel(L.type, L.nh, L.var), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)L.smem);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(bg_kernel(L.type, L.nh, L.var), cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         cudaSharedmemCarveoutMaxShared);
+        }
+        if (!gsegs.empty()) dalloc(reinterpret_cast<void **>(&b->d_gsegs), sizeof(BGSeg) * gsegs.size());
+        if (e == cudaSuccess && !gsegs.empty())
+            e = cudaMemcpy(b->d_gsegs, gsegs.data(), sizeof(BGSeg) * gsegs.size(), cudaMemcpyHostToDevice);
+    }
     dalloc(reinterpret_cast<void **>(&b->d_pairs), sizeof(BPair) * n_pairs);
     dalloc(reinterpret_cast<void **>(&b->d_maps), sizeof(BMaps) * maps.size());
     dalloc(reinterpret_cast<void **>(&b->d_io), sizeof(BIO) * n_pairs);
@@ -601,7 +892,23 @@ msbm_status msbm_batch_create(const msbm_params *pairs, int32_t n_pairs, const i
     return MSBM_OK;
 }
 
+static msbm_status batch_enqueue_grouped(msbm_batch *b, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    for (const BGLaunch &L : b->launches) {
+        BGArgs a;
+        memset(&a, 0, sizeof(a));
+        a.pairs = b->d_pairs; a.maps = b->d_maps; a.io = b->d_io;
+        a.segs = b->d_gsegs + L.seg0; a.nseg = L.nseg;
+        a.evals = b->d_evals; a.err = b->d_err; a.force_timeout = b->force_timeout;
+        void *args[] = {&a};
+        e = cudaLaunchKernel(bg_kernel(L.type, L.nh, L.var), dim3(L.nblocks), dim3(BT_THREADS), args, L.smem, st);
+        if (e != cudaSuccess) break;
+    }
+    return cst(e);
+}
+
 static msbm_status batch_enqueue(msbm_batch *b, cudaStream_t st) {
+    if (b->grouped) return batch_enqueue_grouped(b, st);
     BatchArgs a;
     memset(&a, 0, sizeof(a));
     a.pairs = b->d_pairs; a.maps = b->d_maps; a.io = b->d_io; a.segs = b->d_segs;

