@@ -12,10 +12,27 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+#include <stdio.h>
+
 #include "msbm.h"
 #include "msbm_internal.h"
 
 using namespace msbm;
+
+namespace {
+// NVTX range for profilers (nsys, ncu's range filters): one per pass, level and host frame.
+// Header-only NVTX v3: without a profiler attached the calls do nothing.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    NvtxRange(const char *what, int k) {
+        char buf[48];
+        snprintf(buf, sizeof(buf), "%s %d", what, k);
+        nvtxRangePushA(buf);
+    }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+}  // namespace
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
@@ -325,6 +342,7 @@ msbm_status enqueue_all(msbm_ctx *c, const uint8_t *L, const uint8_t *R, size_t 
         s = cuda_status(e);
     }
     for (int k = K - 1; s == MSBM_OK && k >= 0; --k) {
+        NvtxRange range("msbm level", k);
         if (k <= K - 2) s = cuda_status(cudaStreamWaitEvent(st, c->ev_stat[k], 0));
         if (s == MSBM_OK) s = enqueue_match(c, k, d, cost, st, true);
     }
@@ -527,6 +545,7 @@ msbm_status msbm_disparity(msbm_ctx *ctx, const uint8_t *d_left, const uint8_t *
                            size_t pitch_bytes, int16_t *d_out, float *cost_out) {
     if (!ctx || !d_left || !d_right || !d_out || pitch_bytes < (size_t)ctx->p.width)
         return MSBM_ERR_INVALID_ARG;
+    NvtxRange range("msbm_disparity");
     if (ctx->p.flags & MSBM_FLAG_NO_GRAPH)
         return enqueue_all(ctx, d_left, d_right, pitch_bytes, d_out, cost_out, ctx->stream);
     const void *key[4] = {d_left, d_right, d_out, cost_out};
@@ -607,6 +626,7 @@ msbm_status msbm_disparity_host_frames(msbm_ctx *ctx, int32_t n_frames, const ui
     // (which read set b's maps), its download for its pass.  So frame i+1's upload and
     // frame i-1's download run beside frame i's pass.
     for (int i = 0; i < n_frames && e == cudaSuccess; ++i) {
+        NvtxRange range("msbm host frame", i);
         const int b = i & 1;
         const bool want_cost = h_costs && h_costs[i];
         if (i >= 2) e = cudaStreamWaitEvent(up, ctx->ev_pass[b], 0);
@@ -681,10 +701,14 @@ msbm_status msbm_profile_disparity(msbm_ctx *ctx, const uint8_t *d_left, const u
     msbm_status s = cuda_status(e);
     int i = 0;
     if (s == MSBM_OK) s = cuda_status(cudaEventRecord(ev[i++], st));
-    if (s == MSBM_OK) s = enqueue_pyramid(ctx, d_left, d_right, pitch_bytes, st);
-    if (s == MSBM_OK && K >= 2) s = cuda_status(launch_stats_levels(ctx, K - 1, st));
+    {
+        NvtxRange range("msbm pyramid and statistics");
+        if (s == MSBM_OK) s = enqueue_pyramid(ctx, d_left, d_right, pitch_bytes, st);
+        if (s == MSBM_OK && K >= 2) s = cuda_status(launch_stats_levels(ctx, K - 1, st));
+    }
     if (s == MSBM_OK) s = cuda_status(cudaEventRecord(ev[i++], st));
     for (int k = K - 1; s == MSBM_OK && k >= 0; --k) {
+        NvtxRange range("msbm level", k);
         s = enqueue_match(ctx, k, d_out, cost_out, st, true);
         if (s == MSBM_OK) s = cuda_status(cudaEventRecord(ev[i++], st));
     }
