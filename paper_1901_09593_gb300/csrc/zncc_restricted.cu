@@ -18,8 +18,11 @@ using namespace tiles;
 
 // ---- strip tile (32 x 16)
 constexpr int ST_TY = 16;
-// Minimum CTAs per SM the register allocation must allow.
-constexpr int strip_min_ctas(int nh) { return nh <= 4 ? 6 : 3; }
+// Minimum CTAs per SM the register allocation must allow: seven (72 registers; with each
+// pixel's epilogue run as soon as its window sums are final, <n = 4, G = 7> spills 4 bytes).
+// Level 0 of the 2880 x 1984 pair (9 x 9, r = 3): 104.5 us at seven, 106.5 at eight (64
+// registers), 108.5 at six.
+constexpr int strip_min_ctas(int nh) { return nh <= 4 ? 7 : 3; }
 
 template <int NH, int G>
 __global__ void __launch_bounds__(SCfg<NH, ST_TY>::THREADS, strip_min_ctas(NH))
@@ -113,9 +116,9 @@ cudaError_t launch_restr_nh(const RestrArgs &a, int ty, cudaStream_t st) {
 int restr_tile_rows(int W, int H, int nh, int sms) {
     // The strip tile for windows of 9 x 9 and more where its 32 x 16 grid gives every SM at
     // least eight CTAs.  Measured (level 0 / whole pass): 2880 x 1984, 9 x 9, r = 3:
-    // 114.7 / 235 us against 151.6 / 258 us for the vertical-pair tile; 1400 x 1000, 7 x 7,
-    // r = 2: 26.6 us for both tiles at level 0, the strip tile's left-window plane adding
-    // ~4 us to the pass.
+    // 104.5 / 224 us against 151.6 / 258 us for the vertical-pair tile; 1400 x 1000, 7 x 7,
+    // r = 2: the same level-0 time for both tiles, the pass 59.9 us with the strip tile (its
+    // left-window plane) against 55.8 us.
     const long ctas = (long)((W + 31) / 32) * ((H + 15) / 16);
     return (nh >= 4 && ctas >= 8L * sms) ? ST_TY : VP_TY;
 }

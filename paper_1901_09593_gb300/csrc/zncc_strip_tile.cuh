@@ -70,11 +70,12 @@ __device__ __forceinline__ uint32_t sfsr(uint32_t lo, uint32_t hi, int bytes) {
 // One group of G candidates zg .. zg+G-1 for the thread's four pixels (rows 4*qy + p of the
 // staged tile, p = 0..3).  sRrow0: the thread's first staged right row; rst: right row
 // stride; b0: staging column of the window of candidate zg+G-1 (may be slightly negative:
-// the slack before the span).  Adds each pixel's window sums of a*b for the G candidates to
-// P[p][j] (which start at 0).
-template <int NH, int G, int TY>
+// the slack before the span).  Calls fin(p, X) with pixel p's window sums of a*b for the G
+// candidates (X[j] for candidate zg + j) as soon as they are final, pixel 0 first, so that
+// only one pixel's sums are live at a time.
+template <int NH, int G, int TY, typename Fin>
 __device__ __forceinline__ void strip_sums(const uint8_t *sLrow0, int w0L, int shL, const uint8_t *sRrow0,
-                                           int rst, int b0, uint32_t (&P)[4][G]) {
+                                           int rst, int b0, Fin &&fin) {
     using C = SCfg<NH, TY>;
     constexpr int WIN = C::WIN, NW = C::NW, SROWS = C::SROWS;
     constexpr int NWA = (G - 1 + WIN + 3) / 4 + 1;    // aligned words covering the group
@@ -82,7 +83,7 @@ __device__ __forceinline__ void strip_sums(const uint8_t *sLrow0, int w0L, int s
     const int w0 = b0 >> 2, sh = b0 & 3;               // arithmetic shift: floor
     // chains: M = rows 3 .. 2n (shared by all four windows); T = M + rows 2, 1 (top of
     // pixels 1, 2); B = M + rows 2n+1, 2n+2 (bottom of pixels 1, 2)
-    uint32_t M[G], T2[G], T12[G], B1[G];
+    uint32_t M[G], T2[G], T12[G], B1[G], X[G];
 #pragma unroll
     for (int j = 0; j < G; ++j) M[j] = 0;
     // row order: shared rows first, then 2, 1, 0 (chained from M), then 2n+1 .. 2n+3
@@ -127,17 +128,21 @@ __device__ __forceinline__ void strip_sums(const uint8_t *sLrow0, int w0L, int s
             if (tt >= 3 && tt <= 2 * NH) M[j] = acc;
             else if (tt == 2) T2[j] = acc;                  // M + r2        (pixel 2's top)
             else if (tt == 1) T12[j] = acc;                 // M + r1 + r2   (pixel 1's top)
-            else if (tt == 0) P[0][j] = acc;                // pixel 0: rows 0 .. 2n
+            else if (tt == 0) X[j] = acc;                   // pixel 0: rows 0 .. 2n
             else if (tt == 2 * NH + 1) {                    // M + r(2n+1)
-                P[1][j] = T12[j] + acc - M[j];              // pixel 1: rows 1 .. 2n+1
+                X[j] = T12[j] + acc - M[j];                 // pixel 1: rows 1 .. 2n+1
                 B1[j] = acc;
             } else if (tt == 2 * NH + 2) {                  // M + r(2n+1) + r(2n+2)
-                P[2][j] = T2[j] + acc - M[j];               // pixel 2: rows 2 .. 2n+2
+                X[j] = T2[j] + acc - M[j];                  // pixel 2: rows 2 .. 2n+2
                 B1[j] = acc;
             } else {
-                P[3][j] = acc;                              // pixel 3: rows 3 .. 2n+3
+                X[j] = acc;                                 // pixel 3: rows 3 .. 2n+3
             }
         }
+        if (tt == 0) fin(std::integral_constant<int, 0>{}, X);
+        if (tt == 2 * NH + 1) fin(std::integral_constant<int, 1>{}, X);
+        if (tt == 2 * NH + 2) fin(std::integral_constant<int, 2>{}, X);
+        if (tt == 2 * NH + 3) fin(std::integral_constant<int, 3>{}, X);
     }
 }
 
@@ -229,9 +234,8 @@ __device__ bool strip_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const
     const bool single = ((xlast - zlo + NH) + APX + 1 - ((x0 - zhi - NH + APX) & ~15)) <= 128;
     const bool uni = single && uni_w;
 
-    // left windows of the four pixels: {Sa, rsqrt(Va)} from the left plane (after the first wait)
-    int Sa[4];
-    float rA[4];
+    // left windows of the four pixels: {Sa, rsqrt(Va)} are read from the staged left plane
+    // where they are used
     float best[4];
     int bz[4];
 #pragma unroll
@@ -264,40 +268,30 @@ __device__ bool strip_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const
         }
         if (!tma_batch_wait(&bar, parity, &flag, a.force_timeout != 0, a.err)) return false;
         parity ^= 1;
-        if (pass == 0 && any) {
-#pragma unroll
-            for (int p = 0; p < 4; ++p) {
-                const int2 e = stL[(4 * qy + p) * 32 + qx];
-                Sa[p] = e.x;
-                rA[p] = __int_as_float(e.y);
-            }
-        }
         const int soff = APX - xs_s;           // staging column of image column X: X + soff
 
         // one group of G candidates zg .. zg+G-1 for the four pixels
         auto eval_group = [&](const int zg, auto check_tag) {
             constexpr bool check = decltype(check_tag)::value;
-            uint32_t P[4][G];
             const int b0 = xa - (zg + G - 1) - NH + soff;   // >= -(G-1): inside the slack
-            strip_sums<NH, G, TY>(sLrow0, w0L, shL, sRrow0, 128, b0, P);
+            strip_sums<NH, G, TY>(sLrow0, w0L, shL, sRrow0, 128, b0, [&](auto pc, const uint32_t (&X)[G]) {
+                constexpr int p = decltype(pc)::value;
+                const int sa = stL[(4 * qy + p) * 32 + qx].x;
 #pragma unroll
-            for (int j = 0; j < G; ++j) {
-                const int z = zg + j;
-#pragma unroll
-                for (int p = 0; p < 4; ++p) {
+                for (int j = 0; j < G; ++j) {
+                    const int z = zg + j;
                     // (a branch here measured faster than a predicated, branch-free mask:
                     // 2880 x 1984 pass 235 vs 263 us)
                     if (check && (z < lo_c[p >> 1] || z > hi_c[p >> 1])) continue;
-                    const bool ok = true;
                     const int2 st = stS[(4 * qy + p) * 128 + (xa - z - sxs)];
-                    const int cc = C::N * static_cast<int>(P[p][j]) - Sa[p] * st.x;
+                    const int cc = C::N * static_cast<int>(X[j]) - sa * st.x;
                     const float rho = static_cast<float>(cc) * __int_as_float(st.y);
-                    if (ok && rho > best[p]) {
+                    if (rho > best[p]) {
                         best[p] = rho;
                         bz[p] = z;
                     }
                 }
-            }
+            });
         };
         if (uni) {
             // (threads outside the image have no span: INT_MAX would overflow the offsets)
@@ -335,7 +329,7 @@ __device__ bool strip_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const
         if (!rowv[p]) continue;
         // rsqrt(Va) scales every candidate of the pixel alike: applied once here.  A flat
         // left window (rA = 0) has c = 0 for every candidate, so the smallest z wins with 0.
-        float rho = best[p] * rA[p];
+        float rho = best[p] * __int_as_float(stL[(4 * qy + p) * 32 + qx].y);
         rho = fminf(1.f, fmaxf(-1.f, rho));
         const size_t o = (size_t)(ya + p) * a.W + xa;
         a.d_out[o] = static_cast<int16_t>(bz[p]);
