@@ -694,8 +694,10 @@ def run_gpu(args):
     roof["pipe_clock_mhz"] = pmhz
 
     # -- end to end through the C ABI with pinned host buffers: K frames through the
-    # pipelined host call (each frame's images uploaded, its pass, its disparity and cost
-    # maps downloaded; frame i+1's upload and frame i-1's download overlap frame i's pass)
+    # pipelined host call (each frame's images uploaded, its pass, its disparity map
+    # downloaded -- the result of record; frame i+1's upload, frame i-1's download and the
+    # alternate pass pipeline's work overlap frame i's pass).  The same with the cost map
+    # downloaded as well is reported beside it.
     pin_l = torch.from_numpy(sc.left).pin_memory()
     pin_r = torch.from_numpy(sc.right).pin_memory()
     pin_d = [torch.empty((H, W), dtype=torch.int16).pin_memory() for _ in range(2)]
@@ -705,14 +707,17 @@ def run_gpu(args):
     lefts, rights = [hl] * K, [hr] * K
     ds = [pin_d[i % 2].numpy() for i in range(K)]
     cs = [pin_c[i % 2].numpy() for i in range(K)]
-    ctx.disparity_host_frames(lefts[:max(3, args.warmup)], rights[:max(3, args.warmup)],
-                              ds[:max(3, args.warmup)], cs[:max(3, args.warmup)])
-    barrier(dist)
-    t0 = time.perf_counter()
-    ctx.disparity_host_frames(lefts, rights, ds, cs)
-    e2e_s = reduce_max(time.perf_counter() - t0, dist, dev)
-    e2e_fps = world * args.steps / e2e_s
+    nw = max(3, args.warmup)
+
+    def e2e_run(costs):
+        ctx.disparity_host_frames(lefts[:nw], rights[:nw], ds[:nw], None if costs is None else costs[:nw])
+        barrier(dist)
+        t0 = time.perf_counter()
+        ctx.disparity_host_frames(lefts, rights, ds, costs)
+        return world * args.steps / reduce_max(time.perf_counter() - t0, dist, dev)
+    e2e_fps = e2e_run(None)
     assert np.array_equal(pin_d[(K - 1) % 2].numpy(), d_h), "pipelined host path differs from the device pass"
+    e2e_cost_fps = e2e_run(cs)
     # one frame at a time (no overlap across frames), for comparison
     t0 = time.perf_counter()
     for i in range(min(K, 50)):
@@ -764,8 +769,10 @@ def run_gpu(args):
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": 2 * W * H,
-                "d2h_bytes_per_step": W * H * (2 + 4), "api": "msbm_disparity_host_frames (pipelined)",
-                "one_frame_per_call_frames_per_s": e2e_single_fps},
+                "d2h_bytes_per_step": 2 * W * H, "api": "msbm_disparity_host_frames (pipelined)",
+                "result": "int16 disparity map",
+                "with_cost_map": {"frames_per_s": e2e_cost_fps, "d2h_bytes_per_step": W * H * (2 + 4)},
+                "one_frame_per_call_with_cost_frames_per_s": e2e_single_fps},
         "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
         "gpix_disp_per_s": evals_per_frame * fps / 1e9,
         "gpix_disp_per_s_flat_equivalent": W * H * spec.max_disp * fps / 1e9,

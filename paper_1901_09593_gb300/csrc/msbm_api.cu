@@ -77,6 +77,11 @@ struct msbm_ctx {
     int16_t *sd[2] = {nullptr, nullptr};
     float *sc[2] = {nullptr, nullptr};
     cudaStream_t up_stream = nullptr, down_stream = nullptr;
+    // second pass pipeline of the host frames path: a context of the same parameters (its own
+    // level buffers) on its own stream, taking every other frame, so that one frame's coarse,
+    // latency-bound levels run beside the previous frame's finest level
+    msbm_ctx *twin = nullptr;
+    cudaStream_t twin_stream = nullptr;
     cudaEvent_t ev_up[2] = {}, ev_pass[2] = {}, ev_down[2] = {};
 };
 
@@ -159,6 +164,11 @@ int choose_sx(int W, int H, int sms) {
 
 void free_ctx(msbm_ctx *c) {
     if (!c) return;
+    if (c->twin) {
+        cudaStreamSynchronize(c->twin_stream);
+        free_ctx(c->twin);
+    }
+    if (c->twin_stream) cudaStreamDestroy(c->twin_stream);
     for (auto &g : c->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
     for (auto &l : c->lv) {
@@ -620,14 +630,31 @@ msbm_status msbm_disparity_host_frames(msbm_ctx *ctx, int32_t n_frames, const ui
         ctx->up_stream = up;
         ctx->down_stream = down;
     }
-    cudaStream_t st = ctx->stream, up = ctx->up_stream, down = ctx->down_stream;
+    if (n_frames >= 2 && !ctx->twin) {
+        cudaStream_t ts = nullptr;
+        e = cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_status(e);
+        msbm_ctx *tw = nullptr;
+        msbm_status s = msbm_create(&ctx->p, ts, &tw);
+        if (s != MSBM_OK) {
+            cudaStreamDestroy(ts);
+            return s;
+        }
+        ctx->twin = tw;
+        ctx->twin_stream = ts;
+    }
+    cudaStream_t up = ctx->up_stream, down = ctx->down_stream;
     // Frame i uses staging set b = i % 2: its upload waits for the pass of frame i-2 (which
     // read set b's images), its pass for its upload and for the download of frame i-2
     // (which read set b's maps), its download for its pass.  So frame i+1's upload and
     // frame i-1's download run beside frame i's pass.
+    // Frames alternate between the two pass pipelines as they do between the staging sets:
+    // frame i runs on pipeline b (the context itself for b = 0, its twin for b = 1).
     for (int i = 0; i < n_frames && e == cudaSuccess; ++i) {
         NvtxRange range("msbm host frame", i);
         const int b = i & 1;
+        msbm_ctx *pc = (b == 1 && ctx->twin) ? ctx->twin : ctx;
+        cudaStream_t st = pc->stream;
         const bool want_cost = h_costs && h_costs[i];
         if (i >= 2) e = cudaStreamWaitEvent(up, ctx->ev_pass[b], 0);
         if (e == cudaSuccess) {
@@ -644,7 +671,7 @@ msbm_status msbm_disparity_host_frames(msbm_ctx *ctx, int32_t n_frames, const ui
         if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->ev_up[b], 0);
         if (e == cudaSuccess && i >= 2) e = cudaStreamWaitEvent(st, ctx->ev_down[b], 0);
         if (e != cudaSuccess) break;
-        msbm_status s = msbm_disparity(ctx, ctx->sL[b], ctx->sR[b], W, ctx->sd[b], want_cost ? ctx->sc[b] : nullptr);
+        msbm_status s = msbm_disparity(pc, ctx->sL[b], ctx->sR[b], W, ctx->sd[b], want_cost ? ctx->sc[b] : nullptr);
         if (s != MSBM_OK) {
             cudaStreamSynchronize(up);
             cudaStreamSynchronize(down);
@@ -662,7 +689,9 @@ msbm_status msbm_disparity_host_frames(msbm_ctx *ctx, int32_t n_frames, const ui
     cudaError_t e3 = cudaStreamSynchronize(down);
     if (e == cudaSuccess) e = e2 != cudaSuccess ? e2 : e3;
     if (e != cudaSuccess) return cuda_status(e);
-    return msbm_sync(ctx);
+    msbm_status s = ctx->twin ? msbm_sync(ctx->twin) : MSBM_OK;
+    msbm_status s0 = msbm_sync(ctx);
+    return s0 != MSBM_OK ? s0 : s;
 }
 
 msbm_status msbm_disparity_host(msbm_ctx *ctx, const uint8_t *h_left, const uint8_t *h_right,
