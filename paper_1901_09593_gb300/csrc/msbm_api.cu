@@ -52,7 +52,6 @@ struct msbm_ctx {
     // third stream of the pass: level 0's planes (the largest), from the fork on
     cudaStream_t side_stream2 = nullptr;
     cudaEvent_t ev_fork = nullptr;
-    cudaEvent_t ev_fork0 = nullptr;   // the pyramid's first launch is enqueued (level 0 written)
     cudaEvent_t ev_stat[12] = {};
     std::vector<LevelBuf> lv;
     int *d_err = nullptr;
@@ -180,7 +179,6 @@ void free_ctx(msbm_ctx *c) {
         cudaFree(l.mask);
         cudaFree(l.rstat);
         cudaFree(l.lstat);
-        cudaFree(l.span);
     }
     cudaFree(c->c0);
     cudaFree(c->d_err);
@@ -201,7 +199,6 @@ void free_ctx(msbm_ctx *c) {
     if (c->side_stream) cudaStreamDestroy(c->side_stream);
     if (c->side_stream2) cudaStreamDestroy(c->side_stream2);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
-    if (c->ev_fork0) cudaEventDestroy(c->ev_fork0);
     for (cudaEvent_t ev : c->ev_stat)
         if (ev) cudaEventDestroy(ev);
     delete c;
@@ -213,22 +210,17 @@ inline msbm_status cuda_status(cudaError_t e) {
     return MSBM_ERR_CUDA;
 }
 
-// Reductions fused into the pyramid's first launch (which also writes level 0); the rest go
-// in launches of up to PF_MAXF.
-constexpr int PYR_FIRST = PF_MAXF;
-
-// The pyramid: a plain copy for one level, else fused launches of reductions (the first also
-// writing level 0).  after_first, if given, is recorded once the first launch is enqueued
-// (levels 0 .. its last are then written).
+// The pyramid: a plain copy for one level, else fused launches of up to PF_MAXF reductions
+// each (the first also writing level 0).
 msbm_status enqueue_pyramid(msbm_ctx *c, const uint8_t *L, const uint8_t *R, size_t pitch,
-                            cudaStream_t st, cudaEvent_t after_first = nullptr) {
+                            cudaStream_t st) {
     const int K = c->p.levels;
     if (K == 1) return cuda_status(launch_apron_copy(L, R, pitch, c->lv[0], st));
     cudaError_t e = cudaSuccess;
-    for (int s = 0; e == cudaSuccess && s < K - 1;) {
+    for (int s = 0; e == cudaSuccess && s < K - 1; s += PF_MAXF) {
         PyrFuseArgs a;
         memset(&a, 0, sizeof(a));
-        a.F = std::min(s == 0 ? PYR_FIRST : PF_MAXF, K - 1 - s);
+        a.F = std::min(PF_MAXF, K - 1 - s);
         a.write_src = s == 0;
         a.src[0] = s == 0 ? L : c->lv[s].img(0);
         a.src[1] = s == 0 ? R : c->lv[s].img(1);
@@ -242,8 +234,6 @@ msbm_status enqueue_pyramid(msbm_ctx *c, const uint8_t *L, const uint8_t *R, siz
             a.dpitch[j] = l.pitch;
         }
         e = launch_pyr_fused(a, st);
-        if (e == cudaSuccess && s == 0 && after_first) e = cudaEventRecord(after_first, st);
-        s += a.F;
     }
     return cuda_status(e);
 }
@@ -261,28 +251,8 @@ cudaError_t launch_stats_levels(msbm_ctx *c, int n, cudaStream_t st) {
 }
 
 // stats_ready: the level's right-window statistics plane is already computed in stream order.
-// Whether level k's restricted search reads a span table filled by level k+1's (both on the
-// vertical-pair tile, the plain method: the gated steps change a level's map after its search).
-bool level_reads_spans(const msbm_ctx *c, int k) {
-    const int K = c->p.levels;
-    if (c->p.flags & (MSBM_FLAG_SELECTIVE_MEDIAN | MSBM_FLAG_BETA_FALLBACK)) return false;
-    return k + 1 <= K - 2 && c->lv[k].rty == 8 && c->lv[k + 1].rty == 8 && c->lv[k].span;
-}
-
-// Reset the span tables a pass fills (one small memset each).
-cudaError_t reset_spans(msbm_ctx *c, cudaStream_t st) {
-    cudaError_t e = cudaSuccess;
-    for (int k = 0; e == cudaSuccess && k < c->p.levels; ++k)
-        if (level_reads_spans(c, k))
-            e = cudaMemsetAsync(c->lv[k].span, 0x7F, sizeof(int2) * c->lv[k].span_tx * c->lv[k].span_ty, st);
-    return e;
-}
-
-// spans: in a pass, the restricted search reads and fills the span tables (see
-// level_reads_spans); the step API (foreign priors) never does.
 msbm_status enqueue_level(msbm_ctx *c, int k, const int16_t *prior, int16_t *d, float *cost,
-                          cudaStream_t st, const uint8_t *skip = nullptr, bool stats_ready = false,
-                          bool spans = false) {
+                          cudaStream_t st, const uint8_t *skip = nullptr, bool stats_ready = false) {
     const LevelBuf &l = c->lv[k];
     const int force = (c->p.flags & MSBM_FLAG_TEST_TIMEOUT) ? 1 : 0;
     cudaError_t e;
@@ -313,15 +283,6 @@ msbm_status enqueue_level(msbm_ctx *c, int k, const int16_t *prior, int16_t *d, 
         a.t.d_out = d; a.t.c_out = cost;
         a.t.evals = c->d_evals; a.t.err = c->d_err; a.t.force_timeout = force;
         a.t.rstat = l.rstat; a.t.rspitch = l.rspitch;
-        if (spans && level_reads_spans(c, k)) {
-            a.t.span_in = l.span;
-            a.t.span_in_tx = l.span_tx;
-        }
-        if (spans && k >= 1 && level_reads_spans(c, k - 1)) {
-            a.t.span_out = c->lv[k - 1].span;
-            a.t.span_out_tx = c->lv[k - 1].span_tx;
-            a.t.span_out_ty = c->lv[k - 1].span_ty;
-        }
         e = stats_ready ? cudaSuccess : launch_level_stats(&l, 1, l.nh, st);
         if (e == cudaSuccess) e = launch_zncc_restricted(a, l.nh, l.rty, st);
     }
@@ -348,7 +309,7 @@ msbm_status enqueue_level_beta(msbm_ctx *c, int k, const int16_t *prior, const f
 // + selective median) below it.  Writes the level's final map to d / cost at level 0.
 // stats_ready: the restricted levels' statistics planes are already computed in stream order.
 msbm_status enqueue_match(msbm_ctx *c, int k, int16_t *d, float *cost, cudaStream_t st,
-                          bool stats_ready = false, bool spans = false) {
+                          bool stats_ready = false) {
     const int K = c->p.levels;
     const uint32_t f = c->p.flags;
     LevelBuf &l = c->lv[k];
@@ -367,24 +328,22 @@ msbm_status enqueue_match(msbm_ctx *c, int k, int16_t *d, float *cost, cudaStrea
     if (f & MSBM_FLAG_BETA_FALLBACK)
         s = enqueue_level_beta(c, k, prior, c->lv[k + 1].c, dm, ck, st, stats_ready);
     else
-        s = enqueue_level(c, k, prior, dm, ck, st, nullptr, stats_ready, spans);
+        s = enqueue_level(c, k, prior, dm, ck, st, nullptr, stats_ready);
     if (s == MSBM_OK && med) s = cuda_status(launch_selective_median(dm, ck, l.W, l.H, c->p.alpha, dk, st));
     return s;
 }
 
 msbm_status enqueue_all(msbm_ctx *c, const uint8_t *L, const uint8_t *R, size_t pitch, int16_t *d,
                         float *cost, cudaStream_t st) {
+    msbm_status s = enqueue_pyramid(c, L, R, pitch, st);
     const int K = c->p.levels;
-    msbm_status s = cuda_status(reset_spans(c, st));
-    // level 0's statistics fork as soon as the pyramid's first launch has written level 0
-    if (s == MSBM_OK) s = enqueue_pyramid(c, L, R, pitch, st, K >= 3 ? c->ev_fork0 : nullptr);
     // fork: the statistics planes of levels K-2 .. 1, coarsest first, on one side stream
     // and level 0's on another, beside the coarsest level's full-range search and the
     // coarser restricted levels; each restricted level joins on its own plane only
     if (s == MSBM_OK && K >= 2) {
         cudaError_t e = cudaEventRecord(c->ev_fork, st);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0);
-        if (e == cudaSuccess && K >= 3) e = cudaStreamWaitEvent(c->side_stream2, c->ev_fork0, 0);
+        if (e == cudaSuccess && K >= 3) e = cudaStreamWaitEvent(c->side_stream2, c->ev_fork, 0);
         for (int k = K - 2; e == cudaSuccess && k >= 0; --k) {
             cudaStream_t ss = (k == 0 && K >= 3) ? c->side_stream2 : c->side_stream;
             e = launch_level_stats(&c->lv[k], 1, c->lv[k].nh, ss);
@@ -395,7 +354,7 @@ msbm_status enqueue_all(msbm_ctx *c, const uint8_t *L, const uint8_t *R, size_t 
     for (int k = K - 1; s == MSBM_OK && k >= 0; --k) {
         NvtxRange range("msbm level", k);
         if (k <= K - 2) s = cuda_status(cudaStreamWaitEvent(st, c->ev_stat[k], 0));
-        if (s == MSBM_OK) s = enqueue_match(c, k, d, cost, st, true, true);
+        if (s == MSBM_OK) s = enqueue_match(c, k, d, cost, st, true);
     }
     return s;
 }
@@ -442,7 +401,6 @@ msbm_status msbm_create(const msbm_params *params, void *cuda_stream, msbm_ctx *
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side_stream2, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork0, cudaEventDisableTiming);
     for (int k = 0; e == cudaSuccess && k < params->levels; ++k)
         e = cudaEventCreateWithFlags(&c->ev_stat[k], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(int));
@@ -479,11 +437,6 @@ msbm_status msbm_create(const msbm_params *params, void *cuda_stream, msbm_ctx *
         l.full_sx = choose_sx(W, H, c->num_sms);
         l.coarse = zncc_coarse_fits(W, H, c->num_sms);
         l.rty = restr_tile_rows(W, H, l.nh, c->num_sms);
-        if (e == cudaSuccess && l.rty == 8 && finer) {
-            l.span_tx = (W + 31) / 32;
-            l.span_ty = (H + 7) / 8;
-            e = cudaMalloc(&l.span, sizeof(int2) * l.span_tx * l.span_ty);
-        }
         if (e == cudaSuccess) {
             const int rowsR = l.rty + 2 * l.nh;
             bool ok = encode_u8(&l.tmFL, l.base[0], l.pitch, l.rows, 32 * l.full_sx + 32, rowsT) &&
@@ -776,7 +729,6 @@ msbm_status msbm_profile_disparity(msbm_ctx *ctx, const uint8_t *d_left, const u
     cudaStream_t st = ctx->stream;
     msbm_status s = cuda_status(e);
     int i = 0;
-    if (s == MSBM_OK) s = cuda_status(reset_spans(ctx, st));
     if (s == MSBM_OK) s = cuda_status(cudaEventRecord(ev[i++], st));
     {
         NvtxRange range("msbm pyramid and statistics");
@@ -786,7 +738,7 @@ msbm_status msbm_profile_disparity(msbm_ctx *ctx, const uint8_t *d_left, const u
     if (s == MSBM_OK) s = cuda_status(cudaEventRecord(ev[i++], st));
     for (int k = K - 1; s == MSBM_OK && k >= 0; --k) {
         NvtxRange range("msbm level", k);
-        s = enqueue_match(ctx, k, d_out, cost_out, st, true, true);
+        s = enqueue_match(ctx, k, d_out, cost_out, st, true);
         if (s == MSBM_OK) s = cuda_status(cudaEventRecord(ev[i++], st));
     }
     if (s == MSBM_OK) s = cuda_status(cudaStreamSynchronize(st));

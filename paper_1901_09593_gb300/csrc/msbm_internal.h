@@ -27,8 +27,6 @@ struct LevelBuf {
     int2 *lstat = nullptr;       // left-window statistics plane, same layout
     int rspitch = 0;             // of rspitch entries (a multiple of 16), one per pixel
     int rty = 16;                // rows of this level's restricted tile: 16 (strip tile) or 8
-    int2 *span = nullptr;        // per-tile prior ranges of this level's restricted tiles (or NULL)
-    int span_tx = 0, span_ty = 0;   // its tiles across / down
     // TMA maps over the apron buffers.  Full-range tile (8 + 2n rows high):
     //   tmFL   : left,  32*SX + 32 bytes wide, SX per level
     //   tmR256 : right, 256 bytes wide
@@ -79,16 +77,6 @@ struct RestrTileArgs {
     int force_timeout;
     const int2 *rstat;   // the level's right statistics plane (strip tile: wide spans read it
     int rspitch;         // from global memory)
-    // Per-tile span tables of the vertical-pair tile (NULL: not used).  Entry {min d, -max d}
-    // of the prior cells of one 32 x 8 tile of a level.  span_in: this level's table (its
-    // tiles' prior ranges, span_in_tx tiles across), filled by the coarser level's kernel;
-    // span_out: the next finer level's table (span_out_tx x span_out_ty tiles), which this
-    // kernel fills with atomic minima from its own disparities (reset to 0x7F7F7F7F bytes
-    // before the pass).
-    const int2 *span_in;
-    int span_in_tx;
-    int2 *span_out;
-    int span_out_tx, span_out_ty;
 };
 
 // Arguments of the standalone restricted kernels, ty rows per tile (LevelBuf::rty): the

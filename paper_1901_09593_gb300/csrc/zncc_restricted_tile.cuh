@@ -133,50 +133,6 @@ __device__ bool restr_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const
         lo_u = min(lo_u, lo_c[c]);
         hi_u = max(hi_u, hi_c[c]);
     }
-    const int xlast = min(x0 + RT_TX, a.W) - 1;
-    // Stage the left tile, the right span [x0 - zhi - n, xlast - zlo + n] and (plane mode) the
-    // span's statistics-plane entries on the barrier.  Called by thread 0.
-    auto issue = [&](const int zl, const int zh) {
-        const int xs = (x0 - zh - NH + APX) & ~15;
-        const int width = (xlast - zl + NH) + APX + 1 - xs;
-        const int mode = width <= 128 ? 1 : (width <= 256 ? 2 : 0);
-        const int sx0 = (x0 - zh) & ~1;
-        zlo_s = zl;
-        zhi_s = zh;
-        mode_s = mode;
-        xs_s = xs;
-        uint32_t bytes = ROWS * C::LBOX + (mode == 1 ? ROWS * 128 : (mode == 2 ? ROWS * 256 : 0));
-        if (PLANE) bytes += mode == 1 ? TY * 128 * 8 : (mode == 2 ? TY * 256 * 8 : 0);
-        fence_proxy_async_smem();
-        mbar_arrive_expect_tx(&bar, bytes);
-        tma_load_2d(sL, tmL, &bar, x0 - 16 + APX, y0 - NH + APY);
-        if (mode == 1) tma_load_2d(sR, tmR128, &bar, xs, y0 - NH + APY);
-        if (mode == 2) tma_load_2d(sR, tmR256, &bar, xs, y0 - NH + APY);
-        if (PLANE && mode == 1) tma_load_2d(const_cast<int2 *>(stS), tmS128, &bar, sx0, y0);
-        if (PLANE && mode == 2) tma_load_2d(const_cast<int2 *>(stS), tmS256, &bar, sx0, y0);
-    };
-    if (a.span_in) {
-        // The coarser level recorded its disparities' range over this tile's prior cells:
-        // thread 0 stages at once from the union that range implies (it contains every
-        // pixel's span), and every thread's prior load and evaluation count overlap the
-        // copies in flight.  A range never recorded takes the tile's whole range.
-        if (tid == 0) {
-            const int2 e = a.span_in[(size_t)by * a.span_in_tx + bx];
-            const bool rec = e.x <= 32767 && -e.y <= 32767 && e.x <= -e.y;
-            const int mn2 = rec ? 2 * max(e.x, 0) : 0;
-            const int mx2 = rec ? 2 * max(-e.y, 0) : Dk - 1;
-            issue(max(0, min(mn2, min(Dk - 1, x0)) - a.r), min(min(Dk - 1, xlast), mx2 + a.r));
-        }
-        unsigned cnt = 0;
-#pragma unroll
-        for (int c = 0; c < NCOL; ++c)
-#pragma unroll
-            for (int r2 = 0; r2 < 2; ++r2)
-                if (colv[c] && rowv[r2] && !(a.skip && a.skip[(size_t)(ya + r2) * a.W + xa + c]))
-                    cnt += static_cast<unsigned>(hi_c[c] - lo_c[c] + 1);
-        const unsigned wcnt = __reduce_add_sync(0xFFFFFFFFu, cnt);
-        if ((tid & 31) == 0 && a.evals && wcnt) atomicAdd(a.evals, static_cast<unsigned long long>(wcnt));
-    } else {
     if (tid == 0) {
         zlo_s = INT_MAX; zhi_s = -1; evsum = 0ull;
     }
@@ -199,22 +155,34 @@ __device__ bool restr_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const
         }
     }
     __syncthreads();
-    if (tid == 0) issue(zlo_s, zhi_s);
+    const int zlo = zlo_s, zhi = zhi_s;
+    const int xlast = min(x0 + RT_TX, a.W) - 1;
+    const int rs = x0 - zhi - NH;              // first right column any window reads
+    const int re = xlast - zlo + NH;           // last
+    const int sxs = (x0 - zhi) & ~1;           // plane mode: first staged plane column (even)
+    if (tid == 0) {
+        const int xs = (rs + APX) & ~15;
+        const int width = re + APX + 1 - xs;
+        const int mode = width <= 128 ? 1 : (width <= 256 ? 2 : 0);
+        mode_s = mode;
+        xs_s = xs;
+        uint32_t bytes = ROWS * C::LBOX + (mode == 1 ? ROWS * 128 : (mode == 2 ? ROWS * 256 : 0));
+        if (PLANE) bytes += mode == 1 ? TY * 128 * 8 : (mode == 2 ? TY * 256 * 8 : 0);
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&bar, bytes);
+        tma_load_2d(sL, tmL, &bar, x0 - 16 + APX, y0 - NH + APY);
+        if (mode == 1) tma_load_2d(sR, tmR128, &bar, xs, y0 - NH + APY);
+        if (mode == 2) tma_load_2d(sR, tmR256, &bar, xs, y0 - NH + APY);
+        if (PLANE && mode == 1) tma_load_2d(const_cast<int2 *>(stS), tmS128, &bar, sxs, y0);
+        if (PLANE && mode == 2) tma_load_2d(const_cast<int2 *>(stS), tmS256, &bar, sxs, y0);
     }
     if (!tma_batch_wait(&bar, parity, &flag, a.force_timeout != 0, a.err)) return false;
     parity ^= 1;
-    const int zlo = zlo_s, zhi = zhi_s;
-    const int rs = x0 - zhi - NH;              // first right column any window reads
-    const int sxs = (x0 - zhi) & ~1;           // plane mode: first staged plane column (even)
-    // a span outside the staged union (only possible with a span table that does not hold
-    // this tile's prior range) takes the global-memory path
-    const bool in_union = lo_u >= zlo && hi_u <= zhi;
     const int mode = mode_s, xs = xs_s;
     const int soff = APX - xs;                 // staging column of image column X: X + soff
     const int rst = mode == 1 ? 128 : 256;     // staging row stride (bytes; plane entries)
 
     // ---- right statistics over the span (staged modes, no plane), all threads
-    const int re = xlast - zlo + NH;           // last right column any window reads
     const int SW = re - rs + 1 - 2 * NH;       // statistics columns: image rs + n + v
     if (!PLANE && mode != 0) {
         // vertical window sums of every (output row, span column), spread over all threads
@@ -313,7 +281,7 @@ __device__ bool restr_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const
             bz[c][r2] = lo_c[c];
         }
 
-    if (mode != 0 && in_union) {
+    if (mode != 0) {
         for (int zg = lo_u; zg <= hi_u; zg += G) {
             // accumulators: rows 1..2n shared by both pixel rows, row 0 and row 2n+1 apart
             uint32_t mid[NCOL][G], top[NCOL][G], bot[NCOL][G];
@@ -430,30 +398,7 @@ __device__ bool restr_tile(const RestrTileArgs &a, const CUtensorMap *tmL, const
             a.d_out[o] = static_cast<int16_t>(bz[c][r2]);
             if (a.c_out) a.c_out[o] = rho;
         }
-    if constexpr (NCOL == 1 && TY == 8) if (a.span_out) {
-        // this level's disparities over each 16 x 4 block of the tile: the prior range of
-        // one tile of the next finer level (tile (2 bx + h, 2 by + v))
-        int vmin = INT_MAX, vmax = INT_MIN;
-#pragma unroll
-        for (int c = 0; c < NCOL; ++c)
-#pragma unroll
-            for (int r2 = 0; r2 < 2; ++r2)
-                if (colv[c] && rowv[r2]) {
-                    vmin = min(vmin, bz[c][r2]);
-                    vmax = max(vmax, bz[c][r2]);
-                }
-        const int h = (NCOL * qx) >> 4, v = (2 * qy) >> 2;
-        const unsigned m = __activemask() & (h ? 0xFFFF0000u : 0x0000FFFFu);
-        vmin = __reduce_min_sync(m, vmin);
-        vmax = __reduce_max_sync(m, vmax);
-        const int tx = 2 * bx + h, ty = 2 * by + v;
-        if ((tid & 31) == __ffs(m) - 1 && tx < a.span_out_tx && ty < a.span_out_ty) {
-            int2 *e = a.span_out + (size_t)ty * a.span_out_tx + tx;
-            atomicMin(&e->x, vmin);
-            atomicMin(&e->y, -vmax);
-        }
-    }
-    if (tid == 0 && a.evals && !a.span_in) atomicAdd(a.evals, evsum);
+    if (tid == 0 && a.evals) atomicAdd(a.evals, evsum);
     return true;
 }
 
