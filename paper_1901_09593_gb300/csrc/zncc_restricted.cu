@@ -1,12 +1,16 @@
 // zncc_restricted.cu -- standalone launches of the restricted ZNCC winner-take-all search
-// (Sec. III-C, Eq. 8-9, first branch).  Two tiles, chosen per level by its size and window:
+// (Sec. III-C, Eq. 8-9, first branch).  Two designs, chosen per level by its size and window:
 //  * large levels, windows of 9 x 9 and more: the strip tile (zncc_strip_tile.cuh), one CTA of 128 threads per 32 x 16
 //    tile, each thread a vertical strip of four pixels that share the products of their
 //    common window rows; left- and right-window statistics from the level's planes;
-//  * otherwise: the vertical-pair tile (zncc_restricted_tile.cuh), one CTA of 128
-//    threads per 32 x 8 tile, each thread two pixels of one prior cell: twice the CTAs per
-//    pixel, which hides the per-CTA latency chain (prior load, span reduction, TMA wait)
-//    where the level gives the GPU few tiles.
+//  * otherwise: the cell kernel (zncc_cell_tile.cuh), one thread per prior cell (2 x 2
+//    pixels), operands read through L1 with no staging, barriers or waits.  It replaced the
+//    TMA-staged vertical-pair tile (zncc_restricted_tile.cuh, 32 x 8 pixels per CTA), whose
+//    per-CTA latency chain (prior load, span reduction, TMA wait) left its warps stalled at
+//    barriers: level 0 of the 1400 x 1000 pair (7 x 7, r = 2) 26.6 -> 20.5 us, the pass
+//    56.2 -> 49.6 us.  The staged tile still runs under MSBM_FLAG_TEST_TIMEOUT, whose
+//    bounded TMA wait it exercises.
+#include "zncc_cell_tile.cuh"
 #include "zncc_restricted_tile.cuh"
 #include "zncc_strip_tile.cuh"
 
@@ -56,6 +60,27 @@ __global__ void __launch_bounds__(32 * VP_TY / 2, pair_min_ctas(NH))
                                           blockIdx.y, smem, parity);
 }
 
+// ---- cell kernel: one thread per prior cell, 32 x 4 cells (64 x 8 pixels) per CTA.  Five
+// CTAs per SM (96 registers): level 0 of the 1400 x 1000 pair 20.5 us, against 21.5 at four
+// (128 registers) and 22.5 at six (80 registers, more spills); 256-thread CTAs were slower.
+constexpr int CELL_THREADS = 128;
+constexpr int CELL_MIN_CTAS = 5;
+
+template <int NH, int G>
+__global__ void __launch_bounds__(CELL_THREADS, CELL_MIN_CTAS) zncc_cell_kernel(const RestrTileArgs a) {
+    __shared__ unsigned long long evsum;
+    if (threadIdx.x == 0) evsum = 0ull;
+    __syncthreads();
+    const int cx = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int cy = blockIdx.y * (CELL_THREADS / 32) + (threadIdx.x >> 5);
+    unsigned cnt = 0;
+    if (2 * cx < a.W && 2 * cy < a.H) cnt = cell_search<NH, G>(a, cx, cy);
+    const unsigned wc = __reduce_add_sync(0xFFFFFFFFu, cnt);
+    if ((threadIdx.x & 31) == 0 && wc) atomicAdd(&evsum, static_cast<unsigned long long>(wc));
+    __syncthreads();
+    if (threadIdx.x == 0 && a.evals && evsum) atomicAdd(a.evals, evsum);
+}
+
 template <int NH, int G>
 cudaError_t prepare_t() {
     // dynamic shared memory opt-in, and the largest shared-memory carveout so that shared
@@ -76,7 +101,12 @@ cudaError_t prepare_t() {
 
 template <int NH, int G>
 cudaError_t launch_restr_t(const RestrArgs &a, int ty, cudaStream_t st) {
-    if (ty == ST_TY) {
+    if (ty == VP_TY && !a.t.force_timeout) {
+        // the cell kernel has no device waits; the test flag keeps the staged tile, whose
+        // bounded TMA wait it exercises
+        dim3 grd((a.t.Wp + 31) / 32, (a.t.Hp + CELL_THREADS / 32 - 1) / (CELL_THREADS / 32));
+        zncc_cell_kernel<NH, G><<<grd, CELL_THREADS, 0, st>>>(a.t);
+    } else if (ty == ST_TY) {
         using C = SCfg<NH, ST_TY>;
         static_assert(C::BYTES <= 227 * 1024, "strip tile shape");
         dim3 grd((a.t.W + C::TX - 1) / C::TX, (a.t.H + ST_TY - 1) / ST_TY);
