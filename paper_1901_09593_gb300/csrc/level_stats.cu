@@ -1,12 +1,11 @@
-// level_stats.cu -- the window statistics planes of a pyramid level's two images, read by the
-// restricted ZNCC search (Sec. III-C; the per-window terms of Eq. 2): for every pixel (y, x),
-// S = sum of the (2n+1)^2 window (clamp-to-edge) and rsqrt(N * sum I^2 - S^2), or 0 for a
-// flat window.  Every right window a restricted candidate reads, and every left window, is
-// one entry, so the matching kernel does no window statistics of its own.
+// level_stats.cu -- the right-window statistics plane of a pyramid level, read by the
+// restricted ZNCC search (Sec. III-C; the per-window terms of Eq. 2): for every pixel (y, x)
+// of the right image, S = sum of the (2n+1)^2 window (clamp-to-edge) and
+// rsqrt(N * sum I^2 - S^2), or 0 for a flat window.  Every right window a restricted
+// candidate reads is one entry, computed once instead of once per candidate that reads it.
 //
-// One launch covers several levels and both images, their 64 x 32 tiles
-// (level_stats_tile.cuh) numbered consecutively.  Bound: a few integer operations and 8
-// bytes written per pixel and image.
+// One launch covers several levels, their 64 x 32 tiles (level_stats_tile.cuh) numbered
+// consecutively.  Bound: a few integer operations and 8 bytes written per pixel.
 #include <math.h>
 #include <string.h>
 
@@ -18,7 +17,7 @@ namespace msbm {
 
 namespace {
 
-constexpr int ST_MAXL = 24;      // planes per launch (two per level)
+constexpr int ST_MAXL = 24;      // planes (levels) per launch
 
 struct StatsArgs {
     int n;                          // levels in this launch
@@ -49,28 +48,22 @@ cudaError_t stats_launch(const StatsArgs &a, cudaStream_t st) {
 
 cudaError_t launch_level_stats(const LevelBuf *lv, int n, int nh, cudaStream_t st) {
     if (n < 1) return cudaSuccess;
-    if (2 * n > ST_MAXL) return cudaErrorInvalidValue;
+    if (n > ST_MAXL) return cudaErrorInvalidValue;
     StatsArgs a;
     memset(&a, 0, sizeof(a));
-    // the right plane of every level; the left plane where the level's restricted search
-    // reads it (the strip tile, rty = 16)
     int m = 0;
     for (int i = 0; i < n; ++i) {
         const LevelBuf &l = lv[i];
-        for (int which = 1; which >= 0; --which) {
-            if (which == 0 && l.rty != 16) continue;
-            int2 *out = which ? l.rstat : l.lstat;
-            if (!out) return cudaErrorInvalidValue;
-            a.tiles_x[m] = (l.W + ST_TX - 1) / ST_TX;
-            a.first[m + 1] = a.first[m] + a.tiles_x[m] * ((l.H + ST_TY - 1) / ST_TY);
-            a.R[m] = l.img(which);
-            a.pitch[m] = l.pitch;
-            a.W[m] = l.W;
-            a.H[m] = l.H;
-            a.out[m] = out;
-            a.opitch[m] = l.rspitch;
-            ++m;
-        }
+        if (!l.rstat) return cudaErrorInvalidValue;
+        a.tiles_x[m] = (l.W + ST_TX - 1) / ST_TX;
+        a.first[m + 1] = a.first[m] + a.tiles_x[m] * ((l.H + ST_TY - 1) / ST_TY);
+        a.R[m] = l.img(1);
+        a.pitch[m] = l.pitch;
+        a.W[m] = l.W;
+        a.H[m] = l.H;
+        a.out[m] = l.rstat;
+        a.opitch[m] = l.rspitch;
+        ++m;
     }
     a.n = m;
     switch (nh) {

@@ -44,6 +44,9 @@ struct msbm_ctx {
     int nh = 0;
     int device = 0;
     int num_sms = 0;
+    // matching kernels of the level chain launch as programmatic dependents of their stream
+    // predecessor, so that each is scheduled while the previous level drains
+    bool pdl = true;
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;
     // second stream of the pass: the statistics planes, beside the coarsest level's search
@@ -178,7 +181,6 @@ void free_ctx(msbm_ctx *c) {
         cudaFree(l.dtmp);
         cudaFree(l.mask);
         cudaFree(l.rstat);
-        cudaFree(l.lstat);
     }
     cudaFree(c->c0);
     cudaFree(c->d_err);
@@ -257,7 +259,7 @@ msbm_status enqueue_level(msbm_ctx *c, int k, const int16_t *prior, int16_t *d, 
     const int force = (c->p.flags & MSBM_FLAG_TEST_TIMEOUT) ? 1 : 0;
     cudaError_t e;
     if (!prior && l.coarse) {
-        e = launch_zncc_coarse(l, l.nh, d, cost, c->d_evals, st);
+        e = launch_zncc_coarse(l, l.nh, d, cost, c->d_evals, st, c->pdl);
     } else if (!prior) {
         FullArgs a;
         memset(&a, 0, sizeof(a));
@@ -266,7 +268,7 @@ msbm_status enqueue_level(msbm_ctx *c, int k, const int16_t *prior, int16_t *d, 
         a.t.W = l.W; a.t.H = l.H; a.t.Dk = l.Dk; a.t.zblock = l.full_zblock;
         a.t.d_out = d; a.t.c_out = cost;
         a.t.evals = c->d_evals; a.t.err = c->d_err; a.t.force_timeout = force;
-        e = launch_zncc_full(a, l.nh, l.full_sx, st);
+        e = launch_zncc_full(a, l.nh, l.full_sx, st, c->pdl);
     } else {
         RestrArgs a;
         memset(&a, 0, sizeof(a));
@@ -275,7 +277,6 @@ msbm_status enqueue_level(msbm_ctx *c, int k, const int16_t *prior, int16_t *d, 
         a.tmR256 = l.tmRR256;
         a.tmS = l.tmS128;
         a.tmS256 = l.tmS256;
-        a.tmSL = l.tmSL;
         a.t.skip = skip;
         a.t.Limg = l.img(0); a.t.Rimg = l.img(1); a.t.pitch = l.pitch;
         a.t.W = l.W; a.t.H = l.H; a.t.Dk = l.Dk; a.t.r = c->p.radius;
@@ -284,7 +285,7 @@ msbm_status enqueue_level(msbm_ctx *c, int k, const int16_t *prior, int16_t *d, 
         a.t.evals = c->d_evals; a.t.err = c->d_err; a.t.force_timeout = force;
         a.t.rstat = l.rstat; a.t.rspitch = l.rspitch;
         e = stats_ready ? cudaSuccess : launch_level_stats(&l, 1, l.nh, st);
-        if (e == cudaSuccess) e = launch_zncc_restricted(a, l.nh, l.rty, st);
+        if (e == cudaSuccess) e = launch_zncc_restricted(a, l.nh, st, c->pdl);
     }
     return cuda_status(e);
 }
@@ -428,7 +429,6 @@ msbm_status msbm_create(const msbm_params *params, void *cuda_stream, msbm_ctx *
         if (e == cudaSuccess && k > 0) e = cudaMalloc(&l.c, (size_t)W * H * sizeof(float));
         l.rspitch = (W + 15) / 16 * 16;
         if (e == cudaSuccess) e = cudaMalloc(&l.rstat, (size_t)l.rspitch * H * sizeof(int2));
-        if (e == cudaSuccess) e = cudaMalloc(&l.lstat, (size_t)l.rspitch * H * sizeof(int2));
         const bool finer = k < params->levels - 1;
         if (e == cudaSuccess && finer && (params->flags & MSBM_FLAG_SELECTIVE_MEDIAN))
             e = cudaMalloc(&l.dtmp, (size_t)W * H * sizeof(int16_t));
@@ -436,7 +436,6 @@ msbm_status msbm_create(const msbm_params *params, void *cuda_stream, msbm_ctx *
             e = cudaMalloc(&l.mask, (size_t)W * H);
         l.full_sx = choose_sx(W, H, c->num_sms);
         l.coarse = zncc_coarse_fits(W, H, c->num_sms);
-        l.rty = restr_tile_rows(W, H, l.nh, c->num_sms);
         if (e == cudaSuccess) {
             const int rowsR = l.rty + 2 * l.nh;
             bool ok = encode_u8(&l.tmFL, l.base[0], l.pitch, l.rows, 32 * l.full_sx + 32, rowsT) &&
@@ -445,8 +444,7 @@ msbm_status msbm_create(const msbm_params *params, void *cuda_stream, msbm_ctx *
                       encode_u8(&l.tmRR128, l.base[1], l.pitch, l.rows, 128, rowsR) &&
                       encode_u8(&l.tmRR256, l.base[1], l.pitch, l.rows, 256, rowsR) &&
                       encode_u64(&l.tmS128, l.rstat, l.rspitch, H, 128, l.rty) &&
-                      encode_u64(&l.tmS256, l.rstat, l.rspitch, H, 256, l.rty) &&
-                      encode_u64(&l.tmSL, l.lstat, l.rspitch, H, 32, l.rty);
+                      encode_u64(&l.tmS256, l.rstat, l.rspitch, H, 256, l.rty);
             if (!ok) { c->lv.push_back(l); free_ctx(c); return MSBM_ERR_UNSUPPORTED; }
         }
         if (e == cudaSuccess) e = zncc_full_prepare(l.nh, l.full_sx);

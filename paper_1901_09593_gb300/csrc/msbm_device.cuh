@@ -97,6 +97,17 @@ __device__ __forceinline__ bool tma_batch_wait(uint64_t *bar, uint32_t parity, i
     return ok;
 }
 
+// Programmatic dependent launch (griddepcontrol): a kernel launched with the programmatic
+// stream serialization attribute may be scheduled while its stream predecessor is still
+// running, once every CTA of the predecessor has called pdl_launch_dependents (or exited);
+// pdl_wait returns when the predecessor has completed and its writes are visible.  A kernel
+// launched that way calls pdl_wait before it touches anything the predecessor writes.  For
+// a kernel launched without the attribute both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Unsigned 4-way byte dot product with accumulate (one dp4a instruction).
 __device__ __forceinline__ uint32_t dp4a_u8(uint32_t a, uint32_t b, uint32_t c) {
     return __dp4a(a, b, c);

@@ -6,10 +6,29 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "msbm.h"
 #include "msbm_device.cuh"
 
 namespace msbm {
+
+// Launch k<<<g, b, smem, st>>>(args...); with pdl, as a programmatic dependent of the
+// stream's previous kernel (k must call pdl_wait() before reading what that kernel writes).
+template <typename... P, typename... A>
+cudaError_t launch_k(void (*k)(P...), dim3 g, dim3 b, size_t smem, cudaStream_t st, bool pdl, A &&...args) {
+    cudaLaunchAttribute at;
+    at.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at.val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = g;
+    cfg.blockDim = b;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = &at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
+}
 
 // One pyramid level of both images: two apron buffers (see msbm_device.cuh) plus the
 // tensor maps the ZNCC kernels stage tiles with.
@@ -24,18 +43,16 @@ struct LevelBuf {
     int16_t *dtmp = nullptr;     // pre-median disparity map (SELECTIVE_MEDIAN)
     uint8_t *mask = nullptr;     // fallback mask (BETA_FALLBACK)
     int2 *rstat = nullptr;       // right-window statistics plane {S, bits(rsqrt(V)) or 0}: H rows
-    int2 *lstat = nullptr;       // left-window statistics plane, same layout
     int rspitch = 0;             // of rspitch entries (a multiple of 16), one per pixel
-    int rty = 16;                // rows of this level's restricted tile: 16 (strip tile) or 8
+    int rty = 8;                 // rows of the staged restricted tile (MSBM_FLAG_TEST_TIMEOUT)
     // TMA maps over the apron buffers.  Full-range tile (8 + 2n rows high):
     //   tmFL   : left,  32*SX + 32 bytes wide, SX per level
     //   tmR256 : right, 256 bytes wide
     // Restricted tile (rty + 2n rows high):
     //   tmRL   : left,  64 bytes wide
-    //   tmRR128, tmRR256 : right, 128 / 256 bytes wide (the 256-byte box: rty = 8 only)
+    //   tmRR128, tmRR256 : right, 128 / 256 bytes wide
     //   tmS128, tmS256 : right statistics plane, 128 / 256 entries wide, rty rows
-    //   tmSL   : left statistics plane, 32 entries wide, rty rows (rty = 16 only)
-    CUtensorMap tmFL, tmR256, tmRL, tmRR128, tmRR256, tmS128, tmS256, tmSL;
+    CUtensorMap tmFL, tmR256, tmRL, tmRR128, tmRR256, tmS128, tmS256;
     int full_sx = 4;             // full-range tile width 32*full_sx at this level
     int full_zblock = 0;         // full-range z-block (0 = the tile's maximum)
     bool coarse = false;         // plain full-range search by the small-level kernel
@@ -75,20 +92,19 @@ struct RestrTileArgs {
     unsigned long long *evals;
     int *err;
     int force_timeout;
-    const int2 *rstat;   // the level's right statistics plane (strip tile: wide spans read it
-    int rspitch;         // from global memory)
+    const int2 *rstat;   // the level's right statistics plane (the cell kernel reads it)
+    int rspitch;
 };
 
-// Arguments of the standalone restricted kernels, ty rows per tile (LevelBuf::rty): the
-// strip tile (zncc_strip_tile.cuh) for ty = 16, the vertical-pair tile
-// (zncc_restricted_tile.cuh) for ty = 8.
+// Arguments of the standalone restricted kernels: the cell kernel (zncc_cell_tile.cuh)
+// reads t only; the staged vertical-pair tile (zncc_restricted_tile.cuh, ty = LevelBuf::rty
+// rows) also the tensor maps.
 struct RestrArgs {
     CUtensorMap tmL;     // box {64, ty + 2n} over the left apron buffer
     CUtensorMap tmR128;  // box {128, ty + 2n} over the right apron buffer
-    CUtensorMap tmR256;  // box {256, ty + 2n} over the right apron buffer (ty = 8)
+    CUtensorMap tmR256;  // box {256, ty + 2n} over the right apron buffer
     CUtensorMap tmS;     // box {128, ty} over the right statistics plane
-    CUtensorMap tmS256;  // box {256, ty} over the right statistics plane (ty = 8)
-    CUtensorMap tmSL;    // box {32, ty} over the left statistics plane (ty = 16)
+    CUtensorMap tmS256;  // box {256, ty} over the right statistics plane
     RestrTileArgs t;
 };
 
@@ -108,7 +124,7 @@ struct PyrFuseArgs {
 };
 cudaError_t launch_pyr_fused(const PyrFuseArgs &a, cudaStream_t st);
 cudaError_t launch_level_extract(const LevelBuf &lv, int which, uint8_t *out, cudaStream_t st);
-cudaError_t launch_zncc_full(const FullArgs &a, int nh, int sx, cudaStream_t st);
+cudaError_t launch_zncc_full(const FullArgs &a, int nh, int sx, cudaStream_t st, bool pdl = false);
 // Full-range search of the pixels in l.mask only (beta fallback); needs l.rstat computed.
 cudaError_t launch_zncc_sparse(const LevelBuf &l, int nh, int16_t *d, float *c, unsigned long long *evals,
                                cudaStream_t st);
@@ -116,7 +132,7 @@ cudaError_t launch_zncc_sparse(const LevelBuf &l, int nh, int16_t *d, float *c, 
 // W x H level would not fill the GPU.
 bool zncc_coarse_fits(int W, int H, int sms);
 cudaError_t launch_zncc_coarse(const LevelBuf &l, int nh, int16_t *d, float *c, unsigned long long *evals,
-                               cudaStream_t st);
+                               cudaStream_t st, bool pdl = false);
 cudaError_t launch_beta_gate(const float *Cc, int Wc, int Hc, int W, int H, float beta, uint8_t *mask,
                              cudaStream_t st);
 cudaError_t launch_alpha_refine(const LevelBuf &l, int nh, float alpha, int16_t *d, float *C,
@@ -124,13 +140,9 @@ cudaError_t launch_alpha_refine(const LevelBuf &l, int nh, float alpha, int16_t 
 cudaError_t launch_selective_median(const int16_t *d_in, const float *C, int W, int H, float alpha, int16_t *d_out,
                                     cudaStream_t st);
 cudaError_t zncc_full_prepare(int nh, int sx);
-// Window statistics planes of n consecutive levels (lv[0 .. n-1]) in one launch: the right
-// plane (rstat) of each, and the left plane (lstat) of those with rty = 16.
+// Right-window statistics planes (rstat) of n consecutive levels (lv[0 .. n-1]) in one launch.
 cudaError_t launch_level_stats(const LevelBuf *lv, int n, int nh, cudaStream_t st);
 cudaError_t zncc_restricted_prepare(int nh);
-// Rows of the standalone restricted kernel's tile at a W x H level with window half-width
-// nh (its TMA boxes are rows + 2n high): 16 (the strip tile) or 8 (the vertical-pair tile).
-int restr_tile_rows(int W, int H, int nh, int sms);
-cudaError_t launch_zncc_restricted(const RestrArgs &a, int nh, int ty, cudaStream_t st);
+cudaError_t launch_zncc_restricted(const RestrArgs &a, int nh, cudaStream_t st, bool pdl = false);
 
 }  // namespace msbm

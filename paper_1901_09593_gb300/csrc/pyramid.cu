@@ -71,6 +71,7 @@ constexpr int PF_NT = 256;
 template <int F>
 __global__ void __launch_bounds__(PF_NT) pyr_fused_kernel(const __grid_constant__ PyrFuseArgs a) {
     __shared__ __align__(16) uint8_t sm[PF_SMEM];
+    pdl_launch_dependents();
     pyr_fused_tile<F, PF_NT>(a, a.src[blockIdx.z], a.spitch, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x,
                              gridDim.y, sm);
 }

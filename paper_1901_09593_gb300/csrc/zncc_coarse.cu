@@ -22,14 +22,17 @@ __global__ void __launch_bounds__(SA_NT) zncc_coarse_kernel(const uint8_t *L, co
                                                           int H, int Dk, int16_t *d_out, float *c_out,
                                                           unsigned long long *evals) {
     __shared__ __align__(16) uint8_t sm[CoarseCfg<NH, SA_TY>::BYTES];
+    pdl_launch_dependents();
+    pdl_wait();
     coarse_tile<NH, SA_TY, SA_NT>(L, R, pitch, W, H, Dk, d_out, c_out, evals, blockIdx.x, blockIdx.y, sm);
 }
 
 template <int NH>
-cudaError_t coarse_launch(const LevelBuf &l, int16_t *d, float *c, unsigned long long *evals, cudaStream_t st) {
+cudaError_t coarse_launch(const LevelBuf &l, int16_t *d, float *c, unsigned long long *evals, cudaStream_t st,
+                          bool pdl) {
     dim3 grd((l.W + CO_TX - 1) / CO_TX, (l.H + SA_TY - 1) / SA_TY);
-    zncc_coarse_kernel<NH><<<grd, SA_NT, 0, st>>>(l.img(0), l.img(1), l.pitch, l.W, l.H, l.Dk, d, c, evals);
-    return cudaGetLastError();
+    return launch_k(zncc_coarse_kernel<NH>, grd, dim3(SA_NT), 0, st, pdl, (const uint8_t *)l.img(0),
+                    (const uint8_t *)l.img(1), l.pitch, l.W, l.H, l.Dk, d, c, evals);
 }
 
 }  // namespace
@@ -40,14 +43,14 @@ bool zncc_coarse_fits(int W, int H, int sms) {
 }
 
 cudaError_t launch_zncc_coarse(const LevelBuf &l, int nh, int16_t *d, float *c, unsigned long long *evals,
-                               cudaStream_t st) {
+                               cudaStream_t st, bool pdl) {
     switch (nh) {
-        case 1: return coarse_launch<1>(l, d, c, evals, st);
-        case 2: return coarse_launch<2>(l, d, c, evals, st);
-        case 3: return coarse_launch<3>(l, d, c, evals, st);
-        case 4: return coarse_launch<4>(l, d, c, evals, st);
-        case 5: return coarse_launch<5>(l, d, c, evals, st);
-        case 6: return coarse_launch<6>(l, d, c, evals, st);
+        case 1: return coarse_launch<1>(l, d, c, evals, st, pdl);
+        case 2: return coarse_launch<2>(l, d, c, evals, st, pdl);
+        case 3: return coarse_launch<3>(l, d, c, evals, st, pdl);
+        case 4: return coarse_launch<4>(l, d, c, evals, st, pdl);
+        case 5: return coarse_launch<5>(l, d, c, evals, st, pdl);
+        case 6: return coarse_launch<6>(l, d, c, evals, st, pdl);
         default: return cudaErrorInvalidValue;
     }
 }
