@@ -190,14 +190,14 @@ msbm_status msbm_level_result(msbm_ctx *ctx, int32_t level, int16_t *d_out, floa
 /* Timing aid: run the whole pass once with direct launches, recording a CUDA event
  * before the first kernel and after each stage on the context's stream, wait, and write
  * each stage's milliseconds to stage_ms in launch order:
- *   [0]          the pyramid (level-0 copy and reduces to levels 1 .. K-1, fused launches)
- *                and the right-window statistics planes of levels 0 .. K-2 (one launch here;
- *                the pass itself runs one launch per level on a second stream, beside the
- *                coarsest level's search and the coarser restricted levels),
- *   [1]          full search at level K-1 (+ alpha refinement when enabled),
- *   [2 .. K]     levels K-2 .. 0: restricted search (+ beta gate and the fallback pixels' full search,
+ *   [0]          the pyramid (level-0 copy and reduces to levels 1 .. K-1, fused launches),
+ *   [1]          the right-window statistics planes of levels 0 .. K-2 (one launch here;
+ *                the pass itself runs them on side streams, beside the coarsest level's
+ *                search and the coarser restricted levels; 0 when K = 1),
+ *   [2]          full search at level K-1 (+ alpha refinement when enabled),
+ *   [3 .. K+1]   levels K-2 .. 0: restricted search (+ beta gate and the fallback pixels' full search,
  *                + selective median, when enabled).
- * n_stages must be K + 1.  Results equal msbm_disparity's. */
+ * n_stages must be K + 2.  Results equal msbm_disparity's. */
 msbm_status msbm_profile_disparity(msbm_ctx *ctx, const uint8_t *d_left, const uint8_t *d_right,
                                    size_t pitch_bytes, int16_t *d_out, float *cost_out,
                                    float *stage_ms, int32_t n_stages);

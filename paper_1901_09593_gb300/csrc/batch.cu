@@ -38,6 +38,7 @@
 #include "level_stats_tile.cuh"
 #include "pyramid_fused.cuh"
 #include "pyramid_ops.cuh"
+#include "zncc_cell_tile.cuh"
 #include "zncc_coarse_tile.cuh"
 #include "zncc_full_tile.cuh"
 #include "zncc_restricted_tile.cuh"
@@ -457,6 +458,36 @@ __global__ void __launch_bounds__(BT_THREADS, 8) bg_restr_kernel(const __grid_co
                                                  tile % S.tiles_x, tile / S.tiles_x, smem, parity);
 }
 
+// Restricted level, grouped mode: the cell kernel over the segment's 32 x 8 pixel tiles
+template <int NH, int G>
+__global__ void __launch_bounds__((BT_RTX / 2) * (BT_RTY / 2), 8) bg_cell_kernel(const __grid_constant__ BGArgs a) {
+    constexpr int CX = BT_RTX / 2, CY = BT_RTY / 2;   // cells of a tile
+    __shared__ unsigned long long evsum;
+    if (threadIdx.x == 0) evsum = 0ull;
+    __syncthreads();
+    const BGSeg sg = a.segs[bg_find(a, blockIdx.x)];
+    const BPair &P = a.pairs[sg.pair];
+    const BIO &io = a.io[sg.pair];
+    const BStage &S = P.st[sg.stage];
+    const int k = S.arg, tile = blockIdx.x - sg.start;
+    const BLevel &l = P.lv[k];
+    RestrTileArgs t = {};
+    t.Limg = l.L; t.Rimg = l.R; t.pitch = l.pitch;
+    t.W = l.W; t.H = l.H; t.Dk = l.Dk; t.r = P.r;
+    t.prior = P.lv[k + 1].d; t.Wp = P.lv[k + 1].W; t.Hp = P.lv[k + 1].H;
+    t.d_out = k == 0 ? io.d : l.d;
+    t.c_out = k == 0 ? io.c : l.c;
+    t.rstat = l.rstat; t.rspitch = l.rspitch;
+    const int cx = (tile % S.tiles_x) * CX + static_cast<int>(threadIdx.x) % CX;
+    const int cy = (tile / S.tiles_x) * CY + static_cast<int>(threadIdx.x) / CX;
+    unsigned cnt = 0;
+    if (2 * cx < t.W && 2 * cy < t.H) cnt = cell_search<NH, G>(t, cx, cy);
+    const unsigned wc = __reduce_add_sync(0xFFFFFFFFu, cnt);
+    if ((threadIdx.x & 31) == 0 && wc) atomicAdd(&evsum, static_cast<unsigned long long>(wc));
+    __syncthreads();
+    if (threadIdx.x == 0 && a.evals && evsum) atomicAdd(a.evals, evsum);
+}
+
 size_t batch_smem_bytes(bool full) {
     size_t m = BT_AUX + (size_t)PF_SMEM;
     for (size_t b : {RCfg<1, 32, BT_NCOL, true, BT_RTY>::BYTES, RCfg<2, 32, BT_NCOL, true, BT_RTY>::BYTES,
@@ -529,6 +560,12 @@ namespace msbm {
 namespace {
 
 // One grouped launch: a tile function with its template parameters and its segments.
+// Restricted launches of grouped mode run the cell kernel (zncc_cell_tile.cuh): var = G +
+// BG_CELL, BG_CELL_THREADS threads per 32 x 8 pixel tile (16 x 4 prior cells).  Under
+// MSBM_FLAG_TEST_TIMEOUT they keep the staged tile, whose bounded wait that flag exercises.
+constexpr int BG_CELL = 100;
+constexpr int BG_CELL_THREADS = (BT_RTX / 2) * (BT_RTY / 2);
+
 struct BGLaunch {
     int type;                // BStageType
     int nh, var;             // window half-width; F (pyramid), sx (full), G (restricted)
@@ -554,6 +591,7 @@ size_t bg_smem(int type, int nh, int var) {
                             : pick(nh, FullCfg<1, 2, BT_ZC>::BYTES, FullCfg<2, 2, BT_ZC>::BYTES, FullCfg<3, 2, BT_ZC>::BYTES,
                                    FullCfg<4, 2, BT_ZC>::BYTES);
         case BS_RESTR:
+            if (var >= BG_CELL) return 0;
             return pick(nh, RCfg<1, 32, BT_NCOL, true, BT_RTY>::BYTES, RCfg<2, 32, BT_NCOL, true, BT_RTY>::BYTES,
                         RCfg<3, 32, BT_NCOL, true, BT_RTY>::BYTES, RCfg<4, 32, BT_NCOL, true, BT_RTY>::BYTES);
         default: return 0;
@@ -571,6 +609,10 @@ const void *bg_kernel_nh(int type, int var) {
                             : reinterpret_cast<const void *>(bg_full_kernel<NH, 2>);
         case BS_RESTR:
             switch (var) {
+                case BG_CELL + 1: return reinterpret_cast<const void *>(bg_cell_kernel<NH, 1>);
+                case BG_CELL + 3: return reinterpret_cast<const void *>(bg_cell_kernel<NH, 3>);
+                case BG_CELL + 5: return reinterpret_cast<const void *>(bg_cell_kernel<NH, 5>);
+                case BG_CELL + 7: return reinterpret_cast<const void *>(bg_cell_kernel<NH, 7>);
                 case 1: return reinterpret_cast<const void *>(bg_restr_kernel<NH, 1>);
                 case 3: return reinterpret_cast<const void *>(bg_restr_kernel<NH, 3>);
                 case 5: return reinterpret_cast<const void *>(bg_restr_kernel<NH, 5>);
@@ -817,7 +859,10 @@ msbm_status msbm_batch_create(const msbm_params *pairs, int32_t n_pairs, const i
                     case BS_COARSE: k.order = 100; k.nh = P.nh; break;
                     case BS_FULL: k.order = 100; k.nh = P.nh; k.var = P.lv[S.arg].sx; break;
                     case BS_STATS: k.order = 200; k.nh = P.nh; break;
-                    default: k.order = 300 + (BT_MAXK - S.arg); k.nh = P.nh; k.var = std::min(2 * P.r + 1, 7); break;
+                    default:
+                        k.order = 300 + (BT_MAXK - S.arg); k.nh = P.nh; k.var = std::min(2 * P.r + 1, 7);
+                        if (!b->force_timeout) k.var += BG_CELL;   // the cell kernel (no device waits)
+                        break;
                 }
                 items.push_back({k, {i, st}});
             }
@@ -901,7 +946,8 @@ static msbm_status batch_enqueue_grouped(msbm_batch *b, cudaStream_t st) {
         a.segs = b->d_gsegs + L.seg0; a.nseg = L.nseg;
         a.evals = b->d_evals; a.err = b->d_err; a.force_timeout = b->force_timeout;
         void *args[] = {&a};
-        e = cudaLaunchKernel(bg_kernel(L.type, L.nh, L.var), dim3(L.nblocks), dim3(BT_THREADS), args, L.smem, st);
+        const int threads = (L.type == BS_RESTR && L.var >= BG_CELL) ? BG_CELL_THREADS : BT_THREADS;
+        e = cudaLaunchKernel(bg_kernel(L.type, L.nh, L.var), dim3(L.nblocks), dim3(threads), args, L.smem, st);
         if (e != cudaSuccess) break;
     }
     return cst(e);

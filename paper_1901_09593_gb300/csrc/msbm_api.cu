@@ -719,8 +719,8 @@ msbm_status msbm_profile_disparity(msbm_ctx *ctx, const uint8_t *d_left, const u
     if (!ctx || !d_left || !d_right || !d_out || !stage_ms || pitch_bytes < (size_t)ctx->p.width)
         return MSBM_ERR_INVALID_ARG;
     const int K = ctx->p.levels;
-    if (n_stages != K + 1) return MSBM_ERR_INVALID_ARG;
-    std::vector<cudaEvent_t> ev(K + 2, nullptr);
+    if (n_stages != K + 2) return MSBM_ERR_INVALID_ARG;
+    std::vector<cudaEvent_t> ev(K + 3, nullptr);
     cudaError_t e = cudaSuccess;
     for (auto &x : ev)
         if (e == cudaSuccess) e = cudaEventCreate(&x);
@@ -729,8 +729,12 @@ msbm_status msbm_profile_disparity(msbm_ctx *ctx, const uint8_t *d_left, const u
     int i = 0;
     if (s == MSBM_OK) s = cuda_status(cudaEventRecord(ev[i++], st));
     {
-        NvtxRange range("msbm pyramid and statistics");
+        NvtxRange range("msbm pyramid");
         if (s == MSBM_OK) s = enqueue_pyramid(ctx, d_left, d_right, pitch_bytes, st);
+    }
+    if (s == MSBM_OK) s = cuda_status(cudaEventRecord(ev[i++], st));
+    {
+        NvtxRange range("msbm statistics planes");
         if (s == MSBM_OK && K >= 2) s = cuda_status(launch_stats_levels(ctx, K - 1, st));
     }
     if (s == MSBM_OK) s = cuda_status(cudaEventRecord(ev[i++], st));
@@ -740,7 +744,7 @@ msbm_status msbm_profile_disparity(msbm_ctx *ctx, const uint8_t *d_left, const u
         if (s == MSBM_OK) s = cuda_status(cudaEventRecord(ev[i++], st));
     }
     if (s == MSBM_OK) s = cuda_status(cudaStreamSynchronize(st));
-    for (int j = 0; s == MSBM_OK && j < K + 1; ++j)
+    for (int j = 0; s == MSBM_OK && j < K + 2; ++j)
         s = cuda_status(cudaEventElapsedTime(&stage_ms[j], ev[j], ev[j + 1]));
     for (auto &x : ev)
         if (x) cudaEventDestroy(x);

@@ -266,7 +266,8 @@ class Context:
 
     def profile_disparity(self, left, right, d_out, cost_out):
         """One pass with per-stage CUDA-event timing; returns the list of milliseconds in
-        launch order (pyramid, coarsest full search, restricted levels K-2..0)."""
+        launch order (pyramid, statistics planes, coarsest full search, restricted levels
+        K-2..0)."""
         torch = _torch()
         self._bind_stream()
         pitch = _check_image(left, self.width, self.height, "left")
@@ -275,7 +276,7 @@ class Context:
         _check_map(d_out, self.width, self.height, torch.int16, "d_out")
         if cost_out is not None:
             _check_map(cost_out, self.width, self.height, torch.float32, "cost_out")
-        n = self.levels + 1
+        n = self.levels + 2
         ms = (ctypes.c_float * n)()
         _lib.check(self._lib.msbm_profile_disparity(
             self._ctx, ctypes.c_void_p(left.data_ptr()), ctypes.c_void_p(right.data_ptr()), pitch,
@@ -289,7 +290,7 @@ class Context:
         top = f"full_level{k - 1}" + ("+alpha" if f & _lib.MSBM_FLAG_ALPHA_REFINE else "")
         fin = (("+beta" if f & _lib.MSBM_FLAG_BETA_FALLBACK else "")
                + ("+median" if f & _lib.MSBM_FLAG_SELECTIVE_MEDIAN else ""))
-        return (["pyramid"] + [top] + [f"restricted_level{i}{fin}" for i in range(k - 2, -1, -1)])
+        return (["pyramid", "statistics"] + [top] + [f"restricted_level{i}{fin}" for i in range(k - 2, -1, -1)])
 
     def level_result(self, level: int):
         """Copies of an intermediate level's (d, cost) from the last disparity()."""

@@ -53,6 +53,8 @@ def test_stage_work_units():
     ev = [10, 20, 30, 40]
     bound, work, unit = bench.stage_work("pyramid", spec, wh, ev)
     assert (bound, unit) == ("hbm", "B") and work > 2 * spec.width * spec.height
+    # statistics: one right-image byte read and 8 plane bytes written per pixel of levels 0..K-2
+    assert bench.stage_work("statistics", spec, wh, ev) == ("hbm", sum(9 * w * h for w, h in wh[:-1]), "B")
     # matching stages count the window's dp4a (7 x 7: 7 rows x 2 words) per evaluation
     assert bench.dp4a_per_eval(7) == 14 and bench.dp4a_per_eval(9) == 27 and bench.dp4a_per_eval(5) == 10
     assert bench.stage_work("full_level3", spec, wh, ev) == ("dp4a", 40 * 14, "dp4a")

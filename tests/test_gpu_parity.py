@@ -176,6 +176,12 @@ def test_end_to_end_small(name, seed):
     hd2 = np.zeros_like(d)
     ctx.disparity_host(pl.numpy(), pr.numpy(), hd2, None)
     np.testing.assert_array_equal(hd2, d)
+    # the timed pass (one stage per kernel group) gives the same maps
+    pd_, pc_ = torch.zeros(d.shape, dtype=torch.int16, device="cuda"), torch.zeros(c.shape, device="cuda")
+    ms = ctx.profile_disparity(dev(sc.left), dev(sc.right), pd_, pc_)
+    assert len(ms) == len(ctx.stage_names()) == s.levels + 2 and min(ms) >= 0.0 and ms[0] > 0.0
+    np.testing.assert_array_equal(host(pd_), d)
+    np.testing.assert_array_equal(host(pc_), c)
 
 
 def test_k1_equals_full_level():
