@@ -444,8 +444,11 @@ def bench_batch(args, dev, flush, stream):
     return res
 
 
-def bench_diff(args, dev, flush, stream):
-    """Soft-argmax ZNCC level forward + backward, 8 x 640 x 480, 64 candidates, 7x7, T=0.05."""
+def bench_diff(args, dev, flush, stream, pipes=None):
+    """Soft-argmax ZNCC level forward + backward, 8 x 640 x 480, 64 candidates, 7x7, T=0.05:
+    through the autograd.Function (forward_ms, forward_backward_ms), and each launch of the
+    C ABI alone with its roofline (forward against the measured FFMA rate, backward against
+    HBM)."""
     import numpy as np
     import torch
 
@@ -485,6 +488,49 @@ def bench_diff(args, dev, flush, stream):
     evals = 8 * 480 * sum(min(63, x) + 1 for x in range(640))
     res.update({"workload": "8 x 640 x 480 float32 pairs, 7x7 ZNCC over 64 candidates, soft-argmax T=0.05",
                 "evals": evals, "forward_gpix_disp_per_s": evals / (res["forward_ms"] * 1e-3) / 1e9})
+    # the two C-ABI calls of a training step, each timed alone (the forward keeping the cost
+    # volume and window statistics, the backward reading them)
+    from paper_1901_09593_gb300.softargmax import backward_raw, forward_raw
+    eps = default_eps(7)
+    kept = {}
+
+    def fwd_keep():
+        kept["v"] = forward_raw(L, R, 7, 64, 0.05, eps, True)
+
+    def bwd_kept():
+        d, m, l, sv = kept["v"]
+        backward_raw(L, R, 7, 64, 0.05, eps, d, m, l, g, sv)
+
+    for name, fn in (("forward_kept", fwd_keep), ("backward_kept", bwd_kept)):
+        fn()
+        torch.cuda.synchronize(dev)
+        steps = max(3, min(args.steps, 10))
+        ts = []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ts.append(e0.elapsed_time(e1))
+        res[name + "_ms"] = statistics.median(ts)
+    # roofline: the forward's 49 FFMA per evaluation (the window product; the score and the
+    # online softmax add a few more) against the measured FFMA rate; the backward's bytes
+    # per evaluation against HBM: the kept rho read and alpha written by the coefficient
+    # kernel (8 B), alpha read by the gradient kernel with its tile halo ((32+6)^2/32^2 x 4 B)
+    ffma = (pipes or {}).get("ffma", {}).get("lane_ops_per_s")
+    peaks = load_peaks() or {}
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    fwd_rate = evals * 49 / (res["forward_kept_ms"] * 1e-3)
+    bwd_bytes = evals * (8 + 4 * 38 * 38 / (32 * 32))
+    res["roofline"] = {
+        "forward": {"bound": "ffma", "achieved": fwd_rate / 1e12, "unit": "T FFMA/s",
+                    "peak": ffma / 1e12 if ffma else None, "frac": fwd_rate / ffma if ffma else None},
+        "backward": {"bound": "hbm", "achieved": bwd_bytes / (res["backward_kept_ms"] * 1e-3) / 1e9,
+                     "unit": "GB/s", "peak": hbm,
+                     "frac": bwd_bytes / (res["backward_kept_ms"] * 1e-3) / 1e9 / hbm,
+                     "algorithmic_bytes": bwd_bytes}}
     return res
 
 
@@ -737,7 +783,7 @@ def run_gpu(args):
     additions = {}
     if rank == 0 and not args.no_additions:
         additions["batching"] = bench_batch(args, dev, flush, stream)
-        additions["differentiable"] = bench_diff(args, dev, flush, stream)
+        additions["differentiable"] = bench_diff(args, dev, flush, stream, pipes)
         additions["large_pair"] = bench_pair(args, dev, flush, stream, "large_2880x1984",
                                              "2880x1984 uint8 pair, D=640, K=5, 9x9 window, r=3")
         additions["small_pair"] = bench_pair(args, dev, flush, stream, "small_320x240",

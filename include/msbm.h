@@ -290,6 +290,34 @@ msbm_status msbm_zncc_softargmax_bwd(const float *d_left, const float *d_right, 
                                      float *g_left, float *g_right, void *workspace,
                                      size_t workspace_bytes, void *cuda_stream);
 
+/* Bytes of caller-owned device memory msbm_zncc_softargmax_fwd_saved keeps for the backward
+ * (0 for invalid sizes): rho for every (image, z, pixel), float [batch][ndisp][height][width],
+ * then the left and right window statistics {mean, rsqrt(sum c^2 + eps)}, float2
+ * [batch][height][width] each; every part 256-byte aligned. */
+size_t msbm_zncc_softargmax_saved_bytes(int32_t batch, int32_t height, int32_t width, int32_t window,
+                                        int32_t ndisp);
+
+/* msbm_zncc_softargmax_fwd that also keeps, in `saved` (at least
+ * msbm_zncc_softargmax_saved_bytes, 256-byte aligned: MSBM_ERR_ALIGNMENT otherwise), the
+ * costs rho of Eq. 2 it evaluated (admissible z only) and the window statistics, for
+ * msbm_zncc_softargmax_bwd_saved.  The same d_soft, m, l as msbm_zncc_softargmax_fwd. */
+msbm_status msbm_zncc_softargmax_fwd_saved(const float *d_left, const float *d_right, int32_t batch,
+                                           int32_t height, int32_t width, int32_t window, int32_t ndisp,
+                                           float temperature, float eps, float *d_soft, float *m_out,
+                                           float *l_out, void *saved, size_t saved_bytes, void *cuda_stream);
+
+/* msbm_zncc_softargmax_bwd reading rho and the window statistics from `saved` (written by
+ * msbm_zncc_softargmax_fwd_saved for the same images and arguments, unchanged since) instead
+ * of recomputing them; the same gradients (the saved values are the recomputed ones).
+ * workspace as for msbm_zncc_softargmax_bwd.  Asynchronous on cuda_stream. */
+msbm_status msbm_zncc_softargmax_bwd_saved(const float *d_left, const float *d_right, int32_t batch,
+                                           int32_t height, int32_t width, int32_t window, int32_t ndisp,
+                                           float temperature, float eps, const float *d_soft,
+                                           const float *m_in, const float *l_in, const float *g_d,
+                                           const void *saved, size_t saved_bytes, float *g_left,
+                                           float *g_right, void *workspace, size_t workspace_bytes,
+                                           void *cuda_stream);
+
 /* ---------------------------------------------------------------------------------------
  * Measurement support (the paper has no counterpart): issue-rate probe of one instruction
  * class, the denominator of the matching kernels' rooflines.

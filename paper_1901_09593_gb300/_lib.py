@@ -77,6 +77,14 @@ SIGNATURES = {
     "msbm_zncc_softargmax_bwd": ([c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_int32,
                                   ctypes.c_float, ctypes.c_float, c_void_p, c_void_p, c_void_p, c_void_p,
                                   c_void_p, c_void_p, c_void_p, c_size_t, c_void_p], ctypes.c_int),
+    "msbm_zncc_softargmax_saved_bytes": ([c_int32, c_int32, c_int32, c_int32, c_int32], c_size_t),
+    "msbm_zncc_softargmax_fwd_saved": ([c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_int32,
+                                        ctypes.c_float, ctypes.c_float, c_void_p, c_void_p, c_void_p, c_void_p,
+                                        c_size_t, c_void_p], ctypes.c_int),
+    "msbm_zncc_softargmax_bwd_saved": ([c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_int32,
+                                        ctypes.c_float, ctypes.c_float, c_void_p, c_void_p, c_void_p, c_void_p,
+                                        c_void_p, c_size_t, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p],
+                                       ctypes.c_int),
     "msbm_flat_disparity_noalloc": ([c_void_p, c_void_p, c_size_t, c_int32, c_int32, c_int32, c_int32,
                                      c_void_p, c_void_p, c_void_p, c_void_p], ctypes.c_int),
 }

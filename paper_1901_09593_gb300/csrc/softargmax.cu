@@ -22,9 +22,17 @@
 // centre r:  beta(p) = sum_z g_rho rho / (Saa + eps),  zeta(p) = sum_z alpha mb(p - z),
 // delta(r) = sum_z g_rho rho / (Sbb + eps) and er(r) = sum_z alpha ma at p = r + z.
 // Positions outside the image are folded into the clamped edge pixel.  Two kernels: the
-// coefficients (recomputes rho and the window statistics, writes the alpha volume) and the
+// coefficients (writes the alpha volume and the per-pixel / per-centre sums) and the
 // gradients (box filter of alpha per tile and candidate, both gathers; the box-filtered
 // volume is never stored).  Everything is FP32.
+//
+// Saved or recomputed.  msbm_zncc_softargmax_fwd_saved also keeps, in caller-owned memory,
+// rho for every (image, z, pixel) it evaluated and the left and right window statistics
+// {mean, rsqrt(sum c^2 + eps)}; the matching backward's coefficient kernel then reads them
+// (one coalesced load per (pixel, z)) instead of staging both images and recomputing the
+// (2n+1)^2-term products.  The values are those the recomputation gives, bit for bit (the
+// same code computes them), so both backwards agree.  msbm_zncc_softargmax_fwd / _bwd keep
+// nothing and recompute.
 #include <math.h>
 
 #include "msbm.h"
@@ -50,6 +58,10 @@ struct SaArgs {
     const float *g;
     float *alpha;   // [B][Z][H][W]
     float *zeta, *beta, *ma, *mb, *delta, *er;   // [B][H][W]
+    // saved by the forward (nullptr: not kept / recompute): rho [B][Z][H][W] (admissible z
+    // only), left statistics {ma, rsa} and right statistics {mb, rsb} per pixel [B][H][W]
+    float *rho;
+    float2 *lst, *rst;
 };
 
 template <int NH>
@@ -180,7 +192,9 @@ __global__ void __launch_bounds__(256) sa_fwd_kernel(const SaArgs a) {
     const int tx = threadIdx.x, ty = threadIdx.y, x = x0 + tx, y = y0 + ty;
     if (x >= a.W || y >= a.H) return;
     float m2 = -INFINITY, l = 0.f, s = 0.f, ma, rsa;
-    sa_scan<NH>(a, Lt, Rt, st, RTP, RSW, tx, ty, x, ma, rsa, [&](int z, float, float v2, float, float) {
+    float *rho_p = a.rho ? a.rho + (size_t)b * a.ndisp * plane + (size_t)y * a.W + x : nullptr;
+    sa_scan<NH>(a, Lt, Rt, st, RTP, RSW, tx, ty, x, ma, rsa, [&](int z, float rho, float v2, float, float) {
+        if (rho_p) rho_p[(size_t)z * plane] = rho;
         if (v2 > m2) {
             const float sc = exp2f(m2 - v2);
             l = fmaf(l, sc, 1.f);
@@ -196,6 +210,10 @@ __global__ void __launch_bounds__(256) sa_fwd_kernel(const SaArgs a) {
     a.dsoft[p] = s / l;
     a.m2[p] = m2;
     a.l[p] = l;
+    if (a.lst) {
+        a.lst[p] = make_float2(ma, rsa);
+        a.rst[p] = st[ty * RSW + tx + a.ndisp - 1];   // right centre x
+    }
 }
 
 // Two CTAs per SM: at 7 x 7 the unconstrained build took 148 registers (one CTA per SM);
@@ -225,24 +243,27 @@ __global__ void __launch_bounds__(256, 2) sa_bwd_coef_kernel(const SaArgs a) {
     const bool lockstep = __ballot_sync(0xFFFFFFFFu, inside && min(a.ndisp - 1, x) == a.ndisp - 1) == am;
     if (inside) {
         const size_t p = b * plane + (size_t)y * a.W + x;
-        const float g = a.g[p], d = a.dsoft[p], m2 = a.m2[p], invl = 1.f / a.l[p];
+        const float d = a.dsoft[p], m2 = a.m2[p];
+        const float gs = a.g[p] * a.invT / a.l[p];             // g p_z (z - d) / T = gs 2^(..) (z - d)
         float beta = 0.f, zeta = 0.f, ma = 0.f, rsa = 0.f;
         float *alpha = a.alpha + (size_t)b * a.ndisp * plane + (size_t)y * a.W + x;
         float *accDrow = accD + ty * RSW + tx + a.ndisp - 1;   // right centre x - z at [-z]
         float *accErow = accE + ty * RSW + tx + a.ndisp - 1;
         int zmax = -1;   // ma and rsa are set by sa_scan before its first callback
-        sa_scan<NH>(a, Lt, Rt, st, RTP, RSW, tx, ty, x, ma, rsa, [&](int z, float rho, float v2, float mb, float rsb) {
-            const float pz = exp2f(v2 - m2) * invl;
-            const float grho = g * pz * (static_cast<float>(z) - d) * a.invT;
+        // the same arithmetic as sa_bwd_coef_saved_kernel, so both backwards give the same
+        // coefficients
+        sa_scan<NH>(a, Lt, Rt, st, RTP, RSW, tx, ty, x, ma, rsa, [&](int z, float rho, float, float mb, float rsb) {
+            const float grho = gs * exp2f(fmaf(rho, a.invT2, -m2)) * (static_cast<float>(z) - d);
             const float al = grho * rsa * rsb;
-            beta = fmaf(grho * rho, rsa * rsa, beta);
+            const float gr = grho * rho;
+            beta = fmaf(gr, rsa * rsa, beta);
             zeta = fmaf(al, mb, zeta);
             if (lockstep) {
-                accDrow[-z] += grho * rho * rsb * rsb;
-                accErow[-z] += al * ma;
+                accDrow[-z] = fmaf(gr, rsb * rsb, accDrow[-z]);
+                accErow[-z] = fmaf(al, ma, accErow[-z]);
                 __syncwarp(am);
             } else {
-                atomicAdd(accDrow - z, grho * rho * rsb * rsb);
+                atomicAdd(accDrow - z, gr * rsb * rsb);
                 atomicAdd(accErow - z, al * ma);
             }
             alpha[(size_t)z * plane] = al;
@@ -256,6 +277,91 @@ __global__ void __launch_bounds__(256, 2) sa_bwd_coef_kernel(const SaArgs a) {
     }
     __syncthreads();
     // flush the right-centre accumulators: centre v <-> image column x0 - (ndisp-1) + v
+    float *delta = a.delta + b * plane, *er = a.er + b * plane;
+    for (int i = tid; i < SA_TY * RSW; i += SA_TX * SA_TY) {
+        int ry = i / RSW, v = i - ry * RSW;
+        int yy = y0 + ry, xx = x0 - (a.ndisp - 1) + v;
+        if (yy >= a.H || xx < 0 || xx >= a.W) continue;
+        if (accD[i] != 0.f) atomicAdd(delta + (size_t)yy * a.W + xx, accD[i]);
+        if (accE[i] != 0.f) atomicAdd(er + (size_t)yy * a.W + xx, accE[i]);
+    }
+}
+
+// The coefficient kernel on the forward's saved rho and window statistics: the same
+// per-(pixel, z) coefficients and sums as sa_bwd_coef_kernel, with rho, {ma, rsa} and
+// {mb, rsb} loaded instead of recomputed (no image staging, no window products).
+__global__ void __launch_bounds__(256) sa_bwd_coef_saved_kernel(const SaArgs a) {
+    extern __shared__ float sm[];
+    const int RSW = SA_TX + a.ndisp - 1;
+    float *accD = sm;
+    float *accE = accD + SA_TY * RSW;
+    const int b = blockIdx.z, x0 = blockIdx.x * SA_TX, y0 = blockIdx.y * SA_TY;
+    const size_t plane = (size_t)a.H * a.W;
+    const int tid = threadIdx.y * SA_TX + threadIdx.x;
+    for (int i = tid; i < 2 * SA_TY * RSW; i += SA_TX * SA_TY) accD[i] = 0.f;
+    __syncthreads();
+    const int tx = threadIdx.x, ty = threadIdx.y, x = x0 + tx, y = y0 + ty;
+    // lockstep as in sa_bwd_coef_kernel: ordered plain updates when a warp's in-image lanes
+    // all walk every candidate
+    const bool inside = x < a.W && y < a.H;
+    const unsigned am = __ballot_sync(0xFFFFFFFFu, inside);
+    const bool lockstep = __ballot_sync(0xFFFFFFFFu, inside && min(a.ndisp - 1, x) == a.ndisp - 1) == am;
+    if (inside) {
+        const size_t p = b * plane + (size_t)y * a.W + x;
+        const float d = a.dsoft[p], m2 = a.m2[p];
+        const float gs = a.g[p] * a.invT / a.l[p];             // g p_z (z - d) / T = gs 2^(..) (z - d)
+        const float2 ls = a.lst[p];
+        const float ma = ls.x, rsa = ls.y, rsa2 = rsa * rsa;
+        float beta = 0.f, zeta = 0.f;
+        float *alpha = a.alpha + (size_t)b * a.ndisp * plane + (size_t)y * a.W + x;
+        const float *rho_p = a.rho + (size_t)b * a.ndisp * plane + (size_t)y * a.W + x;
+        const uint32_t pl = static_cast<uint32_t>(plane);       // H * W < 2^32
+        const float2 *rs = a.rst + p;                            // right centre x - z at [-z]
+        float *accDrow = accD + ty * RSW + tx + a.ndisp - 1;
+        float *accErow = accE + ty * RSW + tx + a.ndisp - 1;
+        const int zmax = min(a.ndisp - 1, x);
+        // the loads of SB_AHEAD candidates are issued together: the volume comes from DRAM,
+        // and one candidate's latency per iteration would bound the loop (measured backward:
+        // 1.20 ms one at a time, 0.96 ms four, 1.08 / 1.14 ms eight / sixteen)
+        constexpr int SB_AHEAD = 4;
+        for (int z0 = 0; z0 <= zmax; z0 += SB_AHEAD) {
+            float rv[SB_AHEAD];
+            float2 qv[SB_AHEAD];
+#pragma unroll
+            for (int u = 0; u < SB_AHEAD; ++u) {
+                const int z = z0 + u;
+                rv[u] = z <= zmax ? __ldg(rho_p + static_cast<uint64_t>(static_cast<uint32_t>(z)) * pl) : 0.f;
+                qv[u] = z <= zmax ? __ldg(rs - z) : make_float2(0.f, 0.f);
+            }
+            float zd = static_cast<float>(z0) - d;
+#pragma unroll
+            for (int u = 0; u < SB_AHEAD; ++u, zd += 1.f) {
+                const int z = z0 + u;
+                if (z > zmax) break;
+                const float rho = rv[u], mb = qv[u].x, rsb = qv[u].y;
+                const float grho = gs * exp2f(fmaf(rho, a.invT2, -m2)) * zd;
+                const float al = grho * rsa * rsb;
+                const float gr = grho * rho;
+                beta = fmaf(gr, rsa2, beta);
+                zeta = fmaf(al, mb, zeta);
+                if (lockstep) {
+                    accDrow[-z] = fmaf(gr, rsb * rsb, accDrow[-z]);
+                    accErow[-z] = fmaf(al, ma, accErow[-z]);
+                    __syncwarp(am);
+                } else {
+                    atomicAdd(accDrow - z, gr * rsb * rsb);
+                    atomicAdd(accErow - z, al * ma);
+                }
+                alpha[static_cast<uint64_t>(static_cast<uint32_t>(z)) * pl] = al;
+            }
+        }
+        for (int z = zmax + 1; z < a.ndisp; ++z) alpha[(size_t)z * plane] = 0.f;
+        a.beta[p] = beta;
+        a.zeta[p] = zeta;
+        a.ma[p] = ma;
+        a.mb[p] = rs[0].x;
+    }
+    __syncthreads();
     float *delta = a.delta + b * plane, *er = a.er + b * plane;
     for (int i = tid; i < SA_TY * RSW; i += SA_TX * SA_TY) {
         int ry = i / RSW, v = i - ry * RSW;
@@ -315,9 +421,10 @@ __global__ void __launch_bounds__(256) sa_grad_kernel(const SaArgs a, float *gL,
         }
     const int X = X0 + tx, qx = X - NH;
     const int r0 = SG_PER * ty;                       // this thread's first tile row
-    float Lq[SG_PER], gl[SG_PER];
+    float Lq[SG_PER], gl[SG_PER], racc[SG_PER];
 #pragma unroll
     for (int k = 0; k < SG_PER; ++k) {
+        racc[k] = 0.f;
         const int cy = clampi(Y0 + r0 + k - NH, 0, a.H - 1);
         Lq[k] = Lb[(size_t)cy * a.W + clampi(qx, 0, a.W - 1)];
         gl[k] = 0.f;
@@ -358,26 +465,53 @@ __global__ void __launch_bounds__(256) sa_grad_kernel(const SaArgs a, float *gL,
                 for (int j = 0; j < NJ; ++j) nxt[i][j] = off[i][j] >= 0 ? __ldg(al + off[i][j]) : 0.f;
         }
         __syncthreads();
-        for (int t = ty; t < TR; t += 8) {
+        // horizontal window sums: each of TR x 4 items slides over 8 columns of one row
+        for (int i = tid; i < TR * 4; i += SA_TX * 8) {
+            const int t = i >> 2, c0 = (i & 3) * 8;
+            const float *row = tile + t * TCP + c0;
             float s = 0.f;
 #pragma unroll
-            for (int j = 0; j < WIN; ++j) s += tile[t * TCP + tx + j];
-            hs[t * HSP + tx] = s;
+            for (int j = 0; j < WIN; ++j) s += row[j];
+            float *h = hs + t * HSP + c0;
+            h[0] = s;
+#pragma unroll
+            for (int u = 1; u < 8; ++u) {
+                s += row[u + WIN - 1] - row[u - 1];
+                h[u] = s;
+            }
         }
         __syncthreads();
+        const int c = tx + a.ndisp - 1 - z;           // column of extended X - z
+        float v[SG_PER];
+#pragma unroll
+        for (int k = 0; k < SG_PER; ++k) v[k] = 0.f;
         if (colin && z <= X) {
             float A = 0.f;
 #pragma unroll
             for (int i = 0; i < WIN; ++i) A += hs[(r0 + i) * HSP + tx];
-            const int c = tx + a.ndisp - 1 - z;       // column of extended X - z
 #pragma unroll
             for (int k = 0; k < SG_PER; ++k) {
                 if (k > 0) A += hs[(r0 + k + WIN - 1) * HSP + tx] - hs[(r0 + k - 1) * HSP + tx];
                 gl[k] = fmaf(Rs[(r0 + k) * AW + c], A, gl[k]);
-                accR[(r0 + k) * AW + c] += Lq[k] * A;
+                v[k] = Lq[k] * A;
             }
         }
+        // gR(Y, X - z) += L(q) A_z: the partial of column c moves one lane up per candidate
+        // (lane tx + 1 reaches the same column at z + 1); lane 31's leaves the warp complete
+#pragma unroll
+        for (int k = 0; k < SG_PER; ++k) {
+            racc[k] += v[k];
+            if (tx == SA_TX - 1) accR[(r0 + k) * AW + c] += racc[k];
+            racc[k] = __shfl_up_sync(0xFFFFFFFFu, racc[k], 1);
+            if (tx == 0) racc[k] = 0.f;
+        }
     }
+    // the partials still in flight: lane tx holds column tx - 1 (that lane tx - 1 had at the
+    // last candidate), then the box terms below update the tile's own columns
+#pragma unroll
+    for (int k = 0; k < SG_PER; ++k)
+        if (tx > 0) accR[(r0 + k) * AW + tx - 1] += racc[k];
+    __syncwarp();
     __syncthreads();
     const float *zeta = a.zeta + b * plane, *beta = a.beta + b * plane, *ma = a.ma + b * plane;
     const float *er = a.er + b * plane, *delta = a.delta + b * plane, *mb = a.mb + b * plane;
@@ -436,9 +570,14 @@ cudaError_t sa_run(const SaArgs &a, bool bwd, float *gL, float *gR, cudaStream_t
         sa_fwd_kernel<NH><<<grd, blk, smem, st>>>(a);
         return cudaGetLastError();
     }
-    e = cudaFuncSetAttribute(sa_bwd_coef_kernel<NH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    sa_bwd_coef_kernel<NH><<<grd, blk, smem, st>>>(a);
+    if (a.rho) {
+        const size_t csm = 2 * (size_t)SA_TY * (SA_TX + a.ndisp - 1) * sizeof(float);
+        sa_bwd_coef_saved_kernel<<<grd, blk, csm, st>>>(a);
+    } else {
+        e = cudaFuncSetAttribute(sa_bwd_coef_kernel<NH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        sa_bwd_coef_kernel<NH><<<grd, blk, smem, st>>>(a);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int Wp = a.W + 2 * NH, Hp = a.H + 2 * NH;
     dim3 gext((Wp + SA_TX - 1) / SA_TX, (Hp + SG_TY - 1) / SG_TY, a.B);
@@ -476,6 +615,28 @@ msbm_status sa_validate(const float *L, const float *R, int B, int H, int W, int
 struct SaWorkspace {
     size_t alpha, arrays, total;
 };
+
+// Saved-forward memory: rho [B][Z][H][W], then {ma, rsa} and {mb, rsb} per pixel, each
+// part 256-byte aligned.
+struct SaSaved {
+    size_t rho, stats, total;
+};
+
+SaSaved sa_saved(int B, int H, int W, int ndisp) {
+    SaSaved v;
+    auto al = [](size_t n) { return (n + 255) / 256 * 256; };
+    v.rho = al((size_t)B * ndisp * H * W * sizeof(float));
+    v.stats = al((size_t)B * H * W * sizeof(float2));
+    v.total = v.rho + 2 * v.stats;
+    return v;
+}
+
+void sa_bind_saved(SaArgs &a, void *saved, const SaSaved &v) {
+    uint8_t *m = static_cast<uint8_t *>(saved);
+    a.rho = reinterpret_cast<float *>(m);
+    a.lst = reinterpret_cast<float2 *>(m + v.rho);
+    a.rst = reinterpret_cast<float2 *>(m + v.rho + v.stats);
+}
 
 SaWorkspace sa_workspace(int B, int H, int W, int window, int ndisp) {
     (void)window;
@@ -535,6 +696,69 @@ msbm_status msbm_zncc_softargmax_bwd(const float *d_left, const float *d_right, 
     a.invT2 = LOG2E / temperature; a.invT = 1.f / temperature; a.eps = eps;
     a.dsoft = const_cast<float *>(d_soft); a.m2 = const_cast<float *>(m_in); a.l = const_cast<float *>(l_in);
     a.g = g_d;
+    a.alpha = reinterpret_cast<float *>(ws);
+    float *arr = reinterpret_cast<float *>(ws + w.alpha);
+    const size_t na = w.arrays / sizeof(float);
+    a.zeta = arr; a.beta = arr + na; a.ma = arr + 2 * na; a.mb = arr + 3 * na; a.delta = arr + 4 * na;
+    a.er = arr + 5 * na;
+    const size_t plane_bytes = (size_t)batch * height * width * sizeof(float);
+    cudaError_t e = cudaMemsetAsync(a.delta, 0, 2 * w.arrays, st);   // delta and er accumulate
+    if (e == cudaSuccess) e = cudaMemsetAsync(g_left, 0, plane_bytes, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g_right, 0, plane_bytes, st);
+    if (e == cudaSuccess) e = sa_dispatch(window / 2, a, true, g_left, g_right, st);
+    return e == cudaSuccess ? MSBM_OK : MSBM_ERR_CUDA;
+}
+
+size_t msbm_zncc_softargmax_saved_bytes(int32_t batch, int32_t height, int32_t width, int32_t window,
+                                        int32_t ndisp) {
+    if (!sa_sizes_ok(batch, height, width, window, ndisp)) return 0;
+    return sa_saved(batch, height, width, ndisp).total;
+}
+
+msbm_status msbm_zncc_softargmax_fwd_saved(const float *d_left, const float *d_right, int32_t batch,
+                                           int32_t height, int32_t width, int32_t window, int32_t ndisp,
+                                           float temperature, float eps, float *d_soft, float *m_out, float *l_out,
+                                           void *saved, size_t saved_bytes, void *cuda_stream) {
+    msbm_status s = sa_validate(d_left, d_right, batch, height, width, window, ndisp, temperature, eps);
+    if (s != MSBM_OK) return s;
+    if (!d_soft || !m_out || !l_out || !saved) return MSBM_ERR_INVALID_ARG;
+    const SaSaved v = sa_saved(batch, height, width, ndisp);
+    if (saved_bytes < v.total) return MSBM_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(saved) % 256 != 0) return MSBM_ERR_ALIGNMENT;
+    SaArgs a = {};
+    a.L = d_left; a.R = d_right;
+    a.B = batch; a.H = height; a.W = width; a.ndisp = ndisp;
+    a.invT2 = LOG2E / temperature; a.invT = 1.f / temperature; a.eps = eps;
+    a.dsoft = d_soft; a.m2 = m_out; a.l = l_out;
+    sa_bind_saved(a, saved, v);
+    cudaError_t e = sa_dispatch(window / 2, a, false, nullptr, nullptr, static_cast<cudaStream_t>(cuda_stream));
+    return e == cudaSuccess ? MSBM_OK : MSBM_ERR_CUDA;
+}
+
+msbm_status msbm_zncc_softargmax_bwd_saved(const float *d_left, const float *d_right, int32_t batch,
+                                           int32_t height, int32_t width, int32_t window, int32_t ndisp,
+                                           float temperature, float eps, const float *d_soft, const float *m_in,
+                                           const float *l_in, const float *g_d, const void *saved,
+                                           size_t saved_bytes, float *g_left, float *g_right, void *workspace,
+                                           size_t workspace_bytes, void *cuda_stream) {
+    msbm_status s = sa_validate(d_left, d_right, batch, height, width, window, ndisp, temperature, eps);
+    if (s != MSBM_OK) return s;
+    if (!d_soft || !m_in || !l_in || !g_d || !g_left || !g_right || !workspace || !saved)
+        return MSBM_ERR_INVALID_ARG;
+    const SaSaved v = sa_saved(batch, height, width, ndisp);
+    SaWorkspace w = sa_workspace(batch, height, width, window, ndisp);
+    if (saved_bytes < v.total || workspace_bytes < w.total) return MSBM_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0 || reinterpret_cast<uintptr_t>(saved) % 256 != 0)
+        return MSBM_ERR_ALIGNMENT;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    uint8_t *ws = static_cast<uint8_t *>(workspace);
+    SaArgs a = {};
+    a.L = d_left; a.R = d_right;
+    a.B = batch; a.H = height; a.W = width; a.ndisp = ndisp;
+    a.invT2 = LOG2E / temperature; a.invT = 1.f / temperature; a.eps = eps;
+    a.dsoft = const_cast<float *>(d_soft); a.m2 = const_cast<float *>(m_in); a.l = const_cast<float *>(l_in);
+    a.g = g_d;
+    sa_bind_saved(a, const_cast<void *>(saved), v);
     a.alpha = reinterpret_cast<float *>(ws);
     float *arr = reinterpret_cast<float *>(ws + w.alpha);
     const size_t na = w.arrays / sizeof(float);

@@ -2,8 +2,10 @@
 
 ``ZnccSoftArgmax.apply(left, right, window, ndisp, temperature, eps)`` maps float32 image
 batches (B, H, W) on the GPU to d_soft (B, H, W).  Forward and backward run in libmsbm's
-kernels (msbm_zncc_softargmax_fwd / _bwd); the backward recomputes the window statistics
-and the costs instead of storing the cost volume.
+kernels.  When a gradient is wanted the forward keeps the cost volume and the window
+statistics (msbm_zncc_softargmax_fwd_saved, B x ndisp x H x W floats) for the backward
+(msbm_zncc_softargmax_bwd_saved); ``ZnccSoftArgmax.apply(..., keep=False)`` keeps nothing
+and the backward recomputes them (msbm_zncc_softargmax_fwd / _bwd).
 """
 from __future__ import annotations
 
@@ -33,8 +35,9 @@ def _check(t, name):
         raise ValueError(f"{name} must be a contiguous (B, H, W) tensor")
 
 
-def forward_raw(left, right, window: int, ndisp: int, temperature: float, eps: float):
-    """Returns (d_soft, m, l)."""
+def forward_raw(left, right, window: int, ndisp: int, temperature: float, eps: float, keep: bool = False):
+    """Returns (d_soft, m, l, saved): saved is the kept cost volume and statistics (a uint8
+    device tensor) when keep, else None."""
     torch = _torch()
     _check(left, "left")
     _check(right, "right")
@@ -46,13 +49,21 @@ def forward_raw(left, right, window: int, ndisp: int, temperature: float, eps: f
     m = torch.empty_like(left)
     l = torch.empty_like(left)
     st = torch.cuda.current_stream(left.device).cuda_stream
-    _lib.check(lib.msbm_zncc_softargmax_fwd(_p(left), _p(right), b, h, w, window, ndisp,
-                                            float(temperature), float(eps), _p(d), _p(m), _p(l),
-                                            ctypes.c_void_p(st)), "msbm_zncc_softargmax_fwd")
-    return d, m, l
+    if not keep:
+        _lib.check(lib.msbm_zncc_softargmax_fwd(_p(left), _p(right), b, h, w, window, ndisp,
+                                                float(temperature), float(eps), _p(d), _p(m), _p(l),
+                                                ctypes.c_void_p(st)), "msbm_zncc_softargmax_fwd")
+        return d, m, l, None
+    nbytes = lib.msbm_zncc_softargmax_saved_bytes(b, h, w, window, ndisp)
+    saved = torch.empty(nbytes, dtype=torch.uint8, device=left.device)
+    _lib.check(lib.msbm_zncc_softargmax_fwd_saved(_p(left), _p(right), b, h, w, window, ndisp,
+                                                  float(temperature), float(eps), _p(d), _p(m), _p(l),
+                                                  _p(saved), nbytes, ctypes.c_void_p(st)),
+               "msbm_zncc_softargmax_fwd_saved")
+    return d, m, l, saved
 
 
-def backward_raw(left, right, window, ndisp, temperature, eps, d, m, l, g):
+def backward_raw(left, right, window, ndisp, temperature, eps, d, m, l, g, saved=None):
     torch = _torch()
     lib = _lib.load()
     b, h, w = left.shape
@@ -62,10 +73,17 @@ def backward_raw(left, right, window, ndisp, temperature, eps, d, m, l, g):
     gr = torch.empty_like(left)
     g = g.contiguous()
     st = torch.cuda.current_stream(left.device).cuda_stream
-    _lib.check(lib.msbm_zncc_softargmax_bwd(_p(left), _p(right), b, h, w, window, ndisp,
-                                            float(temperature), float(eps), _p(d), _p(m), _p(l), _p(g),
-                                            _p(gl), _p(gr), _p(ws), nbytes, ctypes.c_void_p(st)),
-               "msbm_zncc_softargmax_bwd")
+    if saved is None:
+        _lib.check(lib.msbm_zncc_softargmax_bwd(_p(left), _p(right), b, h, w, window, ndisp,
+                                                float(temperature), float(eps), _p(d), _p(m), _p(l), _p(g),
+                                                _p(gl), _p(gr), _p(ws), nbytes, ctypes.c_void_p(st)),
+                   "msbm_zncc_softargmax_bwd")
+    else:
+        _lib.check(lib.msbm_zncc_softargmax_bwd_saved(_p(left), _p(right), b, h, w, window, ndisp,
+                                                      float(temperature), float(eps), _p(d), _p(m), _p(l), _p(g),
+                                                      _p(saved), saved.numel(), _p(gl), _p(gr), _p(ws), nbytes,
+                                                      ctypes.c_void_p(st)),
+                   "msbm_zncc_softargmax_bwd_saved")
     return gl, gr
 
 
@@ -76,12 +94,15 @@ def _make_function():
         """d_soft = sum_z z softmax_z(ZNCC_eps(left, right, z) / T) over 0 <= z <= min(ndisp-1, x)."""
 
         @staticmethod
-        def forward(ctx, left, right, window=7, ndisp=64, temperature=0.05, eps=None):
+        def forward(ctx, left, right, window=7, ndisp=64, temperature=0.05, eps=None, keep=True):
             eps = default_eps(window) if eps is None else eps
             left = left.contiguous()
             right = right.contiguous()
-            d, m, l = forward_raw(left, right, window, ndisp, temperature, eps)
+            # keep the cost volume only when a gradient will be asked for
+            keep = bool(keep) and any(ctx.needs_input_grad[:2])
+            d, m, l, saved = forward_raw(left, right, window, ndisp, temperature, eps, keep)
             ctx.save_for_backward(left, right, d, m, l)
+            ctx.kept = saved
             ctx.cfg = (window, ndisp, temperature, eps)
             return d
 
@@ -89,8 +110,9 @@ def _make_function():
         def backward(ctx, g):
             left, right, d, m, l = ctx.saved_tensors
             window, ndisp, temperature, eps = ctx.cfg
-            gl, gr = backward_raw(left, right, window, ndisp, temperature, eps, d, m, l, g)
-            return gl, gr, None, None, None, None
+            gl, gr = backward_raw(left, right, window, ndisp, temperature, eps, d, m, l, g, ctx.kept)
+            ctx.kept = None
+            return gl, gr, None, None, None, None, None
 
     return ZnccSoftArgmax
 

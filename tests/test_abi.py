@@ -171,6 +171,28 @@ def test_softargmax_backward_checks_its_workspace(lib):
     assert lib.msbm_zncc_softargmax_bwd(*args, ctypes.c_void_p(4096 + 128), need, None) == _lib.MSBM_ERR_ALIGNMENT
 
 
+def test_softargmax_saved_bytes_formula_and_checks(lib):
+    # the kept forward: one float per (image, z, pixel), then two float2 per pixel, each part
+    # rounded up to 256 bytes
+    from paper_1901_09593_gb300 import _lib
+    al = lambda v: (v + 255) // 256 * 256
+    for b, h, w, win, nd in [(1, 5, 9, 3, 4), (8, 480, 640, 7, 64)]:
+        assert lib.msbm_zncc_softargmax_saved_bytes(b, h, w, win, nd) == al(b * nd * h * w * 4) + 2 * al(b * h * w * 8)
+    assert lib.msbm_zncc_softargmax_saved_bytes(1, 5, 9, 4, 4) == 0
+    need = lib.msbm_zncc_softargmax_saved_bytes(1, 8, 16, 3, 4)
+    fwd = [_FAKE, _FAKE, 1, 8, 16, 3, 4, 0.1, 0.0, _FAKE, _FAKE, _FAKE]
+    assert lib.msbm_zncc_softargmax_fwd_saved(*fwd, None, need, None) == _lib.MSBM_ERR_INVALID_ARG
+    assert lib.msbm_zncc_softargmax_fwd_saved(*fwd, _FAKE, need - 1, None) == _lib.MSBM_ERR_INVALID_ARG
+    assert lib.msbm_zncc_softargmax_fwd_saved(*fwd, ctypes.c_void_p(4096 + 64), need, None) == _lib.MSBM_ERR_ALIGNMENT
+    ws = lib.msbm_zncc_softargmax_workspace_bytes(1, 8, 16, 3, 4)
+    bwd = [_FAKE, _FAKE, 1, 8, 16, 3, 4, 0.1, 0.0, _FAKE, _FAKE, _FAKE, _FAKE]
+    assert lib.msbm_zncc_softargmax_bwd_saved(*bwd, None, need, _FAKE, _FAKE, _FAKE, ws, None) == _lib.MSBM_ERR_INVALID_ARG
+    assert lib.msbm_zncc_softargmax_bwd_saved(*bwd, _FAKE, need - 1, _FAKE, _FAKE, _FAKE, ws, None) == \
+        _lib.MSBM_ERR_INVALID_ARG
+    assert lib.msbm_zncc_softargmax_bwd_saved(*bwd, ctypes.c_void_p(4096 + 32), need, _FAKE, _FAKE, _FAKE, ws,
+                                              None) == _lib.MSBM_ERR_ALIGNMENT
+
+
 def test_noalloc_rejects_bad_arguments_and_oversized_images_before_device_work(lib):
     from paper_1901_09593_gb300 import _lib
     f = lib.msbm_flat_disparity_noalloc

@@ -34,12 +34,12 @@ def _built():
     oracle.build()
 
 
-def run_gpu(L, R, win, nd, T_, eps, g):
+def run_gpu(L, R, win, nd, T_, eps, g, keep=True):
     import torch
     from paper_1901_09593_gb300.softargmax import ZnccSoftArgmax
     lt = torch.tensor(L, dtype=torch.float32, device="cuda", requires_grad=True)
     rt = torch.tensor(R, dtype=torch.float32, device="cuda", requires_grad=True)
-    d = ZnccSoftArgmax.apply(lt, rt, win, nd, T_, eps)
+    d = ZnccSoftArgmax.apply(lt, rt, win, nd, T_, eps, keep)
     d.backward(torch.tensor(g, dtype=torch.float32, device="cuda"))
     torch.cuda.synchronize()
     return d.detach().cpu().numpy(), lt.grad.cpu().numpy(), rt.grad.cpu().numpy()
@@ -70,15 +70,18 @@ def check_grad(g, gref, what, rtol=1e-3, atol_frac=2e-5):
                                f"max {top:.3g})"
 
 
+@pytest.mark.parametrize("keep", [True, False])
 @pytest.mark.parametrize("win,nd,h,w", [(3, 4, 5, 9), (5, 8, 12, 40), (7, 16, 20, 64), (9, 12, 16, 37),
                                         (7, 64, 24, 100), (5, 1, 6, 10), (7, 20, 9, 11)])
-def test_forward_and_backward_match_oracle_random(win, nd, h, w):
+def test_forward_and_backward_match_oracle_random(win, nd, h, w, keep):
+    """keep: the forward keeps the cost volume for the backward (default) or the backward
+    recomputes it."""
     rng = np.random.default_rng(win * 100 + nd)
     L = rng.random((2, h, w))
     R = rng.random((2, h, w))
     g = rng.standard_normal((2, h, w))
     eps = 1e-6 * win * win
-    d, gl, gr = run_gpu(L, R, win, nd, T, eps, g)
+    d, gl, gr = run_gpu(L, R, win, nd, T, eps, g, keep)
     Lf, Rf = f32(L), f32(R)
     dref = oracle.softargmax_fwd(Lf, Rf, win // 2, nd, T, eps)
     glr, grr = oracle.softargmax_bwd(Lf, Rf, win // 2, nd, T, eps, g)
@@ -139,6 +142,21 @@ def test_full_size_batch_forward_and_one_image_backward():
     check_grad(rt.grad[:1].cpu().numpy(), grr, "640x480 dR")
     # soft disparities track the scene where the match is clear
     assert np.all(np.isfinite(d))
+
+
+def test_kept_and_recomputed_backwards_agree_at_full_size():
+    """The kept volume holds the values the recomputing backward computes, so the two
+    backwards differ only by the order of the cross-CTA float additions."""
+    spec = scenes.SPECS["diff_640x480"]
+    pairs = [scenes.make_float_pair(spec, s) for s in range(2)]
+    L = np.stack([p.left for p in pairs])
+    R = np.stack([p.right for p in pairs])
+    g = np.random.default_rng(5).standard_normal(L.shape)
+    d1, gl1, gr1 = run_gpu(L, R, 7, 64, T, 1e-6 * 49, g, True)
+    d0, gl0, gr0 = run_gpu(L, R, 7, 64, T, 1e-6 * 49, g, False)
+    np.testing.assert_array_equal(d1, d0)
+    for a, b in ((gl1, gl0), (gr1, gr0)):
+        assert np.abs(a - b).max() <= 1e-5 * np.abs(b).max()
 
 
 def test_bad_arguments_are_rejected():
