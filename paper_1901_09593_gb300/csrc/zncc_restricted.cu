@@ -45,9 +45,14 @@ __global__ void __launch_bounds__(32 * VP_TY / 2, pair_min_ctas(NH))
 // slower.
 constexpr int CELL_THREADS = 128;
 constexpr int CELL_MIN_CTAS = 4;
+// A level of windows up to 7 x 7 whose grid fits in one wave at five CTAs per SM (96
+// registers) but not at four takes the five-CTA build: level 1 of the 1400 x 1000 pair (693
+// CTAs) instead of running a second wave of 85 CTAs (pass 49.7 -> 47.9 us).  Larger windows
+// spill at 96 registers (level 2 of the 2880 x 1984 pair, 9 x 9: 12.3 -> 14.3 us), so keep four.
+constexpr int CELL_MIN_CTAS_ONE_WAVE = 5;
 
-template <int NH, int G>
-__global__ void __launch_bounds__(CELL_THREADS, CELL_MIN_CTAS) zncc_cell_kernel(const RestrTileArgs a) {
+template <int NH, int G, int MINB>
+__global__ void __launch_bounds__(CELL_THREADS, MINB) zncc_cell_kernel(const RestrTileArgs a) {
     __shared__ unsigned long long evsum;
     pdl_launch_dependents();
     if (threadIdx.x == 0) evsum = 0ull;
@@ -61,6 +66,20 @@ __global__ void __launch_bounds__(CELL_THREADS, CELL_MIN_CTAS) zncc_cell_kernel(
     if ((threadIdx.x & 31) == 0 && wc) atomicAdd(&evsum, static_cast<unsigned long long>(wc));
     __syncthreads();
     if (threadIdx.x == 0 && a.evals && evsum) atomicAdd(a.evals, evsum);
+}
+
+// SMs of the current device (queried once per process)
+int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+            n = v;
+        else
+            return 1;
+    }
+    return n;
 }
 
 template <int NH, int G>
@@ -80,7 +99,11 @@ template <int NH, int G>
 cudaError_t launch_restr_t(const RestrArgs &a, cudaStream_t st, bool pdl) {
     if (!a.t.force_timeout) {
         dim3 grd((a.t.Wp + 31) / 32, (a.t.Hp + CELL_THREADS / 32 - 1) / (CELL_THREADS / 32));
-        return launch_k(zncc_cell_kernel<NH, G>, grd, dim3(CELL_THREADS), 0, st, pdl, a.t);
+        const long ctas = (long)grd.x * grd.y, sms = sm_count();
+        if (NH <= 3 && ctas > CELL_MIN_CTAS * sms && ctas <= CELL_MIN_CTAS_ONE_WAVE * sms)
+            return launch_k(zncc_cell_kernel<NH, G, CELL_MIN_CTAS_ONE_WAVE>, grd, dim3(CELL_THREADS), 0, st, pdl,
+                            a.t);
+        return launch_k(zncc_cell_kernel<NH, G, CELL_MIN_CTAS>, grd, dim3(CELL_THREADS), 0, st, pdl, a.t);
     } else {
         using C = RCfg<NH, 32, 1, true, VP_TY>;
         static_assert(C::TX == 32 && C::BYTES <= 227 * 1024, "restricted tile shape");
