@@ -166,18 +166,17 @@ msbm_status msbm_disparity_host(msbm_ctx *ctx, const uint8_t *h_left, const uint
 
 /* A sequence of n_frames stereo pairs in HOST memory (a video stream), pipelined, waiting
  * for the last result.  Frame i (arrays of n_frames host pointers; images width x height at
- * pitch_bytes; maps dense) is uploaded on an upload stream into one of two device staging
- * sets, matched, and its maps downloaded on a download stream, so that the upload of frame
- * i+1 and the download of frame i-1 overlap the pass of frame i (they need page-locked
- * buffers to overlap).  With two or more frames the context also keeps a second pass
- * pipeline (a context of the same parameters with its own level buffers and stream,
- * created on the first such call and freed with the context): even frames are matched on
- * the context's stream, odd ones on the second pipeline, so that one frame's coarse levels
- * (small, latency-bound grids) run beside the previous frame's finest level.  The second
- * pipeline's evaluations are not added to msbm_eval_count.  h_costs may be NULL or hold
- * NULLs (no cost map for that frame).  Results equal msbm_disparity_host frame by frame.
- * Returns the first CUDA error, or the device error word of either pipeline as msbm_sync
- * does. */
+ * pitch_bytes; maps dense) is uploaded on an upload stream into one of P device staging sets
+ * (P = min(n_frames, 6)), matched, and its maps downloaded on a download stream, so that the
+ * uploads of the next frames and the downloads of the previous ones overlap the pass of
+ * frame i (they need page-locked buffers to overlap).  Frame i is matched on pass pipeline
+ * i mod P: pipeline 0 is the context's stream, the others are contexts of the same
+ * parameters with their own level buffers and streams, created on the first call that needs
+ * them and freed with the context.  So consecutive frames' passes (chains of small,
+ * latency-bound grids) run side by side.  The other pipelines' evaluations are not added to
+ * msbm_eval_count.  h_costs may be NULL or hold NULLs (no cost map for that frame).  Results
+ * equal msbm_disparity_host frame by frame.  Returns the first CUDA error, or the device
+ * error word of any pipeline as msbm_sync does. */
 msbm_status msbm_disparity_host_frames(msbm_ctx *ctx, int32_t n_frames, const uint8_t *const *h_lefts,
                                        const uint8_t *const *h_rights, size_t pitch_bytes,
                                        int16_t *const *h_ds, float *const *h_costs);

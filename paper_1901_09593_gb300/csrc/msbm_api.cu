@@ -39,6 +39,13 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
+// Pass pipelines (and staging sets) of msbm_disparity_host_frames.  The hierarchical pass is
+// a chain of small, latency-bound launches, so passes of consecutive frames on several
+// pipelines overlap: 1400 x 1000 pair, 128 frames from page-locked buffers, disparity maps
+// back: 20 900 frames/s with two pipelines, 24 990 with three, 27 970 with four, 29 120 with
+// six, 28 720 with eight (with the cost maps too, about 17 200 for all: the host link).
+constexpr int HOST_PIPES = 6;
+
 struct msbm_ctx {
     msbm_params p{};
     int nh = 0;
@@ -76,16 +83,18 @@ struct msbm_ctx {
     float *c0 = nullptr;
     // pipelined host path (msbm_disparity_host_frames): two device staging sets, an upload
     // and a download stream, and per set the events that order its reuse
-    uint8_t *sL[2] = {nullptr, nullptr}, *sR[2] = {nullptr, nullptr};
-    int16_t *sd[2] = {nullptr, nullptr};
-    float *sc[2] = {nullptr, nullptr};
+    uint8_t *sL[HOST_PIPES] = {}, *sR[HOST_PIPES] = {};
+    int16_t *sd[HOST_PIPES] = {};
+    float *sc[HOST_PIPES] = {};
     cudaStream_t up_stream = nullptr, down_stream = nullptr;
     // second pass pipeline of the host frames path: a context of the same parameters (its own
     // level buffers) on its own stream, taking every other frame, so that one frame's coarse,
     // latency-bound levels run beside the previous frame's finest level
-    msbm_ctx *twin = nullptr;
-    cudaStream_t twin_stream = nullptr;
-    cudaEvent_t ev_up[2] = {}, ev_pass[2] = {}, ev_down[2] = {};
+    // further pass pipelines of msbm_disparity_host_frames (contexts with the same
+    // parameters on their own streams); pipeline 0 is this context
+    msbm_ctx *twin[HOST_PIPES] = {};
+    cudaStream_t twin_stream[HOST_PIPES] = {};
+    cudaEvent_t ev_up[HOST_PIPES] = {}, ev_pass[HOST_PIPES] = {}, ev_down[HOST_PIPES] = {};
 };
 
 namespace {
@@ -167,11 +176,13 @@ int choose_sx(int W, int H, int sms) {
 
 void free_ctx(msbm_ctx *c) {
     if (!c) return;
-    if (c->twin) {
-        cudaStreamSynchronize(c->twin_stream);
-        free_ctx(c->twin);
+    for (int q = 1; q < HOST_PIPES; ++q) {
+        if (c->twin[q]) {
+            cudaStreamSynchronize(c->twin_stream[q]);
+            free_ctx(c->twin[q]);
+        }
+        if (c->twin_stream[q]) cudaStreamDestroy(c->twin_stream[q]);
     }
-    if (c->twin_stream) cudaStreamDestroy(c->twin_stream);
     for (auto &g : c->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
     for (auto &l : c->lv) {
@@ -186,7 +197,7 @@ void free_ctx(msbm_ctx *c) {
     cudaFree(c->d_err);
     cudaFreeHost(c->h_err);
     cudaFree(c->d_evals);
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < HOST_PIPES; ++b) {
         cudaFree(c->sL[b]);
         cudaFree(c->sR[b]);
         cudaFree(c->sd[b]);
@@ -608,7 +619,7 @@ msbm_status msbm_disparity_host_frames(msbm_ctx *ctx, int32_t n_frames, const ui
     cudaError_t e = cudaSuccess;
     if (!ctx->up_stream) {
         // staging images are dense (pitch W); images at another pitch are copied row by row
-        for (int b = 0; e == cudaSuccess && b < 2; ++b) {
+        for (int b = 0; e == cudaSuccess && b < HOST_PIPES; ++b) {
             e = cudaMalloc(&ctx->sL[b], W * H);
             if (e == cudaSuccess) e = cudaMalloc(&ctx->sR[b], W * H);
             if (e == cudaSuccess) e = cudaMalloc(&ctx->sd[b], W * H * sizeof(int16_t));
@@ -628,7 +639,9 @@ msbm_status msbm_disparity_host_frames(msbm_ctx *ctx, int32_t n_frames, const ui
         ctx->up_stream = up;
         ctx->down_stream = down;
     }
-    if (n_frames >= 2 && !ctx->twin) {
+    const int np = std::min(n_frames, HOST_PIPES);     // pass pipelines this call uses
+    for (int q = 1; q < np; ++q) {
+        if (ctx->twin[q]) continue;
         cudaStream_t ts = nullptr;
         e = cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking);
         if (e != cudaSuccess) return cuda_status(e);
@@ -638,23 +651,23 @@ msbm_status msbm_disparity_host_frames(msbm_ctx *ctx, int32_t n_frames, const ui
             cudaStreamDestroy(ts);
             return s;
         }
-        ctx->twin = tw;
-        ctx->twin_stream = ts;
+        ctx->twin[q] = tw;
+        ctx->twin_stream[q] = ts;
     }
     cudaStream_t up = ctx->up_stream, down = ctx->down_stream;
-    // Frame i uses staging set b = i % 2: its upload waits for the pass of frame i-2 (which
-    // read set b's images), its pass for its upload and for the download of frame i-2
-    // (which read set b's maps), its download for its pass.  So frame i+1's upload and
-    // frame i-1's download run beside frame i's pass.
-    // Frames alternate between the two pass pipelines as they do between the staging sets:
-    // frame i runs on pipeline b (the context itself for b = 0, its twin for b = 1).
+    // Frame i uses staging set b = i % np: its upload waits for the pass of frame i-np
+    // (which read set b's images), its pass for its upload and for the download of frame
+    // i-np (which read set b's maps), its download for its pass.  So the next frames'
+    // uploads and the previous frames' downloads run beside frame i's pass.  Frames rotate
+    // over the pass pipelines as they do over the staging sets: frame i runs on pipeline b
+    // (the context itself for b = 0, its twin b otherwise), so consecutive passes overlap.
     for (int i = 0; i < n_frames && e == cudaSuccess; ++i) {
         NvtxRange range("msbm host frame", i);
-        const int b = i & 1;
-        msbm_ctx *pc = (b == 1 && ctx->twin) ? ctx->twin : ctx;
+        const int b = i % np;
+        msbm_ctx *pc = b > 0 ? ctx->twin[b] : ctx;
         cudaStream_t st = pc->stream;
         const bool want_cost = h_costs && h_costs[i];
-        if (i >= 2) e = cudaStreamWaitEvent(up, ctx->ev_pass[b], 0);
+        if (i >= np) e = cudaStreamWaitEvent(up, ctx->ev_pass[b], 0);
         if (e == cudaSuccess) {
             if (pitch_bytes == W) {
                 e = cudaMemcpyAsync(ctx->sL[b], h_lefts[i], W * H, cudaMemcpyHostToDevice, up);
@@ -667,7 +680,7 @@ msbm_status msbm_disparity_host_frames(msbm_ctx *ctx, int32_t n_frames, const ui
         }
         if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_up[b], up);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->ev_up[b], 0);
-        if (e == cudaSuccess && i >= 2) e = cudaStreamWaitEvent(st, ctx->ev_down[b], 0);
+        if (e == cudaSuccess && i >= np) e = cudaStreamWaitEvent(st, ctx->ev_down[b], 0);
         if (e != cudaSuccess) break;
         msbm_status s = msbm_disparity(pc, ctx->sL[b], ctx->sR[b], W, ctx->sd[b], want_cost ? ctx->sc[b] : nullptr);
         if (s != MSBM_OK) {
@@ -687,7 +700,12 @@ msbm_status msbm_disparity_host_frames(msbm_ctx *ctx, int32_t n_frames, const ui
     cudaError_t e3 = cudaStreamSynchronize(down);
     if (e == cudaSuccess) e = e2 != cudaSuccess ? e2 : e3;
     if (e != cudaSuccess) return cuda_status(e);
-    msbm_status s = ctx->twin ? msbm_sync(ctx->twin) : MSBM_OK;
+    msbm_status s = MSBM_OK;
+    for (int q = 1; q < HOST_PIPES; ++q) {
+        if (!ctx->twin[q]) continue;
+        const msbm_status sq = msbm_sync(ctx->twin[q]);
+        if (s == MSBM_OK) s = sq;
+    }
     msbm_status s0 = msbm_sync(ctx);
     return s0 != MSBM_OK ? s0 : s;
 }

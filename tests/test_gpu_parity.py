@@ -313,11 +313,13 @@ def test_full_size_flat_every_pixel():
 
 
 @pytest.mark.parametrize("name,n,pinned", [("small_320x240", 5, True), ("small_320x240", 3, False),
-                                           ("bench_1400x1000", 4, True)])
+                                           ("small_320x240", 15, True), ("bench_1400x1000", 4, True),
+                                           ("bench_1400x1000", 13, True)])
 def test_pipelined_host_frames_equal_the_device_path(name, n, pinned):
-    # frames of different scenes through msbm_disparity_host_frames (two staging sets
-    # alternate, uploads and downloads overlap the passes) equal the device-buffer pass
-    # frame by frame; every other frame asks for no cost map
+    # frames of different scenes through msbm_disparity_host_frames (staging sets and pass
+    # pipelines rotate, uploads and downloads overlap the passes; 13 and 15 frames wrap
+    # around all of them more than twice) equal the device-buffer pass frame by frame; every
+    # other frame asks for no cost map
     import torch
     spec = scenes.SPECS[name]
     scs = [scenes.make_pair(spec, 20 + i) for i in range(n)]
