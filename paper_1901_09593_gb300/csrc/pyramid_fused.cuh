@@ -30,6 +30,9 @@ namespace msbm {
 // 16 x 4 tiles of the coarsest fused level: twice the CTAs of 16 x 8 tiles for 7 % more
 // halo work, which shortens the launch (measured on the 1400 x 1000 and 2880 x 1984 pairs)
 constexpr int PF_TX = 16, PF_TY = 4;
+// every written level's own part leaves in 16-byte chunks starting at multiples of 16
+// columns: the coarsest tile width must be a multiple of 16
+static_assert(PF_TX % 16 == 0, "fused pyramid tile width");
 
 template <int F>
 struct PyrGeom {
