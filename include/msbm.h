@@ -273,7 +273,8 @@ msbm_status msbm_zncc_softargmax_fwd(const float *d_left, const float *d_right, 
                                      float *l_out, void *cuda_stream);
 
 /* Bytes of device workspace msbm_zncc_softargmax_bwd needs (0 for invalid sizes): the
- * per-(pixel, z) coefficient volume and six per-pixel arrays. */
+ * per-(pixel, z) coefficient volume, six per-pixel arrays and four floats per position of
+ * the window-extended image ((height + 2n) x (width + 2n), n = window / 2). */
 size_t msbm_zncc_softargmax_workspace_bytes(int32_t batch, int32_t height, int32_t width,
                                             int32_t window, int32_t ndisp);
 

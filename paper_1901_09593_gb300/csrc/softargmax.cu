@@ -62,6 +62,8 @@ struct SaArgs {
     // only), left statistics {ma, rsa} and right statistics {mb, rsb} per pixel [B][H][W]
     float *rho;
     float2 *lst, *rst;
+    // the gradients' box terms per clamp-extended position [B][H+2n][W+2n] (sa_box_kernel)
+    float4 *box;
 };
 
 template <int NH>
@@ -372,6 +374,68 @@ __global__ void __launch_bounds__(256) sa_bwd_coef_saved_kernel(const SaArgs a) 
     }
 }
 
+constexpr int SG_BOX = 32;                        // box-term tile side
+
+// The gradients' box terms (the last three of gL and gR in the file header) per position of
+// the clamp-extended domain (Y in [0, H+2n), X in [0, W+2n); image position q = (Y-n, X-n)),
+// summed over the image pixels of q's window:
+//   x = sum(beta ma) - sum(zeta),  y = sum(beta),  z = sum(delta mb) - sum(er),  w = sum(delta)
+// so that gL(q) gets x - L(q) y and gR(q) gets z - R(q) w.  Per 32 x 32 tile of positions the
+// four summands' (32 + 2n)^2 image region (zero outside the image) is staged in shared
+// memory, then summed horizontally and vertically.
+template <int NH>
+__global__ void __launch_bounds__(256) sa_box_kernel(const SaArgs a) {
+    constexpr int WIN = 2 * NH + 1, TR = SG_BOX + 2 * NH, TCP = TR + 1;
+    __shared__ float sv[4][TR][TCP];
+    __shared__ float hv[4][TR][SG_BOX + 1];
+    const int b = blockIdx.z, X0 = blockIdx.x * SG_BOX, Y0 = blockIdx.y * SG_BOX;
+    const int tid = threadIdx.y * SA_TX + threadIdx.x;
+    const size_t plane = (size_t)a.H * a.W;
+    const float *zeta = a.zeta + b * plane, *beta = a.beta + b * plane, *ma = a.ma + b * plane;
+    const float *er = a.er + b * plane, *delta = a.delta + b * plane, *mb = a.mb + b * plane;
+    for (int i = tid; i < TR * TR; i += SA_TX * 8) {
+        const int t = i / TR, u = i - t * TR;
+        const int yy = Y0 - 2 * NH + t, xx = X0 - 2 * NH + u;
+        float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
+        if (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W) {
+            const size_t o = (size_t)yy * a.W + xx;
+            v1 = beta[o];
+            v0 = fmaf(v1, ma[o], -zeta[o]);
+            v3 = delta[o];
+            v2 = fmaf(v3, mb[o], -er[o]);
+        }
+        sv[0][t][u] = v0;
+        sv[1][t][u] = v1;
+        sv[2][t][u] = v2;
+        sv[3][t][u] = v3;
+    }
+    __syncthreads();
+    for (int i = tid; i < 4 * TR * SG_BOX; i += SA_TX * 8) {
+        const int m = i / (TR * SG_BOX), r = i - m * TR * SG_BOX, t = r / SG_BOX, u = r - t * SG_BOX;
+        float h = 0.f;
+#pragma unroll
+        for (int j = 0; j < WIN; ++j) h += sv[m][t][u + j];
+        hv[m][t][u] = h;
+    }
+    __syncthreads();
+    const int Wp = a.W + 2 * NH, Hp = a.H + 2 * NH;
+    float4 *out = a.box + (size_t)b * Hp * Wp;
+    for (int i = tid; i < SG_BOX * SG_BOX; i += SA_TX * 8) {
+        const int t = i / SG_BOX, u = i - t * SG_BOX;
+        const int Y = Y0 + t, X = X0 + u;
+        if (Y >= Hp || X >= Wp) continue;
+        float r[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            float v = 0.f;
+#pragma unroll
+            for (int k = 0; k < WIN; ++k) v += hv[m][t + k][u];
+            r[m] = v;
+        }
+        out[(size_t)Y * Wp + X] = make_float4(r[0], r[1], r[2], r[3]);
+    }
+}
+
 // Both image gradients over the clamp-extended domain (Y in [0, H+2n), X in [0, W+2n); image
 // position q = (Y-n, X-n), folded into the clamped edge pixel by atomicAdd).  Per 32 x 32
 // tile (each thread a column of 4 positions) and candidate z the CTA box-filters alpha(b, z)
@@ -513,32 +577,15 @@ __global__ void __launch_bounds__(256) sa_grad_kernel(const SaArgs a, float *gL,
         if (tx > 0) accR[(r0 + k) * AW + tx - 1] += racc[k];
     __syncwarp();
     __syncthreads();
-    const float *zeta = a.zeta + b * plane, *beta = a.beta + b * plane, *ma = a.ma + b * plane;
-    const float *er = a.er + b * plane, *delta = a.delta + b * plane, *mb = a.mb + b * plane;
+    const float4 *box = a.box + (size_t)b * Hp * Wp;
 #pragma unroll
     for (int k = 0; k < SG_PER; ++k) {
         const int Y = Y0 + r0 + k, qy = Y - NH;
         if (!colin || Y >= Hp) continue;
-        // box terms over the image pixels whose window covers q
-        float l1 = 0.f, l2 = 0.f, l3 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f;
-        for (int i = -NH; i <= NH; ++i) {
-            const int yy = qy + i;
-            if (yy < 0 || yy >= a.H) continue;
-            for (int j = -NH; j <= NH; ++j) {
-                const int xx = qx + j;
-                if (xx < 0 || xx >= a.W) continue;
-                const size_t o = (size_t)yy * a.W + xx;
-                l1 += zeta[o];
-                l2 += beta[o];
-                l3 = fmaf(beta[o], ma[o], l3);
-                q1 += er[o];
-                q2 += delta[o];
-                q3 = fmaf(delta[o], mb[o], q3);
-            }
-        }
+        const float4 t = box[(size_t)Y * Wp + X];           // the box terms (sa_box_kernel)
         const size_t o = (size_t)clampi(qy, 0, a.H - 1) * a.W + clampi(qx, 0, a.W - 1);
-        atomicAdd(gL + b * plane + o, gl[k] + l3 - l1 - Lq[k] * l2);
-        accR[(r0 + k) * AW + tx + a.ndisp - 1] += q3 - q1 - Rb[o] * q2;
+        atomicAdd(gL + b * plane + o, gl[k] + t.x - Lq[k] * t.y);
+        accR[(r0 + k) * AW + tx + a.ndisp - 1] += t.z - Rb[o] * t.w;
     }
     __syncthreads();
     float *gRb = gR + b * plane;
@@ -580,6 +627,9 @@ cudaError_t sa_run(const SaArgs &a, bool bwd, float *gL, float *gR, cudaStream_t
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int Wp = a.W + 2 * NH, Hp = a.H + 2 * NH;
+    dim3 gbox((Wp + SG_BOX - 1) / SG_BOX, (Hp + SG_BOX - 1) / SG_BOX, a.B);
+    sa_box_kernel<NH><<<gbox, blk, 0, st>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     dim3 gext((Wp + SA_TX - 1) / SA_TX, (Hp + SG_TY - 1) / SG_TY, a.B);
     const size_t gsm = SgCfg<NH>::bytes(a.ndisp);
     e = cudaFuncSetAttribute(sa_grad_kernel<NH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
@@ -613,7 +663,7 @@ msbm_status sa_validate(const float *L, const float *R, int B, int H, int W, int
 }
 
 struct SaWorkspace {
-    size_t alpha, arrays, total;
+    size_t alpha, arrays, box, total;
 };
 
 // Saved-forward memory: rho [B][Z][H][W], then {ma, rsa} and {mb, rsb} per pixel, each
@@ -639,12 +689,13 @@ void sa_bind_saved(SaArgs &a, void *saved, const SaSaved &v) {
 }
 
 SaWorkspace sa_workspace(int B, int H, int W, int window, int ndisp) {
-    (void)window;
     SaWorkspace w;
     auto al = [](size_t v) { return (v + 255) / 256 * 256; };
+    const int nh = window / 2;
     w.alpha = al((size_t)B * ndisp * H * W * sizeof(float));
     w.arrays = al((size_t)B * H * W * sizeof(float));
-    w.total = w.alpha + 6 * w.arrays;
+    w.box = al((size_t)B * (H + 2 * nh) * (W + 2 * nh) * sizeof(float4));
+    w.total = w.alpha + 6 * w.arrays + w.box;
     return w;
 }
 
@@ -701,6 +752,7 @@ msbm_status msbm_zncc_softargmax_bwd(const float *d_left, const float *d_right, 
     const size_t na = w.arrays / sizeof(float);
     a.zeta = arr; a.beta = arr + na; a.ma = arr + 2 * na; a.mb = arr + 3 * na; a.delta = arr + 4 * na;
     a.er = arr + 5 * na;
+    a.box = reinterpret_cast<float4 *>(ws + w.alpha + 6 * w.arrays);
     const size_t plane_bytes = (size_t)batch * height * width * sizeof(float);
     cudaError_t e = cudaMemsetAsync(a.delta, 0, 2 * w.arrays, st);   // delta and er accumulate
     if (e == cudaSuccess) e = cudaMemsetAsync(g_left, 0, plane_bytes, st);
@@ -764,6 +816,7 @@ msbm_status msbm_zncc_softargmax_bwd_saved(const float *d_left, const float *d_r
     const size_t na = w.arrays / sizeof(float);
     a.zeta = arr; a.beta = arr + na; a.ma = arr + 2 * na; a.mb = arr + 3 * na; a.delta = arr + 4 * na;
     a.er = arr + 5 * na;
+    a.box = reinterpret_cast<float4 *>(ws + w.alpha + 6 * w.arrays);
     const size_t plane_bytes = (size_t)batch * height * width * sizeof(float);
     cudaError_t e = cudaMemsetAsync(a.delta, 0, 2 * w.arrays, st);   // delta and er accumulate
     if (e == cudaSuccess) e = cudaMemsetAsync(g_left, 0, plane_bytes, st);

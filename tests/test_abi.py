@@ -135,11 +135,13 @@ def test_batch_create_rejects_bad_counts_and_tuning(lib):
 
 
 def test_softargmax_workspace_bytes_formula_and_invalid_sizes(lib):
-    # the backward's workspace: one float per (image, pixel, candidate) and six floats per
-    # pixel, each part rounded up to 256 bytes
+    # the backward's workspace: one float per (image, pixel, candidate), six floats per
+    # pixel and four per position of the window-extended image, each part rounded up to 256
+    # bytes
     al = lambda v: (v + 255) // 256 * 256
     for b, h, w, win, nd in [(1, 5, 9, 3, 4), (8, 480, 640, 5, 64), (2, 7, 13, 9, 256)]:
-        want = al(b * nd * h * w * 4) + 6 * al(b * h * w * 4)
+        n = win // 2
+        want = al(b * nd * h * w * 4) + 6 * al(b * h * w * 4) + al(b * (h + 2 * n) * (w + 2 * n) * 16)
         assert lib.msbm_zncc_softargmax_workspace_bytes(b, h, w, win, nd) == want
     for args in [(0, 5, 9, 3, 4), (65536, 5, 9, 3, 4), (1, 0, 9, 3, 4), (1, 5, 16385, 3, 4),
                  (1, 5, 9, 1, 4), (1, 5, 9, 4, 4), (1, 5, 9, 11, 4), (1, 5, 9, 3, 0), (1, 5, 9, 3, 257)]:
@@ -256,5 +258,6 @@ def test_header_serves_a_plain_c_program(lib, tmp_path):
                            "-Wl,-rpath," + os.path.dirname(build.SO)])
     r = subprocess.run([str(exe)], capture_output=True, text=True)
     assert r.returncode == 0, r.stdout + r.stderr
-    want = (8 * 16 * 4 * 4 + 255) // 256 * 256 + 6 * ((8 * 16 * 4 + 255) // 256 * 256)
+    al = lambda v: (v + 255) // 256 * 256
+    want = al(8 * 16 * 4 * 4) + 6 * al(8 * 16 * 4) + al((8 + 2) * (16 + 2) * 16)
     assert r.stdout.split() == ["1", "invalid", "argument", "1", str(want)], r.stdout
