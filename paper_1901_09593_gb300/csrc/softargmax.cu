@@ -494,39 +494,32 @@ __global__ void __launch_bounds__(256) sa_grad_kernel(const SaArgs a, float *gL,
         gl[k] = 0.f;
     }
     const bool colin = X < Wp;
-    // this thread's tile elements (t, u) = (ty + 8i, tx + 32j) <-> image (Y0 - 2n + t, X0 - 2n + u);
-    // the next candidate's are loaded into registers while the current one is processed
-    constexpr int NI = (TR + 7) / 8, NJ = (TC + SA_TX - 1) / SA_TX;
-    int off[NI][NJ];                                  // element offset in an alpha plane, or -1
+    // the tile's elements e = tid + 256 k, (t, u) = (e / TC, e % TC) <-> image
+    // (Y0 - 2n + t, X0 - 2n + u); the next candidate's are loaded into registers while the
+    // current one is processed
+    constexpr int NE = (TR * TC + SA_TX * 8 - 1) / (SA_TX * 8);
+    int off[NE];                                      // element offset in an alpha plane, or -1
+    int soff[NE];                                     // its place in the shared tile, or -1
 #pragma unroll
-    for (int i = 0; i < NI; ++i)
-#pragma unroll
-        for (int j = 0; j < NJ; ++j) {
-            const int t = ty + 8 * i, u = tx + SA_TX * j;
-            const int yy = Y0 - 2 * NH + t, xx = X0 - 2 * NH + u;
-            off[i][j] = (t < TR && u < TC && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W) ? yy * a.W + xx : -1;
-        }
-    float nxt[NI][NJ];
+    for (int k = 0; k < NE; ++k) {
+        const int e = tid + SA_TX * 8 * k, t = e / TC, u = e - t * TC;
+        const int yy = Y0 - 2 * NH + t, xx = X0 - 2 * NH + u;
+        soff[k] = e < TR * TC ? t * TCP + u : -1;
+        off[k] = (e < TR * TC && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W) ? yy * a.W + xx : -1;
+    }
+    float nxt[NE];
     const float *al0 = a.alpha + (size_t)b * a.ndisp * plane;
 #pragma unroll
-    for (int i = 0; i < NI; ++i)
-#pragma unroll
-        for (int j = 0; j < NJ; ++j) nxt[i][j] = off[i][j] >= 0 ? __ldg(al0 + off[i][j]) : 0.f;
+    for (int k = 0; k < NE; ++k) nxt[k] = off[k] >= 0 ? __ldg(al0 + off[k]) : 0.f;
     for (int z = 0; z < a.ndisp; ++z) {
         __syncthreads();   // the previous candidate's tile and sums are consumed
 #pragma unroll
-        for (int i = 0; i < NI; ++i)
-#pragma unroll
-            for (int j = 0; j < NJ; ++j) {
-                const int t = ty + 8 * i, u = tx + SA_TX * j;
-                if (t < TR && u < TC) tile[t * TCP + u] = nxt[i][j];
-            }
+        for (int k = 0; k < NE; ++k)
+            if (soff[k] >= 0) tile[soff[k]] = nxt[k];
         if (z + 1 < a.ndisp) {
             const float *al = al0 + (size_t)(z + 1) * plane;
 #pragma unroll
-            for (int i = 0; i < NI; ++i)
-#pragma unroll
-                for (int j = 0; j < NJ; ++j) nxt[i][j] = off[i][j] >= 0 ? __ldg(al + off[i][j]) : 0.f;
+            for (int k = 0; k < NE; ++k) nxt[k] = off[k] >= 0 ? __ldg(al + off[k]) : 0.f;
         }
         __syncthreads();
         // horizontal window sums: each of TR x 4 items slides over 8 columns of one row
