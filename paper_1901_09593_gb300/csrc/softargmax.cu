@@ -77,11 +77,15 @@ struct SaCfg {
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
 // Stage the left tile, the right span and the right-window statistics of one CTA.
-// Layout: Lt[ROWS][LTP], Rt[ROWS][RTP], st[TY][RSW] (float2 {mean, rsqrt(Sbb + eps)}).
-template <int NH>
+// Layout: Lt[ROWS][LTP], Rt[ROWS][RTP], st[TY][RSW] (float2 {mean, rsqrt(Sbb + eps)}).  RTP
+// and RSW are the widths of the right span and of its statistics; RS, when not 0, is a
+// compile-time row stride of Rt (>= RTP; st's is RS - 2n) so that the scan's loads of a
+// column take constant offsets.
+template <int NH, int RS = 0>
 __device__ void sa_stage(const SaArgs &a, const float *L, const float *R, int x0, int y0, float *Lt, float *Rt,
                          float2 *st, int RTP, int RSW) {
     using C = SaCfg<NH>;
+    const int RTPS = RS ? RS : RTP, RSWS = RS ? RS - 2 * NH : RSW;   // row strides
     const int tid = threadIdx.y * SA_TX + threadIdx.x, nthr = SA_TX * SA_TY;
     const int W = a.W, H = a.H;
     for (int i = tid; i < C::ROWS * C::LTP; i += nthr) {
@@ -93,7 +97,7 @@ __device__ void sa_stage(const SaArgs &a, const float *L, const float *R, int x0
     for (int i = tid; i < C::ROWS * RTP; i += nthr) {
         int t = i / RTP, u = i - t * RTP;
         int yy = clampi(y0 - NH + t, 0, H - 1), xx = clampi(rx0 + u, 0, W - 1);
-        Rt[i] = R[(size_t)yy * W + xx];
+        Rt[t * RTPS + u] = R[(size_t)yy * W + xx];
     }
     __syncthreads();
     // right centre v <-> image column x0 - (ndisp-1) + v; its window is Rt cols v .. v+2n
@@ -103,26 +107,27 @@ __device__ void sa_stage(const SaArgs &a, const float *L, const float *R, int x0
 #pragma unroll
         for (int t = 0; t < C::WIN; ++t)
 #pragma unroll
-            for (int j = 0; j < C::WIN; ++j) s += Rt[(ry + t) * RTP + v + j];
+            for (int j = 0; j < C::WIN; ++j) s += Rt[(ry + t) * RTPS + v + j];
         const float mean = s * (1.0f / C::N);
         float q = 0.f;
 #pragma unroll
         for (int t = 0; t < C::WIN; ++t)
 #pragma unroll
             for (int j = 0; j < C::WIN; ++j) {
-                float d = Rt[(ry + t) * RTP + v + j] - mean;
+                float d = Rt[(ry + t) * RTPS + v + j] - mean;
                 q = fmaf(d, d, q);
             }
-        st[i] = make_float2(mean, rsqrtf(q + a.eps));
+        st[ry * RSWS + v] = make_float2(mean, rsqrtf(q + a.eps));
     }
     __syncthreads();
 }
 
 // Per-pixel ZNCC over all admissible candidates, calling visit(z, rho, v2, mb, rsb) for each.
-template <int NH, typename F>
+template <int NH, int RS = 0, typename F>
 __device__ __forceinline__ void sa_scan(const SaArgs &a, const float *Lt, const float *Rt, const float2 *st,
-                                        int RTP, int RSW, int tx, int ty, int x, float &ma_out, float &rsa_out,
+                                        int RTPw, int RSWw, int tx, int ty, int x, float &ma_out, float &rsa_out,
                                         F &&visit) {
+    const int RTP = RS ? RS : RTPw, RSW = RS ? RS - 2 * NH : RSWw;   // row strides (see sa_stage)
     using C = SaCfg<NH>;
     constexpr int WIN = C::WIN;
     float ac[WIN][WIN];
@@ -180,22 +185,25 @@ __device__ __forceinline__ void sa_scan(const SaArgs &a, const float *Lt, const 
     }
 }
 
-template <int NH>
+// ZP: ndisp rounded up to 64, 128 or 256; the staged rows take the compile-time stride of ZP
+// candidates
+template <int NH, int ZP>
 __global__ void __launch_bounds__(256) sa_fwd_kernel(const SaArgs a) {
     using C = SaCfg<NH>;
+    constexpr int RS = SA_TX + ZP - 1 + 2 * NH, RSWS = RS - 2 * NH;
     extern __shared__ float sm[];
-    const int RTP = SA_TX + a.ndisp - 1 + 2 * NH, RSW = SA_TX + a.ndisp - 1;
+    const int RTP = SA_TX + a.ndisp - 1 + 2 * NH, RSW = SA_TX + a.ndisp - 1;   // widths
     float *Lt = sm;
     float *Rt = Lt + C::ROWS * C::LTP;
-    float2 *st = reinterpret_cast<float2 *>(Rt + ((C::ROWS * RTP + 1) & ~1));
+    float2 *st = reinterpret_cast<float2 *>(Rt + ((C::ROWS * RS + 1) & ~1));
     const int b = blockIdx.z, x0 = blockIdx.x * SA_TX, y0 = blockIdx.y * SA_TY;
     const size_t plane = (size_t)a.H * a.W;
-    sa_stage<NH>(a, a.L + b * plane, a.R + b * plane, x0, y0, Lt, Rt, st, RTP, RSW);
+    sa_stage<NH, RS>(a, a.L + b * plane, a.R + b * plane, x0, y0, Lt, Rt, st, RTP, RSW);
     const int tx = threadIdx.x, ty = threadIdx.y, x = x0 + tx, y = y0 + ty;
     if (x >= a.W || y >= a.H) return;
     float m2 = -INFINITY, l = 0.f, s = 0.f, ma, rsa;
     float *rho_p = a.rho ? a.rho + (size_t)b * a.ndisp * plane + (size_t)y * a.W + x : nullptr;
-    sa_scan<NH>(a, Lt, Rt, st, RTP, RSW, tx, ty, x, ma, rsa, [&](int z, float rho, float v2, float, float) {
+    sa_scan<NH, RS>(a, Lt, Rt, st, RTP, RSW, tx, ty, x, ma, rsa, [&](int z, float rho, float v2, float, float) {
         if (rho_p) rho_p[(size_t)z * plane] = rho;
         if (v2 > m2) {
             const float sc = exp2f(m2 - v2);
@@ -214,7 +222,7 @@ __global__ void __launch_bounds__(256) sa_fwd_kernel(const SaArgs a) {
     a.l[p] = l;
     if (a.lst) {
         a.lst[p] = make_float2(ma, rsa);
-        a.rst[p] = st[ty * RSW + tx + a.ndisp - 1];   // right centre x
+        a.rst[p] = st[ty * RSWS + tx + a.ndisp - 1];   // right centre x
     }
 }
 
@@ -605,9 +613,12 @@ cudaError_t sa_run(const SaArgs &a, bool bwd, float *gL, float *gR, cudaStream_t
     size_t smem = sa_fwd_smem(NH, a.ndisp, bwd);
     cudaError_t e;
     if (!bwd) {
-        e = cudaFuncSetAttribute(sa_fwd_kernel<NH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const int zp = a.ndisp <= 64 ? 64 : (a.ndisp <= 128 ? 128 : 256);
+        const size_t fsm = sa_fwd_smem(NH, zp, false);
+        auto kern = zp == 64 ? sa_fwd_kernel<NH, 64> : (zp == 128 ? sa_fwd_kernel<NH, 128> : sa_fwd_kernel<NH, 256>);
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
         if (e != cudaSuccess) return e;
-        sa_fwd_kernel<NH><<<grd, blk, smem, st>>>(a);
+        kern<<<grd, blk, fsm, st>>>(a);
         return cudaGetLastError();
     }
     if (a.rho) {
