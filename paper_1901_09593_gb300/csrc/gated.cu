@@ -2,8 +2,8 @@
 // Eq. 8-9, Sec. III-D), each a small kernel around the matching kernels:
 //  * beta gate (Sec. III-C): the cost prior C_hat^k = BI(C^{k+1}) -- bicubic (Catmull-Rom)
 //    upsampling with fine pixel (y, x) at coarse coordinates (y/2, x/2), clamp-to-edge --
-//    and the fallback mask C_hat <= beta (the fallback pixels' full-range search is
-//    zncc_sparse.cu);
+//    and the fallback mask C_hat <= beta, with the list of 2 x 2 cells that hold a fallback
+//    pixel (the fallback pixels' full-range search, zncc_sparse.cu, walks that list);
 //  * alpha refinement (Eq. 5-7) at the coarsest level: for a pixel with C' <= alpha, the
 //    average of the ZNCC over its 3 x 3 neighbourhood (neighbours inside the image) for
 //    every admissible candidate z <= min(D_k - 1, x), and its argmax / max;
@@ -30,24 +30,46 @@ __device__ __forceinline__ void cr_weights(int i, float w[4], int &base) {
     }
 }
 
+// The gate for the 2 x 2 cell (cx, cy) of one thread, 32 cells of a row per warp.  With
+// cells, the cells holding a masked pixel are also appended to the list cells[2 ..] (one
+// atomic per warp, lane order within it), cells[0] counting them; the caller zeroes
+// cells[0 .. 1] before the launch.
 __global__ void beta_gate_kernel(const float *__restrict__ Cc, int Wc, int Hc, int W, int H, float beta,
-                                 uint8_t *mask) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= W || y >= H) return;
-    float wy[4], wx[4];
-    int by, bx;
-    cr_weights(y, wy, by);
-    cr_weights(x, wx, bx);
-    float s = 0.f;
+                                 uint8_t *mask, unsigned *cells) {
+    const int cx = blockIdx.x * 32 + threadIdx.x, cy = blockIdx.y * blockDim.y + threadIdx.y;
+    bool any = false;
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        const int yy = min(max(by - 1 + a, 0), Hc - 1);
-        float r = 0.f;
+    for (int r2 = 0; r2 < 2; ++r2)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) r = fmaf(wx[b], __ldg(Cc + (size_t)yy * Wc + min(max(bx - 1 + b, 0), Wc - 1)), r);
-        s = fmaf(wy[a], r, s);
-    }
-    mask[(size_t)y * W + x] = !(s > beta) ? 1 : 0;
+        for (int c = 0; c < 2; ++c) {
+            const int x = 2 * cx + c, y = 2 * cy + r2;
+            if (x >= W || y >= H) continue;
+            float wy[4], wx[4];
+            int by, bx;
+            cr_weights(y, wy, by);
+            cr_weights(x, wx, bx);
+            float s = 0.f;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const int yy = min(max(by - 1 + a, 0), Hc - 1);
+                float r = 0.f;
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+                    r = fmaf(wx[b], __ldg(Cc + (size_t)yy * Wc + min(max(bx - 1 + b, 0), Wc - 1)), r);
+                s = fmaf(wy[a], r, s);
+            }
+            const bool m = !(s > beta);
+            mask[(size_t)y * W + x] = m ? 1 : 0;
+            any |= m;
+        }
+    if (!cells) return;
+    const unsigned b = __ballot_sync(0xFFFFFFFFu, any);
+    if (!b) return;
+    const int lane = threadIdx.x;
+    unsigned base = 0;
+    if (lane == 0) base = atomicAdd(cells, static_cast<unsigned>(__popc(b)));
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    if (any) cells[2 + base + __popc(b & ((1u << lane) - 1u))] = static_cast<unsigned>(cy) * ((W + 1) / 2) + cx;
 }
 
 // Alpha refinement on a 16 x 8 tile.  E(q, z), the ZNCC of every pixel q of the tile's
@@ -299,9 +321,14 @@ selective_median_kernel(const int16_t *__restrict__ d_in, const float *__restric
 }  // namespace
 
 cudaError_t launch_beta_gate(const float *Cc, int Wc, int Hc, int W, int H, float beta, uint8_t *mask,
-                             cudaStream_t st) {
-    dim3 blk(32, 8), grd((W + 31) / 32, (H + 7) / 8);
-    beta_gate_kernel<<<grd, blk, 0, st>>>(Cc, Wc, Hc, W, H, beta, mask);
+                             unsigned *cells, cudaStream_t st) {
+    const int ncx = (W + 1) / 2, ncy = (H + 1) / 2;
+    if (cells) {
+        const cudaError_t e = cudaMemsetAsync(cells, 0, 2 * sizeof(unsigned), st);
+        if (e != cudaSuccess) return e;
+    }
+    dim3 blk(32, 4), grd((ncx + 31) / 32, (ncy + 3) / 4);
+    beta_gate_kernel<<<grd, blk, 0, st>>>(Cc, Wc, Hc, W, H, beta, mask, cells);
     return cudaGetLastError();
 }
 

@@ -191,6 +191,7 @@ void free_ctx(msbm_ctx *c) {
         cudaFree(l.c);
         cudaFree(l.dtmp);
         cudaFree(l.mask);
+        cudaFree(l.cells);
         cudaFree(l.rstat);
     }
     cudaFree(c->c0);
@@ -308,7 +309,7 @@ msbm_status enqueue_level_beta(msbm_ctx *c, int k, const int16_t *prior, const f
                                float *cost, cudaStream_t st, bool stats_ready = false) {
     LevelBuf &l = c->lv[k];
     const LevelBuf &lp = c->lv[k + 1];
-    cudaError_t e = launch_beta_gate(cprior, lp.W, lp.H, l.W, l.H, c->p.beta, l.mask, st);
+    cudaError_t e = launch_beta_gate(cprior, lp.W, lp.H, l.W, l.H, c->p.beta, l.mask, l.cells, st);
     if (e != cudaSuccess) return cuda_status(e);
     msbm_status s = enqueue_level(c, k, prior, d, cost, st, l.mask, stats_ready);
     if (s != MSBM_OK) return s;
@@ -445,6 +446,8 @@ msbm_status msbm_create(const msbm_params *params, void *cuda_stream, msbm_ctx *
             e = cudaMalloc(&l.dtmp, (size_t)W * H * sizeof(int16_t));
         if (e == cudaSuccess && finer && (params->flags & MSBM_FLAG_BETA_FALLBACK))
             e = cudaMalloc(&l.mask, (size_t)W * H);
+        if (e == cudaSuccess && finer && (params->flags & MSBM_FLAG_BETA_FALLBACK))
+            e = cudaMalloc(&l.cells, (2 + (size_t)((W + 1) / 2) * ((H + 1) / 2)) * sizeof(unsigned));
         l.full_sx = choose_sx(W, H, c->num_sms);
         l.coarse = zncc_coarse_fits(W, H, c->num_sms);
         if (e == cudaSuccess) {

@@ -42,6 +42,7 @@ struct LevelBuf {
     float *c = nullptr;          // this level's cost map (levels >= 1)
     int16_t *dtmp = nullptr;     // pre-median disparity map (SELECTIVE_MEDIAN)
     uint8_t *mask = nullptr;     // fallback mask (BETA_FALLBACK)
+    unsigned *cells = nullptr;   // fallback cells {count, next, cy * ceil(W/2) + cx ...} (BETA_FALLBACK)
     int2 *rstat = nullptr;       // right-window statistics plane {S, bits(rsqrt(V)) or 0}: H rows
     int rspitch = 0;             // of rspitch entries (a multiple of 16), one per pixel
     int rty = 8;                 // rows of the staged restricted tile (MSBM_FLAG_TEST_TIMEOUT)
@@ -125,7 +126,8 @@ struct PyrFuseArgs {
 cudaError_t launch_pyr_fused(const PyrFuseArgs &a, cudaStream_t st);
 cudaError_t launch_level_extract(const LevelBuf &lv, int which, uint8_t *out, cudaStream_t st);
 cudaError_t launch_zncc_full(const FullArgs &a, int nh, int sx, cudaStream_t st, bool pdl = false);
-// Full-range search of the pixels in l.mask only (beta fallback); needs l.rstat computed.
+// Full-range search of the pixels in l.mask only (beta fallback), over the cell list l.cells
+// that the gate built; needs l.rstat computed.
 cudaError_t launch_zncc_sparse(const LevelBuf &l, int nh, int16_t *d, float *c, unsigned long long *evals,
                                cudaStream_t st);
 // Small-level full-range search (one thread per pixel); fits: the full-range tiles of a
@@ -133,8 +135,10 @@ cudaError_t launch_zncc_sparse(const LevelBuf &l, int nh, int16_t *d, float *c, 
 bool zncc_coarse_fits(int W, int H, int sms);
 cudaError_t launch_zncc_coarse(const LevelBuf &l, int nh, int16_t *d, float *c, unsigned long long *evals,
                                cudaStream_t st, bool pdl = false);
+// beta gate of a W x H level from the coarser Wc x Hc cost; cells (NULL: not built): the
+// list of 2 x 2 cells with a masked pixel, laid out as LevelBuf::cells.
 cudaError_t launch_beta_gate(const float *Cc, int Wc, int Hc, int W, int H, float beta, uint8_t *mask,
-                             cudaStream_t st);
+                             unsigned *cells, cudaStream_t st);
 cudaError_t launch_alpha_refine(const LevelBuf &l, int nh, float alpha, int16_t *d, float *C,
                                 unsigned long long *evals, cudaStream_t st);
 cudaError_t launch_selective_median(const int16_t *d_in, const float *C, int W, int H, float alpha, int16_t *d_out,

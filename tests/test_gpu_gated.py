@@ -81,6 +81,35 @@ def test_beta_level_matches_oracle_with_oracle_priors():
         compare_level(host(d)[same], host(c)[same], do[same], co[same], c2o[same], f"beta level {k}")
 
 
+@pytest.mark.parametrize("win", [3, 7, 13])
+def test_beta_level_window_classes_ragged(win):
+    # the fallback's full-range cell search at a small, the benchmark's and the widest
+    # window, on a level with an odd width and height (cells cut by both edges) and a
+    # disparity range of many candidate groups; where the gate is decided alike everywhere,
+    # the evaluation count is the oracle's too
+    from paper_1901_09593_gb300 import _lib
+    spec = scenes.SceneSpec(317, 239, 4, 96, 2, win, 2, 2.0, False)
+    sc = scenes.make_pair(spec, 11)
+    K, D, r = 2, spec.max_disp, spec.radius
+    ref = oracle.disparity(sc.left, sc.right, D, K, win, r)
+    ctx = ctx_for(spec.width, spec.height, D, K, win, r, _lib.MSBM_FLAG_BETA_FALLBACK)
+    ctx.pyramid(dev(sc.left), dev(sc.right))
+    pa, pb = oracle.pyramid(sc.left, K), oracle.pyramid(sc.right, K)
+    prior, cprior = ref["d"][1], ref["C"][1].astype(np.float32)
+    ctx.eval_count(reset=True)
+    d, c, fb = ctx.match_level_beta(0, dev(prior), dev(cprior))
+    ev_g = ctx.eval_count(reset=True)
+    do, co, c2o, ev, fbo, ch = oracle.match_level_beta(pa[0], pb[0], win // 2, oracle.level_disp(D, 0), r, prior,
+                                                       cprior.astype(np.float64), BETA)
+    fbg = host(fb).astype(bool)
+    assert np.all((fbg == fbo) | (np.abs(ch - BETA) < 1e-5))
+    assert fbo.any() and not fbo.all()
+    if np.array_equal(fbg, fbo):
+        assert ev_g == ev, (ev_g, ev)
+    same = fbg == fbo
+    compare_level(host(d)[same], host(c)[same], do[same], co[same], c2o[same], f"beta level 0, window {win}")
+
+
 def test_gated_pass_end_to_end_small():
     from paper_1901_09593_gb300 import _lib
     sc = scenes.make_pair(scenes.SPECS["small_320x240"], 4)
