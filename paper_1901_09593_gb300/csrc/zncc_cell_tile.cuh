@@ -245,37 +245,52 @@ __device__ __forceinline__ unsigned cell_search(const RestrTileArgs &a, int cx, 
     return cnt;
 }
 
+// Best candidate of each pixel of a beta-fallback cell over part of its full range.
+struct CellBest {
+    float best[2][2];   // max over the part of c * rsqrt(Vb) (rsqrt(Va) not applied), -inf if none
+    int bz[2][2];       // its smallest z
+    float rA[2][2];     // rsqrt(Va), 0 for a flat left window
+    bool m[2][2];       // masked pixels of the cell
+    int hi[2];          // last admissible candidate of each column (-1: column outside)
+};
+
+// Candidate groups of cell (cx, cy) in the full-range search: groups of G from z = 0.
+template <int G>
+__device__ __forceinline__ int cell_full_groups(int W, int Dk, int cx) {
+    const int xa = 2 * cx, hi_u = min(Dk - 1, xa + 1 < W ? xa + 1 : xa);
+    return (hi_u + G) / G;
+}
+
 // Full-range WTA (Eq. 8-9, second branch: every admissible z in 0 .. min(D_k - 1, x)) of the
-// masked pixels of cell (cx, cy), for the beta fallback.  The cell's four pixels share each
-// right row's loads and alignment shifts and the products of their common window rows, as in
-// cell_search; their left windows (words and sums) are built once, before the candidate
-// groups.  Only masked pixels are written and counted.  Same arithmetic as cell_search.
+// masked pixels of cell (cx, cy), for the beta fallback, over candidate groups g0 .. g1 - 1
+// (z = G g0 .. G g1 - 1; the caller merges the parts of a cell).  The cell's four pixels
+// share each right row's loads and alignment shifts and the products of their common window
+// rows, as in cell_search; their left windows (words and sums) are built once, before the
+// candidate groups.  Same arithmetic as cell_search.
 template <int NH, int G>
-__device__ __forceinline__ unsigned cell_search_full(const uint8_t *Limg, const uint8_t *Rimg, int pitch, int W,
-                                                     int H, int Dk, const uint8_t *mask, const int2 *rstat,
-                                                     int rspitch, int16_t *d_out, float *c_out, int cx, int cy) {
+__device__ __forceinline__ CellBest cell_full_part(const uint8_t *Limg, const uint8_t *Rimg, int pitch, int W,
+                                                   int H, int Dk, const uint8_t *mask, const int2 *rstat,
+                                                   int rspitch, int cx, int cy, int g0, int g1) {
     constexpr int WIN = 2 * NH + 1, N = WIN * WIN, NW = (WIN + 3) / 4;
     constexpr uint32_t LASTMASK = (WIN % 4 == 0) ? 0xFFFFFFFFu : ((1u << (8 * (WIN % 4))) - 1u);
     constexpr int NO = G + 1, NWA = (NO - 1 + WIN + 3) / 4 + 1, NWL = NWA + 1;
     const int xa = 2 * cx, ya = 2 * cy;
     const bool colv1 = xa + 1 < W, rowv1 = ya + 1 < H;
-    bool m[2][2];
+    CellBest o;
 #pragma unroll
     for (int c = 0; c < 2; ++c)
 #pragma unroll
-        for (int r2 = 0; r2 < 2; ++r2)
-            m[c][r2] = (c == 0 || colv1) && (r2 == 0 || rowv1) && mask[(size_t)(ya + r2) * W + xa + c] != 0;
-    if (!(m[0][0] || m[0][1] || m[1][0] || m[1][1])) return 0u;
-    int hi_c[2];
+        for (int r2 = 0; r2 < 2; ++r2) {
+            o.m[c][r2] = (c == 0 || colv1) && (r2 == 0 || rowv1) && mask[(size_t)(ya + r2) * W + xa + c] != 0;
+            o.best[c][r2] = -INFINITY;
+            o.bz[c][r2] = 0;
+        }
+    int *hi_c = o.hi;
     hi_c[0] = min(Dk - 1, xa);
     hi_c[1] = colv1 ? min(Dk - 1, xa + 1) : -1;
-    const int hi_u = max(hi_c[0], hi_c[1]);
-    unsigned cnt = 0;
-#pragma unroll
-    for (int c = 0; c < 2; ++c)
-#pragma unroll
-        for (int r2 = 0; r2 < 2; ++r2)
-            if (m[c][r2]) cnt += static_cast<unsigned>(hi_c[c] + 1);
+    float (&best)[2][2] = o.best;
+    int (&bz)[2][2] = o.bz;
+    float (&rA)[2][2] = o.rA;
     const int wpr = pitch >> 2;
     int lsh;
     const uint32_t *Lw = cell_words(Limg + (ptrdiff_t)(ya - NH) * pitch + (xa - NH), lsh);
@@ -283,7 +298,6 @@ __device__ __forceinline__ unsigned cell_search_full(const uint8_t *Limg, const 
     // left words of both columns over all 2n + 2 rows, and the four pixels' left statistics
     uint32_t Lc[WIN + 1][2][NW];
     int Sa[2][2];
-    float rA[2][2];
     {
         uint32_t s_t[2] = {0u, 0u}, q_t[2] = {0u, 0u}, s_m[2] = {0u, 0u}, q_m[2] = {0u, 0u}, s_b[2] = {0u, 0u},
                  q_b[2] = {0u, 0u};
@@ -328,16 +342,7 @@ __device__ __forceinline__ unsigned cell_search_full(const uint8_t *Limg, const 
                 rA[c][r2] = v > 0 ? rsqrtf(static_cast<float>(v)) : 0.f;
             }
     }
-    float best[2][2];
-    int bz[2][2];
-#pragma unroll
-    for (int c = 0; c < 2; ++c)
-#pragma unroll
-        for (int r2 = 0; r2 < 2; ++r2) {
-            best[c][r2] = -INFINITY;
-            bz[c][r2] = 0;
-        }
-    for (int zg = 0; zg <= hi_u; zg += G) {
+    for (int zg = G * g0; zg < G * g1; zg += G) {
         int rsh;
         const uint32_t *Rw = cell_words(Rrow + (xa - (zg + G - 1) - NH), rsh);
         // right statistics of the group's G + 1 window columns X = xa + 1 - zg - mm (column c,
@@ -413,18 +418,7 @@ __device__ __forceinline__ unsigned cell_search_full(const uint8_t *Limg, const 
         else
             wta(std::true_type{});
     }
-#pragma unroll
-    for (int c = 0; c < 2; ++c)
-#pragma unroll
-        for (int r2 = 0; r2 < 2; ++r2) {
-            if (!m[c][r2]) continue;
-            float rho = rA[c][r2] > 0.f ? best[c][r2] * rA[c][r2] : 0.f;
-            rho = fminf(1.f, fmaxf(-1.f, rho));
-            const size_t o = (size_t)(ya + r2) * W + xa + c;
-            d_out[o] = static_cast<int16_t>(bz[c][r2]);
-            if (c_out) c_out[o] = rho;
-        }
-    return cnt;
+    return o;
 }
 
 }  // namespace tiles

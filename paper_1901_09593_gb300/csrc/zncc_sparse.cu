@@ -3,12 +3,14 @@
 // of each pixel whose bicubic cost prior failed the gate.
 //
 // The gate (gated.cu) lists the 2 x 2 cells that hold a masked pixel.  A persistent grid
-// (the CTAs the SMs hold at once) walks that list: each warp takes the next 32 entries with
-// one atomic, one thread per cell, and runs the cell's full-range search
-// (tiles::cell_search_full: the four pixels share each right row's loads and the products
-// of their common window rows; candidates in groups of 7, exact integer sums by dp4a, the
-// right-window statistics from the level's plane).  Work is proportional to the masked
-// cells, and the warps stay full whatever the mask's layout.
+// (the CTAs the SMs hold at once) walks that list: each warp takes the next 32 / P entries
+// with one atomic, P lanes per cell each searching a part of its candidate groups
+// (tiles::cell_full_part: the four pixels share each right row's loads and the products of
+// their common window rows; candidates in groups of 7, exact integer sums by dp4a, the
+// right-window statistics from the level's plane), merged by shuffles.  Work is
+// proportional to the masked cells, the warps stay full whatever the mask's layout, and
+// splitting a cell's range over P lanes makes the units of work small enough that the last
+// ones do not leave most of the GPU idle.
 #include <math.h>
 
 #include <algorithm>
@@ -23,33 +25,79 @@ namespace {
 
 constexpr int SPC_THREADS = 128;
 constexpr int SPC_MIN_CTAS = 3;   // 168 registers a thread
+constexpr int SPC_PART_GROUPS = 4;  // fewest candidate groups a lane searches when lanes share a cell
 
-// candidates per group (fewer at the widest window, whose left words take more registers)
+// candidates per group (fewer at the widest windows, whose left words take more registers)
 template <int NH>
 struct SpcG {
-    static constexpr int value = NH <= 5 ? 7 : 4;
+    static constexpr int value = NH <= 4 ? 7 : (NH == 5 ? 4 : 2);
 };
 
+// P (1, 2 or 4) lanes share a cell, lane l searching part l % P of its candidate groups;
+// the parts merge by shuffles (larger score, then smaller z: the sequential scan's winner) and
+// the part-0 lane writes the cell's masked pixels.
 template <int NH>
 __global__ void __launch_bounds__(SPC_THREADS, SPC_MIN_CTAS)
     zncc_sparse_cell_kernel(const uint8_t *L, const uint8_t *R, int pitch, int W, int H, int Dk, const uint8_t *mask,
-                            const int2 *rstat, int rspitch, unsigned *cells, int16_t *d_out, float *c_out,
+                            const int2 *rstat, int rspitch, unsigned *cells, int P, int16_t *d_out, float *c_out,
                             unsigned long long *evals) {
+    constexpr int G = SpcG<NH>::value;
     const unsigned n = cells[0];
-    const int ncx = (W + 1) / 2, lane = threadIdx.x & 31;
+    const int ncx = (W + 1) / 2, lane = threadIdx.x & 31, part = lane & (P - 1);
+    const unsigned per_warp = 32u / static_cast<unsigned>(P);
     unsigned long long cnt = 0;
     for (;;) {
         unsigned base = 0;
-        if (lane == 0) base = atomicAdd(cells + 1, 32u);
+        if (lane == 0) base = atomicAdd(cells + 1, per_warp);
         base = __shfl_sync(0xFFFFFFFFu, base, 0);
         if (base >= n) break;
-        const unsigned i = base + lane;
+        const unsigned i = base + static_cast<unsigned>(lane) / static_cast<unsigned>(P);
+        tiles::CellBest b;
+        int cx = 0, cy = 0;
         if (i < n) {
             const unsigned e = cells[2 + i];
-            const int cy = static_cast<int>(e / static_cast<unsigned>(ncx));
-            const int cx = static_cast<int>(e - static_cast<unsigned>(cy) * ncx);
-            cnt += tiles::cell_search_full<NH, SpcG<NH>::value>(L, R, pitch, W, H, Dk, mask, rstat, rspitch, d_out,
-                                                                c_out, cx, cy);
+            cy = static_cast<int>(e / static_cast<unsigned>(ncx));
+            cx = static_cast<int>(e - static_cast<unsigned>(cy) * ncx);
+            const int ng = tiles::cell_full_groups<G>(W, Dk, cx);
+            b = tiles::cell_full_part<NH, G>(L, R, pitch, W, H, Dk, mask, rstat, rspitch, cx, cy, part * ng / P,
+                                             (part + 1) * ng / P);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+#pragma unroll
+                for (int r2 = 0; r2 < 2; ++r2) {
+                    b.best[c][r2] = -INFINITY;
+                    b.bz[c][r2] = 0;
+                }
+        }
+        for (int sh = 1; sh < P; sh <<= 1)
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+#pragma unroll
+                for (int r2 = 0; r2 < 2; ++r2) {
+                    const float ob = __shfl_xor_sync(0xFFFFFFFFu, b.best[c][r2], sh);
+                    const int oz = __shfl_xor_sync(0xFFFFFFFFu, b.bz[c][r2], sh);
+                    if (ob > b.best[c][r2] || (ob == b.best[c][r2] && oz < b.bz[c][r2])) {
+                        b.best[c][r2] = ob;
+                        b.bz[c][r2] = oz;
+                    }
+                }
+        if (i < n && part == 0) {
+            const int xa = 2 * cx, ya = 2 * cy;
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+#pragma unroll
+                for (int r2 = 0; r2 < 2; ++r2) {
+                    if (!b.m[c][r2]) continue;
+                    // rsqrt(Va) scales every candidate of the pixel alike: applied once here.  A
+                    // flat left window has c = 0 for every candidate: the smallest z wins with 0.
+                    float rho = b.rA[c][r2] > 0.f ? b.best[c][r2] * b.rA[c][r2] : 0.f;
+                    rho = fminf(1.f, fmaxf(-1.f, rho));
+                    const size_t o = (size_t)(ya + r2) * W + xa + c;
+                    d_out[o] = static_cast<int16_t>(b.bz[c][r2]);
+                    if (c_out) c_out[o] = rho;
+                    cnt += static_cast<unsigned long long>(b.hi[c] + 1);
+                }
         }
     }
     for (int sh = 16; sh > 0; sh >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, sh);
@@ -70,10 +118,14 @@ cudaError_t sparse_launch(const LevelBuf &l, int16_t *d, float *c, unsigned long
         if (e != cudaSuccess) return e;
         resident = std::max(sms * per, 1);
     }
+    // lanes per cell: the most (up to 4) that still give each at least SPC_PART_GROUPS groups
+    const int ng = (std::min(l.Dk, l.W) + SpcG<NH>::value - 1) / SpcG<NH>::value;
+    int P = 1;
+    while (P < 4 && ng / (2 * P) >= SPC_PART_GROUPS) P *= 2;
     const long cells = (long)((l.W + 1) / 2) * ((l.H + 1) / 2);
-    const long ctas = std::max<long>(1, std::min<long>(resident, (cells + SPC_THREADS - 1) / SPC_THREADS));
+    const long ctas = std::max<long>(1, std::min<long>(resident, (cells * P + SPC_THREADS - 1) / SPC_THREADS));
     zncc_sparse_cell_kernel<NH><<<static_cast<unsigned>(ctas), SPC_THREADS, 0, st>>>(
-        l.img(0), l.img(1), l.pitch, l.W, l.H, l.Dk, l.mask, l.rstat, l.rspitch, l.cells, d, c, evals);
+        l.img(0), l.img(1), l.pitch, l.W, l.H, l.Dk, l.mask, l.rstat, l.rspitch, l.cells, P, d, c, evals);
     return cudaGetLastError();
 }
 
