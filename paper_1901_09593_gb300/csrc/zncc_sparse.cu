@@ -17,31 +17,33 @@
 
 #include "msbm_device.cuh"
 #include "msbm_internal.h"
-#include "zncc_cell_tile.cuh"
+#include "zncc_cell_full.cuh"
 
 namespace msbm {
 
 namespace {
 
 constexpr int SPC_THREADS = 128;
-constexpr int SPC_MIN_CTAS = 3;   // 168 registers a thread
 constexpr int SPC_PART_GROUPS = 4;  // fewest candidate groups a lane searches when lanes share a cell
 
-// candidates per group (fewer at the widest windows, whose left words take more registers)
+// candidates per group G and resident CTAs per SM (3: 168 registers a thread) of window
+// half-width NH: fewer candidates at the widest windows, whose left words take more
+// registers; no spills at any NH
 template <int NH>
-struct SpcG {
-    static constexpr int value = NH <= 4 ? 7 : (NH == 5 ? 4 : 2);
+struct SpcCfg {
+    static constexpr int G = NH <= 4 ? 7 : (NH == 5 ? 4 : 2);
+    static constexpr int MB = 3;
 };
 
 // P (1, 2 or 4) lanes share a cell, lane l searching part l % P of its candidate groups;
 // the parts merge by shuffles (larger score, then smaller z: the sequential scan's winner) and
 // the part-0 lane writes the cell's masked pixels.
 template <int NH>
-__global__ void __launch_bounds__(SPC_THREADS, SPC_MIN_CTAS)
+__global__ void __launch_bounds__(SPC_THREADS, SpcCfg<NH>::MB)
     zncc_sparse_cell_kernel(const uint8_t *L, const uint8_t *R, int pitch, int W, int H, int Dk, const uint8_t *mask,
                             const int2 *rstat, int rspitch, unsigned *cells, int P, int16_t *d_out, float *c_out,
                             unsigned long long *evals) {
-    constexpr int G = SpcG<NH>::value;
+    constexpr int G = SpcCfg<NH>::G;
     const unsigned n = cells[0];
     const int ncx = (W + 1) / 2, lane = threadIdx.x & 31, part = lane & (P - 1);
     const unsigned per_warp = 32u / static_cast<unsigned>(P);
@@ -119,7 +121,7 @@ cudaError_t sparse_launch(const LevelBuf &l, int16_t *d, float *c, unsigned long
         resident = std::max(sms * per, 1);
     }
     // lanes per cell: the most (up to 4) that still give each at least SPC_PART_GROUPS groups
-    const int ng = (std::min(l.Dk, l.W) + SpcG<NH>::value - 1) / SpcG<NH>::value;
+    const int ng = (std::min(l.Dk, l.W) + SpcCfg<NH>::G - 1) / SpcCfg<NH>::G;
     int P = 1;
     while (P < 4 && ng / (2 * P) >= SPC_PART_GROUPS) P *= 2;
     const long cells = (long)((l.W + 1) / 2) * ((l.H + 1) / 2);
