@@ -110,6 +110,53 @@ def test_beta_level_window_classes_ragged(win):
     compare_level(host(d)[same], host(c)[same], do[same], co[same], c2o[same], f"beta level 0, window {win}")
 
 
+def test_beta_level_full_size_element_wise():
+    # level 0 of the 1400x1000 benchmark pair (D = 256, 7x7): the gate, the restricted search
+    # of the other pixels and the fallback's full-range search of about a quarter of the level
+    # (one list of some 90 000 cells walked by the persistent grid), every pixel against the
+    # oracle fed the same priors; the evaluation count is the oracle's where the gate agrees
+    from paper_1901_09593_gb300 import _lib
+    sc = scenes.make_pair(scenes.SPECS["bench_1400x1000"], 0)
+    s = sc.spec
+    ref = oracle.disparity(sc.left, sc.right, s.max_disp, s.levels, s.window, s.radius)
+    ctx = ctx_for(s.width, s.height, s.max_disp, s.levels, s.window, s.radius, _lib.MSBM_FLAG_BETA_FALLBACK)
+    ctx.pyramid(dev(sc.left), dev(sc.right))
+    prior, cprior = ref["d"][1], ref["C"][1].astype(np.float32)
+    ctx.eval_count(reset=True)
+    d, c, fb = ctx.match_level_beta(0, dev(prior), dev(cprior))
+    ev_g = ctx.eval_count(reset=True)
+    pa, pb = oracle.pyramid(sc.left, 1), oracle.pyramid(sc.right, 1)
+    do, co, c2o, ev, fbo, ch = oracle.match_level_beta(pa[0], pb[0], s.window // 2, s.max_disp, s.radius, prior,
+                                                       cprior.astype(np.float64), BETA)
+    fbg = host(fb).astype(bool)
+    assert np.all((fbg == fbo) | (np.abs(ch - BETA) < 1e-5))
+    assert 0.1 < fbo.mean() < 0.5
+    if np.array_equal(fbg, fbo):
+        assert ev_g == ev, (ev_g, ev)
+    same = fbg == fbo
+    compare_level(host(d)[same], host(c)[same], do[same], co[same], c2o[same], "beta level 0, 1400x1000")
+
+
+def test_full_method_full_size_matches_oracle():
+    # the whole full method (alpha refinement, beta fallback at every finer level, selective
+    # median) on the benchmark pair against the oracle's: a near-tie at a coarse level may
+    # move a few pixels below it, so the maps are compared by agreement and bad-pixel rate
+    from paper_1901_09593_gb300 import _lib
+    sc = scenes.make_pair(scenes.SPECS["bench_1400x1000"], 0)
+    s = sc.spec
+    ctx = ctx_for(s.width, s.height, s.max_disp, s.levels, s.window, s.radius, _lib.MSBM_FLAGS_FULL_METHOD)
+    ctx.eval_count(reset=True)
+    d, c = ctx.disparity(dev(sc.left), dev(sc.right))
+    ctx.sync()
+    ev_g = ctx.eval_count(reset=True)
+    ref = oracle.disparity_full(sc.left, sc.right, s.max_disp, s.levels, s.window, s.radius, ALPHA, BETA,
+                                oracle.FULL_METHOD)
+    dg = host(d)
+    assert (dg == ref["d"][0]).mean() > 0.995
+    assert abs(scenes.bad_rate(dg, sc.gt, sc.mask) - scenes.bad_rate(ref["d"][0], sc.gt, sc.mask)) < 0.002
+    assert abs(ev_g - ref["evals"]) <= 0.01 * ref["evals"], (ev_g, ref["evals"])
+
+
 def test_gated_pass_end_to_end_small():
     from paper_1901_09593_gb300 import _lib
     sc = scenes.make_pair(scenes.SPECS["small_320x240"], 4)
