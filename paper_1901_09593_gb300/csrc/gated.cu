@@ -208,13 +208,25 @@ struct MergeExchange {
     }
 };
 
-constexpr int MED_TX = 32, MED_TY = 32, MED_R = 2;   // tile; 256 threads of 4 pixels each
-constexpr int MED_RPT = 4;                             // rows per thread (stride MED_TY / MED_RPT)
-constexpr int MED_SW = MED_TX + 2 * MED_R, MED_SH = MED_TY + 2 * MED_R;
+// Lane-wise unsigned 16-bit minimum / maximum of two packed pairs.
+__device__ __forceinline__ uint32_t min_u16x2(uint32_t a, uint32_t b) {
+    uint32_t r;
+    asm("min.u16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
+}
+__device__ __forceinline__ uint32_t max_u16x2(uint32_t a, uint32_t b) {
+    uint32_t r;
+    asm("max.u16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
+}
+
+// tiles of 32 x MED_TY pixels, 256 threads of MED_TY / 8 pixels each (rows 8 apart)
+constexpr int MED_TX = 32, MED_R = 2;
+constexpr int MED_SMALL_TILES_PER_SM = 2;
+constexpr int MED_SW = MED_TX + 2 * MED_R;
 constexpr int MED_NONE = 0x7FFF;     // a neighbour that does not vote (outside, or cost <= alpha)
 
-// Eq. 10 on a 32 x 32 tile (256 threads, 4 pixels each, which amortises the staged halo and
-// the per-CTA barriers over four times the pixels of a 32 x 8 tile): the 5 x 5 neighbourhood
+// Eq. 10 on a 32 x MED_TY tile (256 threads, MED_TY / 8 pixels each): the 5 x 5 neighbourhood
 // (inside the image) is staged in shared memory as voting disparities (cost > alpha) or
 // MED_NONE, costs and disparities loaded together (one round trip).  A voting pixel keeps
 // its disparity; the tile's pixels with cost <= alpha and at least one voter are collected in
@@ -222,11 +234,13 @@ constexpr int MED_NONE = 0x7FFF;     // a neighbour that does not vote (outside,
 // the pixel's 24 neighbours (the pixel does not vote itself) with a merge-exchange network,
 // so the voters come first in ascending order, and takes the lower median of the voters.  A
 // pixel with cost <= alpha and no voter keeps its disparity.
+template <int MED_TY>
 __global__ void __launch_bounds__(256)
 selective_median_kernel(const int16_t *__restrict__ d_in, const float *__restrict__ C, int W, int H, float alpha,
                         int16_t *d_out) {
-    constexpr int NT = 256, NB = (2 * MED_R + 1) * (2 * MED_R + 1) - 1, RS = MED_TY / MED_RPT;
-    static_assert(MED_TX * RS == NT && MED_SW <= 64, "median tile");
+    constexpr int NT = 256, NB = (2 * MED_R + 1) * (2 * MED_R + 1) - 1, RS = 8, MED_RPT = MED_TY / RS;
+    constexpr int MED_SH = MED_TY + 2 * MED_R;
+    static_assert(MED_TX * RS == NT && MED_TY % RS == 0 && MED_SW <= 64, "median tile");
     __shared__ int16_t sv[MED_SH][MED_SW];
     __shared__ uint16_t job[MED_TX * MED_TY];   // tile pixels to sort
     __shared__ unsigned long long vmask[MED_SH];
@@ -289,32 +303,48 @@ selective_median_kernel(const int16_t *__restrict__ d_in, const float *__restric
         if (need) job[first + __popc(bal & ((1u << lane) - 1u))] = static_cast<uint16_t>(ry * MED_TX + tx);
     }
     __syncthreads();
-    const int njob = njob_s;
-    for (int k = tid; k < njob; k += NT) {
-        const int t = job[k], jx = t % MED_TX, jy = t / MED_TX;
-        int v[NB], cnt = 0;
+    // the jobs in pairs, one pair a thread: the two pixels' neighbourhoods share each 32-bit
+    // word of the network (pixel 2k in the low half, 2k + 1 in the high half; an odd count's
+    // last pixel is paired with itself and written once), so one min.u16x2 / max.u16x2 pair
+    // performs a comparator for both.  Voting disparities are 0 .. D_k - 1 < MED_NONE, so
+    // unsigned 16-bit order is their order and the non-voters sort last.
+    const int njob = njob_s, npair = (njob + 1) / 2;
+    for (int k = tid; k < npair; k += NT) {
+        const int ta = job[2 * k], tb = 2 * k + 1 < njob ? job[2 * k + 1] : ta;
+        const int ax = ta % MED_TX, ay = ta / MED_TX, bx = tb % MED_TX, by = tb / MED_TX;
+        uint32_t v[NB];
 #pragma unroll
         for (int m = 0, i = 0; m <= 2 * MED_R; ++m)
 #pragma unroll
             for (int q = 0; q <= 2 * MED_R; ++q) {
                 if (m == MED_R && q == MED_R) continue;
-                v[i] = sv[jy + m][jx + q];
-                cnt += v[i] != MED_NONE;
+                v[i] = static_cast<uint32_t>(static_cast<uint16_t>(sv[ay + m][ax + q])) |
+                       (static_cast<uint32_t>(static_cast<uint16_t>(sv[by + m][bx + q])) << 16);
                 ++i;
             }
+        // voters of each window: the staged rows' vote bits (the centre does not vote)
+        int ca = 0, cb = 0;
+#pragma unroll
+        for (int m = 0; m <= 2 * MED_R; ++m) {
+            ca += __popcll((vmask[ay + m] >> ax) & ((1ull << (2 * MED_R + 1)) - 1ull));
+            cb += __popcll((vmask[by + m] >> bx) & ((1ull << (2 * MED_R + 1)) - 1ull));
+        }
         constexpr MergeExchange<NB> net;
 #pragma unroll
         for (int c = 0; c < net.M; ++c) {
-            const int lo = min(v[net.a[c]], v[net.b[c]]), hi = max(v[net.a[c]], v[net.b[c]]);
+            const uint32_t lo = min_u16x2(v[net.a[c]], v[net.b[c]]), hi = max_u16x2(v[net.a[c]], v[net.b[c]]);
             v[net.a[c]] = lo;
             v[net.b[c]] = hi;
         }
-        const int want = (cnt - 1) / 2;       // at most NB / 2 - 1
-        int out = v[0];
+        const int wa = (ca - 1) / 2, wb = (cb - 1) / 2;    // at most NB / 2 - 1
+        uint32_t oa = v[0], ob = v[0];
 #pragma unroll
-        for (int i = 1; i < NB / 2; ++i)
-            if (i == want) out = v[i];
-        d_out[(size_t)(y0 + jy) * W + x0 + jx] = static_cast<int16_t>(out);
+        for (int i = 1; i < NB / 2; ++i) {
+            if (i == wa) oa = v[i];
+            if (i == wb) ob = v[i];
+        }
+        d_out[(size_t)(y0 + ay) * W + x0 + ax] = static_cast<int16_t>(oa & 0xFFFFu);
+        if (2 * k + 1 < njob) d_out[(size_t)(y0 + by) * W + x0 + bx] = static_cast<int16_t>(ob >> 16);
     }
 }
 
@@ -355,8 +385,26 @@ cudaError_t launch_alpha_refine(const LevelBuf &l, int nh, float alpha, int16_t 
 
 cudaError_t launch_selective_median(const int16_t *d_in, const float *C, int W, int H, float alpha, int16_t *d_out,
                                     cudaStream_t st) {
-    dim3 grd((W + MED_TX - 1) / MED_TX, (H + MED_TY - 1) / MED_TY);
-    selective_median_kernel<<<grd, 256, 0, st>>>(d_in, C, W, H, alpha, d_out);
+    // 32 x 32 tiles amortise the staged halo and the barriers over four times the pixels of
+    // 32 x 8 tiles; a level too small to give every SM two such tiles takes 32 x 8 (measured
+    // on the 1400 x 1000 selective-median pass: 68.1 -> 66.1 us, level 2 taking 32 x 8;
+    // 32 x 8 or 32 x 16 at every level: 70.1 / 68.1 us)
+    const long tiles32 = (long)((W + MED_TX - 1) / MED_TX) * ((H + 31) / 32);
+    static int sms = 0;   // SMs of the device (queried once per process)
+    if (sms == 0) {
+        int dev = 0, v = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        sms = v;
+    }
+    if (tiles32 < MED_SMALL_TILES_PER_SM * sms) {
+        dim3 grd((W + MED_TX - 1) / MED_TX, (H + 7) / 8);
+        selective_median_kernel<8><<<grd, 256, 0, st>>>(d_in, C, W, H, alpha, d_out);
+    } else {
+        dim3 grd((W + MED_TX - 1) / MED_TX, (H + 31) / 32);
+        selective_median_kernel<32><<<grd, 256, 0, st>>>(d_in, C, W, H, alpha, d_out);
+    }
     return cudaGetLastError();
 }
 

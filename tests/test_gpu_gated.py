@@ -27,13 +27,15 @@ def ctx_for(w, h, D, K, win, r, flags):
     return Context(w, h, D, K, win, r, flags, alpha=ALPHA, beta=BETA)
 
 
-def test_selective_median_bit_exact():
+@pytest.mark.parametrize("h,w,dmax", [(37, 83, 60), (1001, 1403, 640)])
+def test_selective_median_bit_exact(h, w, dmax):
+    # a small map (32 x 8 tiles) and a ragged benchmark-sized one (32 x 32 tiles, two sorted
+    # pixels a thread, odd job counts), disparities up to the large pair's range
     from paper_1901_09593_gb300 import _lib
     rng = np.random.default_rng(0)
-    h, w = 37, 83
-    d = rng.integers(0, 60, (h, w)).astype(np.int16)
+    d = rng.integers(0, dmax, (h, w)).astype(np.int16)
     c = (rng.random((h, w)) * 1.3 - 0.2).astype(np.float32)
-    ctx = ctx_for(w, h, 64, 1, 5, 2, _lib.MSBM_FLAG_SELECTIVE_MEDIAN)
+    ctx = ctx_for(w, h, dmax + 1, 1, 5, 2, _lib.MSBM_FLAG_SELECTIVE_MEDIAN)
     out = host(ctx.selective_median(0, dev(d), dev(c)))
     ref = oracle.selective_median(d, c.astype(np.float64), ALPHA)
     np.testing.assert_array_equal(out, ref)
