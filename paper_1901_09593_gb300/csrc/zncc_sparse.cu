@@ -6,8 +6,10 @@
 // (the CTAs the SMs hold at once) walks that list: each warp takes the next 32 / P entries
 // with one atomic, P lanes per cell each searching a part of its candidate groups
 // (tiles::cell_full_part: the four pixels share each right row's loads and the products of
-// their common window rows; candidates in groups of 7, exact integer sums by dp4a, the
-// right-window statistics from the level's plane), merged by shuffles.  Work is
+// their common window rows; candidates in groups of 8, exact integer sums by dp4a, the
+// right-window statistics from the level's plane), merged by shuffles.  Groups of 8: the
+// same alignment shifts per row as 7 (offsets 1-3 and 5-7 of a group's 9 windows), and
+// power-of-two disparity ranges split evenly over the lanes.  Work is
 // proportional to the masked cells, the warps stay full whatever the mask's layout, and
 // splitting a cell's range over P lanes makes the units of work small enough that the last
 // ones do not leave most of the GPU idle.
@@ -31,7 +33,7 @@ constexpr int SPC_PART_GROUPS = 4;  // fewest candidate groups a lane searches w
 // registers; no spills at any NH
 template <int NH>
 struct SpcCfg {
-    static constexpr int G = NH <= 4 ? 7 : (NH == 5 ? 4 : 2);
+    static constexpr int G = NH <= 4 ? 8 : (NH == 5 ? 4 : 2);
     static constexpr int MB = 3;
 };
 
